@@ -1,0 +1,253 @@
+"""Seeded synthetic graph generators (inputs only).
+
+Every graph the library is tested or measured on comes from here.  The module
+builds undirected, unweighted graphs and returns them as a symmetric CSR with
+ascending neighbour lists, no self-loops and no duplicate edges, the input
+class the method assumes (Section III: undirected, unweighted graphs;
+Section V-A: largest connected component of disconnected inputs).
+
+It holds none of the method's arithmetic: no sampling, no BFS with path
+counts, no stopping rule.  Both the CPU oracle and the CUDA library consume
+its output, which keeps the two sides independent of each other.
+
+The synthetic families stand in for the paper's workloads (Section V-A):
+  * R-MAT with the Graph500 parameters (a, b, c, d) = (0.57, 0.19, 0.19, 0.05),
+    which the paper uses for its synthetic experiments and which mimics the
+    complex networks of Table I;
+  * Erdos-Renyi G(n, p) for the small exact-check case;
+  * 2D grids with randomly deleted edges and random geometric graphs as
+    high-diameter stand-ins for the road networks of Table I.
+"""
+from __future__ import annotations
+
+import dataclasses
+import functools
+
+import numpy as np
+
+__all__ = [
+    "Graph", "csr_from_edges", "largest_component", "er_graph", "rmat_graph",
+    "grid_graph", "rgg_graph", "path_graph", "star_graph", "cycle_graph",
+    "complete_graph", "full_grid_graph", "config_graph", "CONFIGS",
+]
+
+
+@dataclasses.dataclass(frozen=True)
+class Graph:
+    """Symmetric CSR: ``offsets`` int64[n+1], ``cols`` int32[nnz], rows sorted."""
+
+    n: int
+    offsets: np.ndarray
+    cols: np.ndarray
+    name: str = ""
+
+    @property
+    def nnz(self) -> int:
+        return int(self.offsets[-1])
+
+    @property
+    def degrees(self) -> np.ndarray:
+        return np.diff(self.offsets)
+
+    @property
+    def max_degree(self) -> int:
+        return int(self.degrees.max()) if self.n else 0
+
+    def offsets32(self) -> np.ndarray:
+        if self.nnz >= 2**31:
+            raise ValueError("graph too large for int32 offsets")
+        return self.offsets.astype(np.int32)
+
+
+def csr_from_edges(n: int, src: np.ndarray, dst: np.ndarray, name: str = "") -> Graph:
+    """Symmetrise an edge list, drop self-loops and duplicates, sort rows."""
+    src = np.asarray(src, dtype=np.int64)
+    dst = np.asarray(dst, dtype=np.int64)
+    keep = src != dst
+    src, dst = src[keep], dst[keep]
+    keys = np.concatenate([src * n + dst, dst * n + src])
+    del src, dst
+    keys.sort()
+    if keys.size:
+        keep = np.empty(keys.size, dtype=bool)
+        keep[0] = True
+        np.not_equal(keys[1:], keys[:-1], out=keep[1:])
+        keys = keys[keep]
+    rows = keys // n
+    cols = (keys - rows * n).astype(np.int32)
+    del keys
+    counts = np.bincount(rows, minlength=n)
+    offsets = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(counts, out=offsets[1:])
+    return Graph(n, offsets, cols, name)
+
+
+def largest_component(g: Graph) -> Graph:
+    """Restrict to the largest connected component (ties: lowest label),
+    renumbering vertices in their original relative order."""
+    import scipy.sparse as sp
+    from scipy.sparse.csgraph import connected_components
+
+    if g.n == 0:
+        return g
+    a = sp.csr_matrix((np.ones(g.nnz, dtype=np.int8), g.cols, g.offsets), shape=(g.n, g.n))
+    ncomp, labels = connected_components(a, directed=False)
+    if ncomp == 1:
+        return g
+    sizes = np.bincount(labels)
+    keep = labels == int(np.argmax(sizes))
+    new_id = np.cumsum(keep) - 1
+    deg = np.diff(g.offsets)
+    rows = np.repeat(np.arange(g.n), deg)
+    emask = keep[rows]
+    src = new_id[rows[emask]]
+    dst = new_id[g.cols[emask]]
+    m = int(keep.sum())
+    counts = np.bincount(src, minlength=m)
+    offsets = np.zeros(m + 1, dtype=np.int64)
+    np.cumsum(counts, out=offsets[1:])
+    # rows are already grouped and ascending because the renumbering is monotone
+    return Graph(m, offsets, dst.astype(np.int32), g.name)
+
+
+def er_graph(n: int, avg_degree: float, seed: int, lcc: bool = True) -> Graph:
+    """Erdos-Renyi G(n, p) with p = avg_degree / (n - 1)."""
+    rng = np.random.default_rng(seed)
+    p = avg_degree / (n - 1)
+    iu, ju = np.triu_indices(n, k=1)
+    mask = rng.random(iu.shape[0]) < p
+    g = csr_from_edges(n, iu[mask], ju[mask], name=f"er{n}")
+    return largest_component(g) if lcc else g
+
+
+def rmat_graph(scale: int, edge_factor: int, seed: int,
+               abcd=(0.57, 0.19, 0.19, 0.05), relabel: bool = True,
+               lcc: bool = False) -> Graph:
+    """R-MAT (Chakrabarti et al.) with ``edge_factor * 2**scale`` edge draws,
+    no noise, random vertex relabelling, symmetrised and deduplicated."""
+    a, b, c, d = abcd
+    n = 1 << scale
+    m = edge_factor * n
+    rng = np.random.default_rng(seed)
+    t_ab, t_abc = a + b, a + b + c
+    chunk = 1 << 22
+    srcs, dsts = [], []
+    for lo in range(0, m, chunk):
+        k = min(chunk, m - lo)
+        i = np.zeros(k, dtype=np.int64)
+        j = np.zeros(k, dtype=np.int64)
+        for lvl in range(scale):
+            u = rng.random(k)
+            ib = u >= t_ab
+            jb = ((u >= a) & (u < t_ab)) | (u >= t_abc)
+            bit = np.int64(1) << (scale - 1 - lvl)
+            i |= ib * bit
+            j |= jb * bit
+        srcs.append(i)
+        dsts.append(j)
+    src = np.concatenate(srcs)
+    dst = np.concatenate(dsts)
+    del srcs, dsts
+    if relabel:
+        perm = rng.permutation(n).astype(np.int64)
+        src, dst = perm[src], perm[dst]
+    g = csr_from_edges(n, src, dst, name=f"rmat{scale}_ef{edge_factor}")
+    return largest_component(g) if lcc else g
+
+
+def grid_graph(k: int, delete_p: float, seed: int, lcc: bool = True) -> Graph:
+    """k x k 4-neighbour grid; each edge deleted independently with prob. delete_p."""
+    rng = np.random.default_rng(seed)
+    idx = np.arange(k * k, dtype=np.int64).reshape(k, k)
+    h_src, h_dst = idx[:, :-1].ravel(), idx[:, 1:].ravel()
+    v_src, v_dst = idx[:-1, :].ravel(), idx[1:, :].ravel()
+    src = np.concatenate([h_src, v_src])
+    dst = np.concatenate([h_dst, v_dst])
+    keep = rng.random(src.shape[0]) >= delete_p
+    g = csr_from_edges(k * k, src[keep], dst[keep], name=f"grid{k}_del{delete_p}")
+    return largest_component(g) if lcc else g
+
+
+def rgg_graph(n: int, avg_degree: float, seed: int, lcc: bool = False) -> Graph:
+    """Random geometric graph in the unit square, radius sqrt(avg_degree/(pi n))."""
+    from scipy.spatial import cKDTree
+
+    rng = np.random.default_rng(seed)
+    pts = rng.random((n, 2))
+    r = float(np.sqrt(avg_degree / (np.pi * n)))
+    pairs = cKDTree(pts).query_pairs(r, output_type="ndarray")
+    g = csr_from_edges(n, pairs[:, 0], pairs[:, 1], name=f"rgg{n}")
+    return largest_component(g) if lcc else g
+
+
+def _from_pairs(n, pairs, name):
+    pairs = np.asarray(pairs, dtype=np.int64).reshape(-1, 2)
+    return csr_from_edges(n, pairs[:, 0], pairs[:, 1], name=name)
+
+
+def path_graph(n: int) -> Graph:
+    return _from_pairs(n, [(i, i + 1) for i in range(n - 1)], f"path{n}")
+
+
+def star_graph(n: int) -> Graph:
+    """Centre 0 joined to leaves 1..n-1."""
+    return _from_pairs(n, [(0, i) for i in range(1, n)], f"star{n}")
+
+
+def cycle_graph(n: int) -> Graph:
+    return _from_pairs(n, [(i, (i + 1) % n) for i in range(n)], f"cycle{n}")
+
+
+def complete_graph(n: int) -> Graph:
+    return _from_pairs(n, [(i, j) for i in range(n) for j in range(i + 1, n)], f"k{n}")
+
+
+def full_grid_graph(rows: int, cols: int) -> Graph:
+    """Full rows x cols grid, vertex id r*cols + c."""
+    pairs = []
+    for r in range(rows):
+        for c in range(cols):
+            v = r * cols + c
+            if c + 1 < cols:
+                pairs.append((v, v + 1))
+            if r + 1 < rows:
+                pairs.append((v, v + cols))
+    return _from_pairs(rows * cols, pairs, f"fullgrid{rows}x{cols}")
+
+
+# Named workloads.  Sizes follow the configurations the library is measured
+# on; the "small" entries are the same families at sizes the oracle finishes
+# in seconds.
+CONFIGS = {
+    # G(n=2000, avg degree 8), seed 1, largest component
+    "er2000": dict(kind="er", n=2000, avg_degree=8, seed=1, lcc=True),
+    # R-MAT scale 20, edge factor 16, Graph500 parameters, generator seed 2
+    "rmat20": dict(kind="rmat", scale=20, edge_factor=16, seed=2),
+    # 4096 x 4096 grid with 10% of the edges deleted (seed 3), largest component
+    "grid4096": dict(kind="grid", k=4096, delete_p=0.1, seed=3, lcc=True),
+    # small members of the same families
+    "rmat12": dict(kind="rmat", scale=12, edge_factor=16, seed=12),
+    "rmat14": dict(kind="rmat", scale=14, edge_factor=16, seed=14),
+    "rmat16": dict(kind="rmat", scale=16, edge_factor=16, seed=16),
+    "grid64": dict(kind="grid", k=64, delete_p=0.1, seed=3, lcc=True),
+    "grid256": dict(kind="grid", k=256, delete_p=0.1, seed=3, lcc=True),
+    "rgg5k": dict(kind="rgg", n=5000, avg_degree=10, seed=7, lcc=True),
+}
+
+
+@functools.lru_cache(maxsize=8)
+def config_graph(name: str) -> Graph:
+    """Build a named workload graph (cached per process)."""
+    cfg = dict(CONFIGS[name])
+    kind = cfg.pop("kind")
+    if kind == "er":
+        g = er_graph(**cfg)
+    elif kind == "rmat":
+        g = rmat_graph(**cfg)
+    elif kind == "grid":
+        g = grid_graph(**cfg)
+    elif kind == "rgg":
+        g = rgg_graph(**cfg)
+    else:
+        raise KeyError(kind)
+    return dataclasses.replace(g, name=name)
