@@ -1,0 +1,422 @@
+#!/usr/bin/env python
+"""Benchmark: KADABRA adaptive-sampling betweenness on one GB300.
+
+Workload: R-MAT scale 20 (2^20 vertices, edge factor 16, Graph500
+(a, b, c, d) = (0.57, 0.19, 0.19, 0.05)), symmetrised, self-loops and
+duplicates removed, int32 CSR; eps = 0.01, delta = 0.1, seed 1.  Synthetic
+data from paper_1910_11039_gb300.inputs (generator seed 2).
+
+A step is one complete adaptive phase (arXiv 1910.11039, Section III-A,
+phase 3): from tau = 0, epochs of E samples each followed by the on-device
+stop check, until the stopping condition holds.  All epochs up to the cap
+omega are enqueued without host synchronisation; launches after the stop
+take no samples.  The graph and the calibrated budgets are resident in HBM
+before the timed region.  L2 is flushed (256 MiB write) before every step.
+
+value  = adaptive samples per second over the K timed steps (device events)
+e2e    = the same metric for whole queries through the C ABI from pinned host
+         buffers: graph upload, diameter bound, calibration, adaptive phase,
+         result download.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "shortest-path samples/sec and time-to-(eps,delta) stop; GTEPS and HBM fraction"
+WORKLOADS = {
+    "rmat20": dict(graph="rmat20", eps=0.01, delta=0.1, seed=1,
+                   desc="R-MAT scale 20, edge factor 16, (a,b,c,d)=(0.57,0.19,0.19,0.05), symmetrised, "
+                        "no self-loops/duplicates, int32 CSR; eps=0.01 delta=0.1 seed=1"),
+    "er2000": dict(graph="er2000", eps=0.05, delta=0.1, seed=1,
+                   desc="Erdos-Renyi G(n=2000, avg degree 8) seed 1, largest component, int32 CSR; "
+                        "eps=0.05 delta=0.1 seed=1"),
+}
+FLUSH_BYTES = 256 << 20
+REASON_BITS = {0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap", 0x8: "hw_slowdown",
+               0x10: "sync_boost", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
+               0x80: "hw_power_brake_slowdown", 0x100: "display_clock_setting"}
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline and reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_rate(g, seed, per_thread, threads):
+    """Run the oracle's sampler on `threads` host threads, each taking
+    `per_thread` consecutive adaptive-phase sample indices; returns
+    (samples/s, samples, e_scan, seconds)."""
+    import oracle
+    oracle.build()
+    results = [None] * threads
+
+    def work(i):
+        results[i] = oracle.run_samples(g, seed, 1, i * per_thread, (i + 1) * per_thread)
+
+    ts = [threading.Thread(target=work, args=(i,)) for i in range(threads)]
+    t0 = time.perf_counter()
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    dt = time.perf_counter() - t0
+    samples = sum(r[1].samples for r in results)
+    e_scan = sum(r[1].e_scan for r in results)
+    return samples / dt, samples, e_scan, dt
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    rows.append((float(parts[1]), float(parts[2]), float(parts[3]), int(parts[4], 16), parts[5:9]))
+                except ValueError:
+                    continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        busy = [r for r in rows if not (r[3] & 0x1)] or rows
+        reasons = set()
+        for r in busy:
+            for bit, name in REASON_BITS.items():
+                if r[3] & bit and bit != 0x1:
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r[0] for r in busy), "sm_max_mhz": max(r[1] for r in rows),
+                "power_w_max": max(r[2] for r in rows), "samples": len(rows), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# roofline helpers
+# ---------------------------------------------------------------------------
+
+def algorithmic_bytes(ls, offset_bytes):
+    """Bytes one launch must move at minimum: per expanded vertex its two row
+    offsets, per scanned adjacency entry its 4-byte column id, per reached
+    vertex a 16-byte state record (level + path count), per back-walk scan a
+    column id, per counted interior vertex a 4-byte counter update."""
+    return (2 * offset_bytes * ls.expanded + 4 * ls.e_scan + 16 * ls.touched + 4 * ls.walk_scan
+            + 4 * ls.interior)
+
+
+def kernel_digest():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1910_11039_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload):
+    """DRAM bytes per sample of the sampling kernel from the committed ncu
+    summary, if it was taken on the current kernel sources."""
+    path = os.path.join(ROOT, "profiles", f"sample_kernel_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m = re.search(r"kernel_digest:\s*([0-9a-f]+)", txt)
+    b = re.search(r"dram_bytes_per_sample:\s*([0-9.eE+]+)", txt)
+    if not m or not b or m.group(1) != kernel_digest():
+        return None
+    return float(b.group(1))
+
+
+def measured_peak_hbm():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# arms
+# ---------------------------------------------------------------------------
+
+def run_reference(args, wl, g, rank, world):
+    if rank != 0:
+        return
+    threads = host_cores()
+    per_thread = max(1, args.ref_samples // threads)
+    seed = wl["seed"]
+    for _ in range(args.warmup):
+        oracle_rate(g, seed, max(1, per_thread // 4), threads)
+    rates, total_s, total_dt = [], 0, 0.0
+    for k in range(args.steps):
+        rate, s, e, dt = oracle_rate(g, seed, per_thread, threads)
+        rates.append(rate)
+        total_s += s
+        total_dt += dt
+    value = total_s / total_dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": wl["desc"], "name": args.workload, "n": g.n, "nnz": g.nnz},
+        "cpu_baseline": {"value": value, "unit": "samples/s", "cores": threads, "kind": "oracle",
+                         "sample": f"{per_thread} adaptive-phase samples per thread x {threads} threads per step"},
+        "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args, wl, g, rank, world, local_rank, cpu_baseline):
+    import numpy as np
+    import torch
+
+    from paper_1910_11039_gb300 import build as B
+    from paper_1910_11039_gb300 import kadabra as K
+
+    B.build()
+    K.load()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+    seed = wl["seed"] + rank          # replicas: independent queries per rank
+    eps, delta = wl["eps"], wl["delta"]
+
+    # ---- device-resident arm ----
+    G = K.Graph.from_inputs(g, skip_validate=True)
+    q = K.Query(G, eps=eps, delta=delta, seed=seed)
+    info0 = q.info()
+    E = args.epoch
+    max_epochs = math.ceil(info0.omega_ceil / E) + 1
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+
+    def step():
+        flush.fill_(rank + 1)
+        q.reset()
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        for _ in range(max_epochs):
+            q.sample_epoch(E)
+            q.check_stop_async()
+        s1.record(stream)
+        s1.synchronize()
+        inf = q.info()
+        return s0.elapsed_time(s1), inf
+
+    for _ in range(args.warmup):
+        step()
+    dist = world > 1
+    if dist:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    t_wall0 = time.perf_counter()
+    times, taus, escans, stops = [], [], [], []
+    for _ in range(args.steps):
+        ms, inf = step()
+        times.append(ms)
+        taus.append(inf.tau)
+        escans.append(inf.e_scan)
+        stops.append(inf.stop_epoch)
+        assert inf.stopped, "adaptive phase did not stop within the omega cap"
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    total_ms = sum(times)
+    if dist:
+        t = torch.tensor([total_ms, wall], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        s = torch.tensor([float(sum(taus)), float(sum(escans))], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(s, op=torch.distributed.ReduceOp.SUM)
+        total_ms_max, wall_max = t.tolist()
+        all_samples, all_escan = s.tolist()
+        torch.distributed.barrier()
+    else:
+        total_ms_max, wall_max = total_ms, wall
+        all_samples, all_escan = float(sum(taus)), float(sum(escans))
+    value = all_samples / (total_ms_max / 1e3)
+    gteps = all_escan / (total_ms_max / 1e3) / 1e9
+
+    # roofline of the sampling kernel over the timed steps' launches
+    launches = [ls for ls in q.launch_log(256) if ls.samples > 0]
+    ob = 4  # int32 offsets
+    peak, peak_kind = measured_peak_hbm()
+    tot_b = sum(algorithmic_bytes(ls, ob) for ls in launches)
+    tot_ms = sum(ls.ms for ls in launches)
+    achieved = tot_b / (tot_ms / 1e3) / 1e9 if tot_ms > 0 else 0.0
+    per_sample = profiled_traffic(args.workload)
+    mean_samples = sum(ls.samples for ls in launches) / max(1, len(launches))
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": per_sample * mean_samples if per_sample else None,
+                "kernel": "sample_kernel", "peak_source": f"{peak_kind} hbm_gbs",
+                "launches": len(launches), "avg_launch_ms": tot_ms / max(1, len(launches)),
+                "algorithmic_bytes_per_launch": tot_b / max(1, len(launches))}
+    n_launch_kernels = args.steps * (2 * max_epochs + 1)   # sample + check per epoch, reset per step
+
+    # ---- end to end through the C ABI with pinned host buffers ----
+    e2e = None
+    if args.e2e_steps > 0:
+        off_h = torch.from_numpy(g.offsets32()).pin_memory()
+        col_h = torch.from_numpy(g.cols).pin_memory()
+        b_h = torch.empty(g.n, dtype=torch.float64).pin_memory()
+        c_h = torch.empty(g.n, dtype=torch.int32).pin_memory()
+        del q, G
+        torch.cuda.synchronize()
+        e_times, e_taus = [], []
+        for k in range(args.e2e_steps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            G2 = K.Graph(g.n, off_h.numpy(), col_h.numpy(), offsets_64=False, skip_validate=True, stream=stream)
+            q2 = K.Query(G2, eps=eps, delta=delta, seed=seed, stream=stream)
+            mx = math.ceil(q2.info().omega_ceil / E) + 1
+            for _ in range(mx):
+                q2.sample_epoch(E)
+                q2.check_stop_async()
+            tau, se = q2.result_into(b_h.data_ptr(), c_h.data_ptr())
+            t1 = time.perf_counter()
+            q2.free()
+            G2.free()
+            if k > 0:      # the first query warms allocator and caches
+                e_times.append(t1 - t0)
+                e_taus.append(tau)
+        n = g.n
+        h2d = g.offsets32().nbytes + g.cols.nbytes + 16 * n
+        d2h = 4 * n + 8 * n + 4 * n
+        e2e = {"value": sum(e_taus) / sum(e_times), "unit": "samples/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "steps": len(e_times),
+               "time_to_stop_ms": 1e3 * statistics.mean(e_times),
+               "step": "graph upload + diameter bound + calibration + adaptive phase + result download"}
+
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": wl["desc"], "name": args.workload, "n": g.n, "nnz": g.nnz, "epoch_len": E,
+                   "max_epochs_enqueued": max_epochs, "slots": info0.slots, "threads": info0.threads,
+                   "omega": info0.omega, "vertex_diameter": info0.vertex_diameter, "n_calib": info0.n_calib,
+                   "l2": "flushed before every step (256 MiB write)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "time_to_stop_ms": total_ms_max / args.steps,
+        "samples_per_step": all_samples / args.steps / world,
+        "stop_epoch": stops[-1],
+        "gteps": gteps,
+        "roofline": roofline,
+        "cpu_baseline": cpu_baseline,
+        "e2e": e2e,
+        "gpu_launches": n_launch_kernels,
+        "clocks": clk,
+        "wall_s": wall_max,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--workload", default="rmat20", choices=list(WORKLOADS))
+    ap.add_argument("--epoch", type=int, default=4096)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-samples", type=int, default=48000,
+                    help="oracle samples for the CPU baseline (split over host cores)")
+    ap.add_argument("--ref-samples", type=int, default=16000, help="oracle samples per reference step")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    assert args.warmup >= 3 or args.impl == "reference" or os.environ.get("KADABRA_BENCH_ALLOW_SHORT"), \
+        "at least 3 warm-up steps"
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    wl = WORKLOADS[args.workload]
+
+    from paper_1910_11039_gb300 import inputs
+    g = inputs.config_graph(wl["graph"])
+
+    if args.impl == "reference":
+        if world > 1 and rank != 0:
+            return
+        run_reference(args, wl, g, rank, world)
+        return
+
+    # CPU baseline first: the oracle runs on host threads before any CUDA call
+    cpu_baseline = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cores = host_cores()
+        per = max(1, args.cpu_samples // cores)
+        rate, s, e, dt = oracle_rate(g, wl["seed"], per, cores)
+        cpu_baseline = {"value": rate, "unit": "samples/s", "cores": cores, "kind": "oracle",
+                        "sample": f"adaptive-phase sample indices [0, {s}) of the same workload, "
+                                  f"{per} per thread on {cores} threads ({dt:.1f} s wall)",
+                        "gteps": e / dt / 1e9}
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    run_gpu(args, wl, g, rank, world, local_rank, cpu_baseline)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

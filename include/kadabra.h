@@ -1,0 +1,255 @@
+/*
+ * kadabra.h -- C ABI of the GB300 KADABRA adaptive-sampling betweenness library.
+ *
+ * The method (arXiv 1910.11039, Section III-A): betweenness
+ *   b(x) = 1/(n(n-1)) * sum_{s != t} sigma_st(x) / sigma_st          (Section I)
+ * is approximated by sampling pairs s != t, drawing one shortest s-t path
+ * uniformly with a bidirectional BFS and adding 1 to the counter c~(x) of each
+ * interior vertex x; after tau samples b~(x) = c~(x) / tau.  Sampling is
+ * adaptive: after every epoch a stopping condition f(...) < eps and
+ * g(...) < eps for all x is evaluated on a consistent snapshot of (tau, c~)
+ * (Section III-B; Algorithms 1 and 2), with a hard cap of omega samples.
+ * The three phases are diameter -> omega, calibration of delta_L / delta_U,
+ * and adaptive sampling (Section III-A).
+ *
+ * Conventions for every call:
+ *   - Every function returns a kadabra_status; nothing throws across the ABI.
+ *     On error the outputs are left untouched and kadabra_last_error()
+ *     returns a message (thread-local, valid until the next call on the
+ *     same thread).
+ *   - `cuda_stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls marked "async" only enqueue work on that stream.
+ *   - Vertex ids are int32 (n < 2^31).  Offsets are int32 or int64.
+ *   - Objects (kadabra_graph, kadabra_query) are owned by the library and
+ *     released with their _free call.  Caller arrays stay owned by the caller.
+ *   - A graph's sampling scratch is shared by its queries: queries of one
+ *     graph must be driven from one stream (or serialised by the caller).
+ */
+#ifndef KADABRA_H
+#define KADABRA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum kadabra_status {
+    KADABRA_OK = 0,
+    KADABRA_ERR_INVALID_ARG = 1,      /* bad argument or malformed CSR            */
+    KADABRA_ERR_OOM = 2,              /* device or host allocation failed         */
+    KADABRA_ERR_CUDA = 3,             /* a CUDA runtime call failed               */
+    KADABRA_ERR_SIGMA_OVERFLOW = 4,   /* strict mode met a path count above 2^K   */
+    KADABRA_ERR_COUNTER_OVERFLOW = 5, /* a 32-bit counter would wrap              */
+    KADABRA_ERR_TIMEOUT = 6,          /* a bounded device wait gave up            */
+    KADABRA_ERR_STATE = 7,            /* call out of order (e.g. result before run)*/
+    KADABRA_ERR_NO_DEVICE = 8         /* no CUDA device / library built without it */
+} kadabra_status;
+
+typedef struct kadabra_graph kadabra_graph;
+typedef struct kadabra_query kadabra_query;
+
+/* flags for kadabra_graph_load */
+#define KADABRA_GRAPH_DEVICE_PTRS   1u  /* offsets / cols are device pointers           */
+#define KADABRA_GRAPH_SKIP_VALIDATE 2u  /* trust the CSR (no host-side checks)           */
+
+/* kadabra_params.flags */
+#define KADABRA_STRICT_SIGMA 1u  /* a per-side path count above 2^K is an error instead
+                                    of being scaled down (see kadabra_sigma_bits)        */
+
+/* kadabra_params.delta_rule */
+#define KADABRA_DELTA_UNIFORM  0  /* delta_L = delta_U = delta / (4n)                     */
+#define KADABRA_DELTA_BALANCED 1  /* calibrated split, exp(-C eps^2 / bhat) + floor       */
+
+/* Parameters of one betweenness query (Section III-A: eps, delta; the rest
+ * are this library's readings of what the paper leaves open). */
+typedef struct kadabra_params {
+    double eps;               /* additive error bound, 0 < eps < 1                         */
+    double delta;             /* failure probability, 0 < delta < 1                        */
+    uint64_t seed;            /* Philox key: sample i of stream tag k draws from
+                                 counter (i, draw, k, 0) under key (seed, 0)               */
+    int64_t vertex_diameter;  /* VD >= 1 if known; <= 0: upper bound 2*ecc+1 per component */
+    int64_t n_calib;          /* calibration samples; <= 0: max(1000, ceil(omega/100))     */
+    int32_t delta_rule;       /* KADABRA_DELTA_UNIFORM or KADABRA_DELTA_BALANCED           */
+    uint32_t flags;           /* KADABRA_STRICT_SIGMA                                       */
+    double beta;              /* balanced rule floor weight (default 1e-3)                 */
+    int32_t slots;            /* samples in flight (one CTA each); 0 = fill the GPU        */
+    int32_t threads;          /* threads per sampling CTA: 128, 256 or 512; 0 = 256        */
+    double scratch_fraction;  /* max share of free device memory for scratch; 0 = 0.6      */
+} kadabra_params;
+
+/* Snapshot of a query (kadabra_query_get_info). */
+typedef struct kadabra_query_info {
+    double omega;               /* maximal number of samples                               */
+    uint64_t omega_ceil;        /* ceil(omega): adaptive sampling never passes it          */
+    int64_t vertex_diameter;    /* VD used for omega                                       */
+    int64_t n_calib;            /* calibration samples taken                               */
+    int32_t sigma_bits;         /* K: per-side path counts are kept <= 2^K                 */
+    int32_t stopped;            /* 1 once the stopping condition held                      */
+    uint64_t tau;               /* adaptive samples taken                                  */
+    int64_t epochs;             /* stop checks run                                         */
+    int64_t stop_epoch;         /* index of the check that stopped, -1 if none             */
+    double max_f, max_g;        /* maxima of f and g at the last check                     */
+    double balance_C;           /* constant of the balanced delta rule                     */
+    /* adaptive-phase counters (summed over all epochs) */
+    uint64_t samples;           /* samples taken                                            */
+    uint64_t connected;         /* samples whose pair was connected                        */
+    uint64_t e_scan;            /* adjacency entries scanned by the BFS (traversed edges)  */
+    uint64_t expanded;          /* frontier vertices expanded                              */
+    uint64_t touched;           /* vertices reached by either BFS side                     */
+    uint64_t interior;          /* interior path vertices counted                          */
+    uint64_t walk_scan;         /* adjacency entries scanned by the path back-walk         */
+    uint64_t scaled;            /* samples whose path counts were scaled                   */
+    uint32_t device_error;      /* sticky device error bits (0 = none)                     */
+    int32_t slots;              /* samples in flight per launch                            */
+    int32_t threads;            /* threads per sampling CTA                                */
+    int32_t offsets_64;         /* 1 if the graph uses int64 offsets                       */
+} kadabra_query_info;
+
+/* Per-sample record written by kadabra_sample_trace (one per sample index). */
+typedef struct kadabra_trace_rec {
+    int64_t s, t;               /* the pair (draw 0)                                       */
+    int64_t d;                  /* d(s,t), -1 if disconnected                              */
+    uint64_t sigma_lo, sigma_hi;/* sigma_st as used for the choice (128 bits)             */
+    int64_t meet_size;          /* size of the meeting set                                 */
+    int64_t chosen;             /* meeting vertex picked, -1 if none                       */
+    int64_t e_scan;             /* adjacency entries scanned by the BFS                    */
+    int64_t n_interior;         /* interior vertices of the sampled path                   */
+    int32_t scaled;             /* 1 if a layer's path counts were scaled                  */
+    int32_t overflow;           /* 1 if strict mode rejected the sample                    */
+} kadabra_trace_rec;
+
+/* ---- errors and version ------------------------------------------------ */
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *kadabra_last_error(void);
+/* Static name of a status code. */
+const char *kadabra_status_string(kadabra_status s);
+/* ABI version of this header (major * 100 + minor). */
+int kadabra_abi_version(void);
+
+/* ---- host utilities (no device needed) --------------------------------- */
+
+/* Fill `p` with defaults: eps 0.01, delta 0.1, seed 1, auto VD, default
+ * calibration size, balanced rule, beta 1e-3, auto slots, 256 threads. */
+void kadabra_params_default(kadabra_params *p);
+
+/* Check that (offsets, cols) is a symmetric CSR with ascending, duplicate-free
+ * neighbour lists, no self-loops and ids in [0, n) (Section III: undirected,
+ * unweighted graphs).  Host pointers.  KADABRA_ERR_INVALID_ARG on the first
+ * violation, with the reason in kadabra_last_error(). */
+kadabra_status kadabra_validate_csr(int64_t n, int64_t nnz, const void *offsets, int offsets_is_64,
+                                    const int32_t *cols);
+
+/* omega = (1/2) / eps^2 * (floor(log2(VD - 2)) + 1 + ln(2/delta)), VD - 2
+ * clamped to >= 1: the maximal number of samples, computed from the diameter
+ * (Section III-A names omega; the formula is this library's reading).
+ * Writes NaN and returns KADABRA_ERR_INVALID_ARG for eps or delta outside (0,1). */
+kadabra_status kadabra_omega(double eps, double delta, int64_t vertex_diameter, double *omega);
+
+/* K = min(63 - bitlen(max_degree), 63 - bitlen(n)): the largest per-side path
+ * count kept exact; above 2^K a BFS layer's counts are shifted right (rounding
+ * up) so that all sums stay exact in 64/128-bit integers. */
+int kadabra_sigma_bits(int64_t n, int64_t max_degree);
+
+/* ---- graph ------------------------------------------------------------- */
+
+/* Copy a CSR graph into library-owned device memory (async on `cuda_stream`
+ * for device pointers, synchronous for host pointers).
+ *   n        number of vertices (1 <= n < 2^31)
+ *   nnz      number of adjacency entries (= offsets[n])
+ *   offsets  n+1 entries, int32 if offsets_is_64 == 0 else int64
+ *   cols     nnz int32 neighbour ids, each row ascending
+ *   flags    KADABRA_GRAPH_DEVICE_PTRS, KADABRA_GRAPH_SKIP_VALIDATE
+ * Host inputs are validated (kadabra_validate_csr) unless skipped. */
+kadabra_status kadabra_graph_load(int64_t n, int64_t nnz, const void *offsets, int offsets_is_64,
+                                  const int32_t *cols, uint32_t flags, void *cuda_stream,
+                                  kadabra_graph **out);
+kadabra_status kadabra_graph_free(kadabra_graph *g);
+kadabra_status kadabra_graph_info(const kadabra_graph *g, int64_t *n, int64_t *nnz,
+                                  int64_t *max_degree, int *offsets_is_64);
+
+/* ---- query: the three phases (Section III-A) --------------------------- */
+
+/* Phases 1 and 2.  Computes VD (or takes it from `p`) and omega, runs the
+ * calibration samples on the device (stream tag 0, sample indices
+ * [0, n_calib)), derives delta_L(x), delta_U(x) on the host and uploads
+ * L_L = -ln delta_L, L_U = -ln delta_U.  Allocates the query's device state.
+ * Synchronises `cuda_stream`.  Rejects eps, delta outside (0,1) and omega
+ * >= 2^32 (the counters are 32-bit). */
+kadabra_status kadabra_calibrate(kadabra_graph *g, const kadabra_params *p, void *cuda_stream,
+                                 kadabra_query **out);
+kadabra_status kadabra_query_free(kadabra_query *q);
+
+/* Phase 3, one epoch (async).  Takes adaptive samples [tau, tau + m) with
+ * m = min(n_samples, omega_ceil - tau) (stream tag 1) and adds each sampled
+ * path's interior vertices to c~.  tau lives on the device and advances when
+ * the launch ends; if a previous check already stopped the query the launch
+ * takes no samples.  Device errors surface at the next synchronising call. */
+kadabra_status kadabra_sample_epoch(kadabra_query *q, int64_t n_samples, void *cuda_stream);
+
+/* Stopping condition on the current snapshot (tau, c~): stop iff tau >= omega
+ * or max_x f(b~(x), delta_L(x), omega, tau) < eps and max_x g(b~(x),
+ * delta_U(x), omega, tau) < eps, evaluated in IEEE double without contraction.
+ * The first check that stops records the stop epoch.  Synchronises and writes
+ * the host outputs (each may be NULL). */
+kadabra_status kadabra_check_stop(kadabra_query *q, int *stopped, double *max_f, double *max_g,
+                                  void *cuda_stream);
+/* Same check, async: the flag stays on the device, where later
+ * kadabra_sample_epoch launches read it. */
+kadabra_status kadabra_check_stop_async(kadabra_query *q, void *cuda_stream);
+
+/* Convenience loop: epochs of `epoch_len` samples, each followed by an async
+ * check, until the query stops or `max_epochs` checks ran.  The host reads the
+ * device flag once every `sync_every` epochs (<= 0: 4).  Writes *stopped. */
+kadabra_status kadabra_run(kadabra_query *q, int64_t epoch_len, int64_t max_epochs,
+                           int64_t sync_every, void *cuda_stream, int *stopped);
+
+/* Restart phase 3 (tau = 0, c~ = 0, not stopped) keeping omega and the
+ * calibrated budgets (async). */
+kadabra_status kadabra_query_reset(kadabra_query *q, void *cuda_stream);
+
+/* Result: b~(x) = c~(x) / tau, computed on the device.  Host outputs, each
+ * optional: btilde[n] (double), counts[n] (uint32 c~), *tau, *stop_epoch.
+ * Synchronises.  KADABRA_ERR_STATE if tau == 0 and btilde is requested. */
+kadabra_status kadabra_result(kadabra_query *q, double *btilde, uint32_t *counts, uint64_t *tau,
+                              int64_t *stop_epoch, void *cuda_stream);
+
+/* Snapshot of omega, tau, epochs, maxima and counters.  Synchronises. */
+kadabra_status kadabra_query_get_info(kadabra_query *q, kadabra_query_info *out, void *cuda_stream);
+
+/* Calibration budgets as uploaded: host L_L[n], L_U[n] (each optional) and the
+ * calibration counts cal[n] (optional).  Synchronises. */
+kadabra_status kadabra_query_budgets(kadabra_query *q, double *L_L, double *L_U, uint32_t *cal,
+                                     void *cuda_stream);
+
+/* Per-sample records for sample indices [first, first + count) of stream
+ * `tag` (0 calibration, 1 adaptive), computed by the same sampling kernel
+ * without touching the query's counters or tau.  Host outputs: recs[count];
+ * interior[count * path_cap] (optional) receives each path's interior
+ * vertices in the order meeting vertex, walk towards s, walk towards t,
+ * truncated to path_cap.  Synchronises. */
+kadabra_status kadabra_sample_trace(kadabra_query *q, int tag, uint64_t first, int64_t count,
+                                    kadabra_trace_rec *recs, int32_t *interior, int64_t path_cap,
+                                    void *cuda_stream);
+
+/* Per-launch instrumentation of kadabra_sample_epoch: each launch is
+ * bracketed by CUDA events on its stream and keeps its own counters; the
+ * query remembers its most recent 256 launches. */
+typedef struct kadabra_launch_stats {
+    float ms;                   /* sampling kernel time between its two events             */
+    uint64_t samples, connected, e_scan, expanded, touched, interior, walk_scan;
+    int32_t grid, threads;      /* launch shape                                             */
+} kadabra_launch_stats;
+/* The most recent launch.  Synchronises on its end event. */
+kadabra_status kadabra_last_launch(kadabra_query *q, kadabra_launch_stats *out);
+/* Up to `max_entries` most recent launches, oldest first, into out[]; *n_out
+ * receives the number written.  Synchronises on the newest end event. */
+kadabra_status kadabra_launch_log(kadabra_query *q, int64_t max_entries, kadabra_launch_stats *out,
+                                  int64_t *n_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KADABRA_H */

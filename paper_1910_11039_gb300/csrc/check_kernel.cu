@@ -1,0 +1,155 @@
+// Epoch-boundary kernels: the stopping condition and the result
+// (arXiv 1910.11039, Section III-A: f(...) < eps and g(...) < eps for all x,
+// checked on a consistent snapshot of (tau, c~), Section III-B).
+//
+// Compiled with -fmad=false and written with explicit IEEE round-to-nearest
+// intrinsics so that every f and g value is the correctly rounded result of
+// the same operation sequence a host evaluation uses:
+//   f = (L_L/tau) * (1/3 - omega/tau + sqrt((1/3 - omega/tau)^2 + ((2 b~) omega) / L_L))
+//   g = (L_U/tau) * (1/3 + omega/tau + sqrt((1/3 + omega/tau)^2 + ((2 b~) omega) / L_U))
+// with b~ = c~(x) / tau.  The maxima are exact (comparisons), so the stop
+// decision does not depend on the reduction order.
+//
+// Traffic: one streaming pass of 20 bytes per vertex (u32 counter, two f64
+// budgets); the grid is a multiple of the SM count.
+
+#include <cstdint>
+
+#include "kadabra_internal.h"
+
+namespace kadabra {
+namespace {
+
+constexpr int kCheckThreads = 256;
+
+__device__ __forceinline__ double fmax_exact(double a, double b) { return b > a ? b : a; }
+
+__global__ void __launch_bounds__(kCheckThreads) check_kernel(CheckLaunch a)
+{
+    __shared__ double sf[kCheckThreads / 32], sg[kCheckThreads / 32];
+    Job *job = a.job;
+    if (*reinterpret_cast<volatile int *>(&job->stopped)) return;   // stays stopped
+    const unsigned long long tau = *reinterpret_cast<volatile unsigned long long *>(&job->tau);
+
+    double mf = 0.0, mg = 0.0;
+    if (tau > 0) {
+        const double tau_d = (double)tau;
+        const double r = __ddiv_rn(a.omega, tau_d);
+        const double third = 1.0 / 3.0;
+        const double af = __dsub_rn(third, r);
+        const double ag = __dadd_rn(third, r);
+        const double af2 = __dmul_rn(af, af);
+        const double ag2 = __dmul_rn(ag, ag);
+        const long long stride = (long long)gridDim.x * blockDim.x;
+        for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < a.n; x += stride) {
+            const unsigned int c = __ldg(a.counts + x);
+            const double2 L = __ldg(a.L + x);
+            const double bt = __ddiv_rn((double)c, tau_d);
+            const double bw = __dmul_rn(__dmul_rn(2.0, bt), a.omega);
+            const double f = __dmul_rn(__ddiv_rn(L.x, tau_d), __dadd_rn(af, __dsqrt_rn(__dadd_rn(af2, __ddiv_rn(bw, L.x)))));
+            const double g = __dmul_rn(__ddiv_rn(L.y, tau_d), __dadd_rn(ag, __dsqrt_rn(__dadd_rn(ag2, __ddiv_rn(bw, L.y)))));
+            mf = fmax_exact(mf, f);
+            mg = fmax_exact(mg, g);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        mf = fmax_exact(mf, __shfl_xor_sync(0xffffffffu, mf, o));
+        mg = fmax_exact(mg, __shfl_xor_sync(0xffffffffu, mg, o));
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        sf[wid] = mf;
+        sg[wid] = mg;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < kCheckThreads / 32; ++i) {
+            mf = fmax_exact(mf, sf[i]);
+            mg = fmax_exact(mg, sg[i]);
+        }
+        // f, g >= +0, so their bit patterns order like the values
+        atomicMax(&job->maxf_bits, (unsigned long long)__double_as_longlong(mf));
+        atomicMax(&job->maxg_bits, (unsigned long long)__double_as_longlong(mg));
+        __threadfence();
+        const unsigned int prev = atomicAdd(&job->check_done, 1u);
+        if (prev == gridDim.x - 1) {
+            __threadfence();
+            double Mf = __longlong_as_double((long long)*reinterpret_cast<volatile unsigned long long *>(&job->maxf_bits));
+            double Mg = __longlong_as_double((long long)*reinterpret_cast<volatile unsigned long long *>(&job->maxg_bits));
+            int stop = 0;
+            if (tau == 0) {
+                Mf = __longlong_as_double(0x7ff0000000000000LL);
+                Mg = Mf;
+            } else {
+                stop = ((double)tau >= a.omega) || (Mf < a.eps && Mg < a.eps);
+            }
+            job->last_maxf = Mf;
+            job->last_maxg = Mg;
+            if (stop) {
+                job->stopped = 1;
+                job->stop_epoch = job->epoch;
+            }
+            job->epoch += 1;
+            job->maxf_bits = 0ULL;
+            job->maxg_bits = 0ULL;
+            job->check_done = 0u;
+            __threadfence();
+        }
+    }
+}
+
+__global__ void result_kernel(long long n, const uint32_t *counts, const Job *job, double *btilde)
+{
+    const double tau_d = (double)job->tau;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += stride)
+        btilde[x] = __ddiv_rn((double)__ldg(counts + x), tau_d);
+}
+
+__global__ void reset_job_kernel(Job *job)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        Job z;
+        unsigned char *p = reinterpret_cast<unsigned char *>(&z);
+        for (size_t i = 0; i < sizeof(Job); ++i) p[i] = 0;
+        z.stop_epoch = -1;
+        *job = z;
+    }
+}
+
+int grid_for(long long n, int threads)
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+    long long want = (n + threads - 1) / threads;
+    long long cap = (long long)sms * 8;    // 8 CTAs of 256 threads per SM: full occupancy
+    long long g = want < cap ? want : cap;
+    return (int)(g > 0 ? g : 1);
+}
+
+}  // namespace
+
+cudaError_t launch_check(const CheckLaunch &a, cudaStream_t st)
+{
+    CheckLaunch b = a;
+    if (b.grid <= 0) b.grid = grid_for(a.n, kCheckThreads);
+    check_kernel<<<b.grid, kCheckThreads, 0, st>>>(b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_result(int64_t n, const uint32_t *counts, const Job *job, double *btilde, cudaStream_t st)
+{
+    result_kernel<<<grid_for(n, 256), 256, 0, st>>>((long long)n, counts, job, btilde);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reset_job(Job *job, cudaStream_t st)
+{
+    reset_job_kernel<<<1, 32, 0, st>>>(job);
+    return cudaGetLastError();
+}
+
+}  // namespace kadabra

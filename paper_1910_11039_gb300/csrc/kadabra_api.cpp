@@ -1,0 +1,870 @@
+// Host side of the C ABI declared in include/kadabra.h.
+//
+// Phase 1 (diameter -> omega) and the calibration arithmetic of phase 2 run
+// here on the host in IEEE double (built with -ffp-contract=off); the
+// sampling, the stop check and the result run in the kernels of
+// sample_kernel.cu and check_kernel.cu (arXiv 1910.11039, Section III-A).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "kadabra.h"
+#include "kadabra_internal.h"
+
+using kadabra::Job;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+kadabra_status fail(kadabra_status st, const std::string &msg)
+{
+    g_last_error = msg;
+    return st;
+}
+
+kadabra_status cuda_fail(cudaError_t e, const char *what)
+{
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    if (e == cudaErrorMemoryAllocation) return fail(KADABRA_ERR_OOM, m);
+    if (e == cudaErrorNoDevice || e == cudaErrorInsufficientDriver) return fail(KADABRA_ERR_NO_DEVICE, m);
+    return fail(KADABRA_ERR_CUDA, m);
+}
+
+#define KCUDA(call, what)                      \
+    do {                                       \
+        cudaError_t _e = (call);               \
+        if (_e != cudaSuccess) return cuda_fail(_e, what); \
+    } while (0)
+
+int bitlen64(uint64_t x)
+{
+    int b = 0;
+    while (x) {
+        ++b;
+        x >>= 1;
+    }
+    return b;
+}
+
+cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+}  // namespace
+
+struct kadabra_graph {
+    int64_t n = 0, nnz = 0, max_degree = 0;
+    int off64 = 0;
+    void *d_off = nullptr;
+    int32_t *d_col = nullptr;
+    std::vector<int64_t> h_off;   // host copy for the diameter phase
+    std::vector<int32_t> h_col;
+    // sampling scratch shared by the graph's queries
+    kadabra::SlotRec *d_recs = nullptr;
+    uint32_t *d_queues = nullptr;
+    int ws_slots = 0;
+    int ws_threads = 0;
+};
+
+struct kadabra_query {
+    kadabra_graph *g = nullptr;
+    kadabra_params p{};
+    double omega = 0.0;
+    uint64_t omega_ceil = 0;
+    int64_t vd = 0;
+    int64_t n_calib = 0;
+    int K = 0;
+    double balance_C = 0.0;
+    int slots = 0;
+    int threads = 256;
+    uint32_t *d_counts = nullptr;
+    uint32_t *d_cal = nullptr;
+    double2 *d_L = nullptr;
+    double *d_btilde = nullptr;
+    Job *d_job = nullptr;       // adaptive stream
+    Job *d_cal_job = nullptr;   // calibration stream
+    Job *d_trace_job = nullptr; // trace runs
+    // launch log: event pair, grid and device counters per sampling launch
+    cudaEvent_t ev0[kadabra::kLaunchLog] = {};
+    cudaEvent_t ev1[kadabra::kLaunchLog] = {};
+    int grid_log[kadabra::kLaunchLog] = {};
+    kadabra::Counters *d_launch = nullptr;   // kLaunchLog entries
+    int64_t launches = 0;
+};
+
+// ---------------------------------------------------------------------------
+// errors, version, params
+// ---------------------------------------------------------------------------
+
+extern "C" const char *kadabra_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" const char *kadabra_status_string(kadabra_status s)
+{
+    switch (s) {
+    case KADABRA_OK: return "KADABRA_OK";
+    case KADABRA_ERR_INVALID_ARG: return "KADABRA_ERR_INVALID_ARG";
+    case KADABRA_ERR_OOM: return "KADABRA_ERR_OOM";
+    case KADABRA_ERR_CUDA: return "KADABRA_ERR_CUDA";
+    case KADABRA_ERR_SIGMA_OVERFLOW: return "KADABRA_ERR_SIGMA_OVERFLOW";
+    case KADABRA_ERR_COUNTER_OVERFLOW: return "KADABRA_ERR_COUNTER_OVERFLOW";
+    case KADABRA_ERR_TIMEOUT: return "KADABRA_ERR_TIMEOUT";
+    case KADABRA_ERR_STATE: return "KADABRA_ERR_STATE";
+    case KADABRA_ERR_NO_DEVICE: return "KADABRA_ERR_NO_DEVICE";
+    }
+    return "KADABRA_ERR_UNKNOWN";
+}
+
+extern "C" int kadabra_abi_version(void) { return 100; }
+
+extern "C" void kadabra_params_default(kadabra_params *p)
+{
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->eps = 0.01;
+    p->delta = 0.1;
+    p->seed = 1;
+    p->vertex_diameter = 0;
+    p->n_calib = 0;
+    p->delta_rule = KADABRA_DELTA_BALANCED;
+    p->flags = 0;
+    p->beta = 1e-3;
+    p->slots = 0;
+    p->threads = 256;
+    p->scratch_fraction = 0.6;
+}
+
+// ---------------------------------------------------------------------------
+// host utilities
+// ---------------------------------------------------------------------------
+
+template <typename OffT>
+static kadabra_status validate(int64_t n, int64_t nnz, const OffT *off, const int32_t *col)
+{
+    if (n < 1 || n >= (int64_t(1) << 31)) return fail(KADABRA_ERR_INVALID_ARG, "n must be in [1, 2^31)");
+    if (nnz < 0) return fail(KADABRA_ERR_INVALID_ARG, "nnz must be >= 0");
+    if (!off || (nnz > 0 && !col)) return fail(KADABRA_ERR_INVALID_ARG, "null CSR array");
+    if ((int64_t)off[0] != 0) return fail(KADABRA_ERR_INVALID_ARG, "offsets[0] != 0");
+    if ((int64_t)off[n] != nnz) return fail(KADABRA_ERR_INVALID_ARG, "offsets[n] != nnz");
+    for (int64_t v = 0; v < n; ++v) {
+        const int64_t b = (int64_t)off[v], e = (int64_t)off[v + 1];
+        if (e < b) return fail(KADABRA_ERR_INVALID_ARG, "offsets not non-decreasing at vertex " + std::to_string(v));
+        for (int64_t i = b; i < e; ++i) {
+            const int64_t w = col[i];
+            if (w < 0 || w >= n) return fail(KADABRA_ERR_INVALID_ARG, "neighbour id out of range at vertex " + std::to_string(v));
+            if (w == v) return fail(KADABRA_ERR_INVALID_ARG, "self-loop at vertex " + std::to_string(v));
+            if (i > b && col[i - 1] >= w)
+                return fail(KADABRA_ERR_INVALID_ARG, "neighbour list not strictly ascending at vertex " + std::to_string(v));
+        }
+    }
+    // symmetry: every (v, w) has (w, v), found by binary search in w's row
+    for (int64_t v = 0; v < n; ++v) {
+        for (int64_t i = (int64_t)off[v]; i < (int64_t)off[v + 1]; ++i) {
+            const int64_t w = col[i];
+            int64_t lo = (int64_t)off[w], hi = (int64_t)off[w + 1];
+            while (lo < hi) {
+                const int64_t mid = (lo + hi) / 2;
+                if (col[mid] < v) lo = mid + 1;
+                else hi = mid;
+            }
+            if (lo == (int64_t)off[w + 1] || col[lo] != v)
+                return fail(KADABRA_ERR_INVALID_ARG, "CSR not symmetric: edge " + std::to_string(v) + "->" +
+                                                         std::to_string(w) + " has no reverse");
+        }
+    }
+    return KADABRA_OK;
+}
+
+extern "C" kadabra_status kadabra_validate_csr(int64_t n, int64_t nnz, const void *offsets, int offsets_is_64,
+                                               const int32_t *cols)
+{
+    if (offsets_is_64) return validate(n, nnz, static_cast<const int64_t *>(offsets), cols);
+    if (nnz >= (int64_t(1) << 31)) return fail(KADABRA_ERR_INVALID_ARG, "nnz too large for int32 offsets");
+    return validate(n, nnz, static_cast<const int32_t *>(offsets), cols);
+}
+
+extern "C" kadabra_status kadabra_omega(double eps, double delta, int64_t vertex_diameter, double *omega)
+{
+    if (!omega) return fail(KADABRA_ERR_INVALID_ARG, "omega is null");
+    if (!(eps > 0.0 && eps < 1.0) || !(delta > 0.0 && delta < 1.0)) {
+        *omega = NAN;
+        return fail(KADABRA_ERR_INVALID_ARG, "eps and delta must lie in (0, 1)");
+    }
+    int64_t x = vertex_diameter - 2;
+    if (x < 1) x = 1;
+    const int floor_log2 = bitlen64((uint64_t)x) - 1;
+    *omega = (0.5 / (eps * eps)) * ((double)floor_log2 + 1.0 + std::log(2.0 / delta));
+    return KADABRA_OK;
+}
+
+extern "C" int kadabra_sigma_bits(int64_t n, int64_t max_degree)
+{
+    const int a = 63 - bitlen64((uint64_t)max_degree);
+    const int b = 63 - bitlen64((uint64_t)n);
+    return a < b ? a : b;
+}
+
+// Vertex-diameter upper bound: per component, 2 * ecc(smallest id) + 1.
+static int64_t vd_bound(const kadabra_graph *g)
+{
+    const int64_t n = g->n;
+    std::vector<int32_t> dist((size_t)n, -1);
+    std::vector<int32_t> q((size_t)n);
+    int64_t best = 1;
+    for (int64_t r = 0; r < n; ++r) {
+        if (dist[(size_t)r] != -1) continue;
+        int64_t head = 0, tail = 0, ecc = 0;
+        dist[(size_t)r] = 0;
+        q[(size_t)tail++] = (int32_t)r;
+        while (head < tail) {
+            const int32_t u = q[(size_t)head++];
+            const int32_t du = dist[(size_t)u];
+            if (du > ecc) ecc = du;
+            for (int64_t i = g->h_off[(size_t)u]; i < g->h_off[(size_t)u + 1]; ++i) {
+                const int32_t w = g->h_col[(size_t)i];
+                if (dist[(size_t)w] == -1) {
+                    dist[(size_t)w] = du + 1;
+                    q[(size_t)tail++] = w;
+                }
+            }
+        }
+        if (2 * ecc + 1 > best) best = 2 * ecc + 1;
+    }
+    return best;
+}
+
+// delta_L / delta_U -> L = -ln(delta).  Balanced rule: bisection for C with
+// sum_x exp(-C eps^2 / bhat(x)) <= (1 - beta) delta / 4 (bhat = cal / n_cal),
+// delta_L = delta_U = exp(-C eps^2 / bhat) + beta delta / (4n).  The per-vertex
+// sum runs in vertex order; exp is evaluated once per distinct count value
+// (identical arguments give identical results).
+static void budgets(int64_t n, const std::vector<uint32_t> &cal, int64_t n_cal, double eps, double delta, int rule,
+                    double beta, std::vector<double> &LL, std::vector<double> &LU, double *C_out)
+{
+    LL.assign((size_t)n, 0.0);
+    LU.assign((size_t)n, 0.0);
+    if (rule == KADABRA_DELTA_UNIFORM) {
+        const double dl = delta / (4.0 * (double)n);
+        for (int64_t x = 0; x < n; ++x) {
+            LL[(size_t)x] = -std::log(dl);
+            LU[(size_t)x] = -std::log(dl);
+        }
+        *C_out = 0.0;
+        return;
+    }
+    uint32_t cmax = 0;
+    for (uint32_t c : cal) cmax = c > cmax ? c : cmax;
+    std::vector<double> term((size_t)cmax + 1, 0.0);
+    auto fill_terms = [&](double C) {
+        for (uint32_t c = 1; c <= cmax; ++c) {
+            const double bhat = (double)c / (double)n_cal;
+            term[c] = std::exp(-((C * (eps * eps)) / bhat));
+        }
+    };
+    const double budget = (1.0 - beta) * delta / 4.0;
+    double lo = 0.0;
+    double hi = std::log(4.0 * (double)n / ((1.0 - beta) * delta)) / (eps * eps);
+    while (hi - lo > eps / 10.0) {
+        const double mid = (lo + hi) / 2.0;
+        fill_terms(mid);
+        double sum = 0.0;
+        for (int64_t x = 0; x < n; ++x)
+            if (cal[(size_t)x] != 0) sum += term[cal[(size_t)x]];
+        if (sum <= budget) hi = mid;
+        else lo = mid;
+    }
+    const double C = hi;
+    fill_terms(C);
+    const double floor_term = beta * delta / (4.0 * (double)n);
+    for (int64_t x = 0; x < n; ++x) {
+        const uint32_t c = cal[(size_t)x];
+        const double dl = c == 0 ? floor_term : term[c] + floor_term;
+        LL[(size_t)x] = -std::log(dl);
+        LU[(size_t)x] = -std::log(dl);
+    }
+    *C_out = C;
+}
+
+// ---------------------------------------------------------------------------
+// graph
+// ---------------------------------------------------------------------------
+
+static void free_graph_device(kadabra_graph *g)
+{
+    cudaFree(g->d_off);
+    cudaFree(g->d_col);
+    cudaFree(g->d_recs);
+    cudaFree(g->d_queues);
+    g->d_off = g->d_col = nullptr;
+    g->d_recs = nullptr;
+    g->d_queues = nullptr;
+}
+
+extern "C" kadabra_status kadabra_graph_load(int64_t n, int64_t nnz, const void *offsets, int offsets_is_64,
+                                             const int32_t *cols, uint32_t flags, void *cuda_stream,
+                                             kadabra_graph **out)
+{
+    if (!out) return fail(KADABRA_ERR_INVALID_ARG, "out is null");
+    if (n < 1 || n >= (int64_t(1) << 31)) return fail(KADABRA_ERR_INVALID_ARG, "n must be in [1, 2^31)");
+    if (nnz < 0 || !offsets || (nnz > 0 && !cols)) return fail(KADABRA_ERR_INVALID_ARG, "bad CSR arguments");
+    if (!offsets_is_64 && nnz >= (int64_t(1) << 31))
+        return fail(KADABRA_ERR_INVALID_ARG, "nnz too large for int32 offsets");
+    const bool dev = (flags & KADABRA_GRAPH_DEVICE_PTRS) != 0;
+    const size_t ob = (size_t)(n + 1) * (offsets_is_64 ? 8 : 4);
+    const size_t cb = (size_t)nnz * 4;
+    cudaStream_t st = as_stream(cuda_stream);
+
+    kadabra_graph *g = new kadabra_graph();
+    g->n = n;
+    g->nnz = nnz;
+    g->off64 = offsets_is_64 ? 1 : 0;
+    g->h_off.resize((size_t)n + 1);
+    g->h_col.resize((size_t)nnz);
+    // host copy (diameter phase, degree statistics)
+    std::vector<unsigned char> off_raw;
+    const void *hoff = offsets;
+    const int32_t *hcol = cols;
+    if (dev) {
+        off_raw.resize(ob);
+        cudaError_t e = cudaMemcpyAsync(off_raw.data(), offsets, ob, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && cb) e = cudaMemcpyAsync(g->h_col.data(), cols, cb, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            delete g;
+            return cuda_fail(e, "copy CSR to host");
+        }
+        hoff = off_raw.data();
+        hcol = g->h_col.data();
+    }
+    if (!(flags & KADABRA_GRAPH_SKIP_VALIDATE)) {
+        kadabra_status s = kadabra_validate_csr(n, nnz, hoff, offsets_is_64, hcol);
+        if (s != KADABRA_OK) {
+            delete g;
+            return s;
+        }
+    }
+    for (int64_t v = 0; v <= n; ++v)
+        g->h_off[(size_t)v] = offsets_is_64 ? static_cast<const int64_t *>(hoff)[v] : static_cast<const int32_t *>(hoff)[v];
+    if (!dev && cb) std::memcpy(g->h_col.data(), cols, cb);
+    int64_t md = 0;
+    for (int64_t v = 0; v < n; ++v) {
+        const int64_t d = g->h_off[(size_t)v + 1] - g->h_off[(size_t)v];
+        md = d > md ? d : md;
+    }
+    g->max_degree = md;
+
+    cudaError_t e = cudaMalloc(&g->d_off, ob);
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&g->d_col), cb ? cb : 4);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(g->d_off, offsets, ob, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && cb)
+        e = cudaMemcpyAsync(g->d_col, cols, cb, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        free_graph_device(g);
+        delete g;
+        return cuda_fail(e, "upload CSR");
+    }
+    *out = g;
+    return KADABRA_OK;
+}
+
+extern "C" kadabra_status kadabra_graph_free(kadabra_graph *g)
+{
+    if (!g) return KADABRA_OK;
+    cudaDeviceSynchronize();
+    free_graph_device(g);
+    delete g;
+    return KADABRA_OK;
+}
+
+extern "C" kadabra_status kadabra_graph_info(const kadabra_graph *g, int64_t *n, int64_t *nnz, int64_t *max_degree,
+                                             int *offsets_is_64)
+{
+    if (!g) return fail(KADABRA_ERR_INVALID_ARG, "graph is null");
+    if (n) *n = g->n;
+    if (nnz) *nnz = g->nnz;
+    if (max_degree) *max_degree = g->max_degree;
+    if (offsets_is_64) *offsets_is_64 = g->off64;
+    return KADABRA_OK;
+}
+
+// Sampling scratch: slots * n * (32 B record + 4 B queue entry).
+static kadabra_status ensure_workspace(kadabra_graph *g, int want_slots, int threads, double fraction)
+{
+    int dev = 0, sms = 0, per_sm = 0;
+    KCUDA(cudaGetDevice(&dev), "cudaGetDevice");
+    KCUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
+    KCUDA(kadabra::sample_occupancy(threads, g->off64, &per_sm), "occupancy");
+    if (per_sm < 1) per_sm = 1;
+    int slots = want_slots > 0 ? want_slots : sms * per_sm;
+    const size_t per_slot = (size_t)g->n * (sizeof(kadabra::SlotRec) + sizeof(uint32_t));
+    if (g->d_recs && g->ws_slots >= slots && g->ws_threads == threads) return KADABRA_OK;
+    cudaDeviceSynchronize();
+    cudaFree(g->d_recs);
+    cudaFree(g->d_queues);
+    g->d_recs = nullptr;
+    g->d_queues = nullptr;
+    g->ws_slots = 0;
+    size_t free_b = 0, total_b = 0;
+    KCUDA(cudaMemGetInfo(&free_b, &total_b), "cudaMemGetInfo");
+    if (fraction <= 0.0 || fraction > 0.95) fraction = 0.6;
+    const size_t budget = (size_t)((double)free_b * fraction);
+    size_t fit = per_slot ? budget / per_slot : (size_t)slots;
+    if ((size_t)slots > fit) slots = (int)fit;
+    if (slots < 1) return fail(KADABRA_ERR_OOM, "not enough device memory for one sampling slot");
+    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&g->d_recs), (size_t)slots * (size_t)g->n * sizeof(kadabra::SlotRec));
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&g->d_queues), (size_t)slots * (size_t)g->n * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMemset(g->d_recs, 0, (size_t)slots * (size_t)g->n * sizeof(kadabra::SlotRec));
+    if (e != cudaSuccess) {
+        cudaFree(g->d_recs);
+        cudaFree(g->d_queues);
+        g->d_recs = nullptr;
+        g->d_queues = nullptr;
+        return cuda_fail(e, "allocate sampling scratch");
+    }
+    g->ws_slots = slots;
+    g->ws_threads = threads;
+    return KADABRA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// query
+// ---------------------------------------------------------------------------
+
+static void free_query_device(kadabra_query *q)
+{
+    cudaFree(q->d_counts);
+    cudaFree(q->d_cal);
+    cudaFree(q->d_L);
+    cudaFree(q->d_btilde);
+    cudaFree(q->d_job);
+    cudaFree(q->d_cal_job);
+    cudaFree(q->d_trace_job);
+    cudaFree(q->d_launch);
+    for (int i = 0; i < kadabra::kLaunchLog; ++i) {
+        if (q->ev0[i]) cudaEventDestroy(q->ev0[i]);
+        if (q->ev1[i]) cudaEventDestroy(q->ev1[i]);
+    }
+}
+
+static kadabra_status device_error_status(const Job &j)
+{
+    if (j.error & kadabra::kErrSigmaOverflow)
+        return fail(KADABRA_ERR_SIGMA_OVERFLOW, "strict mode: a per-side path count exceeded 2^K");
+    if (j.error & kadabra::kErrCounterOverflow) return fail(KADABRA_ERR_COUNTER_OVERFLOW, "a 32-bit counter wrapped");
+    if (j.error & (kadabra::kErrAddOverflow | kadabra::kErrSelect))
+        return fail(KADABRA_ERR_CUDA, "internal sampling invariant violated (error bits " + std::to_string(j.error) + ")");
+    return KADABRA_OK;
+}
+
+static kadabra::SampleLaunch base_launch(const kadabra_query *q)
+{
+    kadabra::SampleLaunch a{};
+    a.n = q->g->n;
+    a.off = q->g->d_off;
+    a.off64 = q->g->off64;
+    a.col = q->g->d_col;
+    a.recs = q->g->d_recs;
+    a.queues = q->g->d_queues;
+    a.seed = q->p.seed;
+    a.K = q->K;
+    a.strict = (q->p.flags & KADABRA_STRICT_SIGMA) ? 1 : 0;
+    a.threads = q->threads;
+    return a;
+}
+
+// Never launch more CTAs than the graph's scratch has slots (another query
+// may have re-sized it), nor more than there are samples.
+static int clamp_grid(const kadabra_query *q, int64_t count)
+{
+    int64_t g = q->slots < q->g->ws_slots ? q->slots : q->g->ws_slots;
+    if (count < g) g = count;
+    return (int)g;
+}
+
+extern "C" kadabra_status kadabra_calibrate(kadabra_graph *g, const kadabra_params *pin, void *cuda_stream,
+                                            kadabra_query **out)
+{
+    if (!g || !out) return fail(KADABRA_ERR_INVALID_ARG, "graph or out is null");
+    kadabra_params p;
+    if (pin) p = *pin;
+    else kadabra_params_default(&p);
+    if (!(p.eps > 0.0 && p.eps < 1.0) || !(p.delta > 0.0 && p.delta < 1.0))
+        return fail(KADABRA_ERR_INVALID_ARG, "eps and delta must lie in (0, 1)");
+    if (p.delta_rule != KADABRA_DELTA_UNIFORM && p.delta_rule != KADABRA_DELTA_BALANCED)
+        return fail(KADABRA_ERR_INVALID_ARG, "unknown delta_rule");
+    if (!(p.beta > 0.0 && p.beta < 1.0)) return fail(KADABRA_ERR_INVALID_ARG, "beta must lie in (0, 1)");
+    if (p.threads == 0) p.threads = 256;
+    if (p.threads != 128 && p.threads != 256 && p.threads != 512)
+        return fail(KADABRA_ERR_INVALID_ARG, "threads must be 128, 256 or 512");
+    if (g->n < 2) return fail(KADABRA_ERR_INVALID_ARG, "sampling pairs needs n >= 2");
+    cudaStream_t st = as_stream(cuda_stream);
+
+    kadabra_query *q = new kadabra_query();
+    q->g = g;
+    q->p = p;
+    q->threads = p.threads;
+    q->K = kadabra_sigma_bits(g->n, g->max_degree);
+    // phase 1: diameter -> omega
+    q->vd = p.vertex_diameter > 0 ? p.vertex_diameter : vd_bound(g);
+    kadabra_omega(p.eps, p.delta, q->vd, &q->omega);
+    q->omega_ceil = (uint64_t)std::ceil(q->omega);
+    if (q->omega_ceil >= (uint64_t(1) << 32)) {
+        delete q;
+        return fail(KADABRA_ERR_INVALID_ARG, "omega >= 2^32: counters are 32-bit");
+    }
+    q->n_calib = p.n_calib;
+    if (q->n_calib <= 0) {
+        q->n_calib = (int64_t)std::ceil(q->omega / 100.0);
+        if (q->n_calib < 1000) q->n_calib = 1000;
+    }
+    if (q->n_calib >= (int64_t(1) << 32)) {
+        delete q;
+        return fail(KADABRA_ERR_INVALID_ARG, "n_calib must be < 2^32");
+    }
+
+    kadabra_status s = ensure_workspace(g, p.slots, p.threads, p.scratch_fraction);
+    if (s != KADABRA_OK) {
+        delete q;
+        return s;
+    }
+    q->slots = p.slots > 0 && p.slots < g->ws_slots ? p.slots : g->ws_slots;
+
+    const size_t n = (size_t)g->n;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&q->d_counts), n * 4);
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&q->d_cal), n * 4);
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&q->d_L), n * sizeof(double2));
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&q->d_btilde), n * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&q->d_job), sizeof(Job));
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&q->d_cal_job), sizeof(Job));
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&q->d_trace_job), sizeof(Job));
+    if (e == cudaSuccess)
+        e = cudaMalloc(reinterpret_cast<void **>(&q->d_launch), sizeof(kadabra::Counters) * kadabra::kLaunchLog);
+    for (int i = 0; i < kadabra::kLaunchLog && e == cudaSuccess; ++i) {
+        e = cudaEventCreate(&q->ev0[i]);
+        if (e == cudaSuccess) e = cudaEventCreate(&q->ev1[i]);
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(q->d_counts, 0, n * 4, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(q->d_cal, 0, n * 4, st);
+    if (e == cudaSuccess) e = kadabra::launch_reset_job(q->d_job, st);
+    if (e == cudaSuccess) e = kadabra::launch_reset_job(q->d_cal_job, st);
+    if (e == cudaSuccess) e = kadabra::launch_reset_job(q->d_trace_job, st);
+    if (e != cudaSuccess) {
+        free_query_device(q);
+        delete q;
+        return cuda_fail(e, "allocate query state");
+    }
+
+    // phase 2: calibration samples (stream tag 0) on the device
+    kadabra::SampleLaunch a = base_launch(q);
+    a.counts = q->d_cal;
+    a.job = q->d_cal_job;
+    a.tag = 0;
+    a.use_stop = 0;
+    a.epoch_len = q->n_calib;
+    a.clip = 0;
+    a.grid = clamp_grid(q, q->n_calib);
+    e = kadabra::launch_sample(a, st);
+    std::vector<uint32_t> cal(n);
+    Job cj{};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(cal.data(), q->d_cal, n * 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&cj, q->d_cal_job, sizeof(Job), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        free_query_device(q);
+        delete q;
+        return cuda_fail(e, "calibration samples");
+    }
+    s = device_error_status(cj);
+    if (s != KADABRA_OK) {
+        free_query_device(q);
+        delete q;
+        return s;
+    }
+    std::vector<double> LL, LU;
+    budgets(g->n, cal, q->n_calib, p.eps, p.delta, p.delta_rule, p.beta, LL, LU, &q->balance_C);
+    std::vector<double2> L(n);
+    for (size_t x = 0; x < n; ++x) L[x] = make_double2(LL[x], LU[x]);
+    e = cudaMemcpyAsync(q->d_L, L.data(), n * sizeof(double2), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        free_query_device(q);
+        delete q;
+        return cuda_fail(e, "upload budgets");
+    }
+    *out = q;
+    return KADABRA_OK;
+}
+
+extern "C" kadabra_status kadabra_query_free(kadabra_query *q)
+{
+    if (!q) return KADABRA_OK;
+    cudaDeviceSynchronize();
+    free_query_device(q);
+    delete q;
+    return KADABRA_OK;
+}
+
+extern "C" kadabra_status kadabra_sample_epoch(kadabra_query *q, int64_t n_samples, void *cuda_stream)
+{
+    if (!q) return fail(KADABRA_ERR_INVALID_ARG, "query is null");
+    if (n_samples < 0 || n_samples >= (int64_t(1) << 32))
+        return fail(KADABRA_ERR_INVALID_ARG, "n_samples must be in [0, 2^32)");
+    if (n_samples == 0) return KADABRA_OK;
+    cudaStream_t st = as_stream(cuda_stream);
+    kadabra::SampleLaunch a = base_launch(q);
+    a.counts = q->d_counts;
+    a.job = q->d_job;
+    a.tag = 1;
+    a.use_stop = 1;
+    a.epoch_len = n_samples;
+    a.clip = q->omega_ceil;
+    a.grid = clamp_grid(q, n_samples);
+    const int slot = (int)(q->launches % kadabra::kLaunchLog);
+    a.launch_ctr = q->d_launch + slot;
+    KCUDA(cudaMemsetAsync(a.launch_ctr, 0, sizeof(kadabra::Counters), st), "reset launch counters");
+    KCUDA(cudaEventRecord(q->ev0[slot], st), "event");
+    KCUDA(kadabra::launch_sample(a, st), "sampling kernel launch");
+    KCUDA(cudaEventRecord(q->ev1[slot], st), "event");
+    q->grid_log[slot] = a.grid;
+    ++q->launches;
+    return KADABRA_OK;
+}
+
+extern "C" kadabra_status kadabra_check_stop_async(kadabra_query *q, void *cuda_stream)
+{
+    if (!q) return fail(KADABRA_ERR_INVALID_ARG, "query is null");
+    kadabra::CheckLaunch c{};
+    c.n = q->g->n;
+    c.counts = q->d_counts;
+    c.L = q->d_L;
+    c.job = q->d_job;
+    c.omega = q->omega;
+    c.eps = q->p.eps;
+    c.grid = 0;
+    KCUDA(kadabra::launch_check(c, as_stream(cuda_stream)), "stop-check kernel launch");
+    return KADABRA_OK;
+}
+
+static kadabra_status read_job(kadabra_query *q, Job *j, cudaStream_t st)
+{
+    KCUDA(cudaMemcpyAsync(j, q->d_job, sizeof(Job), cudaMemcpyDeviceToHost, st), "read query state");
+    KCUDA(cudaStreamSynchronize(st), "synchronise");
+    return KADABRA_OK;
+}
+
+extern "C" kadabra_status kadabra_check_stop(kadabra_query *q, int *stopped, double *max_f, double *max_g,
+                                             void *cuda_stream)
+{
+    kadabra_status s = kadabra_check_stop_async(q, cuda_stream);
+    if (s != KADABRA_OK) return s;
+    Job j{};
+    s = read_job(q, &j, as_stream(cuda_stream));
+    if (s != KADABRA_OK) return s;
+    s = device_error_status(j);
+    if (s != KADABRA_OK) return s;
+    if (stopped) *stopped = j.stopped;
+    if (max_f) *max_f = j.last_maxf;
+    if (max_g) *max_g = j.last_maxg;
+    return KADABRA_OK;
+}
+
+extern "C" kadabra_status kadabra_run(kadabra_query *q, int64_t epoch_len, int64_t max_epochs, int64_t sync_every,
+                                      void *cuda_stream, int *stopped)
+{
+    if (!q) return fail(KADABRA_ERR_INVALID_ARG, "query is null");
+    if (epoch_len <= 0 || max_epochs <= 0) return fail(KADABRA_ERR_INVALID_ARG, "epoch_len and max_epochs must be > 0");
+    if (sync_every <= 0) sync_every = 4;
+    cudaStream_t st = as_stream(cuda_stream);
+    Job j{};
+    for (int64_t e = 0; e < max_epochs; ++e) {
+        kadabra_status s = kadabra_sample_epoch(q, epoch_len, cuda_stream);
+        if (s == KADABRA_OK) s = kadabra_check_stop_async(q, cuda_stream);
+        if (s != KADABRA_OK) return s;
+        if ((e + 1) % sync_every == 0 || e + 1 == max_epochs) {
+            s = read_job(q, &j, st);
+            if (s != KADABRA_OK) return s;
+            s = device_error_status(j);
+            if (s != KADABRA_OK) return s;
+            if (j.stopped) break;
+        }
+    }
+    if (stopped) *stopped = j.stopped;
+    return KADABRA_OK;
+}
+
+extern "C" kadabra_status kadabra_query_reset(kadabra_query *q, void *cuda_stream)
+{
+    if (!q) return fail(KADABRA_ERR_INVALID_ARG, "query is null");
+    cudaStream_t st = as_stream(cuda_stream);
+    KCUDA(cudaMemsetAsync(q->d_counts, 0, (size_t)q->g->n * 4, st), "reset counters");
+    KCUDA(kadabra::launch_reset_job(q->d_job, st), "reset state");
+    return KADABRA_OK;
+}
+
+extern "C" kadabra_status kadabra_result(kadabra_query *q, double *btilde, uint32_t *counts, uint64_t *tau,
+                                         int64_t *stop_epoch, void *cuda_stream)
+{
+    if (!q) return fail(KADABRA_ERR_INVALID_ARG, "query is null");
+    cudaStream_t st = as_stream(cuda_stream);
+    Job j{};
+    kadabra_status s = read_job(q, &j, st);
+    if (s != KADABRA_OK) return s;
+    s = device_error_status(j);
+    if (s != KADABRA_OK) return s;
+    const size_t n = (size_t)q->g->n;
+    if (btilde) {
+        if (j.tau == 0) return fail(KADABRA_ERR_STATE, "no adaptive samples taken yet");
+        KCUDA(kadabra::launch_result(q->g->n, q->d_counts, q->d_job, q->d_btilde, st), "result kernel launch");
+        KCUDA(cudaMemcpyAsync(btilde, q->d_btilde, n * sizeof(double), cudaMemcpyDeviceToHost, st), "copy result");
+    }
+    if (counts) KCUDA(cudaMemcpyAsync(counts, q->d_counts, n * 4, cudaMemcpyDeviceToHost, st), "copy counts");
+    KCUDA(cudaStreamSynchronize(st), "synchronise");
+    if (tau) *tau = j.tau;
+    if (stop_epoch) *stop_epoch = j.stop_epoch;
+    return KADABRA_OK;
+}
+
+extern "C" kadabra_status kadabra_query_get_info(kadabra_query *q, kadabra_query_info *out, void *cuda_stream)
+{
+    if (!q || !out) return fail(KADABRA_ERR_INVALID_ARG, "query or out is null");
+    Job j{};
+    kadabra_status s = read_job(q, &j, as_stream(cuda_stream));
+    if (s != KADABRA_OK) return s;
+    kadabra_query_info I;
+    std::memset(&I, 0, sizeof(I));
+    I.omega = q->omega;
+    I.omega_ceil = q->omega_ceil;
+    I.vertex_diameter = q->vd;
+    I.n_calib = q->n_calib;
+    I.sigma_bits = q->K;
+    I.stopped = j.stopped;
+    I.tau = j.tau;
+    I.epochs = j.epoch;
+    I.stop_epoch = j.stop_epoch;
+    I.max_f = j.last_maxf;
+    I.max_g = j.last_maxg;
+    I.balance_C = q->balance_C;
+    I.samples = j.total.samples;
+    I.connected = j.total.connected;
+    I.e_scan = j.total.e_scan;
+    I.expanded = j.total.expanded;
+    I.touched = j.total.touched;
+    I.interior = j.total.interior;
+    I.walk_scan = j.total.walk_scan;
+    I.scaled = j.total.scaled;
+    I.device_error = j.error;
+    I.slots = q->slots;
+    I.threads = q->threads;
+    I.offsets_64 = q->g->off64;
+    *out = I;
+    return KADABRA_OK;
+}
+
+extern "C" kadabra_status kadabra_query_budgets(kadabra_query *q, double *L_L, double *L_U, uint32_t *cal,
+                                                void *cuda_stream)
+{
+    if (!q) return fail(KADABRA_ERR_INVALID_ARG, "query is null");
+    cudaStream_t st = as_stream(cuda_stream);
+    const size_t n = (size_t)q->g->n;
+    std::vector<double2> L(n);
+    KCUDA(cudaMemcpyAsync(L.data(), q->d_L, n * sizeof(double2), cudaMemcpyDeviceToHost, st), "copy budgets");
+    if (cal) KCUDA(cudaMemcpyAsync(cal, q->d_cal, n * 4, cudaMemcpyDeviceToHost, st), "copy calibration counts");
+    KCUDA(cudaStreamSynchronize(st), "synchronise");
+    for (size_t x = 0; x < n; ++x) {
+        if (L_L) L_L[x] = L[x].x;
+        if (L_U) L_U[x] = L[x].y;
+    }
+    return KADABRA_OK;
+}
+
+extern "C" kadabra_status kadabra_sample_trace(kadabra_query *q, int tag, uint64_t first, int64_t count,
+                                               kadabra_trace_rec *recs, int32_t *interior, int64_t path_cap,
+                                               void *cuda_stream)
+{
+    if (!q || !recs) return fail(KADABRA_ERR_INVALID_ARG, "query or recs is null");
+    if (tag != 0 && tag != 1) return fail(KADABRA_ERR_INVALID_ARG, "tag must be 0 or 1");
+    if (count <= 0 || count >= (int64_t(1) << 31)) return fail(KADABRA_ERR_INVALID_ARG, "count out of range");
+    if (interior && path_cap <= 0) return fail(KADABRA_ERR_INVALID_ARG, "path_cap must be > 0");
+    static_assert(sizeof(kadabra::TraceRec) == sizeof(kadabra_trace_rec), "trace record layout");
+    cudaStream_t st = as_stream(cuda_stream);
+    kadabra::TraceRec *d_tr = nullptr;
+    int32_t *d_path = nullptr;
+    KCUDA(cudaMalloc(reinterpret_cast<void **>(&d_tr), (size_t)count * sizeof(kadabra::TraceRec)), "trace buffer");
+    if (interior) {
+        cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&d_path), (size_t)count * (size_t)path_cap * 4);
+        if (e != cudaSuccess) {
+            cudaFree(d_tr);
+            return cuda_fail(e, "trace path buffer");
+        }
+    }
+    kadabra::SampleLaunch a = base_launch(q);
+    a.counts = nullptr;
+    a.job = q->d_trace_job;
+    a.tag = (uint32_t)tag;
+    a.use_stop = 0;
+    a.epoch_len = count;
+    a.clip = 0;
+    a.trace = d_tr;
+    a.trace_path = d_path;
+    a.trace_cap = interior ? path_cap : 0;
+    a.grid = clamp_grid(q, count);
+    unsigned long long tau0 = first;
+    cudaError_t e = kadabra::launch_reset_job(q->d_trace_job, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&q->d_trace_job->tau, &tau0, 8, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = kadabra::launch_sample(a, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(recs, d_tr, (size_t)count * sizeof(kadabra::TraceRec), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && interior)
+        e = cudaMemcpyAsync(interior, d_path, (size_t)count * (size_t)path_cap * 4, cudaMemcpyDeviceToHost, st);
+    Job j{};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&j, q->d_trace_job, sizeof(Job), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(d_tr);
+    cudaFree(d_path);
+    if (e != cudaSuccess) return cuda_fail(e, "trace run");
+    return (j.error & ~kadabra::kErrSigmaOverflow) ? device_error_status(j) : KADABRA_OK;
+}
+
+extern "C" kadabra_status kadabra_launch_log(kadabra_query *q, int64_t max_entries, kadabra_launch_stats *out,
+                                             int64_t *n_out)
+{
+    if (!q || !out || !n_out || max_entries < 0) return fail(KADABRA_ERR_INVALID_ARG, "bad arguments");
+    int64_t have = q->launches < kadabra::kLaunchLog ? q->launches : kadabra::kLaunchLog;
+    int64_t m = have < max_entries ? have : max_entries;
+    *n_out = 0;
+    if (m == 0) return KADABRA_OK;
+    const int newest = (int)((q->launches - 1) % kadabra::kLaunchLog);
+    KCUDA(cudaEventSynchronize(q->ev1[newest]), "event sync");
+    std::vector<kadabra::Counters> c(kadabra::kLaunchLog);
+    KCUDA(cudaMemcpy(c.data(), q->d_launch, sizeof(kadabra::Counters) * kadabra::kLaunchLog, cudaMemcpyDeviceToHost),
+          "read launch counters");
+    for (int64_t k = 0; k < m; ++k) {
+        const int slot = (int)((q->launches - m + k) % kadabra::kLaunchLog);
+        float ms = 0.f;
+        KCUDA(cudaEventElapsedTime(&ms, q->ev0[slot], q->ev1[slot]), "event time");
+        kadabra_launch_stats &o = out[k];
+        o.ms = ms;
+        o.samples = c[slot].samples;
+        o.connected = c[slot].connected;
+        o.e_scan = c[slot].e_scan;
+        o.expanded = c[slot].expanded;
+        o.touched = c[slot].touched;
+        o.interior = c[slot].interior;
+        o.walk_scan = c[slot].walk_scan;
+        o.grid = q->grid_log[slot];
+        o.threads = q->threads;
+    }
+    *n_out = m;
+    return KADABRA_OK;
+}
+
+extern "C" kadabra_status kadabra_last_launch(kadabra_query *q, kadabra_launch_stats *out)
+{
+    if (!q || !out) return fail(KADABRA_ERR_INVALID_ARG, "query or out is null");
+    if (q->launches == 0) return fail(KADABRA_ERR_STATE, "no sampling launch yet");
+    int64_t got = 0;
+    return kadabra_launch_log(q, 1, out, &got);
+}

@@ -1,0 +1,103 @@
+// Internal types shared by the host side (kadabra_api.cpp) and the kernels.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace kadabra {
+
+// Per-vertex sampling state of one in-flight sample (one "slot"), 32 bytes so
+// that every probe of a vertex touches a single 32-byte sector.
+//   lvl[side] = BFS distance + 1 from that side's source, 0 = not reached
+//   sig[side] = number of shortest paths from that side's source
+// Invariant between samples: every record of a slot is all-zero (the sample
+// that touched a record clears it before the slot takes its next sample).
+struct alignas(32) SlotRec {
+    uint32_t lvl[2];
+    uint32_t pad[2];
+    unsigned long long sig[2];
+};
+static_assert(sizeof(SlotRec) == 32, "SlotRec must be one sector");
+
+// Counters a launch accumulates (one atomicAdd per CTA at exit).
+struct Counters {
+    unsigned long long samples, connected, e_scan, expanded, touched, interior, walk_scan, scaled;
+};
+
+// Device-resident state of one sample stream (adaptive, calibration, trace).
+struct Job {
+    unsigned long long tau;        // samples already taken by this stream
+    unsigned int work;             // next sample offset inside the running launch
+    unsigned int done_ctas;        // CTAs that finished the running launch
+    int stopped;                   // stop flag (adaptive stream)
+    int pad0;
+    long long epoch;               // checks run so far
+    long long stop_epoch;          // check that stopped, -1 if none
+    unsigned long long maxf_bits;  // running maxima of the check in flight
+    unsigned long long maxg_bits;
+    unsigned int check_done;       // CTAs that finished the running check
+    unsigned int error;            // sticky error bits (kErr*)
+    double last_maxf, last_maxg;   // maxima of the last completed check
+    Counters total;                // since the query started (reset with the query)
+};
+
+constexpr int kLaunchLog = 256;    // sampling launches remembered per query
+
+enum : unsigned int {
+    kErrSigmaOverflow = 1u,    // strict mode: a layer's path count exceeded 2^K
+    kErrAddOverflow = 2u,      // a 64-bit path-count add wrapped (never expected)
+    kErrCounterOverflow = 4u,  // a 32-bit c~ counter wrapped
+    kErrSelect = 8u,           // weighted choice found no element (never expected)
+};
+
+// Per-sample trace record (mirrors kadabra_trace_rec).
+struct TraceRec {
+    long long s, t, d;
+    unsigned long long sigma_lo, sigma_hi;
+    long long meet_size, chosen, e_scan, n_interior;
+    int scaled, overflow;
+};
+
+struct SampleLaunch {
+    int64_t n;
+    const void *off;           // int32 or int64 offsets (n + 1)
+    int off64;
+    const int32_t *col;
+    SlotRec *recs;             // slots * n
+    uint32_t *queues;          // slots * n
+    uint32_t *counts;          // c~[n]; nullptr: do not count (trace runs)
+    Job *job;
+    Counters *launch_ctr;      // this launch's own counters (zeroed before the launch), may be null
+    uint64_t seed;
+    uint32_t tag;              // 0 calibration, 1 adaptive
+    int K;                     // sigma bits
+    int strict;
+    int use_stop;              // honour job->stopped
+    int64_t epoch_len;         // requested samples
+    uint64_t clip;             // never pass this tau (0 = no clip)
+    TraceRec *trace;           // optional per-sample records (index - tau)
+    int32_t *trace_path;       // optional interior vertices, trace_cap per sample
+    int64_t trace_cap;
+    int grid;
+    int threads;
+};
+
+cudaError_t launch_sample(const SampleLaunch &a, cudaStream_t st);
+cudaError_t sample_occupancy(int threads, int off64, int *ctas_per_sm);
+
+struct CheckLaunch {
+    int64_t n;
+    const uint32_t *counts;
+    const double2 *L;          // (L_L, L_U) per vertex
+    Job *job;
+    double omega;
+    double eps;
+    int grid;
+};
+
+cudaError_t launch_check(const CheckLaunch &a, cudaStream_t st);
+cudaError_t launch_result(int64_t n, const uint32_t *counts, const Job *job, double *btilde,
+                          cudaStream_t st);
+cudaError_t launch_reset_job(Job *job, cudaStream_t st);
+
+}  // namespace kadabra

@@ -1,0 +1,752 @@
+// KADABRA sampling kernel for sm_103a (arXiv 1910.11039, Section III-A).
+//
+// One CTA owns one "slot" (the scratch of one in-flight sample) and takes
+// sample indices from a per-launch work counter until the epoch's range is
+// exhausted; a launch is one epoch of the adaptive phase (or the calibration
+// phase).  Per sample:
+//   A1  pair s != t from Philox draw 0;
+//   A2  balanced bidirectional BFS: the side whose frontier has the smaller
+//       degree sum (ties: s) expands one whole layer; path counts sigma are
+//       accumulated with 64-bit atomics (integer sums, so order-free); the
+//       search ends when the new layer touches the other ball (meeting set M)
+//       or dies out (disconnected pair);
+//   A3  meeting vertex w chosen with probability sigma_s(w) sigma_t(w) /
+//       sigma_st in ascending-id order (radix select on ids, 128-bit weights),
+//       then a walk from w to s and from w to t picking each predecessor with
+//       probability proportional to its sigma, in CSR order;
+//   A4  c~(x) += 1 for every interior vertex of the path;
+//   the last CTA of the launch advances tau (A5: stream order makes the
+//   counter vector at the next kernel a consistent snapshot).
+//
+// Layout in HBM (per slot): SlotRec[n] (32 B per vertex: BFS level and path
+// count for each side) and a uint32 queue of n entries shared by both sides
+// (s-side grows from the front, t-side from the back; the balls are disjoint
+// until they meet, so n entries always suffice).  Records are cleared by the
+// sample that set them, so no per-sample O(n) reset is needed.
+//
+// Mutable slot state is read with ld.global.cg (L2) so that values written by
+// atomics of other threads in the CTA are never served stale from L1.
+
+#include <cstdint>
+
+#include "kadabra_internal.h"
+#include "philox.cuh"
+
+namespace kadabra {
+namespace {
+
+constexpr int kMeetCap = 512;      // meeting vertices kept in shared memory
+constexpr int kBuckets = 256;      // radix-select digit width: 8 bits
+
+__device__ __forceinline__ unsigned int ldcg(const unsigned int *p) { return __ldcg(p); }
+__device__ __forceinline__ unsigned long long ldcg(const unsigned long long *p) { return __ldcg(p); }
+
+__device__ __forceinline__ int bitlen64(unsigned long long x) { return 64 - __clzll(x); }
+
+template <typename OffT>
+struct GraphRef {
+    const OffT *off;
+    const int32_t *col;
+    long long n;
+    __device__ __forceinline__ long long begin(long long v) const { return (long long)__ldg(off + v); }
+    __device__ __forceinline__ long long end(long long v) const { return (long long)__ldg(off + v + 1); }
+};
+
+template <int NT>
+struct Smem {
+    // sample
+    unsigned long long idx;
+    long long s, t;
+    unsigned int qlen[2];            // entries appended to each side's queue
+    unsigned int fbeg[2], fend[2];   // current frontier = queue positions [fbeg, fend)
+    unsigned int layer[2];           // radius reached by each side
+    unsigned long long fdeg[2];      // degree sum of each frontier
+    int X;                           // side expanded this layer
+    int status;                      // 0 running, 1 met, 2 disconnected, 3 strict overflow
+    int shift;                       // right shift applied to the new layer
+    int scaled;
+    unsigned int err;
+    // per-layer accumulators
+    unsigned int new_count;
+    unsigned int meet_count;
+    unsigned long long new_deg;
+    unsigned long long max_sig;
+    unsigned long long e_scan;       // this sample
+    unsigned long long expanded;
+    // selection and walk
+    unsigned long long r_lo, r_hi;   // residual of the 128-bit choice
+    unsigned long long sig_lo, sig_hi;
+    unsigned int prefix;
+    long long chosen;
+    long long next_v;
+    int found;
+    unsigned long long walk_total;
+    unsigned int cur;                // work item taken by this CTA
+    unsigned long long tmp[NT / 32];
+    unsigned long long tmp2[NT / 32];
+    unsigned int meet[kMeetCap];
+    unsigned long long wlo[kMeetCap];
+    unsigned long long whi[kMeetCap];
+    union {
+        struct {
+            long long cbeg[NT];
+            unsigned long long cpos[NT];
+            unsigned long long csig[NT];
+        } ex;
+        struct {
+            unsigned long long blo[kBuckets];
+            unsigned long long bhi[kBuckets];
+        } sel;
+    } u;
+};
+
+// ---- block-wide primitives ------------------------------------------------
+
+template <int NT>
+__device__ __forceinline__ unsigned long long block_sum(unsigned long long v, Smem<NT> &sh)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) sh.tmp[wid] = v;
+    __syncthreads();
+    unsigned long long tot = 0;
+#pragma unroll
+    for (int i = 0; i < NT / 32; ++i) tot += sh.tmp[i];
+    __syncthreads();
+    return tot;
+}
+
+template <int NT>
+__device__ __forceinline__ unsigned long long block_max(unsigned long long v, Smem<NT> &sh)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = w > v ? w : v;
+    }
+    if (lane == 0) sh.tmp[wid] = v;
+    __syncthreads();
+    unsigned long long m = 0;
+#pragma unroll
+    for (int i = 0; i < NT / 32; ++i) m = sh.tmp[i] > m ? sh.tmp[i] : m;
+    __syncthreads();
+    return m;
+}
+
+// Exclusive prefix sum over the block; *total receives the block sum.
+template <int NT>
+__device__ __forceinline__ unsigned long long block_excl_scan(unsigned long long v, unsigned long long *total,
+                                                              Smem<NT> &sh)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned long long incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) sh.tmp[wid] = incl;
+    __syncthreads();
+    unsigned long long before = 0, tot = 0;
+#pragma unroll
+    for (int i = 0; i < NT / 32; ++i) {
+        if (i < wid) before += sh.tmp[i];
+        tot += sh.tmp[i];
+    }
+    __syncthreads();
+    *total = tot;
+    return before + incl - v;
+}
+
+// 128-bit helpers (lo, hi pairs)
+__device__ __forceinline__ void add128(unsigned long long &lo, unsigned long long &hi, unsigned long long blo,
+                                       unsigned long long bhi)
+{
+    const unsigned long long l = lo + blo;
+    hi += bhi + (l < lo ? 1ULL : 0ULL);
+    lo = l;
+}
+
+__device__ __forceinline__ bool less128(unsigned long long alo, unsigned long long ahi, unsigned long long blo,
+                                        unsigned long long bhi)
+{
+    return ahi < bhi || (ahi == bhi && alo < blo);
+}
+
+__device__ __forceinline__ void smem_add128(unsigned long long *lo, unsigned long long *hi, unsigned long long vlo,
+                                            unsigned long long vhi)
+{
+    const unsigned long long old = atomicAdd(lo, vlo);
+    const unsigned long long carry = (old + vlo < old) ? 1ULL : 0ULL;
+    if (vhi + carry) atomicAdd(hi, vhi + carry);
+}
+
+template <int NT>
+__device__ __forceinline__ void block_sum128(unsigned long long &lo, unsigned long long &hi, Smem<NT> &sh)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long ol = __shfl_xor_sync(0xffffffffu, lo, o);
+        const unsigned long long oh = __shfl_xor_sync(0xffffffffu, hi, o);
+        add128(lo, hi, ol, oh);
+    }
+    if (lane == 0) {
+        sh.tmp[wid] = lo;
+        sh.tmp2[wid] = hi;
+    }
+    __syncthreads();
+    unsigned long long tl = 0, th = 0;
+#pragma unroll
+    for (int i = 0; i < NT / 32; ++i) add128(tl, th, sh.tmp[i], sh.tmp2[i]);
+    __syncthreads();
+    lo = tl;
+    hi = th;
+}
+
+// ---- queue of one side ---------------------------------------------------
+
+__device__ __forceinline__ unsigned int qget(const uint32_t *q, long long n, int side, unsigned int i)
+{
+    return side == 0 ? __ldcg(q + i) : __ldcg(q + (n - 1 - i));
+}
+
+__device__ __forceinline__ void qset(uint32_t *q, long long n, int side, unsigned int i, unsigned int v)
+{
+    if (side == 0)
+        __stcg(q + i, v);
+    else
+        __stcg(q + (n - 1 - i), v);
+}
+
+// ---- one sample ------------------------------------------------------------
+
+struct LocalStats {
+    unsigned long long samples, connected, e_scan, expanded, touched, interior, walk_scan, scaled;
+};
+
+template <int NT, typename OffT>
+__device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotRec *rec, uint32_t *queue,
+                           Smem<NT> &sh, unsigned long long idx, unsigned long long trace_i, LocalStats &ls)
+{
+    const int tid = threadIdx.x;
+    const long long n = G.n;
+
+    // A1: pair (draw 0)
+    if (tid == 0) {
+        const U64x4 x = sample_draw(a.seed, a.tag, idx, 0);
+        const unsigned long long s = __umul64hi(x.v[0], (unsigned long long)n);
+        unsigned long long t = __umul64hi(x.v[1], (unsigned long long)(n - 1));
+        if (t >= s) ++t;
+        sh.idx = idx;
+        sh.s = (long long)s;
+        sh.t = (long long)t;
+        __stcg(&rec[s].lvl[0], 1u);
+        __stcg(&rec[s].sig[0], 1ULL);
+        __stcg(&rec[t].lvl[1], 1u);
+        __stcg(&rec[t].sig[1], 1ULL);
+        qset(queue, n, 0, 0, (unsigned int)s);
+        qset(queue, n, 1, 0, (unsigned int)t);
+        sh.qlen[0] = sh.qlen[1] = 1;
+        sh.fbeg[0] = sh.fbeg[1] = 0;
+        sh.fend[0] = sh.fend[1] = 1;
+        sh.layer[0] = sh.layer[1] = 0;
+        sh.fdeg[0] = (unsigned long long)(G.end(s) - G.begin(s));
+        sh.fdeg[1] = (unsigned long long)(G.end(t) - G.begin(t));
+        sh.status = 0;
+        sh.scaled = 0;
+        sh.err = 0;
+        sh.e_scan = 0;
+        sh.expanded = 0;
+        sh.meet_count = 0;
+        sh.chosen = -1;
+    }
+    __syncthreads();
+
+    // A2: balanced bidirectional BFS, one whole layer per step
+    for (;;) {
+        if (tid == 0) {
+            sh.X = (sh.fdeg[0] <= sh.fdeg[1]) ? 0 : 1;
+            sh.new_count = 0;
+            sh.meet_count = 0;
+        }
+        __syncthreads();
+        const int X = sh.X, Y = 1 - X;
+        const unsigned int nl = sh.layer[X] + 2;    // level code of the new layer
+        const unsigned int fb = sh.fbeg[X], fe = sh.fend[X];
+        const unsigned int qbase = sh.qlen[X];
+        unsigned long long my_max = 0, my_deg = 0, my_scan = 0;
+        unsigned int my_err = 0;
+
+        for (unsigned int cb = fb; cb < fe; cb += NT) {
+            const unsigned int i = cb + tid;
+            long long b = 0;
+            unsigned long long d = 0, sg = 0;
+            if (i < fe) {
+                const unsigned int u = qget(queue, n, X, i);
+                b = G.begin(u);
+                d = (unsigned long long)(G.end(u) - b);
+                sg = ldcg(&rec[u].sig[X]);
+            }
+            unsigned long long total;
+            const unsigned long long excl = block_excl_scan<NT>(d, &total, sh);
+            sh.u.ex.cbeg[tid] = b;
+            sh.u.ex.cpos[tid] = excl;
+            sh.u.ex.csig[tid] = sg;
+            const int cnt = (int)min((unsigned int)NT, fe - cb);
+            __syncthreads();
+            my_scan += (tid == 0) ? total : 0ULL;
+            for (unsigned long long e = tid; e < total; e += NT) {
+                // owner: the last j with cpos[j] <= e
+                int lo = 0, hi = cnt - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (sh.u.ex.cpos[mid] <= e) lo = mid;
+                    else hi = mid - 1;
+                }
+                const long long w = __ldg(G.col + sh.u.ex.cbeg[lo] + (long long)(e - sh.u.ex.cpos[lo]));
+                const unsigned long long su = sh.u.ex.csig[lo];
+                SlotRec *r = rec + w;
+                unsigned int lv = ldcg(&r->lvl[X]);
+                bool claimed = false;
+                if (lv == 0) {
+                    const unsigned int old = atomicCAS(&r->lvl[X], 0u, nl);
+                    if (old == 0) {
+                        claimed = true;
+                        lv = nl;
+                    } else {
+                        lv = old;
+                    }
+                }
+                if (lv == nl) {
+                    const unsigned long long o = atomicAdd(&r->sig[X], su);
+                    const unsigned long long nv = o + su;
+                    if (nv < o) my_err |= kErrAddOverflow;
+                    my_max = nv > my_max ? nv : my_max;
+                }
+                if (claimed) {
+                    if (ldcg(&r->lvl[Y]) != 0) {
+                        const unsigned int p = atomicAdd(&sh.meet_count, 1u);
+                        if (p < kMeetCap) sh.meet[p] = (unsigned int)w;
+                    } else {
+                        const unsigned int p = atomicAdd(&sh.new_count, 1u);
+                        qset(queue, n, X, qbase + p, (unsigned int)w);
+                        my_deg += (unsigned long long)(G.end(w) - G.begin(w));
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        const unsigned long long lmax = block_max<NT>(my_max, sh);
+        const unsigned long long ldeg = block_sum<NT>(my_deg, sh);
+        if (my_err) atomicOr(&sh.err, my_err);
+        if (tid == 0) {
+            sh.e_scan += my_scan;
+            sh.expanded += fe - fb;
+            sh.layer[X] += 1;
+            sh.qlen[X] += sh.new_count;
+            int shift = 0;
+            if (sh.meet_count > 0) {
+                sh.status = 1;
+            } else if (sh.new_count == 0) {
+                sh.status = 2;
+            } else {
+                shift = bitlen64(lmax) - a.K;
+                if (shift > 0) {
+                    sh.scaled = 1;
+                    if (a.strict) {
+                        sh.status = 3;
+                        shift = 0;
+                    }
+                } else {
+                    shift = 0;
+                }
+                sh.fbeg[X] = qbase;
+                sh.fend[X] = qbase + sh.new_count;
+                sh.fdeg[X] = ldeg;
+            }
+            sh.shift = shift;
+        }
+        __syncthreads();
+        if (sh.status != 0) break;
+        if (sh.shift > 0) {
+            // keep the layer's counts <= 2^K, rounding up so that they stay >= 1
+            const int shv = sh.shift;
+            for (unsigned int i = sh.fbeg[X] + tid; i < sh.fend[X]; i += NT) {
+                const unsigned int v = qget(queue, n, X, i);
+                const unsigned long long sv = ldcg(&rec[v].sig[X]);
+                __stcg(&rec[v].sig[X], ((sv - 1ULL) >> shv) + 1ULL);
+            }
+            __syncthreads();
+        }
+    }
+
+    // A3 + A4: choose the meeting vertex, walk back, count interior vertices
+    const int met = sh.status == 1;
+    unsigned long long path_len = 0, walk_scan = 0;
+    if (met) {
+        const int X = sh.X, Y = 1 - X;
+        const unsigned int nl = sh.layer[X] + 1;    // level code of X's last layer
+        const unsigned int mcnt = sh.meet_count;
+        const bool in_smem = mcnt <= (unsigned int)kMeetCap;
+        // weights sigma_s(w) * sigma_t(w) and their 128-bit total
+        unsigned long long tlo = 0, thi = 0;
+        if (in_smem) {
+            for (unsigned int i = tid; i < mcnt; i += NT) {
+                const unsigned int w = sh.meet[i];
+                const unsigned long long p = ldcg(&rec[w].sig[0]), q = ldcg(&rec[w].sig[1]);
+                const unsigned long long lo = p * q, hi = __umul64hi(p, q);
+                sh.wlo[i] = lo;
+                sh.whi[i] = hi;
+                add128(tlo, thi, lo, hi);
+            }
+        } else {
+            for (unsigned int i = sh.fbeg[Y] + tid; i < sh.fend[Y]; i += NT) {
+                const unsigned int w = qget(queue, n, Y, i);
+                if (ldcg(&rec[w].lvl[X]) != nl) continue;
+                const unsigned long long p = ldcg(&rec[w].sig[0]), q = ldcg(&rec[w].sig[1]);
+                add128(tlo, thi, p * q, __umul64hi(p, q));
+            }
+        }
+        block_sum128<NT>(tlo, thi, sh);
+        if (tid == 0) {
+            sh.sig_lo = tlo;
+            sh.sig_hi = thi;
+            if (in_smem && mcnt == 1) {
+                sh.chosen = sh.meet[0];
+            } else {
+                const U64x4 x = sample_draw(a.seed, a.tag, idx, 1);
+                const unsigned __int128 R = ((unsigned __int128)x.v[1] << 64) | x.v[0];
+                const unsigned __int128 T = ((unsigned __int128)thi << 64) | tlo;
+                const unsigned __int128 r = R % T;
+                sh.r_lo = (unsigned long long)r;
+                sh.r_hi = (unsigned long long)(r >> 64);
+                sh.prefix = 0;
+                sh.chosen = -1;
+            }
+        }
+        __syncthreads();
+        if (sh.chosen < 0) {
+            // radix select over vertex ids, 8 bits per pass, most significant first:
+            // the first id (ascending) whose inclusive weight prefix exceeds r
+            const int nbits = bitlen64((unsigned long long)(n - 1)) > 0 ? bitlen64((unsigned long long)(n - 1)) : 1;
+            const int npass = (nbits + 7) / 8;
+            for (int p = npass - 1; p >= 0; --p) {
+                const int shft = 8 * p;
+                for (int b = tid; b < kBuckets; b += NT) {
+                    sh.u.sel.blo[b] = 0;
+                    sh.u.sel.bhi[b] = 0;
+                }
+                __syncthreads();
+                const unsigned int pref = sh.prefix;
+                const bool top = (p == npass - 1);
+                if (in_smem) {
+                    for (unsigned int i = tid; i < mcnt; i += NT) {
+                        const unsigned int w = sh.meet[i];
+                        if (!top && (w >> (shft + 8)) != pref) continue;
+                        const int dg = (w >> shft) & 255;
+                        smem_add128(&sh.u.sel.blo[dg], &sh.u.sel.bhi[dg], sh.wlo[i], sh.whi[i]);
+                    }
+                } else {
+                    for (unsigned int i = sh.fbeg[Y] + tid; i < sh.fend[Y]; i += NT) {
+                        const unsigned int w = qget(queue, n, Y, i);
+                        if (ldcg(&rec[w].lvl[X]) != nl) continue;
+                        if (!top && (w >> (shft + 8)) != pref) continue;
+                        const unsigned long long pp = ldcg(&rec[w].sig[0]), qq = ldcg(&rec[w].sig[1]);
+                        const int dg = (w >> shft) & 255;
+                        smem_add128(&sh.u.sel.blo[dg], &sh.u.sel.bhi[dg], pp * qq, __umul64hi(pp, qq));
+                    }
+                }
+                if (tid == 0) sh.found = 0;
+                __syncthreads();
+                if (tid < 32) {
+                    // lane l owns buckets [8l, 8l + 8)
+                    unsigned long long slo = 0, shi = 0;
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) add128(slo, shi, sh.u.sel.blo[tid * 8 + j], sh.u.sel.bhi[tid * 8 + j]);
+                    // exclusive scan of lane sums
+                    unsigned long long ilo = slo, ihi = shi;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const unsigned long long yl = __shfl_up_sync(0xffffffffu, ilo, o);
+                        const unsigned long long yh = __shfl_up_sync(0xffffffffu, ihi, o);
+                        if (tid >= o) add128(ilo, ihi, yl, yh);
+                    }
+                    // excl = incl - own
+                    unsigned long long elo = ilo - slo;
+                    unsigned long long ehi = ihi - shi - (ilo < slo ? 1ULL : 0ULL);
+                    const unsigned long long rlo = sh.r_lo, rhi = sh.r_hi;
+                    __syncwarp();   // every lane has read r before one lane rewrites it
+                    // this lane holds r if excl <= r < incl
+                    if (!less128(rlo, rhi, elo, ehi) && less128(rlo, rhi, ilo, ihi)) {
+                        for (int j = 0; j < 8; ++j) {
+                            unsigned long long nlo = elo, nhi = ehi;
+                            add128(nlo, nhi, sh.u.sel.blo[tid * 8 + j], sh.u.sel.bhi[tid * 8 + j]);
+                            if (less128(rlo, rhi, nlo, nhi)) {
+                                // residual r - excl
+                                const unsigned long long dlo = rlo - elo;
+                                const unsigned long long dhi = rhi - ehi - (rlo < elo ? 1ULL : 0ULL);
+                                sh.r_lo = dlo;
+                                sh.r_hi = dhi;
+                                sh.prefix = (pref << 8) | (unsigned int)(tid * 8 + j);
+                                sh.found = 1;
+                                break;
+                            }
+                            elo = nlo;
+                            ehi = nhi;
+                        }
+                    }
+                }
+                __syncthreads();
+                if (!sh.found) break;
+            }
+            if (tid == 0) {
+                const bool ok = sh.found && (long long)sh.prefix < n && ldcg(&rec[sh.prefix].lvl[X]) == nl &&
+                                ldcg(&rec[sh.prefix].lvl[Y]) != 0;
+                sh.chosen = ok ? (long long)sh.prefix : -1;
+                if (!ok) sh.err |= kErrSelect;
+            }
+            __syncthreads();
+        }
+
+        const long long w = sh.chosen;
+        if (tid == 0 && w >= 0) {
+            if (w != sh.s && w != sh.t) {
+                if (a.counts) {
+                    const unsigned int old = atomicAdd(&a.counts[w], 1u);
+                    if (old == 0xffffffffu) sh.err |= kErrCounterOverflow;
+                }
+                if (a.trace_path && (long long)path_len < a.trace_cap)
+                    a.trace_path[trace_i * a.trace_cap + path_len] = (int32_t)w;
+                ++path_len;
+            }
+        }
+        // walk towards s (side 0), then towards t (side 1); draws 2, 3, ...
+        unsigned long long k = 2;
+        bool walk_ok = w >= 0;
+        for (int Z = 0; Z < 2 && walk_ok; ++Z) {
+            long long v = w;
+            for (;;) {
+                const unsigned int lz = ldcg(&rec[v].lvl[Z]);
+                if (lz <= 1) break;      // reached the source of side Z
+                const unsigned int target = lz - 1;
+                const long long b = G.begin(v);
+                const long long d = G.end(v) - b;
+                walk_scan += (unsigned long long)d;
+                const U64x4 x = sample_draw(a.seed, a.tag, idx, k);
+                ++k;
+                if (tid == 0) sh.next_v = -1;
+                __syncthreads();
+                if (d <= NT) {
+                    long long u = -1;
+                    unsigned long long wt = 0;
+                    if (tid < d) {
+                        u = __ldg(G.col + b + tid);
+                        if (ldcg(&rec[u].lvl[Z]) == target) wt = ldcg(&rec[u].sig[Z]);
+                    }
+                    unsigned long long total;
+                    const unsigned long long ex = block_excl_scan<NT>(wt, &total, sh);
+                    const unsigned long long r = __umul64hi(x.v[0], total);
+                    if (wt > 0 && ex <= r && r < ex + wt) sh.next_v = u;
+                    __syncthreads();
+                } else {
+                    unsigned long long part = 0;
+                    for (long long j = tid; j < d; j += NT) {
+                        const long long u = __ldg(G.col + b + j);
+                        if (ldcg(&rec[u].lvl[Z]) == target) part += ldcg(&rec[u].sig[Z]);
+                    }
+                    const unsigned long long total = block_sum<NT>(part, sh);
+                    const unsigned long long r = __umul64hi(x.v[0], total);
+                    unsigned long long carry = 0;
+                    if (tid == 0) sh.found = 0;
+                    __syncthreads();
+                    for (long long c0 = 0; c0 < d; c0 += NT) {
+                        const long long j = c0 + tid;
+                        long long u = -1;
+                        unsigned long long wt = 0;
+                        if (j < d) {
+                            u = __ldg(G.col + b + j);
+                            if (ldcg(&rec[u].lvl[Z]) == target) wt = ldcg(&rec[u].sig[Z]);
+                        }
+                        unsigned long long ctot;
+                        const unsigned long long ex = carry + block_excl_scan<NT>(wt, &ctot, sh);
+                        if (wt > 0 && ex <= r && r < ex + wt) {
+                            sh.next_v = u;
+                            sh.found = 1;
+                        }
+                        carry += ctot;
+                        __syncthreads();
+                        if (sh.found) break;
+                    }
+                }
+                v = sh.next_v;
+                if (v < 0) {
+                    // no predecessor found: an invariant is broken; record it, stop the walk
+                    if (tid == 0) sh.err |= kErrSelect;
+                    walk_ok = false;
+                    __syncthreads();
+                    break;
+                }
+                if (tid == 0 && ldcg(&rec[v].lvl[Z]) > 1) {
+                    if (a.counts) {
+                        const unsigned int old = atomicAdd(&a.counts[v], 1u);
+                        if (old == 0xffffffffu) sh.err |= kErrCounterOverflow;
+                    }
+                    if (a.trace_path && (long long)path_len < a.trace_cap)
+                        a.trace_path[trace_i * a.trace_cap + path_len] = (int32_t)v;
+                    ++path_len;
+                }
+                __syncthreads();   // sh.next_v is rewritten by the next step
+            }
+        }
+    }
+
+    // per-sample bookkeeping (thread 0)
+    if (tid == 0) {
+        ls.samples += 1;
+        ls.connected += met ? 1 : 0;
+        ls.e_scan += sh.e_scan;
+        ls.expanded += sh.expanded;
+        ls.touched += (unsigned long long)sh.qlen[0] + sh.qlen[1] + (met ? sh.meet_count : 0u);
+        ls.interior += path_len;
+        ls.walk_scan += walk_scan;
+        ls.scaled += sh.scaled ? 1 : 0;
+        if (sh.status == 3) sh.err |= kErrSigmaOverflow;
+        if (sh.err) atomicOr(&a.job->error, sh.err);
+        if (a.trace) {
+            TraceRec tr;
+            tr.s = sh.s;
+            tr.t = sh.t;
+            tr.d = met ? (long long)sh.layer[0] + sh.layer[1] : -1;
+            tr.sigma_lo = met ? sh.sig_lo : 0;
+            tr.sigma_hi = met ? sh.sig_hi : 0;
+            tr.meet_size = met ? sh.meet_count : 0;
+            tr.chosen = met ? sh.chosen : -1;
+            tr.e_scan = (long long)sh.e_scan;
+            tr.n_interior = (long long)path_len;
+            tr.scaled = sh.scaled;
+            tr.overflow = sh.status == 3;
+            a.trace[trace_i] = tr;
+        }
+    }
+
+    // clear every record this sample touched (meeting vertices sit in the
+    // other side's queue), restoring the all-zero invariant
+    __syncthreads();
+    const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+    for (int side = 0; side < 2; ++side) {
+        const unsigned int len = sh.qlen[side];
+        for (unsigned int i = tid; i < len; i += NT) {
+            const unsigned int v = qget(queue, n, side, i);
+            uint4 *p = reinterpret_cast<uint4 *>(rec + v);
+            __stcg(p, z);
+            __stcg(p + 1, z);
+        }
+    }
+    __syncthreads();
+}
+
+template <int NT, typename OffT>
+__global__ void __launch_bounds__(NT, 2048 / NT / 2) sample_kernel(SampleLaunch a)
+{
+    __shared__ Smem<NT> sh;
+    __shared__ unsigned long long s_base;
+    __shared__ unsigned long long s_count;
+    const int tid = threadIdx.x;
+    GraphRef<OffT> G{reinterpret_cast<const OffT *>(a.off), a.col, (long long)a.n};
+    SlotRec *rec = a.recs + (size_t)blockIdx.x * (size_t)a.n;
+    uint32_t *queue = a.queues + (size_t)blockIdx.x * (size_t)a.n;
+    Job *job = a.job;
+
+    if (tid == 0) {
+        const unsigned long long base = *reinterpret_cast<volatile unsigned long long *>(&job->tau);
+        const int stopped = a.use_stop ? *reinterpret_cast<volatile int *>(&job->stopped) : 0;
+        unsigned long long count = stopped ? 0ULL : (unsigned long long)a.epoch_len;
+        if (a.clip) {
+            const unsigned long long room = a.clip > base ? a.clip - base : 0ULL;
+            count = count < room ? count : room;
+        }
+        s_base = base;
+        s_count = count;
+    }
+    __syncthreads();
+    const unsigned long long base = s_base, count = s_count;
+
+    LocalStats ls = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (;;) {
+        if (tid == 0) sh.cur = atomicAdd(&job->work, 1u);
+        __syncthreads();
+        const unsigned long long i = sh.cur;
+        if (i >= count) break;
+        run_sample<NT, OffT>(a, G, rec, queue, sh, base + i, i, ls);
+    }
+
+    if (tid == 0) {
+        Counters *cs[2] = {&job->total, a.launch_ctr};
+        for (int c = 0; c < 2; ++c) {
+            if (!cs[c]) continue;
+            atomicAdd(&cs[c]->samples, ls.samples);
+            atomicAdd(&cs[c]->connected, ls.connected);
+            atomicAdd(&cs[c]->e_scan, ls.e_scan);
+            atomicAdd(&cs[c]->expanded, ls.expanded);
+            atomicAdd(&cs[c]->touched, ls.touched);
+            atomicAdd(&cs[c]->interior, ls.interior);
+            atomicAdd(&cs[c]->walk_scan, ls.walk_scan);
+            atomicAdd(&cs[c]->scaled, ls.scaled);
+        }
+        // the last CTA out publishes the new tau and re-arms the counters
+        __threadfence();
+        const unsigned int prev = atomicAdd(&job->done_ctas, 1u);
+        if (prev == gridDim.x - 1) {
+            __threadfence();
+            *reinterpret_cast<volatile unsigned long long *>(&job->tau) = base + count;
+            *reinterpret_cast<volatile unsigned int *>(&job->work) = 0u;
+            *reinterpret_cast<volatile unsigned int *>(&job->done_ctas) = 0u;
+            __threadfence();
+        }
+    }
+}
+
+template <int NT>
+cudaError_t launch_nt(const SampleLaunch &a, cudaStream_t st)
+{
+    if (a.off64)
+        sample_kernel<NT, long long><<<a.grid, NT, 0, st>>>(a);
+    else
+        sample_kernel<NT, int><<<a.grid, NT, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int NT>
+cudaError_t occupancy_nt(int off64, int *ctas)
+{
+    if (off64) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, sample_kernel<NT, long long>, NT, 0);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, sample_kernel<NT, int>, NT, 0);
+}
+
+}  // namespace
+
+cudaError_t launch_sample(const SampleLaunch &a, cudaStream_t st)
+{
+    if (a.grid <= 0) return cudaSuccess;
+    switch (a.threads) {
+    case 128: return launch_nt<128>(a, st);
+    case 256: return launch_nt<256>(a, st);
+    case 512: return launch_nt<512>(a, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t sample_occupancy(int threads, int off64, int *ctas_per_sm)
+{
+    switch (threads) {
+    case 128: return occupancy_nt<128>(off64, ctas_per_sm);
+    case 256: return occupancy_nt<256>(off64, ctas_per_sm);
+    case 512: return occupancy_nt<512>(off64, ctas_per_sm);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace kadabra

@@ -1,0 +1,271 @@
+"""GPU parity: the CUDA library (through its C ABI) against the CPU oracle.
+
+Integer results (pairs, distances, path counts, meeting sets, sampled paths,
+counters, tau, stop epoch) must match bit for bit; the stop-check maxima
+must agree to 1e-12 relative (both sides use the same IEEE operation
+sequence, so they are expected to be identical).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1910_11039_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+REL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def K():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1910_11039_gb300 import build as B
+    B.build()
+    from paper_1910_11039_gb300 import kadabra
+    kadabra.load()
+    torch.cuda.set_device(0)
+    return kadabra
+
+
+def layered_graph(m, layers=4):
+    """Complete bipartite joins between consecutive layers of m vertices:
+    pairs two layers apart meet in a whole layer (meeting sets of size m)."""
+    src, dst = [], []
+    for L in range(layers - 1):
+        a = np.arange(L * m, (L + 1) * m)
+        b = np.arange((L + 1) * m, (L + 2) * m)
+        aa, bb = np.meshgrid(a, b, indexing="ij")
+        src.append(aa.ravel())
+        dst.append(bb.ravel())
+    return I.csr_from_edges(layers * m, np.concatenate(src), np.concatenate(dst), name=f"layered{m}")
+
+
+GRAPHS = {
+    "er2000": lambda: I.config_graph("er2000"),
+    "rmat12": lambda: I.config_graph("rmat12"),
+    "rmat14": lambda: I.config_graph("rmat14"),
+    "grid64": lambda: I.config_graph("grid64"),
+    "rgg5k": lambda: I.config_graph("rgg5k"),
+    "fullgrid64": lambda: I.full_grid_graph(64, 64),    # path counts beyond 2^K: scaled layers
+    "star": lambda: I.star_graph(257),
+    "path": lambda: I.path_graph(300),
+    "edge": lambda: I.path_graph(2),
+    "layered": lambda: layered_graph(700),              # meeting sets larger than shared memory
+}
+
+
+def oracle_trace(orc, g, seed, tag, first, count):
+    ws = orc.Workspace(g)
+    out = []
+    for i in range(first, first + count):
+        path, info = ws.sample(seed, tag, i)
+        out.append((path, info))
+    return out
+
+
+def compare_trace(recs, paths, ora, cap):
+    for k, (r, (path, info)) in enumerate(zip(recs, ora)):
+        got = (r.s, r.t, r.d, r.sigma, r.meet_size, r.chosen, r.e_scan, r.n_interior, r.scaled)
+        want = (info.s, info.t, info.d, info.sigma, info.meet_size, info.chosen, info.e_scan,
+                info.n_interior, info.scaled)
+        assert got == want, (k, got, want)
+        m = min(len(path), cap)
+        assert np.array_equal(paths[k, :m], path[:m]), k
+
+
+@pytest.mark.parametrize("name", list(GRAPHS))
+def test_trace_matches_oracle(K, orc, name):
+    g = GRAPHS[name]()
+    G = K.Graph.from_inputs(g)
+    q = K.Query(G, eps=0.05, delta=0.1, seed=7, n_calib=100)
+    count = 300
+    cap = 512
+    recs, paths = q.sample_trace(1, 1000, count, path_cap=cap)
+    compare_trace(recs, paths, oracle_trace(orc, g, 7, 1, 1000, count), cap)
+    if name == "layered":
+        assert max(r.meet_size for r in recs) > 512
+    if name == "fullgrid64":
+        assert any(r.scaled for r in recs)
+
+
+@pytest.mark.parametrize("name", ["er2000", "rmat14", "grid64", "fullgrid64", "layered"])
+@pytest.mark.parametrize("rule", [0, 1])
+def test_calibration_matches_oracle(K, orc, name, rule):
+    g = GRAPHS[name]()
+    G = K.Graph.from_inputs(g)
+    q = K.Query(G, eps=0.05, delta=0.1, seed=3, n_calib=700, delta_rule=rule)
+    LL, LU, cal = q.budgets()
+    want_cal, _ = orc.run_samples(g, 3, 0, 0, 700)
+    assert np.array_equal(cal, want_cal)
+    wLL, wLU, C = orc.calibrate_L(want_cal, 700, 0.05, 0.1, rule=rule, beta=1e-3)
+    np.testing.assert_allclose(LL, wLL, rtol=REL, atol=0)
+    np.testing.assert_allclose(LU, wLU, rtol=REL, atol=0)
+    info = q.info()
+    assert info.balance_C == C
+    assert info.omega == orc.omega(0.05, 0.1, orc.vertex_diameter_bound(g))
+
+
+@pytest.mark.parametrize("name,E,epochs", [
+    ("er2000", 97, 5), ("rmat12", 500, 3), ("rmat14", 1000, 2), ("grid64", 300, 3),
+    ("rgg5k", 256, 2), ("fullgrid64", 200, 2), ("star", 64, 3), ("layered", 400, 2),
+])
+def test_epoch_counters_bit_exact(K, orc, name, E, epochs):
+    g = GRAPHS[name]()
+    G = K.Graph.from_inputs(g)
+    q = K.Query(G, eps=0.01, delta=0.1, seed=11, n_calib=100)
+    for e in range(epochs):
+        q.sample_epoch(E)
+        res = q.result(btilde=False)
+        assert res["tau"] == (e + 1) * E
+        want, st = orc.run_samples(g, 11, 1, 0, (e + 1) * E)
+        assert np.array_equal(res["counts"], want), (name, e)
+    info = q.info()
+    assert info.samples == epochs * E and info.e_scan == st.e_scan
+    assert info.connected == st.connected and info.interior == st.interior
+    assert info.scaled == st.scaled
+
+
+@pytest.mark.parametrize("name,eps,E", [
+    ("er2000", 0.05, 100), ("grid64", 0.05, 250), ("rmat14", 0.03, 500), ("rgg5k", 0.05, 300),
+    ("star", 0.05, 50), ("path", 0.05, 200),
+])
+@pytest.mark.parametrize("rule", [0, 1])
+def test_full_run_matches_oracle(K, orc, name, eps, E, rule):
+    g = GRAPHS[name]()
+    G = K.Graph.from_inputs(g)
+    q = K.Query(G, eps=eps, delta=0.1, seed=1, delta_rule=rule)
+    stopped, epochs = False, 0
+    while not stopped:
+        q.sample_epoch(E)
+        stopped, mf, mg = q.check_stop()
+        epochs += 1
+        assert epochs < 100000
+    res = q.result()
+    counts, cal, LL, LU, R = orc.kadabra(g, eps, 0.1, seed=1, epoch_len=E, delta_rule=rule)
+    assert R.stopped
+    assert res["tau"] == R.tau and res["stop_epoch"] == R.stop_epoch == epochs - 1
+    assert np.array_equal(res["counts"], counts)
+    assert math.isclose(mf, R.max_f, rel_tol=REL, abs_tol=0) and math.isclose(mg, R.max_g, rel_tol=REL, abs_tol=0)
+    np.testing.assert_array_equal(res["btilde"], counts / np.float64(R.tau))
+    if g.n <= 5000:
+        b = orc.brandes(g)
+        assert np.abs(res["btilde"] - b).max() <= eps
+
+
+def test_run_loop_matches_manual_epochs(K, orc):
+    g = GRAPHS["er2000"]()
+    G = K.Graph.from_inputs(g)
+    q = K.Query(G, eps=0.05, delta=0.1, seed=1)
+    assert q.run(100, sync_every=3)
+    res = q.result()
+    counts, cal, LL, LU, R = orc.kadabra(g, 0.05, 0.1, seed=1, epoch_len=100)
+    assert res["tau"] == R.tau and res["stop_epoch"] == R.stop_epoch
+    assert np.array_equal(res["counts"], counts)
+    # epochs enqueued after the stop take no samples
+    q.sample_epoch(100)
+    assert q.result(btilde=False)["tau"] == R.tau
+
+
+def test_reset_reproduces(K):
+    g = GRAPHS["rmat12"]()
+    G = K.Graph.from_inputs(g)
+    q = K.Query(G, eps=0.02, delta=0.1, seed=5)
+    q.run(300)
+    a = q.result()
+    q.reset()
+    q.run(300)
+    b = q.result()
+    assert a["tau"] == b["tau"] and a["stop_epoch"] == b["stop_epoch"]
+    assert np.array_equal(a["counts"], b["counts"])
+
+
+@pytest.mark.parametrize("variant", ["off64", "threads128", "threads512", "one_slot", "device_ptrs"])
+def test_launch_variants_agree(K, orc, variant):
+    import torch
+    g = GRAPHS["rmat14"]()
+    kw = {}
+    if variant == "off64":
+        G = K.Graph.from_inputs(g, offsets_64=True)
+    elif variant == "device_ptrs":
+        off = torch.from_numpy(g.offsets32()).cuda()
+        col = torch.from_numpy(g.cols).cuda()
+        G = K.Graph(g.n, off, col, device_ptrs=True)
+    else:
+        G = K.Graph.from_inputs(g)
+        kw = {"threads128": dict(threads=128), "threads512": dict(threads=512), "one_slot": dict(slots=1)}[variant]
+    q = K.Query(G, eps=0.02, delta=0.1, seed=2, n_calib=100, **kw)
+    q.sample_epoch(1500)
+    res = q.result(btilde=False)
+    want, _ = orc.run_samples(g, 2, 1, 0, 1500)
+    assert np.array_equal(res["counts"], want)
+
+
+def test_omega_clip_and_single_samples(K, orc):
+    g = GRAPHS["er2000"]()
+    G = K.Graph.from_inputs(g)
+    q = K.Query(G, eps=0.2, delta=0.1, seed=4, n_calib=50)
+    info = q.info()
+    for _ in range(3):
+        q.sample_epoch(1)
+    assert q.result(btilde=False)["tau"] == 3
+    q.sample_epoch(1 << 31)     # clipped at ceil(omega)
+    res = q.result(btilde=False)
+    assert res["tau"] == info.omega_ceil
+    want, _ = orc.run_samples(g, 4, 1, 0, info.omega_ceil)
+    assert np.array_equal(res["counts"], want)
+    stopped, mf, mg = q.check_stop()
+    assert stopped  # tau >= omega
+
+
+def test_strict_mode_reports_sigma_overflow(K):
+    g = GRAPHS["fullgrid64"]()
+    G = K.Graph.from_inputs(g)
+    q = K.Query(G, eps=0.05, delta=0.1, seed=7, n_calib=10, flags=K.STRICT_SIGMA)
+    q.sample_epoch(2000)
+    with pytest.raises(K.KadabraError) as ei:
+        q.check_stop()
+    assert ei.value.status == 4
+
+
+def test_disconnected_pairs_count_but_add_nothing(K, orc):
+    # two disjoint paths: pairs across components are taken and contribute nothing
+    a = I.path_graph(50)
+    src = np.concatenate([np.arange(49), np.arange(50, 99)])
+    dst = src + 1
+    g = I.csr_from_edges(100, src, dst)
+    G = K.Graph.from_inputs(g)
+    q = K.Query(G, eps=0.05, delta=0.1, seed=9, n_calib=100)
+    q.sample_epoch(4000)
+    res = q.result(btilde=False)
+    want, st = orc.run_samples(g, 9, 1, 0, 4000)
+    assert np.array_equal(res["counts"], want)
+    assert 0 < st.connected < 4000
+    assert q.info().connected == st.connected
+
+
+@pytest.mark.slow
+def test_rmat20_full_size_epoch_and_trace(K, orc):
+    """R-MAT scale 20 (the measured workload) at full size, in the launch
+    configuration the benchmark times: one epoch bit-exact, plus per-sample
+    records of a sampled index range."""
+    g = I.config_graph("rmat20")
+    G = K.Graph.from_inputs(g)
+    q = K.Query(G, eps=0.01, delta=0.1, seed=1)
+    E = 4096
+    q.sample_epoch(E)
+    res = q.result(btilde=False)
+    want, st = orc.run_samples(g, 1, 1, 0, E)
+    assert np.array_equal(res["counts"], want)
+    info = q.info()
+    assert info.e_scan == st.e_scan and info.connected == st.connected
+    recs, paths = q.sample_trace(1, 123456, 64, path_cap=64)
+    compare_trace(recs, paths, oracle_trace(orc, g, 1, 1, 123456, 64), 64)
+    # calibration counts and budgets at full size
+    LL, LU, cal = q.budgets()
+    want_cal, _ = orc.run_samples(g, 1, 0, 0, info.n_calib)
+    assert np.array_equal(cal, want_cal)
+    wLL, wLU, _ = orc.calibrate_L(want_cal, info.n_calib, 0.01, 0.1)
+    np.testing.assert_allclose(LL, wLL, rtol=REL, atol=0)
