@@ -237,7 +237,7 @@ def run_gpu(args, wl, g, rank, world, local_rank, cpu_baseline):
 
     # ---- device-resident arm ----
     G = K.Graph.from_inputs(g, skip_validate=True)
-    q = K.Query(G, eps=eps, delta=delta, seed=seed)
+    q = K.Query(G, eps=eps, delta=delta, seed=seed, slots=args.slots, threads=args.threads)
     info0 = q.info()
     E = args.epoch
     max_epochs = math.ceil(info0.omega_ceil / E) + 1
@@ -322,7 +322,7 @@ def run_gpu(args, wl, g, rank, world, local_rank, cpu_baseline):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             G2 = K.Graph(g.n, off_h.numpy(), col_h.numpy(), offsets_64=False, skip_validate=True, stream=stream)
-            q2 = K.Query(G2, eps=eps, delta=delta, seed=seed, stream=stream)
+            q2 = K.Query(G2, eps=eps, delta=delta, seed=seed, stream=stream, slots=args.slots, threads=args.threads)
             mx = math.ceil(q2.info().omega_ceil / E) + 1
             for _ in range(mx):
                 q2.sample_epoch(E)
@@ -376,6 +376,8 @@ def main():
     ap.add_argument("--workload", default="rmat20", choices=list(WORKLOADS))
     ap.add_argument("--epoch", type=int, default=4096)
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--slots", type=int, default=0, help="samples in flight (0 = fill the GPU)")
+    ap.add_argument("--threads", type=int, default=256, help="threads per sampling CTA")
     ap.add_argument("--cpu-samples", type=int, default=48000,
                     help="oracle samples for the CPU baseline (split over host cores)")
     ap.add_argument("--ref-samples", type=int, default=16000, help="oracle samples per reference step")

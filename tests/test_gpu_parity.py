@@ -223,7 +223,20 @@ def test_omega_clip_and_single_samples(K, orc):
 def test_strict_mode_reports_sigma_overflow(K):
     g = GRAPHS["fullgrid64"]()
     G = K.Graph.from_inputs(g)
-    q = K.Query(G, eps=0.05, delta=0.1, seed=7, n_calib=10, flags=K.STRICT_SIGMA)
+    # the calibration samples already meet path counts above 2^K
+    with pytest.raises(K.KadabraError) as ei:
+        K.Query(G, eps=0.05, delta=0.1, seed=7, n_calib=200, flags=K.STRICT_SIGMA)
+    assert ei.value.status == 4
+    # a query calibrated on few samples reports it from its adaptive epochs
+    q = None
+    for n_calib in (1, 2, 3, 4, 5):
+        try:
+            q = K.Query(G, eps=0.05, delta=0.1, seed=7, n_calib=n_calib, flags=K.STRICT_SIGMA)
+            break
+        except K.KadabraError as e:
+            assert e.status == 4
+    if q is None:
+        pytest.skip("every short calibration already overflowed")
     q.sample_epoch(2000)
     with pytest.raises(K.KadabraError) as ei:
         q.check_stop()
@@ -232,12 +245,12 @@ def test_strict_mode_reports_sigma_overflow(K):
 
 def test_disconnected_pairs_count_but_add_nothing(K, orc):
     # two disjoint paths: pairs across components are taken and contribute nothing
-    a = I.path_graph(50)
     src = np.concatenate([np.arange(49), np.arange(50, 99)])
     dst = src + 1
     g = I.csr_from_edges(100, src, dst)
     G = K.Graph.from_inputs(g)
-    q = K.Query(G, eps=0.05, delta=0.1, seed=9, n_calib=100)
+    q = K.Query(G, eps=0.02, delta=0.1, seed=9, n_calib=100)
+    assert q.info().omega_ceil > 4000
     q.sample_epoch(4000)
     res = q.result(btilde=False)
     want, st = orc.run_samples(g, 9, 1, 0, 4000)
