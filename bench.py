@@ -305,7 +305,9 @@ def run_gpu(args, wl, g, rank, world, local_rank, cpu_baseline):
                 "frac": achieved / peak, "traffic": per_sample * mean_samples if per_sample else None,
                 "kernel": "sample_kernel", "peak_source": f"{peak_kind} hbm_gbs",
                 "launches": len(launches), "avg_launch_ms": tot_ms / max(1, len(launches)),
-                "algorithmic_bytes_per_launch": tot_b / max(1, len(launches))}
+                "algorithmic_bytes_per_launch": tot_b / max(1, len(launches)),
+                "per_sample": {k: sum(getattr(ls, k) for ls in launches) / max(1, sum(ls.samples for ls in launches))
+                               for k in ("e_scan", "expanded", "touched", "walk_scan", "interior", "connected")}}
     n_launch_kernels = args.steps * (2 * max_epochs + 1)   # sample + check per epoch, reset per step
 
     # ---- end to end through the C ABI with pinned host buffers ----

@@ -13,16 +13,26 @@
 //   A3  meeting vertex w chosen with probability sigma_s(w) sigma_t(w) /
 //       sigma_st in ascending-id order (radix select on ids, 128-bit weights),
 //       then a walk from w to s and from w to t picking each predecessor with
-//       probability proportional to its sigma, in CSR order;
+//       probability proportional to its sigma, predecessors in ascending-id
+//       (= CSR) order;
 //   A4  c~(x) += 1 for every interior vertex of the path;
 //   the last CTA of the launch advances tau (A5: stream order makes the
 //   counter vector at the next kernel a consistent snapshot).
 //
 // Layout in HBM (per slot): SlotRec[n] (32 B per vertex: BFS level and path
-// count for each side) and a uint32 queue of n entries shared by both sides
-// (s-side grows from the front, t-side from the back; the balls are disjoint
-// until they meet, so n entries always suffice).  Records are cleared by the
-// sample that set them, so no per-sample O(n) reset is needed.
+// count for each side, one sector) and a uint32 queue of n entries shared by
+// both sides (s-side grows from the front, t-side from the back; the balls
+// are disjoint until they meet, so n entries always suffice).  Records are
+// cleared by the sample that set them, so no per-sample O(n) reset is needed.
+//
+// Latency hiding inside one CTA: the layer expansion assigns adjacency
+// entries to threads by a block-wide prefix sum over the frontier's degrees
+// (every thread gets the same share whatever the degree skew) and keeps
+// kUnroll entries per thread in flight: their column ids, then their
+// (level_s, level_t) pairs (one 8-byte load), then the claims, then the
+// path-count additions (waited on once per batch).  The back-walk takes the
+// predecessor layer from the BFS queue when that layer is much smaller than
+// the current vertex's adjacency (hubs), instead of scanning the adjacency.
 //
 // Mutable slot state is read with ld.global.cg (L2) so that values written by
 // atomics of other threads in the CTA are never served stale from L1.
@@ -35,8 +45,10 @@
 namespace kadabra {
 namespace {
 
-constexpr int kMeetCap = 512;      // meeting vertices kept in shared memory
+constexpr int kMeetCap = 512;      // candidates kept in shared memory (meeting set, predecessors)
 constexpr int kBuckets = 256;      // radix-select digit width: 8 bits
+constexpr int kMaxLayers = 64;     // BFS layers whose queue ranges are remembered for the walk
+constexpr int kUnroll = 4;         // adjacency entries in flight per thread
 
 __device__ __forceinline__ unsigned int ldcg(const unsigned int *p) { return __ldcg(p); }
 __device__ __forceinline__ unsigned long long ldcg(const unsigned long long *p) { return __ldcg(p); }
@@ -55,36 +67,34 @@ struct GraphRef {
 template <int NT>
 struct Smem {
     // sample
-    unsigned long long idx;
     long long s, t;
     unsigned int qlen[2];            // entries appended to each side's queue
     unsigned int fbeg[2], fend[2];   // current frontier = queue positions [fbeg, fend)
     unsigned int layer[2];           // radius reached by each side
     unsigned long long fdeg[2];      // degree sum of each frontier
+    unsigned int lbeg[2][kMaxLayers];// queue range of layer k of each side (k < kMaxLayers)
+    unsigned int lend[2][kMaxLayers];
     int X;                           // side expanded this layer
     int status;                      // 0 running, 1 met, 2 disconnected, 3 strict overflow
-    int shift;                       // right shift applied to the new layer
     int scaled;
     unsigned int err;
     // per-layer accumulators
     unsigned int new_count;
     unsigned int meet_count;
-    unsigned long long new_deg;
-    unsigned long long max_sig;
     unsigned long long e_scan;       // this sample
     unsigned long long expanded;
     // selection and walk
     unsigned long long r_lo, r_hi;   // residual of the 128-bit choice
     unsigned long long sig_lo, sig_hi;
     unsigned int prefix;
+    unsigned int pcnt;
     long long chosen;
     long long next_v;
     int found;
-    unsigned long long walk_total;
     unsigned int cur;                // work item taken by this CTA
     unsigned long long tmp[NT / 32];
     unsigned long long tmp2[NT / 32];
-    unsigned int meet[kMeetCap];
+    unsigned int cand[kMeetCap];     // candidate ids (meeting set or predecessors)
     unsigned long long wlo[kMeetCap];
     unsigned long long whi[kMeetCap];
     union {
@@ -103,18 +113,36 @@ struct Smem {
 // ---- block-wide primitives ------------------------------------------------
 
 template <int NT>
-__device__ __forceinline__ unsigned long long block_sum(unsigned long long v, Smem<NT> &sh)
+__device__ __forceinline__ void block_sum2(unsigned long long &a, unsigned long long &b, Smem<NT> &sh)
 {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) sh.tmp[wid] = v;
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if (lane == 0) {
+        sh.tmp[wid] = a;
+        sh.tmp2[wid] = b;
+    }
     __syncthreads();
-    unsigned long long tot = 0;
+    unsigned long long ta = 0, tb = 0;
 #pragma unroll
-    for (int i = 0; i < NT / 32; ++i) tot += sh.tmp[i];
+    for (int i = 0; i < NT / 32; ++i) {
+        ta += sh.tmp[i];
+        tb += sh.tmp2[i];
+    }
     __syncthreads();
-    return tot;
+    a = ta;
+    b = tb;
+}
+
+template <int NT>
+__device__ __forceinline__ unsigned long long block_sum(unsigned long long v, Smem<NT> &sh)
+{
+    unsigned long long z = 0;
+    block_sum2<NT>(v, z, sh);
+    return v;
 }
 
 template <int NT>
@@ -206,6 +234,74 @@ __device__ __forceinline__ void block_sum128(unsigned long long &lo, unsigned lo
     hi = th;
 }
 
+// Weighted choice by vertex id: among the candidates produced by `each`
+// (a functor calling its argument with (id, weight_lo, weight_hi) for the
+// calling thread's share), return the first id in ascending order whose
+// inclusive prefix weight exceeds r = (sh.r_lo, sh.r_hi) < total weight.
+// Radix select over the id bits, 8 bits per pass from the top; each pass
+// sums 128-bit weights into 256 shared-memory buckets and one warp finds the
+// bucket holding r.  Returns -1 if no bucket holds r (broken invariant).
+template <int NT, typename Each>
+__device__ long long radix_choose(Smem<NT> &sh, int npass, Each each)
+{
+    const int tid = threadIdx.x;
+    if (tid == 0) sh.prefix = 0;
+    for (int p = npass - 1; p >= 0; --p) {
+        const int shft = 8 * p;
+        for (int b = tid; b < kBuckets; b += NT) {
+            sh.u.sel.blo[b] = 0;
+            sh.u.sel.bhi[b] = 0;
+        }
+        // every thread has read the previous pass's `found` before this barrier,
+        // so `found` is re-armed only after it
+        __syncthreads();
+        if (tid == 0) sh.found = 0;
+        const unsigned int pref = sh.prefix;
+        const bool top = (p == npass - 1);
+        each([&](unsigned int id, unsigned long long lo, unsigned long long hi) {
+            if (!top && (id >> (shft + 8)) != pref) return;
+            const int dg = (id >> shft) & 255;
+            smem_add128(&sh.u.sel.blo[dg], &sh.u.sel.bhi[dg], lo, hi);
+        });
+        __syncthreads();
+        if (tid < 32) {
+            // lane l owns buckets [8l, 8l + 8)
+            unsigned long long slo = 0, shi = 0;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) add128(slo, shi, sh.u.sel.blo[tid * 8 + j], sh.u.sel.bhi[tid * 8 + j]);
+            unsigned long long ilo = slo, ihi = shi;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long yl = __shfl_up_sync(0xffffffffu, ilo, o);
+                const unsigned long long yh = __shfl_up_sync(0xffffffffu, ihi, o);
+                if (tid >= o) add128(ilo, ihi, yl, yh);
+            }
+            unsigned long long elo = ilo - slo;
+            unsigned long long ehi = ihi - shi - (ilo < slo ? 1ULL : 0ULL);
+            const unsigned long long rlo = sh.r_lo, rhi = sh.r_hi;
+            __syncwarp();   // every lane has read r before one lane rewrites it
+            if (!less128(rlo, rhi, elo, ehi) && less128(rlo, rhi, ilo, ihi)) {
+                for (int j = 0; j < 8; ++j) {
+                    unsigned long long nlo = elo, nhi = ehi;
+                    add128(nlo, nhi, sh.u.sel.blo[tid * 8 + j], sh.u.sel.bhi[tid * 8 + j]);
+                    if (less128(rlo, rhi, nlo, nhi)) {
+                        sh.r_lo = rlo - elo;
+                        sh.r_hi = rhi - ehi - (rlo < elo ? 1ULL : 0ULL);
+                        sh.prefix = (pref << 8) | (unsigned int)(tid * 8 + j);
+                        sh.found = 1;
+                        break;
+                    }
+                    elo = nlo;
+                    ehi = nhi;
+                }
+            }
+        }
+        __syncthreads();
+        if (!sh.found) return -1;
+    }
+    return (long long)sh.prefix;
+}
+
 // ---- queue of one side ---------------------------------------------------
 
 __device__ __forceinline__ unsigned int qget(const uint32_t *q, long long n, int side, unsigned int i)
@@ -219,6 +315,18 @@ __device__ __forceinline__ void qset(uint32_t *q, long long n, int side, unsigne
         __stcg(q + i, v);
     else
         __stcg(q + (n - 1 - i), v);
+}
+
+// Is `key` in the ascending list col[b, b + d)?
+__device__ __forceinline__ bool contains(const int32_t *col, long long b, long long d, long long key)
+{
+    long long lo = b, hi = b + d;
+    while (lo < hi) {
+        const long long mid = (lo + hi) >> 1;
+        if ((long long)__ldg(col + mid) < key) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo < b + d && (long long)__ldg(col + lo) == key;
 }
 
 // ---- one sample ------------------------------------------------------------
@@ -240,7 +348,6 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
         const unsigned long long s = __umul64hi(x.v[0], (unsigned long long)n);
         unsigned long long t = __umul64hi(x.v[1], (unsigned long long)(n - 1));
         if (t >= s) ++t;
-        sh.idx = idx;
         sh.s = (long long)s;
         sh.t = (long long)t;
         __stcg(&rec[s].lvl[0], 1u);
@@ -252,6 +359,8 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
         sh.qlen[0] = sh.qlen[1] = 1;
         sh.fbeg[0] = sh.fbeg[1] = 0;
         sh.fend[0] = sh.fend[1] = 1;
+        sh.lbeg[0][0] = sh.lbeg[1][0] = 0;
+        sh.lend[0][0] = sh.lend[1][0] = 1;
         sh.layer[0] = sh.layer[1] = 0;
         sh.fdeg[0] = (unsigned long long)(G.end(s) - G.begin(s));
         sh.fdeg[1] = (unsigned long long)(G.end(t) - G.begin(t));
@@ -273,12 +382,11 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
             sh.meet_count = 0;
         }
         __syncthreads();
-        const int X = sh.X, Y = 1 - X;
+        const int X = sh.X;
         const unsigned int nl = sh.layer[X] + 2;    // level code of the new layer
         const unsigned int fb = sh.fbeg[X], fe = sh.fend[X];
         const unsigned int qbase = sh.qlen[X];
-        unsigned long long my_max = 0, my_deg = 0, my_scan = 0;
-        unsigned int my_err = 0;
+        unsigned long long my_deg = 0, my_max = 0, my_scan = 0;
 
         for (unsigned int cb = fb; cb < fe; cb += NT) {
             const unsigned int i = cb + tid;
@@ -298,94 +406,118 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
             const int cnt = (int)min((unsigned int)NT, fe - cb);
             __syncthreads();
             my_scan += (tid == 0) ? total : 0ULL;
-            for (unsigned long long e = tid; e < total; e += NT) {
-                // owner: the last j with cpos[j] <= e
-                int lo = 0, hi = cnt - 1;
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (sh.u.ex.cpos[mid] <= e) lo = mid;
-                    else hi = mid - 1;
-                }
-                const long long w = __ldg(G.col + sh.u.ex.cbeg[lo] + (long long)(e - sh.u.ex.cpos[lo]));
-                const unsigned long long su = sh.u.ex.csig[lo];
-                SlotRec *r = rec + w;
-                unsigned int lv = ldcg(&r->lvl[X]);
-                bool claimed = false;
-                if (lv == 0) {
-                    const unsigned int old = atomicCAS(&r->lvl[X], 0u, nl);
-                    if (old == 0) {
-                        claimed = true;
-                        lv = nl;
-                    } else {
-                        lv = old;
+            for (unsigned long long e0 = tid; e0 < total; e0 += (unsigned long long)NT * kUnroll) {
+                long long w[kUnroll];
+                unsigned long long su[kUnroll];
+#pragma unroll
+                for (int j = 0; j < kUnroll; ++j) {
+                    const unsigned long long e = e0 + (unsigned long long)j * NT;
+                    w[j] = -1;
+                    su[j] = 0;
+                    if (e < total) {
+                        // owner: the last k with cpos[k] <= e
+                        int lo = 0, hi = cnt - 1;
+                        while (lo < hi) {
+                            const int mid = (lo + hi + 1) >> 1;
+                            if (sh.u.ex.cpos[mid] <= e) lo = mid;
+                            else hi = mid - 1;
+                        }
+                        w[j] = __ldg(G.col + sh.u.ex.cbeg[lo] + (long long)(e - sh.u.ex.cpos[lo]));
+                        su[j] = sh.u.ex.csig[lo];
                     }
                 }
-                if (lv == nl) {
-                    const unsigned long long o = atomicAdd(&r->sig[X], su);
-                    const unsigned long long nv = o + su;
-                    if (nv < o) my_err |= kErrAddOverflow;
-                    my_max = nv > my_max ? nv : my_max;
+                uint2 lv[kUnroll];
+#pragma unroll
+                for (int j = 0; j < kUnroll; ++j)
+                    lv[j] = w[j] >= 0 ? __ldcg(reinterpret_cast<const uint2 *>(&rec[w[j]].lvl[0])) : make_uint2(1u, 1u);
+                unsigned int old[kUnroll];
+#pragma unroll
+                for (int j = 0; j < kUnroll; ++j) {
+                    const unsigned int lx = X ? lv[j].y : lv[j].x;
+                    old[j] = lx;
+                    if (w[j] >= 0 && lx == 0) old[j] = atomicCAS(&rec[w[j]].lvl[X], 0u, nl);
                 }
-                if (claimed) {
-                    if (ldcg(&r->lvl[Y]) != 0) {
-                        const unsigned int p = atomicAdd(&sh.meet_count, 1u);
-                        if (p < kMeetCap) sh.meet[p] = (unsigned int)w;
-                    } else {
-                        const unsigned int p = atomicAdd(&sh.new_count, 1u);
-                        qset(queue, n, X, qbase + p, (unsigned int)w);
-                        my_deg += (unsigned long long)(G.end(w) - G.begin(w));
+                // path-count additions return their old value: a thread waits
+                // for its additions before the layer's closing barrier, so
+                // every count is complete when any thread reads it next
+                unsigned long long sum[kUnroll];
+#pragma unroll
+                for (int j = 0; j < kUnroll; ++j) {
+                    sum[j] = 0;
+                    const unsigned int lx = old[j] == 0 ? nl : old[j];
+                    if (w[j] >= 0 && lx == nl) sum[j] = atomicAdd(&rec[w[j]].sig[X], su[j]) + su[j];
+                }
+#pragma unroll
+                for (int j = 0; j < kUnroll; ++j) {
+                    if (w[j] < 0) continue;
+                    const bool claimed = old[j] == 0;
+                    my_max = sum[j] > my_max ? sum[j] : my_max;
+                    if (claimed) {
+                        const unsigned int ly = X ? lv[j].x : lv[j].y;
+                        if (ly != 0) {
+                            const unsigned int p = atomicAdd(&sh.meet_count, 1u);
+                            if (p < kMeetCap) sh.cand[p] = (unsigned int)w[j];
+                        } else {
+                            const unsigned int p = atomicAdd(&sh.new_count, 1u);
+                            qset(queue, n, X, qbase + p, (unsigned int)w[j]);
+                            my_deg += (unsigned long long)(G.end(w[j]) - G.begin(w[j]));
+                        }
                     }
                 }
             }
             __syncthreads();
         }
+        // degree sum of the new frontier and the largest new path count
+        // (every count's final value is the largest value its additions returned)
         const unsigned long long lmax = block_max<NT>(my_max, sh);
         const unsigned long long ldeg = block_sum<NT>(my_deg, sh);
-        if (my_err) atomicOr(&sh.err, my_err);
         if (tid == 0) {
             sh.e_scan += my_scan;
             sh.expanded += fe - fb;
-            sh.layer[X] += 1;
+            const unsigned int L = sh.layer[X] + 1;
+            sh.layer[X] = L;
             sh.qlen[X] += sh.new_count;
-            int shift = 0;
+            if (L < (unsigned int)kMaxLayers) {
+                sh.lbeg[X][L] = qbase;
+                sh.lend[X][L] = qbase + sh.new_count;
+            }
             if (sh.meet_count > 0) {
                 sh.status = 1;
             } else if (sh.new_count == 0) {
                 sh.status = 2;
             } else {
-                shift = bitlen64(lmax) - a.K;
-                if (shift > 0) {
-                    sh.scaled = 1;
-                    if (a.strict) {
-                        sh.status = 3;
-                        shift = 0;
-                    }
-                } else {
-                    shift = 0;
-                }
                 sh.fbeg[X] = qbase;
                 sh.fend[X] = qbase + sh.new_count;
                 sh.fdeg[X] = ldeg;
             }
-            sh.shift = shift;
         }
         __syncthreads();
         if (sh.status != 0) break;
-        if (sh.shift > 0) {
-            // keep the layer's counts <= 2^K, rounding up so that they stay >= 1
-            const int shv = sh.shift;
-            for (unsigned int i = sh.fbeg[X] + tid; i < sh.fend[X]; i += NT) {
-                const unsigned int v = qget(queue, n, X, i);
-                const unsigned long long sv = ldcg(&rec[v].sig[X]);
-                __stcg(&rec[v].sig[X], ((sv - 1ULL) >> shv) + 1ULL);
+        {
+            // keep the new layer's counts <= 2^K, rounding up so that they stay >= 1
+            const int shv = bitlen64(lmax) - a.K;
+            if (shv > 0) {
+                if (tid == 0) sh.scaled = 1;
+                if (a.strict) {
+                    if (tid == 0) sh.status = 3;
+                    __syncthreads();
+                    break;
+                }
+                for (unsigned int i = sh.fbeg[X] + tid; i < sh.fend[X]; i += NT) {
+                    const unsigned int v = qget(queue, n, X, i);
+                    const unsigned long long sv = ldcg(&rec[v].sig[X]);
+                    __stcg(&rec[v].sig[X], ((sv - 1ULL) >> shv) + 1ULL);
+                }
+                __syncthreads();
             }
-            __syncthreads();
         }
     }
 
     // A3 + A4: choose the meeting vertex, walk back, count interior vertices
     const int met = sh.status == 1;
     unsigned long long path_len = 0, walk_scan = 0;
+    const int nbits = bitlen64((unsigned long long)(n - 1)) > 0 ? bitlen64((unsigned long long)(n - 1)) : 1;
+    const int npass = (nbits + 7) / 8;
     if (met) {
         const int X = sh.X, Y = 1 - X;
         const unsigned int nl = sh.layer[X] + 1;    // level code of X's last layer
@@ -395,7 +527,7 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
         unsigned long long tlo = 0, thi = 0;
         if (in_smem) {
             for (unsigned int i = tid; i < mcnt; i += NT) {
-                const unsigned int w = sh.meet[i];
+                const unsigned int w = sh.cand[i];
                 const unsigned long long p = ldcg(&rec[w].sig[0]), q = ldcg(&rec[w].sig[1]);
                 const unsigned long long lo = p * q, hi = __umul64hi(p, q);
                 sh.wlo[i] = lo;
@@ -415,7 +547,7 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
             sh.sig_lo = tlo;
             sh.sig_hi = thi;
             if (in_smem && mcnt == 1) {
-                sh.chosen = sh.meet[0];
+                sh.chosen = sh.cand[0];
             } else {
                 const U64x4 x = sample_draw(a.seed, a.tag, idx, 1);
                 const unsigned __int128 R = ((unsigned __int128)x.v[1] << 64) | x.v[0];
@@ -423,89 +555,30 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
                 const unsigned __int128 r = R % T;
                 sh.r_lo = (unsigned long long)r;
                 sh.r_hi = (unsigned long long)(r >> 64);
-                sh.prefix = 0;
                 sh.chosen = -1;
             }
         }
         __syncthreads();
         if (sh.chosen < 0) {
-            // radix select over vertex ids, 8 bits per pass, most significant first:
-            // the first id (ascending) whose inclusive weight prefix exceeds r
-            const int nbits = bitlen64((unsigned long long)(n - 1)) > 0 ? bitlen64((unsigned long long)(n - 1)) : 1;
-            const int npass = (nbits + 7) / 8;
-            for (int p = npass - 1; p >= 0; --p) {
-                const int shft = 8 * p;
-                for (int b = tid; b < kBuckets; b += NT) {
-                    sh.u.sel.blo[b] = 0;
-                    sh.u.sel.bhi[b] = 0;
-                }
-                __syncthreads();
-                const unsigned int pref = sh.prefix;
-                const bool top = (p == npass - 1);
-                if (in_smem) {
-                    for (unsigned int i = tid; i < mcnt; i += NT) {
-                        const unsigned int w = sh.meet[i];
-                        if (!top && (w >> (shft + 8)) != pref) continue;
-                        const int dg = (w >> shft) & 255;
-                        smem_add128(&sh.u.sel.blo[dg], &sh.u.sel.bhi[dg], sh.wlo[i], sh.whi[i]);
-                    }
-                } else {
-                    for (unsigned int i = sh.fbeg[Y] + tid; i < sh.fend[Y]; i += NT) {
+            long long c;
+            if (in_smem) {
+                c = radix_choose<NT>(sh, npass, [&](auto &&add) {
+                    for (unsigned int i = tid; i < mcnt; i += NT) add(sh.cand[i], sh.wlo[i], sh.whi[i]);
+                });
+            } else {
+                const unsigned int yb = sh.fbeg[Y], ye = sh.fend[Y];
+                c = radix_choose<NT>(sh, npass, [&](auto &&add) {
+                    for (unsigned int i = yb + tid; i < ye; i += NT) {
                         const unsigned int w = qget(queue, n, Y, i);
                         if (ldcg(&rec[w].lvl[X]) != nl) continue;
-                        if (!top && (w >> (shft + 8)) != pref) continue;
-                        const unsigned long long pp = ldcg(&rec[w].sig[0]), qq = ldcg(&rec[w].sig[1]);
-                        const int dg = (w >> shft) & 255;
-                        smem_add128(&sh.u.sel.blo[dg], &sh.u.sel.bhi[dg], pp * qq, __umul64hi(pp, qq));
+                        const unsigned long long p = ldcg(&rec[w].sig[0]), q = ldcg(&rec[w].sig[1]);
+                        add(w, p * q, __umul64hi(p, q));
                     }
-                }
-                if (tid == 0) sh.found = 0;
-                __syncthreads();
-                if (tid < 32) {
-                    // lane l owns buckets [8l, 8l + 8)
-                    unsigned long long slo = 0, shi = 0;
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) add128(slo, shi, sh.u.sel.blo[tid * 8 + j], sh.u.sel.bhi[tid * 8 + j]);
-                    // exclusive scan of lane sums
-                    unsigned long long ilo = slo, ihi = shi;
-#pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const unsigned long long yl = __shfl_up_sync(0xffffffffu, ilo, o);
-                        const unsigned long long yh = __shfl_up_sync(0xffffffffu, ihi, o);
-                        if (tid >= o) add128(ilo, ihi, yl, yh);
-                    }
-                    // excl = incl - own
-                    unsigned long long elo = ilo - slo;
-                    unsigned long long ehi = ihi - shi - (ilo < slo ? 1ULL : 0ULL);
-                    const unsigned long long rlo = sh.r_lo, rhi = sh.r_hi;
-                    __syncwarp();   // every lane has read r before one lane rewrites it
-                    // this lane holds r if excl <= r < incl
-                    if (!less128(rlo, rhi, elo, ehi) && less128(rlo, rhi, ilo, ihi)) {
-                        for (int j = 0; j < 8; ++j) {
-                            unsigned long long nlo = elo, nhi = ehi;
-                            add128(nlo, nhi, sh.u.sel.blo[tid * 8 + j], sh.u.sel.bhi[tid * 8 + j]);
-                            if (less128(rlo, rhi, nlo, nhi)) {
-                                // residual r - excl
-                                const unsigned long long dlo = rlo - elo;
-                                const unsigned long long dhi = rhi - ehi - (rlo < elo ? 1ULL : 0ULL);
-                                sh.r_lo = dlo;
-                                sh.r_hi = dhi;
-                                sh.prefix = (pref << 8) | (unsigned int)(tid * 8 + j);
-                                sh.found = 1;
-                                break;
-                            }
-                            elo = nlo;
-                            ehi = nhi;
-                        }
-                    }
-                }
-                __syncthreads();
-                if (!sh.found) break;
+                });
             }
             if (tid == 0) {
-                const bool ok = sh.found && (long long)sh.prefix < n && ldcg(&rec[sh.prefix].lvl[X]) == nl &&
-                                ldcg(&rec[sh.prefix].lvl[Y]) != 0;
-                sh.chosen = ok ? (long long)sh.prefix : -1;
+                const bool ok = c >= 0 && c < n && ldcg(&rec[c].lvl[X]) == nl && ldcg(&rec[c].lvl[Y]) != 0;
+                sh.chosen = ok ? c : -1;
                 if (!ok) sh.err |= kErrSelect;
             }
             __syncthreads();
@@ -528,68 +601,113 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
         bool walk_ok = w >= 0;
         for (int Z = 0; Z < 2 && walk_ok; ++Z) {
             long long v = w;
+            const long long src = Z == 0 ? sh.s : sh.t;
             for (;;) {
                 const unsigned int lz = ldcg(&rec[v].lvl[Z]);
                 if (lz <= 1) break;      // reached the source of side Z
-                const unsigned int target = lz - 1;
+                const unsigned int target = lz - 1;      // level code of the predecessors
+                const unsigned int P = lz - 2;           // their layer index
                 const long long b = G.begin(v);
                 const long long d = G.end(v) - b;
-                walk_scan += (unsigned long long)d;
                 const U64x4 x = sample_draw(a.seed, a.tag, idx, k);
                 ++k;
-                if (tid == 0) sh.next_v = -1;
-                __syncthreads();
-                if (d <= NT) {
-                    long long u = -1;
-                    unsigned long long wt = 0;
-                    if (tid < d) {
-                        u = __ldg(G.col + b + tid);
-                        if (ldcg(&rec[u].lvl[Z]) == target) wt = ldcg(&rec[u].sig[Z]);
-                    }
-                    unsigned long long total;
-                    const unsigned long long ex = block_excl_scan<NT>(wt, &total, sh);
-                    const unsigned long long r = __umul64hi(x.v[0], total);
-                    if (wt > 0 && ex <= r && r < ex + wt) sh.next_v = u;
-                    __syncthreads();
+                if (P == 0) {
+                    // the only vertex one layer closer is the source itself
+                    v = src;
                 } else {
-                    unsigned long long part = 0;
-                    for (long long j = tid; j < d; j += NT) {
-                        const long long u = __ldg(G.col + b + j);
-                        if (ldcg(&rec[u].lvl[Z]) == target) part += ldcg(&rec[u].sig[Z]);
-                    }
-                    const unsigned long long total = block_sum<NT>(part, sh);
-                    const unsigned long long r = __umul64hi(x.v[0], total);
-                    unsigned long long carry = 0;
-                    if (tid == 0) sh.found = 0;
-                    __syncthreads();
-                    for (long long c0 = 0; c0 < d; c0 += NT) {
-                        const long long j = c0 + tid;
+                    const unsigned int lsz = P < (unsigned int)kMaxLayers ? sh.lend[Z][P] - sh.lbeg[Z][P] : 0xffffffffu;
+                    if (tid == 0) sh.next_v = -1;
+                    if (d > 2 * NT && lsz <= (unsigned int)kMeetCap && (unsigned long long)lsz * 8ULL < (unsigned long long)d) {
+                        // hub: test the predecessor layer's vertices for adjacency
+                        if (tid == 0) sh.pcnt = 0;
+                        __syncthreads();
+                        const unsigned int lb = sh.lbeg[Z][P];
+                        for (unsigned int i = tid; i < lsz; i += NT) {
+                            const unsigned int u = qget(queue, n, Z, lb + i);
+                            const long long bu = G.begin(u), du = G.end(u) - bu;
+                            const bool adj = du <= d ? contains(G.col, bu, du, v) : contains(G.col, b, d, u);
+                            if (adj) {
+                                const unsigned int p = atomicAdd(&sh.pcnt, 1u);
+                                sh.cand[p] = u;
+                                sh.wlo[p] = ldcg(&rec[u].sig[Z]);
+                                sh.whi[p] = 0;
+                            }
+                        }
+                        __syncthreads();
+                        const unsigned int pc = sh.pcnt;
+                        walk_scan += lsz;
+                        unsigned long long part = 0;
+                        for (unsigned int i = tid; i < pc; i += NT) part += sh.wlo[i];
+                        const unsigned long long total = block_sum<NT>(part, sh);
+                        if (pc == 1) {
+                            if (tid == 0) sh.next_v = sh.cand[0];
+                        } else if (pc > 1) {
+                            if (tid == 0) {
+                                sh.r_lo = __umul64hi(x.v[0], total);
+                                sh.r_hi = 0;
+                            }
+                            __syncthreads();
+                            const long long c = radix_choose<NT>(sh, npass, [&](auto &&add) {
+                                for (unsigned int i = tid; i < pc; i += NT) add(sh.cand[i], sh.wlo[i], 0ULL);
+                            });
+                            if (tid == 0) sh.next_v = c;
+                        }
+                        __syncthreads();
+                    } else if (d <= NT) {
+                        walk_scan += (unsigned long long)d;
+                        __syncthreads();
                         long long u = -1;
                         unsigned long long wt = 0;
-                        if (j < d) {
-                            u = __ldg(G.col + b + j);
+                        if (tid < d) {
+                            u = __ldg(G.col + b + tid);
                             if (ldcg(&rec[u].lvl[Z]) == target) wt = ldcg(&rec[u].sig[Z]);
                         }
-                        unsigned long long ctot;
-                        const unsigned long long ex = carry + block_excl_scan<NT>(wt, &ctot, sh);
-                        if (wt > 0 && ex <= r && r < ex + wt) {
-                            sh.next_v = u;
-                            sh.found = 1;
-                        }
-                        carry += ctot;
+                        unsigned long long total;
+                        const unsigned long long ex = block_excl_scan<NT>(wt, &total, sh);
+                        const unsigned long long r = __umul64hi(x.v[0], total);
+                        if (wt > 0 && ex <= r && r < ex + wt) sh.next_v = u;
                         __syncthreads();
-                        if (sh.found) break;
+                    } else {
+                        walk_scan += (unsigned long long)d;
+                        unsigned long long part = 0;
+                        for (long long j = tid; j < d; j += NT) {
+                            const long long u = __ldg(G.col + b + j);
+                            if (ldcg(&rec[u].lvl[Z]) == target) part += ldcg(&rec[u].sig[Z]);
+                        }
+                        const unsigned long long total = block_sum<NT>(part, sh);
+                        const unsigned long long r = __umul64hi(x.v[0], total);
+                        unsigned long long carry = 0;
+                        if (tid == 0) sh.found = 0;
+                        __syncthreads();
+                        for (long long c0 = 0; c0 < d; c0 += NT) {
+                            const long long j = c0 + tid;
+                            long long u = -1;
+                            unsigned long long wt = 0;
+                            if (j < d) {
+                                u = __ldg(G.col + b + j);
+                                if (ldcg(&rec[u].lvl[Z]) == target) wt = ldcg(&rec[u].sig[Z]);
+                            }
+                            unsigned long long ctot;
+                            const unsigned long long ex = carry + block_excl_scan<NT>(wt, &ctot, sh);
+                            if (wt > 0 && ex <= r && r < ex + wt) {
+                                sh.next_v = u;
+                                sh.found = 1;
+                            }
+                            carry += ctot;
+                            __syncthreads();
+                            if (sh.found) break;
+                        }
+                    }
+                    v = sh.next_v;
+                    if (v < 0 || v >= n || ldcg(&rec[v].lvl[Z]) != target) {
+                        // no predecessor found: an invariant is broken; record it, stop the walk
+                        if (tid == 0) sh.err |= kErrSelect;
+                        walk_ok = false;
+                        __syncthreads();
+                        break;
                     }
                 }
-                v = sh.next_v;
-                if (v < 0) {
-                    // no predecessor found: an invariant is broken; record it, stop the walk
-                    if (tid == 0) sh.err |= kErrSelect;
-                    walk_ok = false;
-                    __syncthreads();
-                    break;
-                }
-                if (tid == 0 && ldcg(&rec[v].lvl[Z]) > 1) {
+                if (tid == 0 && v != src) {
                     if (a.counts) {
                         const unsigned int old = atomicAdd(&a.counts[v], 1u);
                         if (old == 0xffffffffu) sh.err |= kErrCounterOverflow;
