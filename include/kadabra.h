@@ -43,7 +43,8 @@ typedef enum kadabra_status {
     KADABRA_ERR_COUNTER_OVERFLOW = 5, /* a 32-bit counter would wrap              */
     KADABRA_ERR_TIMEOUT = 6,          /* a bounded device wait gave up            */
     KADABRA_ERR_STATE = 7,            /* call out of order (e.g. result before run)*/
-    KADABRA_ERR_NO_DEVICE = 8         /* no CUDA device / library built without it */
+    KADABRA_ERR_NO_DEVICE = 8,        /* no CUDA device / library built without it */
+    KADABRA_ERR_DEPTH = 9             /* a BFS side needed more than 65533 layers  */
 } kadabra_status;
 
 typedef struct kadabra_graph kadabra_graph;
@@ -74,7 +75,7 @@ typedef struct kadabra_params {
     uint32_t flags;           /* KADABRA_STRICT_SIGMA                                       */
     double beta;              /* balanced rule floor weight (default 1e-3)                 */
     int32_t slots;            /* samples in flight (one CTA each); 0 = fill the GPU        */
-    int32_t threads;          /* threads per sampling CTA: 128, 256 or 512; 0 = 256        */
+    int32_t threads;          /* threads per sampling CTA: 128, 256, 512, 1024; 0 = 256    */
     double scratch_fraction;  /* max share of free device memory for scratch; 0 = 0.6      */
 } kadabra_params;
 
@@ -116,7 +117,10 @@ typedef struct kadabra_trace_rec {
     int64_t e_scan;             /* adjacency entries scanned by the BFS                    */
     int64_t n_interior;         /* interior vertices of the sampled path                   */
     int32_t scaled;             /* 1 if a layer's path counts were scaled                  */
-    int32_t overflow;           /* 1 if strict mode rejected the sample                    */
+    int32_t overflow;           /* 1 strict mode rejected the sample, 2 too many layers    */
+    int64_t ns;                 /* device time spent on the sample (ns, global timer)      */
+    int64_t phase_ns[4];        /* of which: BFS, meeting-vertex choice, back-walk, and
+                                   (not included in ns) clearing the touched records       */
 } kadabra_trace_rec;
 
 /* ---- errors and version ------------------------------------------------ */
@@ -147,9 +151,12 @@ kadabra_status kadabra_validate_csr(int64_t n, int64_t nnz, const void *offsets,
  * Writes NaN and returns KADABRA_ERR_INVALID_ARG for eps or delta outside (0,1). */
 kadabra_status kadabra_omega(double eps, double delta, int64_t vertex_diameter, double *omega);
 
-/* K = min(63 - bitlen(max_degree), 63 - bitlen(n)): the largest per-side path
- * count kept exact; above 2^K a BFS layer's counts are shifted right (rounding
- * up) so that all sums stay exact in 64/128-bit integers. */
+/* K = min(47 - bitlen(max_degree), 63 - bitlen(n)): per-side path counts up
+ * to 2^K are exact; a BFS layer whose largest count exceeds 2^K has all its
+ * counts shifted right by the excess (rounding up, so they stay >= 1), which
+ * keeps every per-side count below 2^47 and every meeting-set weight sum
+ * within 128 bits.  The paper does not say how counts beyond a machine word
+ * are handled; this is the library's reading. */
 int kadabra_sigma_bits(int64_t n, int64_t max_degree);
 
 /* ---- graph ------------------------------------------------------------- */

@@ -113,6 +113,7 @@ extern "C" const char *kadabra_status_string(kadabra_status s)
     case KADABRA_ERR_TIMEOUT: return "KADABRA_ERR_TIMEOUT";
     case KADABRA_ERR_STATE: return "KADABRA_ERR_STATE";
     case KADABRA_ERR_NO_DEVICE: return "KADABRA_ERR_NO_DEVICE";
+    case KADABRA_ERR_DEPTH: return "KADABRA_ERR_DEPTH";
     }
     return "KADABRA_ERR_UNKNOWN";
 }
@@ -201,7 +202,7 @@ extern "C" kadabra_status kadabra_omega(double eps, double delta, int64_t vertex
 
 extern "C" int kadabra_sigma_bits(int64_t n, int64_t max_degree)
 {
-    const int a = 63 - bitlen64((uint64_t)max_degree);
+    const int a = 47 - bitlen64((uint64_t)max_degree);
     const int b = 63 - bitlen64((uint64_t)n);
     return a < b ? a : b;
 }
@@ -391,7 +392,7 @@ extern "C" kadabra_status kadabra_graph_info(const kadabra_graph *g, int64_t *n,
     return KADABRA_OK;
 }
 
-// Sampling scratch: slots * n * (32 B record + 4 B queue entry).
+// Sampling scratch: slots * n * (16 B record + 4 B queue entry).
 static kadabra_status ensure_workspace(kadabra_graph *g, int want_slots, int threads, double fraction)
 {
     int dev = 0, sms = 0, per_sm = 0;
@@ -455,6 +456,8 @@ static kadabra_status device_error_status(const Job &j)
     if (j.error & kadabra::kErrSigmaOverflow)
         return fail(KADABRA_ERR_SIGMA_OVERFLOW, "strict mode: a per-side path count exceeded 2^K");
     if (j.error & kadabra::kErrCounterOverflow) return fail(KADABRA_ERR_COUNTER_OVERFLOW, "a 32-bit counter wrapped");
+    if (j.error & kadabra::kErrDepth)
+        return fail(KADABRA_ERR_DEPTH, "a BFS side needed more than 65533 layers (16-bit levels)");
     if (j.error & (kadabra::kErrAddOverflow | kadabra::kErrSelect))
         return fail(KADABRA_ERR_CUDA, "internal sampling invariant violated (error bits " + std::to_string(j.error) + ")");
     return KADABRA_OK;
@@ -498,8 +501,8 @@ extern "C" kadabra_status kadabra_calibrate(kadabra_graph *g, const kadabra_para
         return fail(KADABRA_ERR_INVALID_ARG, "unknown delta_rule");
     if (!(p.beta > 0.0 && p.beta < 1.0)) return fail(KADABRA_ERR_INVALID_ARG, "beta must lie in (0, 1)");
     if (p.threads == 0) p.threads = 256;
-    if (p.threads != 128 && p.threads != 256 && p.threads != 512)
-        return fail(KADABRA_ERR_INVALID_ARG, "threads must be 128, 256 or 512");
+    if (p.threads != 128 && p.threads != 256 && p.threads != 512 && p.threads != 1024)
+        return fail(KADABRA_ERR_INVALID_ARG, "threads must be 128, 256, 512 or 1024");
     if (g->n < 2) return fail(KADABRA_ERR_INVALID_ARG, "sampling pairs needs n >= 2");
     cudaStream_t st = as_stream(cuda_stream);
 
@@ -825,7 +828,7 @@ extern "C" kadabra_status kadabra_sample_trace(kadabra_query *q, int tag, uint64
     cudaFree(d_tr);
     cudaFree(d_path);
     if (e != cudaSuccess) return cuda_fail(e, "trace run");
-    return (j.error & ~kadabra::kErrSigmaOverflow) ? device_error_status(j) : KADABRA_OK;
+    return (j.error & ~(kadabra::kErrSigmaOverflow | kadabra::kErrDepth)) ? device_error_status(j) : KADABRA_OK;
 }
 
 extern "C" kadabra_status kadabra_launch_log(kadabra_query *q, int64_t max_entries, kadabra_launch_stats *out,

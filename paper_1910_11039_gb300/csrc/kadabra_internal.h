@@ -6,18 +6,19 @@
 
 namespace kadabra {
 
-// Per-vertex sampling state of one in-flight sample (one "slot"), 32 bytes so
-// that every probe of a vertex touches a single 32-byte sector.
-//   lvl[side] = BFS distance + 1 from that side's source, 0 = not reached
-//   sig[side] = number of shortest paths from that side's source
+// Per-vertex sampling state of one in-flight sample (one "slot"): one 64-bit
+// word per BFS side, word = sigma << 16 | level, where
+//   level = BFS distance + 1 from that side's source (0 = not reached; at most
+//           0xffff, so a side explores at most 65533 layers),
+//   sigma = number of shortest paths from that side's source (< 2^47 by the
+//           choice of K, so additions of sigma << 16 never carry out).
+// A first discovery claims the vertex and sets its count with one CAS.
 // Invariant between samples: every record of a slot is all-zero (the sample
 // that touched a record clears it before the slot takes its next sample).
-struct alignas(32) SlotRec {
-    uint32_t lvl[2];
-    uint32_t pad[2];
-    unsigned long long sig[2];
+struct alignas(16) SlotRec {
+    unsigned long long w[2];
 };
-static_assert(sizeof(SlotRec) == 32, "SlotRec must be one sector");
+static_assert(sizeof(SlotRec) == 16, "SlotRec is two 64-bit words");
 
 // Counters a launch accumulates (one atomicAdd per CTA at exit).
 struct Counters {
@@ -48,6 +49,7 @@ enum : unsigned int {
     kErrAddOverflow = 2u,      // a 64-bit path-count add wrapped (never expected)
     kErrCounterOverflow = 4u,  // a 32-bit c~ counter wrapped
     kErrSelect = 8u,           // weighted choice found no element (never expected)
+    kErrDepth = 16u,           // a BFS side would exceed 65533 layers (16-bit levels)
 };
 
 // Per-sample trace record (mirrors kadabra_trace_rec).
@@ -56,6 +58,8 @@ struct TraceRec {
     unsigned long long sigma_lo, sigma_hi;
     long long meet_size, chosen, e_scan, n_interior;
     int scaled, overflow;
+    long long ns;              // device time of the sample (global timer), cleanup excluded
+    long long phase_ns[4];     // BFS, meeting-vertex choice, back-walk, record clearing
 };
 
 struct SampleLaunch {

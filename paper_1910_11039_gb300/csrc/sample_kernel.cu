@@ -19,8 +19,8 @@
 //   the last CTA of the launch advances tau (A5: stream order makes the
 //   counter vector at the next kernel a consistent snapshot).
 //
-// Layout in HBM (per slot): SlotRec[n] (32 B per vertex: BFS level and path
-// count for each side, one sector) and a uint32 queue of n entries shared by
+// Layout in HBM (per slot): SlotRec[n] (16 B per vertex: for each side one
+// word holding the path count and the BFS level) and a uint32 queue of n entries shared by
 // both sides (s-side grows from the front, t-side from the back; the balls
 // are disjoint until they meet, so n entries always suffice).  Records are
 // cleared by the sample that set them, so no per-sample O(n) reset is needed.
@@ -36,6 +36,11 @@
 //
 // Mutable slot state is read with ld.global.cg (L2) so that values written by
 // atomics of other threads in the CTA are never served stale from L1.
+//
+// Scratch footprint matters more than it seems: the probes of all in-flight
+// samples land at random in slots * n * 16 bytes, and the per-edge cost under
+// full load grows with that footprint (translation and DRAM row misses), so
+// the record is kept at 16 bytes and the slot count is bounded.
 
 #include <cstdint>
 
@@ -48,12 +53,38 @@ namespace {
 constexpr int kMeetCap = 512;      // candidates kept in shared memory (meeting set, predecessors)
 constexpr int kBuckets = 256;      // radix-select digit width: 8 bits
 constexpr int kMaxLayers = 64;     // BFS layers whose queue ranges are remembered for the walk
-constexpr int kUnroll = 4;         // adjacency entries in flight per thread
+#ifndef KADABRA_UNROLL
+#define KADABRA_UNROLL 2
+#endif
+constexpr int kUnroll = KADABRA_UNROLL;   // adjacency entries in flight per thread
+constexpr unsigned int kNone = 0xffffffffu;
 
 __device__ __forceinline__ unsigned int ldcg(const unsigned int *p) { return __ldcg(p); }
 __device__ __forceinline__ unsigned long long ldcg(const unsigned long long *p) { return __ldcg(p); }
 
 __device__ __forceinline__ int bitlen64(unsigned long long x) { return 64 - __clzll(x); }
+
+// record words: sigma << 16 | level
+__device__ __forceinline__ unsigned int lvl_of(unsigned long long w) { return (unsigned int)(w & 0xffffULL); }
+__device__ __forceinline__ unsigned long long sig_of(unsigned long long w) { return w >> 16; }
+__device__ __forceinline__ unsigned long long pack(unsigned int lvl, unsigned long long sig)
+{
+    return (sig << 16) | (unsigned long long)lvl;
+}
+// both sides' words of a record, one 16-byte load from L2
+__device__ __forceinline__ void load_rec(const SlotRec *r, unsigned long long &w0, unsigned long long &w1)
+{
+    const uint4 v = __ldcg(reinterpret_cast<const uint4 *>(r));
+    w0 = (unsigned long long)v.x | ((unsigned long long)v.y << 32);
+    w1 = (unsigned long long)v.z | ((unsigned long long)v.w << 32);
+}
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 template <typename OffT>
 struct GraphRef {
@@ -75,7 +106,7 @@ struct Smem {
     unsigned int lbeg[2][kMaxLayers];// queue range of layer k of each side (k < kMaxLayers)
     unsigned int lend[2][kMaxLayers];
     int X;                           // side expanded this layer
-    int status;                      // 0 running, 1 met, 2 disconnected, 3 strict overflow
+    int status;                      // 0 running, 1 met, 2 disconnected, 3 strict overflow, 4 too deep
     int scaled;
     unsigned int err;
     // per-layer accumulators
@@ -341,19 +372,19 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
 {
     const int tid = threadIdx.x;
     const long long n = G.n;
+    unsigned long long t_start = 0, t_bfs = 0, t_sel = 0, t_walk = 0;
 
     // A1: pair (draw 0)
     if (tid == 0) {
+        if (a.trace) t_start = global_ns();
         const U64x4 x = sample_draw(a.seed, a.tag, idx, 0);
         const unsigned long long s = __umul64hi(x.v[0], (unsigned long long)n);
         unsigned long long t = __umul64hi(x.v[1], (unsigned long long)(n - 1));
         if (t >= s) ++t;
         sh.s = (long long)s;
         sh.t = (long long)t;
-        __stcg(&rec[s].lvl[0], 1u);
-        __stcg(&rec[s].sig[0], 1ULL);
-        __stcg(&rec[t].lvl[1], 1u);
-        __stcg(&rec[t].sig[1], 1ULL);
+        __stcg(&rec[s].w[0], pack(1u, 1ULL));
+        __stcg(&rec[t].w[1], pack(1u, 1ULL));
         qset(queue, n, 0, 0, (unsigned int)s);
         qset(queue, n, 1, 0, (unsigned int)t);
         sh.qlen[0] = sh.qlen[1] = 1;
@@ -377,16 +408,20 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
     // A2: balanced bidirectional BFS, one whole layer per step
     for (;;) {
         if (tid == 0) {
-            sh.X = (sh.fdeg[0] <= sh.fdeg[1]) ? 0 : 1;
+            const int Xs = (sh.fdeg[0] <= sh.fdeg[1]) ? 0 : 1;
+            sh.X = Xs;
             sh.new_count = 0;
             sh.meet_count = 0;
+            if (sh.layer[Xs] + 2u > 0xffffu) sh.status = 4;   // levels are 16-bit
         }
         __syncthreads();
+        if (sh.status != 0) break;
         const int X = sh.X;
         const unsigned int nl = sh.layer[X] + 2;    // level code of the new layer
         const unsigned int fb = sh.fbeg[X], fe = sh.fend[X];
         const unsigned int qbase = sh.qlen[X];
-        unsigned long long my_deg = 0, my_max = 0, my_scan = 0;
+        unsigned long long my_max = 0, my_scan = 0;
+        const int lane = tid & 31;
 
         for (unsigned int cb = fb; cb < fe; cb += NT) {
             const unsigned int i = cb + tid;
@@ -396,7 +431,7 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
                 const unsigned int u = qget(queue, n, X, i);
                 b = G.begin(u);
                 d = (unsigned long long)(G.end(u) - b);
-                sg = ldcg(&rec[u].sig[X]);
+                sg = sig_of(ldcg(&rec[u].w[X]));
             }
             unsigned long long total;
             const unsigned long long excl = block_excl_scan<NT>(d, &total, sh);
@@ -406,70 +441,105 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
             const int cnt = (int)min((unsigned int)NT, fe - cb);
             __syncthreads();
             my_scan += (tid == 0) ? total : 0ULL;
-            for (unsigned long long e0 = tid; e0 < total; e0 += (unsigned long long)NT * kUnroll) {
-                long long w[kUnroll];
-                unsigned long long su[kUnroll];
+            // warp-uniform batches: lane l of warp k handles entries
+            // e0 + l + j*NT, j < kUnroll, with e0 = 32k + (multiple of NT*kUnroll);
+            // each phase issues all kUnroll memory operations before waiting
+            const unsigned long long wbase = (unsigned long long)(tid & ~31);
+            for (unsigned long long e0 = wbase; e0 < total; e0 += (unsigned long long)NT * kUnroll) {
+                unsigned int w[kUnroll];
+                int own[kUnroll];
 #pragma unroll
                 for (int j = 0; j < kUnroll; ++j) {
-                    const unsigned long long e = e0 + (unsigned long long)j * NT;
-                    w[j] = -1;
-                    su[j] = 0;
+                    const unsigned long long e = e0 + (unsigned long long)lane + (unsigned long long)j * NT;
+                    w[j] = kNone;
+                    own[j] = 0;
                     if (e < total) {
                         // owner: the last k with cpos[k] <= e
-                        int lo = 0, hi = cnt - 1;
+                        int lo = j > 0 ? own[j - 1] : 0, hi = cnt - 1;
                         while (lo < hi) {
                             const int mid = (lo + hi + 1) >> 1;
                             if (sh.u.ex.cpos[mid] <= e) lo = mid;
                             else hi = mid - 1;
                         }
-                        w[j] = __ldg(G.col + sh.u.ex.cbeg[lo] + (long long)(e - sh.u.ex.cpos[lo]));
-                        su[j] = sh.u.ex.csig[lo];
+                        own[j] = lo;
+                        w[j] = (unsigned int)__ldg(G.col + sh.u.ex.cbeg[lo] + (long long)(e - sh.u.ex.cpos[lo]));
                     }
                 }
-                uint2 lv[kUnroll];
-#pragma unroll
-                for (int j = 0; j < kUnroll; ++j)
-                    lv[j] = w[j] >= 0 ? __ldcg(reinterpret_cast<const uint2 *>(&rec[w[j]].lvl[0])) : make_uint2(1u, 1u);
-                unsigned int old[kUnroll];
+                // phase 2: (level_s, level_t) of every target, one 8-byte load each
+                unsigned int lx[kUnroll];
+                unsigned int ymask = 0;
 #pragma unroll
                 for (int j = 0; j < kUnroll; ++j) {
-                    const unsigned int lx = X ? lv[j].y : lv[j].x;
-                    old[j] = lx;
-                    if (w[j] >= 0 && lx == 0) old[j] = atomicCAS(&rec[w[j]].lvl[X], 0u, nl);
+                    lx[j] = 1u;
+                    if (w[j] != kNone) {
+                        unsigned long long w0, w1;
+                        load_rec(rec + w[j], w0, w1);
+                        lx[j] = lvl_of(X ? w1 : w0);
+                        ymask |= (lvl_of(X ? w0 : w1) != 0 ? 1u : 0u) << j;
+                    }
                 }
-                // path-count additions return their old value: a thread waits
-                // for its additions before the layer's closing barrier, so
-                // every count is complete when any thread reads it next
-                unsigned long long sum[kUnroll];
+                // phase 3: claim unseen targets for the new layer; the claim
+                // stores the level and the first path-count contribution at once
+                unsigned int cmask = 0;
 #pragma unroll
                 for (int j = 0; j < kUnroll; ++j) {
-                    sum[j] = 0;
-                    const unsigned int lx = old[j] == 0 ? nl : old[j];
-                    if (w[j] >= 0 && lx == nl) sum[j] = atomicAdd(&rec[w[j]].sig[X], su[j]) + su[j];
-                }
-#pragma unroll
-                for (int j = 0; j < kUnroll; ++j) {
-                    if (w[j] < 0) continue;
-                    const bool claimed = old[j] == 0;
-                    my_max = sum[j] > my_max ? sum[j] : my_max;
-                    if (claimed) {
-                        const unsigned int ly = X ? lv[j].x : lv[j].y;
-                        if (ly != 0) {
-                            const unsigned int p = atomicAdd(&sh.meet_count, 1u);
-                            if (p < kMeetCap) sh.cand[p] = (unsigned int)w[j];
-                        } else {
-                            const unsigned int p = atomicAdd(&sh.new_count, 1u);
-                            qset(queue, n, X, qbase + p, (unsigned int)w[j]);
-                            my_deg += (unsigned long long)(G.end(w[j]) - G.begin(w[j]));
+                    if (w[j] != kNone && lx[j] == 0) {
+                        const unsigned long long su = sh.u.ex.csig[own[j]];
+                        const unsigned long long old = atomicCAS(&rec[w[j]].w[X], 0ULL, pack(nl, su));
+                        if (old == 0) {
+                            cmask |= 1u << j;
+                            my_max = su > my_max ? su : my_max;
                         }
+                        lx[j] = old == 0 ? nl : lvl_of(old);
+                    }
+                }
+                // phase 4: path counts of targets in the new layer; the additions
+                // return their old value, so a thread has waited for all of them
+                // before the layer's closing barrier and every count is complete
+                // when any thread reads it next
+#pragma unroll
+                for (int j = 0; j < kUnroll; ++j) {
+                    if (w[j] != kNone && lx[j] == nl && !((cmask >> j) & 1u)) {
+                        const unsigned long long su = sh.u.ex.csig[own[j]];
+                        const unsigned long long nv = sig_of(atomicAdd(&rec[w[j]].w[X], su << 16)) + su;
+                        my_max = nv > my_max ? nv : my_max;
+                    }
+                }
+                // phase 5: claimed targets join the new frontier (warp-aggregated
+                // queue slots) or, if the other side already holds them, the
+                // meeting set
+#pragma unroll
+                for (int j = 0; j < kUnroll; ++j) {
+                    const bool claimed = (cmask >> j) & 1u;
+                    const bool meets = claimed && ((ymask >> j) & 1u);
+                    const bool joins = claimed && !meets;
+                    const unsigned int m = __ballot_sync(0xffffffffu, joins);
+                    if (m) {
+                        const int leader = __ffs(m) - 1;
+                        unsigned int slot0 = 0;
+                        if (lane == leader) slot0 = atomicAdd(&sh.new_count, (unsigned int)__popc(m));
+                        slot0 = __shfl_sync(0xffffffffu, slot0, leader);
+                        if (joins) qset(queue, n, X, qbase + slot0 + __popc(m & ((1u << lane) - 1u)), w[j]);
+                    }
+                    if (meets) {
+                        const unsigned int p = atomicAdd(&sh.meet_count, 1u);
+                        if (p < kMeetCap) sh.cand[p] = w[j];
                     }
                 }
             }
             __syncthreads();
         }
-        // degree sum of the new frontier and the largest new path count
-        // (every count's final value is the largest value its additions returned)
+        // largest new path count (every count's final value is the largest
+        // value its additions returned) and the new frontier's degree sum
         const unsigned long long lmax = block_max<NT>(my_max, sh);
+        unsigned long long my_deg = 0;
+        if (sh.meet_count == 0) {
+            const unsigned int nc = sh.new_count;
+            for (unsigned int i = tid; i < nc; i += NT) {
+                const unsigned int v = qget(queue, n, X, qbase + i);
+                my_deg += (unsigned long long)(G.end(v) - G.begin(v));
+            }
+        }
         const unsigned long long ldeg = block_sum<NT>(my_deg, sh);
         if (tid == 0) {
             sh.e_scan += my_scan;
@@ -505,8 +575,8 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
                 }
                 for (unsigned int i = sh.fbeg[X] + tid; i < sh.fend[X]; i += NT) {
                     const unsigned int v = qget(queue, n, X, i);
-                    const unsigned long long sv = ldcg(&rec[v].sig[X]);
-                    __stcg(&rec[v].sig[X], ((sv - 1ULL) >> shv) + 1ULL);
+                    const unsigned long long wv = ldcg(&rec[v].w[X]);
+                    __stcg(&rec[v].w[X], pack(lvl_of(wv), ((sig_of(wv) - 1ULL) >> shv) + 1ULL));
                 }
                 __syncthreads();
             }
@@ -514,6 +584,7 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
     }
 
     // A3 + A4: choose the meeting vertex, walk back, count interior vertices
+    if (tid == 0 && a.trace) t_bfs = global_ns();
     const int met = sh.status == 1;
     unsigned long long path_len = 0, walk_scan = 0;
     const int nbits = bitlen64((unsigned long long)(n - 1)) > 0 ? bitlen64((unsigned long long)(n - 1)) : 1;
@@ -528,7 +599,9 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
         if (in_smem) {
             for (unsigned int i = tid; i < mcnt; i += NT) {
                 const unsigned int w = sh.cand[i];
-                const unsigned long long p = ldcg(&rec[w].sig[0]), q = ldcg(&rec[w].sig[1]);
+                unsigned long long w0, w1;
+                load_rec(rec + w, w0, w1);
+                const unsigned long long p = sig_of(w0), q = sig_of(w1);
                 const unsigned long long lo = p * q, hi = __umul64hi(p, q);
                 sh.wlo[i] = lo;
                 sh.whi[i] = hi;
@@ -537,8 +610,10 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
         } else {
             for (unsigned int i = sh.fbeg[Y] + tid; i < sh.fend[Y]; i += NT) {
                 const unsigned int w = qget(queue, n, Y, i);
-                if (ldcg(&rec[w].lvl[X]) != nl) continue;
-                const unsigned long long p = ldcg(&rec[w].sig[0]), q = ldcg(&rec[w].sig[1]);
+                unsigned long long w0, w1;
+                load_rec(rec + w, w0, w1);
+                if (lvl_of(X ? w1 : w0) != nl) continue;
+                const unsigned long long p = sig_of(w0), q = sig_of(w1);
                 add128(tlo, thi, p * q, __umul64hi(p, q));
             }
         }
@@ -570,14 +645,16 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
                 c = radix_choose<NT>(sh, npass, [&](auto &&add) {
                     for (unsigned int i = yb + tid; i < ye; i += NT) {
                         const unsigned int w = qget(queue, n, Y, i);
-                        if (ldcg(&rec[w].lvl[X]) != nl) continue;
-                        const unsigned long long p = ldcg(&rec[w].sig[0]), q = ldcg(&rec[w].sig[1]);
+                        unsigned long long w0, w1;
+                        load_rec(rec + w, w0, w1);
+                        if (lvl_of(X ? w1 : w0) != nl) continue;
+                        const unsigned long long p = sig_of(w0), q = sig_of(w1);
                         add(w, p * q, __umul64hi(p, q));
                     }
                 });
             }
             if (tid == 0) {
-                const bool ok = c >= 0 && c < n && ldcg(&rec[c].lvl[X]) == nl && ldcg(&rec[c].lvl[Y]) != 0;
+                const bool ok = c >= 0 && c < n && lvl_of(ldcg(&rec[c].w[X])) == nl && lvl_of(ldcg(&rec[c].w[Y])) != 0;
                 sh.chosen = ok ? c : -1;
                 if (!ok) sh.err |= kErrSelect;
             }
@@ -585,6 +662,7 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
         }
 
         const long long w = sh.chosen;
+        if (tid == 0 && a.trace) t_sel = global_ns();
         if (tid == 0 && w >= 0) {
             if (w != sh.s && w != sh.t) {
                 if (a.counts) {
@@ -603,7 +681,7 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
             long long v = w;
             const long long src = Z == 0 ? sh.s : sh.t;
             for (;;) {
-                const unsigned int lz = ldcg(&rec[v].lvl[Z]);
+                const unsigned int lz = lvl_of(ldcg(&rec[v].w[Z]));
                 if (lz <= 1) break;      // reached the source of side Z
                 const unsigned int target = lz - 1;      // level code of the predecessors
                 const unsigned int P = lz - 2;           // their layer index
@@ -629,7 +707,7 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
                             if (adj) {
                                 const unsigned int p = atomicAdd(&sh.pcnt, 1u);
                                 sh.cand[p] = u;
-                                sh.wlo[p] = ldcg(&rec[u].sig[Z]);
+                                sh.wlo[p] = sig_of(ldcg(&rec[u].w[Z]));
                                 sh.whi[p] = 0;
                             }
                         }
@@ -660,7 +738,8 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
                         unsigned long long wt = 0;
                         if (tid < d) {
                             u = __ldg(G.col + b + tid);
-                            if (ldcg(&rec[u].lvl[Z]) == target) wt = ldcg(&rec[u].sig[Z]);
+                            const unsigned long long wu = ldcg(&rec[u].w[Z]);
+                            if (lvl_of(wu) == target) wt = sig_of(wu);
                         }
                         unsigned long long total;
                         const unsigned long long ex = block_excl_scan<NT>(wt, &total, sh);
@@ -672,7 +751,8 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
                         unsigned long long part = 0;
                         for (long long j = tid; j < d; j += NT) {
                             const long long u = __ldg(G.col + b + j);
-                            if (ldcg(&rec[u].lvl[Z]) == target) part += ldcg(&rec[u].sig[Z]);
+                            const unsigned long long wu = ldcg(&rec[u].w[Z]);
+                            if (lvl_of(wu) == target) part += sig_of(wu);
                         }
                         const unsigned long long total = block_sum<NT>(part, sh);
                         const unsigned long long r = __umul64hi(x.v[0], total);
@@ -685,7 +765,8 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
                             unsigned long long wt = 0;
                             if (j < d) {
                                 u = __ldg(G.col + b + j);
-                                if (ldcg(&rec[u].lvl[Z]) == target) wt = ldcg(&rec[u].sig[Z]);
+                                const unsigned long long wu = ldcg(&rec[u].w[Z]);
+                                if (lvl_of(wu) == target) wt = sig_of(wu);
                             }
                             unsigned long long ctot;
                             const unsigned long long ex = carry + block_excl_scan<NT>(wt, &ctot, sh);
@@ -699,7 +780,7 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
                         }
                     }
                     v = sh.next_v;
-                    if (v < 0 || v >= n || ldcg(&rec[v].lvl[Z]) != target) {
+                    if (v < 0 || v >= n || lvl_of(ldcg(&rec[v].w[Z])) != target) {
                         // no predecessor found: an invariant is broken; record it, stop the walk
                         if (tid == 0) sh.err |= kErrSelect;
                         walk_ok = false;
@@ -723,6 +804,10 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
 
     // per-sample bookkeeping (thread 0)
     if (tid == 0) {
+        if (a.trace) {
+            t_walk = global_ns();
+            if (!met) t_sel = t_bfs;
+        }
         ls.samples += 1;
         ls.connected += met ? 1 : 0;
         ls.e_scan += sh.e_scan;
@@ -732,6 +817,7 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
         ls.walk_scan += walk_scan;
         ls.scaled += sh.scaled ? 1 : 0;
         if (sh.status == 3) sh.err |= kErrSigmaOverflow;
+        if (sh.status == 4) sh.err |= kErrDepth;
         if (sh.err) atomicOr(&a.job->error, sh.err);
         if (a.trace) {
             TraceRec tr;
@@ -745,7 +831,12 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
             tr.e_scan = (long long)sh.e_scan;
             tr.n_interior = (long long)path_len;
             tr.scaled = sh.scaled;
-            tr.overflow = sh.status == 3;
+            tr.overflow = sh.status == 3 ? 1 : (sh.status == 4 ? 2 : 0);
+            tr.ns = (long long)(t_walk - t_start);
+            tr.phase_ns[0] = (long long)(t_bfs - t_start);
+            tr.phase_ns[1] = (long long)(t_sel - t_bfs);
+            tr.phase_ns[2] = (long long)(t_walk - t_sel);
+            tr.phase_ns[3] = 0;
             a.trace[trace_i] = tr;
         }
     }
@@ -758,16 +849,15 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
         const unsigned int len = sh.qlen[side];
         for (unsigned int i = tid; i < len; i += NT) {
             const unsigned int v = qget(queue, n, side, i);
-            uint4 *p = reinterpret_cast<uint4 *>(rec + v);
-            __stcg(p, z);
-            __stcg(p + 1, z);
+            __stcg(reinterpret_cast<uint4 *>(rec + v), z);
         }
     }
     __syncthreads();
+    if (tid == 0 && a.trace) a.trace[trace_i].phase_ns[3] = (long long)(global_ns() - t_walk);
 }
 
 template <int NT, typename OffT>
-__global__ void __launch_bounds__(NT, 2048 / NT / 2) sample_kernel(SampleLaunch a)
+__global__ void __launch_bounds__(NT, (2048 / NT / 2) > 0 ? (2048 / NT / 2) : 1) sample_kernel(SampleLaunch a)
 {
     __shared__ Smem<NT> sh;
     __shared__ unsigned long long s_base;
@@ -853,6 +943,7 @@ cudaError_t launch_sample(const SampleLaunch &a, cudaStream_t st)
     case 128: return launch_nt<128>(a, st);
     case 256: return launch_nt<256>(a, st);
     case 512: return launch_nt<512>(a, st);
+    case 1024: return launch_nt<1024>(a, st);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -863,6 +954,7 @@ cudaError_t sample_occupancy(int threads, int off64, int *ctas_per_sm)
     case 128: return occupancy_nt<128>(off64, ctas_per_sm);
     case 256: return occupancy_nt<256>(off64, ctas_per_sm);
     case 512: return occupancy_nt<512>(off64, ctas_per_sm);
+    case 1024: return occupancy_nt<1024>(off64, ctas_per_sm);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(_HERE, "lib", "libkadabra.so")
 OK = 0
 STATUS = {0: "KADABRA_OK", 1: "KADABRA_ERR_INVALID_ARG", 2: "KADABRA_ERR_OOM", 3: "KADABRA_ERR_CUDA",
           4: "KADABRA_ERR_SIGMA_OVERFLOW", 5: "KADABRA_ERR_COUNTER_OVERFLOW", 6: "KADABRA_ERR_TIMEOUT",
-          7: "KADABRA_ERR_STATE", 8: "KADABRA_ERR_NO_DEVICE"}
+          7: "KADABRA_ERR_STATE", 8: "KADABRA_ERR_NO_DEVICE", 9: "KADABRA_ERR_DEPTH"}
 
 GRAPH_DEVICE_PTRS = 1
 GRAPH_SKIP_VALIDATE = 2
@@ -59,7 +59,7 @@ class TraceRec(C.Structure):
     _fields_ = [("s", C.c_int64), ("t", C.c_int64), ("d", C.c_int64), ("sigma_lo", C.c_uint64),
                 ("sigma_hi", C.c_uint64), ("meet_size", C.c_int64), ("chosen", C.c_int64),
                 ("e_scan", C.c_int64), ("n_interior", C.c_int64), ("scaled", C.c_int32),
-                ("overflow", C.c_int32)]
+                ("overflow", C.c_int32), ("ns", C.c_int64), ("phase_ns", C.c_int64 * 4)]
 
     @property
     def sigma(self) -> int:
