@@ -379,7 +379,7 @@ def main():
     ap.add_argument("--epoch", type=int, default=4096)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--slots", type=int, default=0, help="samples in flight (0 = fill the GPU)")
-    ap.add_argument("--threads", type=int, default=256, help="threads per sampling CTA")
+    ap.add_argument("--threads", type=int, default=1024, help="threads per sampling CTA")
     ap.add_argument("--cpu-samples", type=int, default=48000,
                     help="oracle samples for the CPU baseline (split over host cores)")
     ap.add_argument("--ref-samples", type=int, default=16000, help="oracle samples per reference step")

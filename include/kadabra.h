@@ -75,7 +75,7 @@ typedef struct kadabra_params {
     uint32_t flags;           /* KADABRA_STRICT_SIGMA                                       */
     double beta;              /* balanced rule floor weight (default 1e-3)                 */
     int32_t slots;            /* samples in flight (one CTA each); 0 = fill the GPU        */
-    int32_t threads;          /* threads per sampling CTA: 128, 256, 512, 1024; 0 = 256    */
+    int32_t threads;          /* threads per sampling CTA: 128, 256, 512, 1024; 0 = 1024   */
     double scratch_fraction;  /* max share of free device memory for scratch; 0 = 0.6      */
 } kadabra_params;
 
@@ -135,7 +135,7 @@ int kadabra_abi_version(void);
 /* ---- host utilities (no device needed) --------------------------------- */
 
 /* Fill `p` with defaults: eps 0.01, delta 0.1, seed 1, auto VD, default
- * calibration size, balanced rule, beta 1e-3, auto slots, 256 threads. */
+ * calibration size, balanced rule, beta 1e-3, auto slots, 1024 threads. */
 void kadabra_params_default(kadabra_params *p);
 
 /* Check that (offsets, cols) is a symmetric CSR with ascending, duplicate-free

@@ -59,7 +59,7 @@ struct kadabra_graph {
     int64_t n = 0, nnz = 0, max_degree = 0;
     int off64 = 0;
     void *d_off = nullptr;
-    int32_t *d_col = nullptr;
+    uint2 *d_adj = nullptr;       // (neighbour, neighbour degree) per adjacency entry
     std::vector<int64_t> h_off;   // host copy for the diameter phase
     std::vector<int32_t> h_col;
     // sampling scratch shared by the graph's queries
@@ -133,7 +133,7 @@ extern "C" void kadabra_params_default(kadabra_params *p)
     p->flags = 0;
     p->beta = 1e-3;
     p->slots = 0;
-    p->threads = 256;
+    p->threads = 1024;
     p->scratch_fraction = 0.6;
 }
 
@@ -295,10 +295,11 @@ static void budgets(int64_t n, const std::vector<uint32_t> &cal, int64_t n_cal, 
 static void free_graph_device(kadabra_graph *g)
 {
     cudaFree(g->d_off);
-    cudaFree(g->d_col);
+    cudaFree(g->d_adj);
     cudaFree(g->d_recs);
     cudaFree(g->d_queues);
-    g->d_off = g->d_col = nullptr;
+    g->d_off = nullptr;
+    g->d_adj = nullptr;
     g->d_recs = nullptr;
     g->d_queues = nullptr;
 }
@@ -356,13 +357,19 @@ extern "C" kadabra_status kadabra_graph_load(int64_t n, int64_t nnz, const void 
     }
     g->max_degree = md;
 
+    // device copy: offsets, and the adjacency as (neighbour, neighbour degree)
+    // pairs built on the device from a temporary copy of the columns
+    int32_t *d_cols_tmp = nullptr;
     cudaError_t e = cudaMalloc(&g->d_off, ob);
-    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&g->d_col), cb ? cb : 4);
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&g->d_adj), (size_t)(nnz > 0 ? nnz : 1) * sizeof(uint2));
+    if (e == cudaSuccess && !dev && cb) e = cudaMalloc(reinterpret_cast<void **>(&d_cols_tmp), cb);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(g->d_off, offsets, ob, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess && cb)
-        e = cudaMemcpyAsync(g->d_col, cols, cb, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !dev && cb) e = cudaMemcpyAsync(d_cols_tmp, cols, cb, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = kadabra::launch_build_adj(nnz, g->d_off, g->off64, dev ? cols : d_cols_tmp, g->d_adj, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(d_cols_tmp);
     if (e != cudaSuccess) {
         free_graph_device(g);
         delete g;
@@ -469,7 +476,7 @@ static kadabra::SampleLaunch base_launch(const kadabra_query *q)
     a.n = q->g->n;
     a.off = q->g->d_off;
     a.off64 = q->g->off64;
-    a.col = q->g->d_col;
+    a.adj = q->g->d_adj;
     a.recs = q->g->d_recs;
     a.queues = q->g->d_queues;
     a.seed = q->p.seed;
@@ -500,7 +507,7 @@ extern "C" kadabra_status kadabra_calibrate(kadabra_graph *g, const kadabra_para
     if (p.delta_rule != KADABRA_DELTA_UNIFORM && p.delta_rule != KADABRA_DELTA_BALANCED)
         return fail(KADABRA_ERR_INVALID_ARG, "unknown delta_rule");
     if (!(p.beta > 0.0 && p.beta < 1.0)) return fail(KADABRA_ERR_INVALID_ARG, "beta must lie in (0, 1)");
-    if (p.threads == 0) p.threads = 256;
+    if (p.threads == 0) p.threads = 1024;
     if (p.threads != 128 && p.threads != 256 && p.threads != 512 && p.threads != 1024)
         return fail(KADABRA_ERR_INVALID_ARG, "threads must be 128, 256, 512 or 1024");
     if (g->n < 2) return fail(KADABRA_ERR_INVALID_ARG, "sampling pairs needs n >= 2");

@@ -66,7 +66,7 @@ struct SampleLaunch {
     int64_t n;
     const void *off;           // int32 or int64 offsets (n + 1)
     int off64;
-    const int32_t *col;
+    const uint2 *adj;          // (neighbour id, neighbour degree) per adjacency entry
     SlotRec *recs;             // slots * n
     uint32_t *queues;          // slots * n
     uint32_t *counts;          // c~[n]; nullptr: do not count (trace runs)
@@ -87,6 +87,8 @@ struct SampleLaunch {
 };
 
 cudaError_t launch_sample(const SampleLaunch &a, cudaStream_t st);
+cudaError_t launch_build_adj(int64_t nnz, const void *off, int off64, const int32_t *col, uint2 *adj,
+                             cudaStream_t st);
 cudaError_t sample_occupancy(int threads, int off64, int *ctas_per_sm);
 
 struct CheckLaunch {

@@ -86,11 +86,15 @@ __device__ __forceinline__ unsigned long long global_ns()
     return t;
 }
 
+// Adjacency entries are (neighbour id, neighbour degree) pairs: the degree
+// of a newly reached vertex arrives with its id in the same coalesced load,
+// so the frontier degree sums need no random row-offset reads.
 template <typename OffT>
 struct GraphRef {
     const OffT *off;
-    const int32_t *col;
+    const uint2 *adj;
     long long n;
+    __device__ __forceinline__ long long col(long long e) const { return (long long)__ldg(&adj[e].x); }
     __device__ __forceinline__ long long begin(long long v) const { return (long long)__ldg(off + v); }
     __device__ __forceinline__ long long end(long long v) const { return (long long)__ldg(off + v + 1); }
 };
@@ -348,16 +352,16 @@ __device__ __forceinline__ void qset(uint32_t *q, long long n, int side, unsigne
         __stcg(q + (n - 1 - i), v);
 }
 
-// Is `key` in the ascending list col[b, b + d)?
-__device__ __forceinline__ bool contains(const int32_t *col, long long b, long long d, long long key)
+// Is `key` in the ascending neighbour list adj[b, b + d)?
+__device__ __forceinline__ bool contains(const uint2 *adj, long long b, long long d, long long key)
 {
     long long lo = b, hi = b + d;
     while (lo < hi) {
         const long long mid = (lo + hi) >> 1;
-        if ((long long)__ldg(col + mid) < key) lo = mid + 1;
+        if ((long long)__ldg(&adj[mid].x) < key) lo = mid + 1;
         else hi = mid;
     }
-    return lo < b + d && (long long)__ldg(col + lo) == key;
+    return lo < b + d && (long long)__ldg(&adj[lo].x) == key;
 }
 
 // ---- one sample ------------------------------------------------------------
@@ -420,7 +424,7 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
         const unsigned int nl = sh.layer[X] + 2;    // level code of the new layer
         const unsigned int fb = sh.fbeg[X], fe = sh.fend[X];
         const unsigned int qbase = sh.qlen[X];
-        unsigned long long my_max = 0, my_scan = 0;
+        unsigned long long my_max = 0, my_scan = 0, my_deg = 0;
         const int lane = tid & 31;
 
         for (unsigned int cb = fb; cb < fe; cb += NT) {
@@ -447,11 +451,13 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
             const unsigned long long wbase = (unsigned long long)(tid & ~31);
             for (unsigned long long e0 = wbase; e0 < total; e0 += (unsigned long long)NT * kUnroll) {
                 unsigned int w[kUnroll];
+                unsigned int dw[kUnroll];
                 int own[kUnroll];
 #pragma unroll
                 for (int j = 0; j < kUnroll; ++j) {
                     const unsigned long long e = e0 + (unsigned long long)lane + (unsigned long long)j * NT;
                     w[j] = kNone;
+                    dw[j] = 0;
                     own[j] = 0;
                     if (e < total) {
                         // owner: the last k with cpos[k] <= e
@@ -462,7 +468,9 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
                             else hi = mid - 1;
                         }
                         own[j] = lo;
-                        w[j] = (unsigned int)__ldg(G.col + sh.u.ex.cbeg[lo] + (long long)(e - sh.u.ex.cpos[lo]));
+                        const uint2 c = __ldg(G.adj + sh.u.ex.cbeg[lo] + (long long)(e - sh.u.ex.cpos[lo]));
+                        w[j] = c.x;
+                        dw[j] = c.y;
                     }
                 }
                 // phase 2: (level_s, level_t) of every target, one 8-byte load each
@@ -519,7 +527,10 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
                         unsigned int slot0 = 0;
                         if (lane == leader) slot0 = atomicAdd(&sh.new_count, (unsigned int)__popc(m));
                         slot0 = __shfl_sync(0xffffffffu, slot0, leader);
-                        if (joins) qset(queue, n, X, qbase + slot0 + __popc(m & ((1u << lane) - 1u)), w[j]);
+                        if (joins) {
+                            qset(queue, n, X, qbase + slot0 + __popc(m & ((1u << lane) - 1u)), w[j]);
+                            my_deg += dw[j];
+                        }
                     }
                     if (meets) {
                         const unsigned int p = atomicAdd(&sh.meet_count, 1u);
@@ -532,14 +543,6 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
         // largest new path count (every count's final value is the largest
         // value its additions returned) and the new frontier's degree sum
         const unsigned long long lmax = block_max<NT>(my_max, sh);
-        unsigned long long my_deg = 0;
-        if (sh.meet_count == 0) {
-            const unsigned int nc = sh.new_count;
-            for (unsigned int i = tid; i < nc; i += NT) {
-                const unsigned int v = qget(queue, n, X, qbase + i);
-                my_deg += (unsigned long long)(G.end(v) - G.begin(v));
-            }
-        }
         const unsigned long long ldeg = block_sum<NT>(my_deg, sh);
         if (tid == 0) {
             sh.e_scan += my_scan;
@@ -703,8 +706,8 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
                         for (unsigned int i = tid; i < lsz; i += NT) {
                             const unsigned int u = qget(queue, n, Z, lb + i);
                             const long long bu = G.begin(u), du = G.end(u) - bu;
-                            const bool adj = du <= d ? contains(G.col, bu, du, v) : contains(G.col, b, d, u);
-                            if (adj) {
+                            const bool isadj = du <= d ? contains(G.adj, bu, du, v) : contains(G.adj, b, d, u);
+                            if (isadj) {
                                 const unsigned int p = atomicAdd(&sh.pcnt, 1u);
                                 sh.cand[p] = u;
                                 sh.wlo[p] = sig_of(ldcg(&rec[u].w[Z]));
@@ -737,7 +740,7 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
                         long long u = -1;
                         unsigned long long wt = 0;
                         if (tid < d) {
-                            u = __ldg(G.col + b + tid);
+                            u = G.col(b + tid);
                             const unsigned long long wu = ldcg(&rec[u].w[Z]);
                             if (lvl_of(wu) == target) wt = sig_of(wu);
                         }
@@ -750,7 +753,7 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
                         walk_scan += (unsigned long long)d;
                         unsigned long long part = 0;
                         for (long long j = tid; j < d; j += NT) {
-                            const long long u = __ldg(G.col + b + j);
+                            const long long u = G.col(b + j);
                             const unsigned long long wu = ldcg(&rec[u].w[Z]);
                             if (lvl_of(wu) == target) part += sig_of(wu);
                         }
@@ -764,7 +767,7 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
                             long long u = -1;
                             unsigned long long wt = 0;
                             if (j < d) {
-                                u = __ldg(G.col + b + j);
+                                u = G.col(b + j);
                                 const unsigned long long wu = ldcg(&rec[u].w[Z]);
                                 if (lvl_of(wu) == target) wt = sig_of(wu);
                             }
@@ -863,7 +866,7 @@ __global__ void __launch_bounds__(NT, (2048 / NT / 2) > 0 ? (2048 / NT / 2) : 1)
     __shared__ unsigned long long s_base;
     __shared__ unsigned long long s_count;
     const int tid = threadIdx.x;
-    GraphRef<OffT> G{reinterpret_cast<const OffT *>(a.off), a.col, (long long)a.n};
+    GraphRef<OffT> G{reinterpret_cast<const OffT *>(a.off), a.adj, (long long)a.n};
     SlotRec *rec = a.recs + (size_t)blockIdx.x * (size_t)a.n;
     uint32_t *queue = a.queues + (size_t)blockIdx.x * (size_t)a.n;
     Job *job = a.job;
@@ -917,6 +920,17 @@ __global__ void __launch_bounds__(NT, (2048 / NT / 2) > 0 ? (2048 / NT / 2) : 1)
     }
 }
 
+// adj[e] = (col[e], degree of col[e]) for every adjacency entry
+template <typename OffT>
+__global__ void build_adj_kernel(long long nnz, const OffT *off, const int32_t *col, uint2 *adj)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += stride) {
+        const int32_t w = __ldg(col + e);
+        adj[e] = make_uint2((unsigned int)w, (unsigned int)((long long)__ldg(off + w + 1) - (long long)__ldg(off + w)));
+    }
+}
+
 template <int NT>
 cudaError_t launch_nt(const SampleLaunch &a, cudaStream_t st)
 {
@@ -946,6 +960,21 @@ cudaError_t launch_sample(const SampleLaunch &a, cudaStream_t st)
     case 1024: return launch_nt<1024>(a, st);
     default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_build_adj(int64_t nnz, const void *off, int off64, const int32_t *col, uint2 *adj, cudaStream_t st)
+{
+    if (nnz <= 0) return cudaSuccess;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long want = (nnz + 255) / 256;
+    const int grid = (int)(want < (long long)sms * 16 ? want : (long long)sms * 16);
+    if (off64)
+        build_adj_kernel<long long><<<grid, 256, 0, st>>>((long long)nnz, static_cast<const long long *>(off), col, adj);
+    else
+        build_adj_kernel<int><<<grid, 256, 0, st>>>((long long)nnz, static_cast<const int *>(off), col, adj);
+    return cudaGetLastError();
 }
 
 cudaError_t sample_occupancy(int threads, int off64, int *ctas_per_sm)

@@ -59,7 +59,7 @@ def test_status_strings_and_version(K):
 
 def test_params_default(K):
     p = K.params_default()
-    assert p.eps == 0.01 and p.delta == 0.1 and p.seed == 1 and p.threads == 256
+    assert p.eps == 0.01 and p.delta == 0.1 and p.seed == 1 and p.threads == 1024
     assert p.delta_rule == K.DELTA_BALANCED and p.beta == 1e-3
 
 
