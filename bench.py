@@ -7,10 +7,13 @@ duplicates removed, int32 CSR; eps = 0.01, delta = 0.1, seed 1.  Synthetic
 data from paper_1910_11039_gb300.inputs (generator seed 2).
 
 A step is one complete adaptive phase (arXiv 1910.11039, Section III-A,
-phase 3): from tau = 0, epochs of E samples each followed by the on-device
-stop check, until the stopping condition holds.  All epochs up to the cap
-omega are enqueued without host synchronisation; launches after the stop
-take no samples.  The graph and the calibrated budgets are resident in HBM
+phase 3): from tau = 0, epochs of E samples each checked against the stopping
+condition, until it holds.  Default form ("pipelined"): one persistent launch
+in which epochs flow through rotating frames and the CTA that completes an
+epoch checks it while the others keep sampling (the paper's epoch framework,
+Section IV).  Form "epochs": one sampling launch plus one stop-check launch
+per epoch, all enqueued without host synchronisation (launches after the stop
+take no samples).  The graph and the calibrated budgets are resident in HBM
 before the timed region.  L2 is flushed (256 MiB write) before every step.
 
 value  = adaptive samples per second over the K timed steps (device events)
@@ -166,10 +169,10 @@ def kernel_digest():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload):
-    """DRAM bytes per sample of the sampling kernel from the committed ncu
+def profiled_traffic(workload, kernel):
+    """DRAM bytes per sample of the timed kernel from the committed ncu
     summary, if it was taken on the current kernel sources."""
-    path = os.path.join(ROOT, "profiles", f"sample_kernel_{workload}.md")
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
     if not os.path.exists(path):
         return None
     txt = open(path).read()
@@ -243,15 +246,21 @@ def run_gpu(args, wl, g, rank, world, local_rank, cpu_baseline):
     max_epochs = math.ceil(info0.omega_ceil / E) + 1
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
 
+    def adaptive_phase(qq):
+        if args.mode == "pipelined":
+            qq.run_pipelined(E, frames=args.frames)
+        else:
+            for _ in range(max_epochs):
+                qq.sample_epoch(E)
+                qq.check_stop_async()
+
     def step():
         flush.fill_(rank + 1)
         q.reset()
         s0 = torch.cuda.Event(enable_timing=True)
         s1 = torch.cuda.Event(enable_timing=True)
         s0.record(stream)
-        for _ in range(max_epochs):
-            q.sample_epoch(E)
-            q.check_stop_async()
+        adaptive_phase(q)
         s1.record(stream)
         s1.synchronize()
         inf = q.info()
@@ -299,16 +308,18 @@ def run_gpu(args, wl, g, rank, world, local_rank, cpu_baseline):
     tot_b = sum(algorithmic_bytes(ls, ob) for ls in launches)
     tot_ms = sum(ls.ms for ls in launches)
     achieved = tot_b / (tot_ms / 1e3) / 1e9 if tot_ms > 0 else 0.0
-    per_sample = profiled_traffic(args.workload)
+    per_sample = profiled_traffic(args.workload, "pipe_kernel" if args.mode == "pipelined" else "sample_kernel")
     mean_samples = sum(ls.samples for ls in launches) / max(1, len(launches))
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": per_sample * mean_samples if per_sample else None,
-                "kernel": "sample_kernel", "peak_source": f"{peak_kind} hbm_gbs",
+                "kernel": "pipe_kernel" if args.mode == "pipelined" else "sample_kernel", "peak_source": f"{peak_kind} hbm_gbs",
                 "launches": len(launches), "avg_launch_ms": tot_ms / max(1, len(launches)),
                 "algorithmic_bytes_per_launch": tot_b / max(1, len(launches)),
                 "per_sample": {k: sum(getattr(ls, k) for ls in launches) / max(1, sum(ls.samples for ls in launches))
                                for k in ("e_scan", "expanded", "touched", "walk_scan", "interior", "connected")}}
-    n_launch_kernels = args.steps * (2 * max_epochs + 1)   # sample + check per epoch, reset per step
+    # our kernels per step: reset + (pipelined: class maxima + one persistent launch;
+    # epochs: one sampling and one check launch per enqueued epoch)
+    n_launch_kernels = args.steps * (3 if args.mode == "pipelined" else 2 * max_epochs + 1)
 
     # ---- end to end through the C ABI with pinned host buffers ----
     e2e = None
@@ -325,10 +336,12 @@ def run_gpu(args, wl, g, rank, world, local_rank, cpu_baseline):
             t0 = time.perf_counter()
             G2 = K.Graph(g.n, off_h.numpy(), col_h.numpy(), offsets_64=False, skip_validate=True, stream=stream)
             q2 = K.Query(G2, eps=eps, delta=delta, seed=seed, stream=stream, slots=args.slots, threads=args.threads)
-            mx = math.ceil(q2.info().omega_ceil / E) + 1
-            for _ in range(mx):
-                q2.sample_epoch(E)
-                q2.check_stop_async()
+            if args.mode == "pipelined":
+                q2.run_pipelined(E, frames=args.frames)
+            else:
+                for _ in range(math.ceil(q2.info().omega_ceil / E) + 1):
+                    q2.sample_epoch(E)
+                    q2.check_stop_async()
             tau, se = q2.result_into(b_h.data_ptr(), c_h.data_ptr())
             t1 = time.perf_counter()
             q2.free()
@@ -351,7 +364,9 @@ def run_gpu(args, wl, g, rank, world, local_rank, cpu_baseline):
         "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": wl["desc"], "name": args.workload, "n": g.n, "nnz": g.nnz, "epoch_len": E,
-                   "max_epochs_enqueued": max_epochs, "slots": info0.slots, "threads": info0.threads,
+                   "mode": args.mode, "frames": args.frames if args.mode == "pipelined" else None,
+                   "max_epochs_enqueued": max_epochs if args.mode == "epochs" else None,
+                   "slots": info0.slots, "threads": info0.threads,
                    "omega": info0.omega, "vertex_diameter": info0.vertex_diameter, "n_calib": info0.n_calib,
                    "l2": "flushed before every step (256 MiB write)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -376,7 +391,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default="rmat20", choices=list(WORKLOADS))
-    ap.add_argument("--epoch", type=int, default=4096)
+    ap.add_argument("--epoch", type=int, default=1024)
+    ap.add_argument("--mode", default="pipelined", choices=["pipelined", "epochs"])
+    ap.add_argument("--frames", type=int, default=8, help="epoch frames in flight (pipelined mode)")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--slots", type=int, default=0, help="samples in flight (0 = fill the GPU)")
     ap.add_argument("--threads", type=int, default=1024, help="threads per sampling CTA")

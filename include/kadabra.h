@@ -105,6 +105,7 @@ typedef struct kadabra_query_info {
     int32_t slots;              /* samples in flight per launch                            */
     int32_t threads;            /* threads per sampling CTA                                */
     int32_t offsets_64;         /* 1 if the graph uses int64 offsets                       */
+    int32_t budget_classes;     /* distinct (L_L, L_U) pairs                               */
 } kadabra_query_info;
 
 /* Per-sample record written by kadabra_sample_trace (one per sample index). */
@@ -211,6 +212,27 @@ kadabra_status kadabra_check_stop_async(kadabra_query *q, void *cuda_stream);
  * device flag once every `sync_every` epochs (<= 0: 4).  Writes *stopped. */
 kadabra_status kadabra_run(kadabra_query *q, int64_t epoch_len, int64_t max_epochs,
                            int64_t sync_every, void *cuda_stream, int *stopped);
+
+/* Phase 3 as one persistent launch (async), the GPU form of the paper's
+ * epoch framework (Section IV-A/B, Algorithm 2: threads keep sampling into the
+ * state frame of their epoch while a completed epoch is aggregated and
+ * checked).  Sample i belongs to epoch i / epoch_len and logs its interior
+ * vertices in frame (epoch mod frames); the CTA that completes the oldest
+ * unchecked epoch folds that log into c~ and evaluates the stopping condition
+ * on exactly samples [0, (e + 1) epoch_len) while all other CTAs keep
+ * sampling later epochs.  The check evaluates f and g once per budget class
+ * (vertices with equal (L_L, L_U)) at the class's largest counter, which
+ * gives exactly the per-vertex maxima because f and g are monotone in c~.
+ * Samples of epochs after the stopping epoch are discarded, so tau, c~ and
+ * the stop epoch equal those of repeated kadabra_sample_epoch(epoch_len) +
+ * kadabra_check_stop from the same starting tau.
+ *   frames: 1..16 epoch logs of epoch_len * (VD - 2) entries (<= 0: 8); a CTA
+ *   waits for a free frame before sampling more than `frames` epochs ahead of
+ *   the oldest unchecked one.  That wait is bounded; if it gives up, the launch
+ *   ends and the next synchronising call returns KADABRA_ERR_TIMEOUT.  A path
+ *   with more than VD - 2 interior vertices (a vertex_diameter parameter below
+ *   the true one) ends the launch with KADABRA_ERR_INVALID_ARG. */
+kadabra_status kadabra_run_pipelined(kadabra_query *q, int64_t epoch_len, int frames, void *cuda_stream);
 
 /* Restart phase 3 (tau = 0, c~ = 0, not stopped) keeping omega and the
  * calibrated budgets (async). */

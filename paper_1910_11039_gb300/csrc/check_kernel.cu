@@ -16,13 +16,12 @@
 #include <cstdint>
 
 #include "kadabra_internal.h"
+#include "stop_math.cuh"
 
 namespace kadabra {
 namespace {
 
 constexpr int kCheckThreads = 256;
-
-__device__ __forceinline__ double fmax_exact(double a, double b) { return b > a ? b : a; }
 
 __global__ void __launch_bounds__(kCheckThreads) check_kernel(CheckLaunch a)
 {
@@ -33,21 +32,11 @@ __global__ void __launch_bounds__(kCheckThreads) check_kernel(CheckLaunch a)
 
     double mf = 0.0, mg = 0.0;
     if (tau > 0) {
-        const double tau_d = (double)tau;
-        const double r = __ddiv_rn(a.omega, tau_d);
-        const double third = 1.0 / 3.0;
-        const double af = __dsub_rn(third, r);
-        const double ag = __dadd_rn(third, r);
-        const double af2 = __dmul_rn(af, af);
-        const double ag2 = __dmul_rn(ag, ag);
+        const StopConsts k = stop_consts(tau, a.omega);
         const long long stride = (long long)gridDim.x * blockDim.x;
         for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < a.n; x += stride) {
-            const unsigned int c = __ldg(a.counts + x);
-            const double2 L = __ldg(a.L + x);
-            const double bt = __ddiv_rn((double)c, tau_d);
-            const double bw = __dmul_rn(__dmul_rn(2.0, bt), a.omega);
-            const double f = __dmul_rn(__ddiv_rn(L.x, tau_d), __dadd_rn(af, __dsqrt_rn(__dadd_rn(af2, __ddiv_rn(bw, L.x)))));
-            const double g = __dmul_rn(__ddiv_rn(L.y, tau_d), __dadd_rn(ag, __dsqrt_rn(__dadd_rn(ag2, __ddiv_rn(bw, L.y)))));
+            double f, g;
+            stop_fg(k, __ldg(a.counts + x), __ldg(a.L + x), f, g);
             mf = fmax_exact(mf, f);
             mg = fmax_exact(mg, g);
         }

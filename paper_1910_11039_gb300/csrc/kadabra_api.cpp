@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -93,6 +94,15 @@ struct kadabra_query {
     int grid_log[kadabra::kLaunchLog] = {};
     kadabra::Counters *d_launch = nullptr;   // kLaunchLog entries
     int64_t launches = 0;
+    // budget classes: vertices with equal (L_L, L_U)
+    uint32_t *d_cls = nullptr;               // class of every vertex
+    double2 *d_Ltab = nullptr;               // budgets of every class
+    unsigned int *d_cmax = nullptr;          // largest c~ per class (pipelined launches)
+    int nclass = 0;
+    // pipelined adaptive phase
+    uint32_t *d_logs = nullptr;              // epoch logs of interior vertices
+    size_t logs_alloc = 0;                   // entries allocated
+    kadabra::PipeState *d_pipe = nullptr;
 };
 
 // ---------------------------------------------------------------------------
@@ -452,6 +462,11 @@ static void free_query_device(kadabra_query *q)
     cudaFree(q->d_cal_job);
     cudaFree(q->d_trace_job);
     cudaFree(q->d_launch);
+    cudaFree(q->d_cls);
+    cudaFree(q->d_Ltab);
+    cudaFree(q->d_cmax);
+    cudaFree(q->d_logs);
+    cudaFree(q->d_pipe);
     for (int i = 0; i < kadabra::kLaunchLog; ++i) {
         if (q->ev0[i]) cudaEventDestroy(q->ev0[i]);
         if (q->ev1[i]) cudaEventDestroy(q->ev1[i]);
@@ -463,6 +478,10 @@ static kadabra_status device_error_status(const Job &j)
     if (j.error & kadabra::kErrSigmaOverflow)
         return fail(KADABRA_ERR_SIGMA_OVERFLOW, "strict mode: a per-side path count exceeded 2^K");
     if (j.error & kadabra::kErrCounterOverflow) return fail(KADABRA_ERR_COUNTER_OVERFLOW, "a 32-bit counter wrapped");
+    if (j.error & kadabra::kErrLogOverflow)
+        return fail(KADABRA_ERR_INVALID_ARG, "a sampled path had more interior vertices than VD - 2 (vertex diameter bound too small)");
+    if (j.error & kadabra::kErrTimeout)
+        return fail(KADABRA_ERR_TIMEOUT, "a pipelined launch gave up waiting for a free counter frame");
     if (j.error & kadabra::kErrDepth)
         return fail(KADABRA_ERR_DEPTH, "a BFS side needed more than 65533 layers (16-bit levels)");
     if (j.error & (kadabra::kErrAddOverflow | kadabra::kErrSelect))
@@ -598,7 +617,37 @@ extern "C" kadabra_status kadabra_calibrate(kadabra_graph *g, const kadabra_para
     budgets(g->n, cal, q->n_calib, p.eps, p.delta, p.delta_rule, p.beta, LL, LU, &q->balance_C);
     std::vector<double2> L(n);
     for (size_t x = 0; x < n; ++x) L[x] = make_double2(LL[x], LU[x]);
+    // budget classes (distinct (L_L, L_U) pairs, numbered in order of first appearance)
+    std::vector<uint32_t> cls(n);
+    std::vector<double2> Ltab;
+    {
+        struct PairHash {
+            size_t operator()(const std::pair<uint64_t, uint64_t> &k) const
+            {
+                return std::hash<uint64_t>()(k.first * 0x9E3779B97F4A7C15ULL ^ k.second);
+            }
+        };
+        std::unordered_map<std::pair<uint64_t, uint64_t>, uint32_t, PairHash> ids;
+        for (size_t x = 0; x < n; ++x) {
+            uint64_t a, b;
+            std::memcpy(&a, &LL[x], 8);
+            std::memcpy(&b, &LU[x], 8);
+            auto it = ids.find({a, b});
+            if (it == ids.end()) {
+                it = ids.emplace(std::make_pair(a, b), (uint32_t)Ltab.size()).first;
+                Ltab.push_back(L[x]);
+            }
+            cls[x] = it->second;
+        }
+    }
+    q->nclass = (int)Ltab.size();
     e = cudaMemcpyAsync(q->d_L, L.data(), n * sizeof(double2), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&q->d_cls), n * 4);
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&q->d_Ltab), Ltab.size() * sizeof(double2));
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&q->d_cmax), Ltab.size() * 4);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(q->d_cls, cls.data(), n * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(q->d_Ltab, Ltab.data(), Ltab.size() * sizeof(double2), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
         free_query_device(q);
@@ -640,6 +689,64 @@ extern "C" kadabra_status kadabra_sample_epoch(kadabra_query *q, int64_t n_sampl
     KCUDA(kadabra::launch_sample(a, st), "sampling kernel launch");
     KCUDA(cudaEventRecord(q->ev1[slot], st), "event");
     q->grid_log[slot] = a.grid;
+    ++q->launches;
+    return KADABRA_OK;
+}
+
+extern "C" kadabra_status kadabra_run_pipelined(kadabra_query *q, int64_t epoch_len, int frames, void *cuda_stream)
+{
+    if (!q) return fail(KADABRA_ERR_INVALID_ARG, "query is null");
+    if (epoch_len <= 0 || epoch_len >= (int64_t(1) << 40)) return fail(KADABRA_ERR_INVALID_ARG, "epoch_len out of range");
+    if (frames <= 0) frames = 8;
+    if (frames > kadabra::kMaxFrames) return fail(KADABRA_ERR_INVALID_ARG, "frames must be <= 16");
+    cudaStream_t st = as_stream(cuda_stream);
+    const size_t n = (size_t)q->g->n;
+    // an epoch logs at most (VD - 2) interior vertices per sample
+    const uint64_t per_sample = q->vd > 3 ? (uint64_t)(q->vd - 2) : 1ULL;
+    const uint64_t cap = (uint64_t)epoch_len * per_sample;
+    if (cap >= (uint64_t(1) << 32)) return fail(KADABRA_ERR_INVALID_ARG, "epoch_len * (VD - 2) must be < 2^32");
+    const size_t need = (size_t)frames * (size_t)cap;
+    if (q->logs_alloc < need) {
+        cudaFree(q->d_logs);
+        q->d_logs = nullptr;
+        q->logs_alloc = 0;
+        KCUDA(cudaMalloc(reinterpret_cast<void **>(&q->d_logs), need * 4), "allocate epoch logs");
+        q->logs_alloc = need;
+    }
+    if (!q->d_pipe) KCUDA(cudaMalloc(reinterpret_cast<void **>(&q->d_pipe), sizeof(kadabra::PipeState)), "allocate pipeline state");
+    KCUDA(cudaMemsetAsync(q->d_pipe, 0, sizeof(kadabra::PipeState), st), "clear pipeline state");
+    // per-class maxima of the counters the run starts from
+    KCUDA(cudaMemsetAsync(q->d_cmax, 0, (size_t)q->nclass * 4, st), "clear class maxima");
+    KCUDA(kadabra::launch_class_max(q->g->n, q->d_counts, q->d_cls, q->d_cmax, st), "class maxima");
+    (void)n;
+    kadabra::PipeLaunch P{};
+    P.s = base_launch(q);
+    P.s.counts = q->d_counts;
+    P.s.job = q->d_job;
+    P.s.tag = 1;
+    P.s.use_stop = 1;
+    P.s.epoch_len = epoch_len;
+    P.s.clip = q->omega_ceil;
+    P.s.grid = clamp_grid(q, int64_t(1) << 40);
+    P.logs = q->d_logs;
+    P.log_cap = (unsigned int)cap;
+    P.F = frames;
+    P.E = epoch_len;
+    P.cls = q->d_cls;
+    P.Ltab = q->d_Ltab;
+    P.cmax = q->d_cmax;
+    P.nclass = q->nclass;
+    P.omega = q->omega;
+    P.eps = q->p.eps;
+    P.ps = q->d_pipe;
+    P.spin_limit = 1ULL << 24;
+    const int slot = (int)(q->launches % kadabra::kLaunchLog);
+    P.s.launch_ctr = q->d_launch + slot;
+    KCUDA(cudaMemsetAsync(P.s.launch_ctr, 0, sizeof(kadabra::Counters), st), "reset launch counters");
+    KCUDA(cudaEventRecord(q->ev0[slot], st), "event");
+    KCUDA(kadabra::launch_pipe(P, st), "pipelined kernel launch");
+    KCUDA(cudaEventRecord(q->ev1[slot], st), "event");
+    q->grid_log[slot] = P.s.grid;
     ++q->launches;
     return KADABRA_OK;
 }
@@ -770,6 +877,7 @@ extern "C" kadabra_status kadabra_query_get_info(kadabra_query *q, kadabra_query
     I.slots = q->slots;
     I.threads = q->threads;
     I.offsets_64 = q->g->off64;
+    I.budget_classes = q->nclass;
     *out = I;
     return KADABRA_OK;
 }

@@ -50,6 +50,8 @@ enum : unsigned int {
     kErrCounterOverflow = 4u,  // a 32-bit c~ counter wrapped
     kErrSelect = 8u,           // weighted choice found no element (never expected)
     kErrDepth = 16u,           // a BFS side would exceed 65533 layers (16-bit levels)
+    kErrTimeout = 32u,         // a bounded wait for a free counter frame gave up
+    kErrLogOverflow = 64u,     // an epoch log overflowed (a path longer than VD - 2)
 };
 
 // Per-sample trace record (mirrors kadabra_trace_rec).
@@ -90,6 +92,40 @@ cudaError_t launch_sample(const SampleLaunch &a, cudaStream_t st);
 cudaError_t launch_build_adj(int64_t nnz, const void *off, int off64, const int32_t *col, uint2 *adj,
                              cudaStream_t st);
 cudaError_t sample_occupancy(int threads, int off64, int *ctas_per_sm);
+
+// Pipelined adaptive phase (one persistent launch): epochs rotate through F
+// counter frames; see pipe_kernel in sample_kernel.cu.
+constexpr int kMaxFrames = 16;
+
+struct PipeState {
+    unsigned long long next_idx;        // next sample (relative to the launch's base tau) to hand out
+    long long next_check;               // next epoch (relative) to fold into c~ and check
+    unsigned int done[kMaxFrames];      // finished samples of the epoch each frame holds
+    unsigned int log_len[kMaxFrames];   // interior vertices logged by the epoch each frame holds
+    int checker;                        // 1 while a CTA folds and checks
+    int abort;                          // set when a bounded wait gave up
+    unsigned int exited;                // CTAs that left the launch
+    unsigned int pad;
+};
+
+struct PipeLaunch {
+    SampleLaunch s;            // graph, scratch, seed, K, job (tag 1, no trace)
+    uint32_t *logs;            // F logs of log_cap interior-vertex ids
+    unsigned int log_cap;
+    int F;                     // frames (epoch logs) in rotation (1..kMaxFrames)
+    long long E;               // samples per epoch
+    const uint32_t *cls;       // budget class of every vertex
+    const double2 *Ltab;       // (L_L, L_U) of every class
+    unsigned int *cmax;        // largest c~ in every class (kept current by the folds)
+    int nclass;
+    double omega, eps;
+    PipeState *ps;
+    unsigned long long spin_limit;   // polls of a frame wait before giving up
+};
+
+cudaError_t launch_pipe(const PipeLaunch &a, cudaStream_t st);
+cudaError_t launch_class_max(int64_t n, const uint32_t *counts, const uint32_t *cls, unsigned int *cmax,
+                             cudaStream_t st);
 
 struct CheckLaunch {
     int64_t n;

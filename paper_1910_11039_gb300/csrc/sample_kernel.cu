@@ -46,6 +46,7 @@
 
 #include "kadabra_internal.h"
 #include "philox.cuh"
+#include "stop_math.cuh"
 
 namespace kadabra {
 namespace {
@@ -366,13 +367,36 @@ __device__ __forceinline__ bool contains(const uint2 *adj, long long b, long lon
 
 // ---- one sample ------------------------------------------------------------
 
+// Where a sample's interior vertices go: straight into c~ (epoch launches,
+// calibration), or into the log of the sample's epoch (pipelined launch).
+struct CountSink {
+    uint32_t *counts;
+    uint32_t *log;
+    unsigned int *len;
+    unsigned int cap;
+    __device__ __forceinline__ unsigned int add(long long v) const
+    {
+        if (counts) {
+            const unsigned int old = atomicAdd(&counts[v], 1u);
+            return old == 0xffffffffu ? kErrCounterOverflow : 0u;
+        }
+        if (log) {
+            const unsigned int p = atomicAdd(len, 1u);
+            if (p >= cap) return kErrLogOverflow;
+            __stcg(log + p, (unsigned int)v);
+        }
+        return 0u;
+    }
+};
+
 struct LocalStats {
     unsigned long long samples, connected, e_scan, expanded, touched, interior, walk_scan, scaled;
 };
 
 template <int NT, typename OffT>
 __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotRec *rec, uint32_t *queue,
-                           Smem<NT> &sh, unsigned long long idx, unsigned long long trace_i, LocalStats &ls)
+                           Smem<NT> &sh, unsigned long long idx, unsigned long long trace_i, LocalStats &ls,
+                           const CountSink &sink)
 {
     const int tid = threadIdx.x;
     const long long n = G.n;
@@ -668,10 +692,7 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
         if (tid == 0 && a.trace) t_sel = global_ns();
         if (tid == 0 && w >= 0) {
             if (w != sh.s && w != sh.t) {
-                if (a.counts) {
-                    const unsigned int old = atomicAdd(&a.counts[w], 1u);
-                    if (old == 0xffffffffu) sh.err |= kErrCounterOverflow;
-                }
+                sh.err |= sink.add(w);
                 if (a.trace_path && (long long)path_len < a.trace_cap)
                     a.trace_path[trace_i * a.trace_cap + path_len] = (int32_t)w;
                 ++path_len;
@@ -792,10 +813,7 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
                     }
                 }
                 if (tid == 0 && v != src) {
-                    if (a.counts) {
-                        const unsigned int old = atomicAdd(&a.counts[v], 1u);
-                        if (old == 0xffffffffu) sh.err |= kErrCounterOverflow;
-                    }
+                    sh.err |= sink.add(v);
                     if (a.trace_path && (long long)path_len < a.trace_cap)
                         a.trace_path[trace_i * a.trace_cap + path_len] = (int32_t)v;
                     ++path_len;
@@ -891,7 +909,7 @@ __global__ void __launch_bounds__(NT, (2048 / NT / 2) > 0 ? (2048 / NT / 2) : 1)
         __syncthreads();
         const unsigned long long i = sh.cur;
         if (i >= count) break;
-        run_sample<NT, OffT>(a, G, rec, queue, sh, base + i, i, ls);
+        run_sample<NT, OffT>(a, G, rec, queue, sh, base + i, i, ls, CountSink{a.counts, nullptr, nullptr, 0u});
     }
 
     if (tid == 0) {
@@ -917,6 +935,260 @@ __global__ void __launch_bounds__(NT, (2048 / NT / 2) > 0 ? (2048 / NT / 2) : 1)
             *reinterpret_cast<volatile unsigned int *>(&job->done_ctas) = 0u;
             __threadfence();
         }
+    }
+}
+
+// ---- pipelined adaptive phase ---------------------------------------------
+//
+// The paper's epoch framework (Section IV-A/B, Algorithm 2) lets every thread
+// keep sampling across an epoch transition: samples are written to the state
+// frame of their own epoch, and the stopping condition is checked on the
+// aggregate of complete epochs only.  On one GPU the same idea becomes: a
+// persistent launch hands out sample indices in order; sample i belongs to
+// epoch e = i / E and logs its interior vertices in frame e mod F; the CTA
+// that finishes the last sample of epoch e (which must be the next epoch in
+// order) folds frame e into c~ and evaluates the stopping condition on exactly
+// samples [0, (e+1) E), while every other CTA keeps sampling later epochs.  A
+// frame is the epoch's log of interior vertices (at most VD - 2 per sample);
+// folding it costs O(E * path length), not O(n).  A CTA may start a sample of
+// epoch e only once epoch e - F has been folded (its frame is free); that
+// wait is bounded.  Samples of epochs after the
+// stopping epoch are discarded, so tau, c~ and the stop epoch are those of
+// epoch-by-epoch sampling with the same E.
+
+template <int NT>
+struct PipeSmem {
+    int take;                 // 1: this CTA has a sample to run
+    long long epoch;          // its epoch
+    unsigned long long idx;   // its sample index (relative)
+    int try_check;
+    int acquired;
+    int go;                   // inner loop: fold the next epoch
+    int again;                // after releasing the checker role: try to take it again
+    long long chk_epoch;
+    double mf[NT / 32], mg[NT / 32];
+};
+
+// Fold one epoch's log into c~ and evaluate the stopping functions (CTA-wide).
+//
+// The check needs max_x f(c~(x), L(x)) and max_x g(...).  Vertices with the
+// same budgets (L_L, L_U) form a class; every step of f and g is a correctly
+// rounded monotone operation, so for fixed budgets the computed f and g are
+// non-decreasing in c~(x), and the maximum over a class is attained at the
+// class's largest counter.  The fold keeps those per-class maxima current
+// (counters only grow), so the check evaluates f and g once per class and
+// obtains exactly the per-vertex maxima.  Returns error bits.
+template <int NT>
+__device__ unsigned int fold_and_check(const PipeLaunch &P, uint32_t *counts, const uint32_t *log, unsigned int len,
+                                       unsigned long long tau, PipeSmem<NT> &ps, double &Mf, double &Mg)
+{
+    unsigned int err = 0;
+    for (unsigned int i = threadIdx.x; i < len; i += NT) {
+        const unsigned int x = __ldcg(log + i);
+        const unsigned int c = atomicAdd(&counts[x], 1u) + 1u;
+        if (c == 0u) err |= kErrCounterOverflow;
+        // the old maximum is consumed, so the update completes before the barrier
+        const unsigned int before = atomicMax(&P.cmax[__ldg(P.cls + x)], c);
+        if (before == 0xffffffffu) err |= kErrCounterOverflow;
+    }
+    __syncthreads();
+    const StopConsts k = stop_consts(tau, P.omega);
+    double mf = 0.0, mg = 0.0;
+    for (int cl = threadIdx.x; cl < P.nclass; cl += NT) {
+        double f, g;
+        stop_fg(k, __ldcg(P.cmax + cl), __ldg(P.Ltab + cl), f, g);
+        mf = fmax_exact(mf, f);
+        mg = fmax_exact(mg, g);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        mf = fmax_exact(mf, __shfl_xor_sync(0xffffffffu, mf, o));
+        mg = fmax_exact(mg, __shfl_xor_sync(0xffffffffu, mg, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        ps.mf[threadIdx.x >> 5] = mf;
+        ps.mg[threadIdx.x >> 5] = mg;
+    }
+    __syncthreads();
+    Mf = 0.0;
+    Mg = 0.0;
+#pragma unroll
+    for (int i = 0; i < NT / 32; ++i) {
+        Mf = fmax_exact(Mf, ps.mf[i]);
+        Mg = fmax_exact(Mg, ps.mg[i]);
+    }
+    __syncthreads();
+    return err;
+}
+
+template <int NT, typename OffT>
+__global__ void __launch_bounds__(NT, (2048 / NT / 2) > 0 ? (2048 / NT / 2) : 1) pipe_kernel(PipeLaunch P)
+{
+    __shared__ Smem<NT> sh;
+    __shared__ PipeSmem<NT> pm;
+    const SampleLaunch &a = P.s;
+    const int tid = threadIdx.x;
+    GraphRef<OffT> G{reinterpret_cast<const OffT *>(a.off), a.adj, (long long)a.n};
+    SlotRec *rec = a.recs + (size_t)blockIdx.x * (size_t)a.n;
+    uint32_t *queue = a.queues + (size_t)blockIdx.x * (size_t)a.n;
+    Job *job = a.job;
+    PipeState *st = P.ps;
+    volatile PipeState *vst = P.ps;
+    volatile Job *vjob = a.job;
+
+    __shared__ unsigned long long s_base, s_R;
+    if (tid == 0) {
+        s_base = vjob->tau;
+        s_R = a.clip > s_base ? a.clip - s_base : 0ULL;
+    }
+    __syncthreads();
+    const unsigned long long base = s_base, R = s_R;
+    const unsigned long long E = (unsigned long long)P.E;
+    const long long nE = (long long)((R + E - 1) / E);     // epochs up to the cap
+    auto epoch_size = [&](long long e) -> unsigned long long {
+        const unsigned long long lo = (unsigned long long)e * E;
+        return R - lo < E ? R - lo : E;
+    };
+
+    LocalStats ls = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (;;) {
+        if (tid == 0) {
+            pm.take = 0;
+            if (!vst->abort && !vjob->stopped) {
+                const unsigned long long i = atomicAdd(&st->next_idx, 1ULL);
+                if (i < R) {
+                    const long long e = (long long)(i / E);
+                    // wait until epoch e - F has been folded (bounded)
+                    unsigned long long polls = 0;
+                    bool ok = true;
+                    while (e >= vst->next_check + P.F) {
+                        if (vjob->stopped || vst->abort) {
+                            ok = false;
+                            break;
+                        }
+                        if (++polls > P.spin_limit) {
+                            atomicOr(&job->error, kErrTimeout);
+                            vst->abort = 1;
+                            ok = false;
+                            break;
+                        }
+                        __nanosleep(256);
+                    }
+                    __threadfence();
+                    if (ok) {
+                        pm.take = 1;
+                        pm.epoch = e;
+                        pm.idx = i;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (!pm.take) break;
+        const long long e = pm.epoch;
+        const int f = (int)(e % P.F);
+        run_sample<NT, OffT>(a, G, rec, queue, sh, base + pm.idx, pm.idx, ls,
+                             CountSink{nullptr, P.logs + (size_t)f * P.log_cap, &st->log_len[f], P.log_cap});
+        if (tid == 0) {
+            __threadfence();    // this sample's counter updates before its completion
+            const unsigned int d = atomicAdd(&st->done[e % P.F], 1u) + 1u;
+            pm.try_check = (d == epoch_size(e)) ? 1 : 0;
+        }
+        __syncthreads();
+        if (!pm.try_check) continue;
+        // this CTA completed an epoch: fold and check every complete epoch in order
+        for (;;) {
+            if (tid == 0) pm.acquired = atomicCAS(&st->checker, 0, 1) == 0;
+            __syncthreads();
+            if (!pm.acquired) break;
+            for (;;) {
+                if (tid == 0) {
+                    const long long ce = vst->next_check;
+                    pm.go = ce < nE && !vjob->stopped && vst->done[ce % P.F] == epoch_size(ce);
+                    pm.chk_epoch = ce;
+                    __threadfence();
+                }
+                __syncthreads();
+                if (!pm.go) break;
+                const long long ce = pm.chk_epoch;
+                const unsigned long long tau = base + (unsigned long long)ce * E + epoch_size(ce);
+                double Mf, Mg;
+                const int cf = (int)(ce % P.F);
+                const unsigned int llen = vst->log_len[cf];
+                unsigned int ferr = 0;
+                if (llen > P.log_cap) {
+                    ferr = kErrLogOverflow;
+                    Mf = Mg = 0.0;
+                } else {
+                    ferr = fold_and_check<NT>(P, a.counts, P.logs + (size_t)cf * P.log_cap, llen, tau, pm, Mf, Mg);
+                }
+                if (ferr) {
+                    atomicOr(&job->error, ferr);
+                    if (tid == 0) vst->abort = 1;
+                    __syncthreads();
+                    break;
+                }
+                if (tid == 0) {
+                    const int stop = ((double)tau >= P.omega) || (Mf < P.eps && Mg < P.eps);
+                    job->tau = tau;
+                    job->last_maxf = Mf;
+                    job->last_maxg = Mg;
+                    if (stop) {
+                        job->stop_epoch = job->epoch;
+                        job->stopped = 1;
+                    }
+                    job->epoch += 1;
+                    st->done[ce % P.F] = 0u;
+                    st->log_len[ce % P.F] = 0u;
+                    __threadfence();
+                    st->next_check = ce + 1;     // frees the frame for epoch ce + F
+                    __threadfence();
+                }
+                __syncthreads();
+            }
+            // release, then look again: an epoch completed while this CTA held
+            // the checker role is picked up here
+            if (tid == 0) {
+                __threadfence();
+                atomicExch(&st->checker, 0);
+                __threadfence();
+                const long long ce = vst->next_check;
+                pm.again = ce < nE && !vjob->stopped && vst->done[ce % P.F] == epoch_size(ce);
+            }
+            __syncthreads();
+            if (!pm.again) break;
+        }
+    }
+
+    if (tid == 0) {
+        atomicAdd(&job->total.samples, ls.samples);
+        atomicAdd(&job->total.connected, ls.connected);
+        atomicAdd(&job->total.e_scan, ls.e_scan);
+        atomicAdd(&job->total.expanded, ls.expanded);
+        atomicAdd(&job->total.touched, ls.touched);
+        atomicAdd(&job->total.interior, ls.interior);
+        atomicAdd(&job->total.walk_scan, ls.walk_scan);
+        atomicAdd(&job->total.scaled, ls.scaled);
+        if (a.launch_ctr) {
+            atomicAdd(&a.launch_ctr->samples, ls.samples);
+            atomicAdd(&a.launch_ctr->connected, ls.connected);
+            atomicAdd(&a.launch_ctr->e_scan, ls.e_scan);
+            atomicAdd(&a.launch_ctr->expanded, ls.expanded);
+            atomicAdd(&a.launch_ctr->touched, ls.touched);
+            atomicAdd(&a.launch_ctr->interior, ls.interior);
+            atomicAdd(&a.launch_ctr->walk_scan, ls.walk_scan);
+            atomicAdd(&a.launch_ctr->scaled, ls.scaled);
+        }
+    }
+}
+
+// cmax[class] = max c~ over the class's vertices (cmax zeroed beforehand)
+__global__ void class_max_kernel(long long n, const uint32_t *counts, const uint32_t *cls, unsigned int *cmax)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += stride) {
+        const unsigned int c = __ldg(counts + x);
+        if (c) atomicMax(&cmax[__ldg(cls + x)], c);
     }
 }
 
@@ -974,6 +1246,41 @@ cudaError_t launch_build_adj(int64_t nnz, const void *off, int off64, const int3
         build_adj_kernel<long long><<<grid, 256, 0, st>>>((long long)nnz, static_cast<const long long *>(off), col, adj);
     else
         build_adj_kernel<int><<<grid, 256, 0, st>>>((long long)nnz, static_cast<const int *>(off), col, adj);
+    return cudaGetLastError();
+}
+
+template <int NT>
+cudaError_t launch_pipe_nt(const PipeLaunch &a, cudaStream_t st)
+{
+    if (a.s.off64)
+        pipe_kernel<NT, long long><<<a.s.grid, NT, 0, st>>>(a);
+    else
+        pipe_kernel<NT, int><<<a.s.grid, NT, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pipe(const PipeLaunch &a, cudaStream_t st)
+{
+    if (a.s.grid <= 0) return cudaSuccess;
+    if (a.F < 1 || a.F > kMaxFrames || a.E < 1) return cudaErrorInvalidValue;
+    switch (a.s.threads) {
+    case 128: return launch_pipe_nt<128>(a, st);
+    case 256: return launch_pipe_nt<256>(a, st);
+    case 512: return launch_pipe_nt<512>(a, st);
+    case 1024: return launch_pipe_nt<1024>(a, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_class_max(int64_t n, const uint32_t *counts, const uint32_t *cls, unsigned int *cmax,
+                             cudaStream_t st)
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long want = (n + 255) / 256;
+    const int grid = (int)(want < (long long)sms * 8 ? want : (long long)sms * 8);
+    class_max_kernel<<<grid > 0 ? grid : 1, 256, 0, st>>>((long long)n, counts, cls, cmax);
     return cudaGetLastError();
 }
 

@@ -52,7 +52,8 @@ class QueryInfo(C.Structure):
                 ("samples", C.c_uint64), ("connected", C.c_uint64), ("e_scan", C.c_uint64),
                 ("expanded", C.c_uint64), ("touched", C.c_uint64), ("interior", C.c_uint64),
                 ("walk_scan", C.c_uint64), ("scaled", C.c_uint64), ("device_error", C.c_uint32),
-                ("slots", C.c_int32), ("threads", C.c_int32), ("offsets_64", C.c_int32)]
+                ("slots", C.c_int32), ("threads", C.c_int32), ("offsets_64", C.c_int32),
+                ("budget_classes", C.c_int32)]
 
 
 class TraceRec(C.Structure):
@@ -96,6 +97,7 @@ SIGNATURES = {
     "kadabra_check_stop": (_ST, [_P, C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_double), _P]),
     "kadabra_check_stop_async": (_ST, [_P, _P]),
     "kadabra_run": (_ST, [_P, _I64, _I64, _I64, _P, C.POINTER(C.c_int)]),
+    "kadabra_run_pipelined": (_ST, [_P, _I64, C.c_int, _P]),
     "kadabra_query_reset": (_ST, [_P, _P]),
     "kadabra_result": (_ST, [_P, _P, _P, C.POINTER(_U64), C.POINTER(_I64), _P]),
     "kadabra_query_get_info": (_ST, [_P, C.POINTER(QueryInfo), _P]),
@@ -261,6 +263,10 @@ class Query:
         st = C.c_int()
         _check(load().kadabra_run(self.handle, epoch_len, max_epochs, sync_every, _stream(stream), C.byref(st)))
         return bool(st.value)
+
+    def run_pipelined(self, epoch_len, frames=8, stream=None):
+        """Whole adaptive phase as one persistent launch (async)."""
+        _check(load().kadabra_run_pipelined(self.handle, epoch_len, frames, _stream(stream)))
 
     def reset(self, stream=None):
         _check(load().kadabra_query_reset(self.handle, _stream(stream)))

@@ -169,6 +169,44 @@ def test_run_loop_matches_manual_epochs(K, orc):
     assert q.result(btilde=False)["tau"] == R.tau
 
 
+@pytest.mark.parametrize("name,eps,E,frames", [
+    ("er2000", 0.05, 100, 8), ("er2000", 0.05, 7, 1), ("grid64", 0.05, 250, 2), ("rmat14", 0.03, 500, 8),
+    ("rmat14", 0.03, 64, 3), ("rgg5k", 0.05, 300, 16), ("star", 0.05, 50, 4), ("path", 0.05, 200, 8),
+    ("fullgrid64", 0.05, 150, 4),
+])
+def test_pipelined_run_matches_oracle(K, orc, name, eps, E, frames):
+    g = GRAPHS[name]()
+    G = K.Graph.from_inputs(g)
+    q = K.Query(G, eps=eps, delta=0.1, seed=1)
+    q.run_pipelined(E, frames=frames)
+    res = q.result()
+    info = q.info()
+    counts, cal, LL, LU, R = orc.kadabra(g, eps, 0.1, seed=1, epoch_len=E)
+    assert R.stopped and info.stopped == 1
+    assert res["tau"] == R.tau and res["stop_epoch"] == R.stop_epoch == info.epochs - 1
+    assert np.array_equal(res["counts"], counts)
+    assert math.isclose(info.max_f, R.max_f, rel_tol=REL, abs_tol=0)
+    assert math.isclose(info.max_g, R.max_g, rel_tol=REL, abs_tol=0)
+    # a second pipelined launch on a stopped query takes no samples
+    q.run_pipelined(E, frames=frames)
+    assert q.result(btilde=False)["tau"] == R.tau
+
+
+def test_pipelined_run_after_reset_and_until_omega(K, orc):
+    g = GRAPHS["er2000"]()
+    G = K.Graph.from_inputs(g)
+    # eps so small relative to the graph that the run ends at the omega cap
+    q = K.Query(G, eps=0.2, delta=0.9, seed=6, n_calib=50, delta_rule=0)
+    q.run_pipelined(33, frames=2)
+    info = q.info()
+    counts, cal, LL, LU, R = orc.kadabra(g, 0.2, 0.9, seed=6, epoch_len=33, n_calib=50, delta_rule=0)
+    assert info.tau == R.tau and info.stop_epoch == R.stop_epoch
+    assert np.array_equal(q.result()["counts"], counts)
+    q.reset()
+    q.run_pipelined(33, frames=5)
+    assert q.info().tau == R.tau and np.array_equal(q.result()["counts"], counts)
+
+
 def test_reset_reproduces(K):
     g = GRAPHS["rmat12"]()
     G = K.Graph.from_inputs(g)
