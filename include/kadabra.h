@@ -277,6 +277,33 @@ kadabra_status kadabra_last_launch(kadabra_query *q, kadabra_launch_stats *out);
 kadabra_status kadabra_launch_log(kadabra_query *q, int64_t max_entries, kadabra_launch_stats *out,
                                   int64_t *n_out);
 
+/* ---- allocation-free sampling ------------------------------------------ */
+
+/* Size of the library's file-scope device scratch array used by
+ * kadabra_sample_static.  Every device that loads the library holds it until
+ * the process exits. */
+#define KADABRA_STATIC_SCRATCH_BYTES (64u << 20)
+
+/* Adaptive-phase style sampling for callers that cannot allocate device
+ * memory: for example, a service that plans all memory at start-up and
+ * forbids allocation afterwards, or code inside a framework that owns the
+ * device allocator.  The paper has no counterpart; this is a packaging of the
+ * sampling kernel.
+ * Takes sample indices [first, first + count) of stream `tag` (0 calibration,
+ * 1 adaptive) under `seed`, exactly as kadabra_sample_epoch / the calibration
+ * do, and adds each sampled path's interior vertices to counts[n] (device
+ * pointer, caller-owned, accumulated, not cleared).  The scratch lives in a
+ * fixed array of KADABRA_STATIC_SCRATCH_BYTES inside the library; nothing is
+ * allocated.  Graphs need n * 20 bytes per in-flight sample, so n must satisfy
+ * n * 20 <= KADABRA_STATIC_SCRATCH_BYTES - 256 (else KADABRA_ERR_INVALID_ARG),
+ * and fewer samples run in parallel as n grows.
+ * The first call on a device looks up the array's device address (make that
+ * first call before any stream capture).  All calls share the array: calls
+ * that overlap on the GPU race and must be serialised by the caller.
+ * Synchronises `cuda_stream` and reports device errors. */
+kadabra_status kadabra_sample_static(const kadabra_graph *g, uint64_t seed, int tag, uint64_t first, int64_t count,
+                                     uint32_t *counts, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -31,6 +31,7 @@ CXX_FLAGS = ["-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-fno-fast-math"
 UNITS = [
     ("sample_kernel.cu", "nvcc", []),
     ("check_kernel.cu", "nvcc", ["-fmad=false"]),
+    ("sample_static.cu", "nvcc", []),
     ("kadabra_api.cpp", "cxx", []),
 ]
 

@@ -105,6 +105,28 @@ struct kadabra_query {
     kadabra::PipeState *d_pipe = nullptr;
 };
 
+namespace kadabra {
+
+bool graph_view(const kadabra_graph *g, GraphView *out)
+{
+    if (!g || !out) return false;
+    out->n = g->n;
+    out->nnz = g->nnz;
+    out->max_degree = g->max_degree;
+    out->off64 = g->off64;
+    out->off = g->d_off;
+    out->adj = g->d_adj;
+    return true;
+}
+
+int set_last_error(int status, const char *msg)
+{
+    g_last_error = msg;
+    return status;
+}
+
+}  // namespace kadabra
+
 // ---------------------------------------------------------------------------
 // errors, version, params
 // ---------------------------------------------------------------------------

@@ -4,6 +4,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+struct kadabra_graph;
+
 namespace kadabra {
 
 // Per-vertex sampling state of one in-flight sample (one "slot"): one 64-bit
@@ -138,6 +140,21 @@ struct CheckLaunch {
 };
 
 cudaError_t launch_check(const CheckLaunch &a, cudaStream_t st);
+
+// Read-only view of a loaded graph's device arrays (kadabra_api.cpp).
+struct GraphView {
+    int64_t n, nnz, max_degree;
+    int off64;
+    const void *off;
+    const uint2 *adj;
+};
+bool graph_view(const struct ::kadabra_graph *g, GraphView *out);
+// Record the message returned by kadabra_last_error() on this thread.
+int set_last_error(int status, const char *msg);
+
+// Allocation-free sampling (sample_static.cu).
+cudaError_t static_scratch_address(void **out);
+cudaError_t launch_static_job_init(Job *job, unsigned long long first, cudaStream_t st);
 cudaError_t launch_result(int64_t n, const uint32_t *counts, const Job *job, double *btilde,
                           cudaStream_t st);
 cudaError_t launch_reset_job(Job *job, cudaStream_t st);

@@ -1,0 +1,158 @@
+// Allocation-free sampling: the sampling kernel with its scratch (job state,
+// per-slot records and queues) in one file-scope device array instead of
+// memory the library allocates.
+//
+// Who needs this: callers that must not allocate device memory after start-up
+// -- services that plan all memory once and forbid allocation on the request
+// path, code embedded in a host framework that owns the device allocator, or
+// work issued where cudaMalloc is not allowed.  They pass only their own
+// inputs (a loaded graph) and outputs (a device counter array).
+//
+// The array is fixed at kStaticScratchBytes and exists on every device that
+// loads this library, for as long as the process runs.  Every call reuses it,
+// so calls that overlap on the GPU (different streams, or different host
+// threads without ordering) race on it; serialise them.
+
+#include <cstdint>
+#include <mutex>
+
+#include <cuda_runtime.h>
+
+#include "kadabra.h"
+#include "kadabra_internal.h"
+
+namespace kadabra {
+
+constexpr size_t kStaticScratchBytes = size_t(KADABRA_STATIC_SCRATCH_BYTES);
+constexpr size_t kStaticJobBytes = 256;   // the Job record, padded to the array's alignment
+static_assert(sizeof(Job) <= kStaticJobBytes, "job state must fit its reserved bytes");
+
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mutex;
+void *g_static_ptr[kMaxDevices] = {};
+
+__global__ void static_job_init(Job *job, unsigned long long first)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        Job z;
+        unsigned char *p = reinterpret_cast<unsigned char *>(&z);
+        for (size_t i = 0; i < sizeof(Job); ++i) p[i] = 0;
+        z.stop_epoch = -1;
+        z.tau = first;
+        *job = z;
+    }
+}
+
+}  // namespace
+
+// Device address of the static scratch on the current device; looked up once
+// per device (the first call on a device does it).
+cudaError_t static_scratch_address(void **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_static_mutex);
+    if (!g_static_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess) return e;
+        g_static_ptr[dev] = p;
+    }
+    *out = g_static_ptr[dev];
+    return cudaSuccess;
+}
+
+cudaError_t launch_static_job_init(Job *job, unsigned long long first, cudaStream_t st)
+{
+    static_job_init<<<1, 32, 0, st>>>(job, first);
+    return cudaGetLastError();
+}
+
+}  // namespace kadabra
+
+namespace {
+
+kadabra_status static_fail(kadabra_status st, const char *msg)
+{
+    return (kadabra_status)kadabra::set_last_error((int)st, msg);
+}
+
+kadabra_status static_cuda_fail(cudaError_t e)
+{
+    return static_fail(e == cudaErrorNoDevice ? KADABRA_ERR_NO_DEVICE : KADABRA_ERR_CUDA, cudaGetErrorString(e));
+}
+
+}  // namespace
+
+// Layout of the array for one call: [Job | slots * n records | slots * n queue entries].
+extern "C" kadabra_status kadabra_sample_static(const kadabra_graph *g, uint64_t seed, int tag, uint64_t first,
+                                                int64_t count, uint32_t *counts, void *cuda_stream)
+{
+    using namespace kadabra;
+    GraphView G;
+    if (!graph_view(g, &G)) return static_fail(KADABRA_ERR_INVALID_ARG, "graph is null");
+    if (!counts) return static_fail(KADABRA_ERR_INVALID_ARG, "counts is null");
+    if (tag != 0 && tag != 1) return static_fail(KADABRA_ERR_INVALID_ARG, "tag must be 0 or 1");
+    if (count < 0 || count >= (int64_t(1) << 32)) return static_fail(KADABRA_ERR_INVALID_ARG, "count must be in [0, 2^32)");
+    if (G.n < 2) return static_fail(KADABRA_ERR_INVALID_ARG, "sampling pairs needs n >= 2");
+    const size_t per_slot = (size_t)G.n * (sizeof(SlotRec) + sizeof(uint32_t));
+    const size_t max_slots = (kStaticScratchBytes - kStaticJobBytes) / per_slot;
+    if (max_slots < 1)
+        return static_fail(KADABRA_ERR_INVALID_ARG,
+                           "graph too large for the static scratch: n * 20 bytes must fit in "
+                           "KADABRA_STATIC_SCRATCH_BYTES - 256");
+    if (count == 0) return KADABRA_OK;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
+    const int threads = 1024;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = sample_occupancy(threads, G.off64, &per_sm);
+    if (e != cudaSuccess) return static_cuda_fail(e);
+    size_t slots = (size_t)(sms > 0 ? sms : 1) * (size_t)(per_sm > 0 ? per_sm : 1);
+    if (slots > max_slots) slots = max_slots;
+    if (slots > (size_t)count) slots = (size_t)count;
+
+    void *base = nullptr;
+    e = static_scratch_address(&base);
+    if (e != cudaSuccess) return static_cuda_fail(e);
+    unsigned char *bytes = static_cast<unsigned char *>(base);
+    Job *job = reinterpret_cast<Job *>(bytes);
+    SlotRec *recs = reinterpret_cast<SlotRec *>(bytes + kStaticJobBytes);
+    uint32_t *queues = reinterpret_cast<uint32_t *>(bytes + kStaticJobBytes + slots * (size_t)G.n * sizeof(SlotRec));
+
+    // the sampler requires all-zero records and a fresh job record
+    e = cudaMemsetAsync(recs, 0, slots * (size_t)G.n * sizeof(SlotRec), st);
+    if (e == cudaSuccess) e = launch_static_job_init(job, first, st);
+    SampleLaunch a{};
+    a.n = G.n;
+    a.off = G.off;
+    a.off64 = G.off64;
+    a.adj = G.adj;
+    a.recs = recs;
+    a.queues = queues;
+    a.counts = counts;
+    a.job = job;
+    a.seed = seed;
+    a.tag = (uint32_t)tag;
+    a.K = kadabra_sigma_bits(G.n, G.max_degree);
+    a.epoch_len = count;
+    a.grid = (int)slots;
+    a.threads = threads;
+    if (e == cudaSuccess) e = launch_sample(a, st);
+    unsigned int err = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&err, &job->error, sizeof(err), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return static_cuda_fail(e);
+    if (err & kErrSigmaOverflow) return static_fail(KADABRA_ERR_SIGMA_OVERFLOW, "a per-side path count exceeded 2^K");
+    if (err & kErrCounterOverflow) return static_fail(KADABRA_ERR_COUNTER_OVERFLOW, "a 32-bit counter wrapped");
+    if (err & kErrDepth) return static_fail(KADABRA_ERR_DEPTH, "a BFS side needed more than 65533 layers");
+    if (err) return static_fail(KADABRA_ERR_CUDA, "internal sampling invariant violated");
+    return KADABRA_OK;
+}

@@ -105,6 +105,7 @@ SIGNATURES = {
     "kadabra_sample_trace": (_ST, [_P, C.c_int, _U64, _I64, _P, _P, _I64, _P]),
     "kadabra_last_launch": (_ST, [_P, C.POINTER(LaunchStats)]),
     "kadabra_launch_log": (_ST, [_P, _I64, _P, C.POINTER(_I64)]),
+    "kadabra_sample_static": (_ST, [_P, _U64, C.c_int, _U64, _I64, _P, _P]),
 }
 
 _lock = threading.Lock()
@@ -327,6 +328,14 @@ class Query:
             self.free()
         except Exception:
             pass
+
+
+def sample_static(graph: Graph, seed, tag, first, count, counts_device_ptr, stream=None):
+    """kadabra_sample_static: sampling with the library's fixed scratch array
+    (no device allocation); adds interior-vertex counts to a caller-owned
+    device array."""
+    _check(load().kadabra_sample_static(graph.handle, seed, tag, first, count, C.c_void_p(int(counts_device_ptr)),
+                                        _stream(stream)))
 
 
 # C-ABI names, for callers that prefer the flat interface
