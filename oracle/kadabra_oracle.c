@@ -441,14 +441,18 @@ double orc_omega(double eps, double delta, int64_t vd)
  * rule 1 (balanced): delta_L = delta_U = exp(-C eps^2 / bhat(x)) + beta delta / (4n),
  *   bhat(x) = cal(x) / n_cal, C the bisection result on [0, ln(4n/((1-beta)delta))/eps^2]
  *   so that sum_x exp(-C eps^2 / bhat(x)) <= (1 - beta) delta / 4, i.e. the
- *   per-vertex budgets sum to at most delta/2 (the rest of delta goes to omega). */
-static double balanced_sum(int64_t n, const uint32_t *cal, int64_t n_cal, double eps, double C)
+ *   per-vertex budgets sum to at most delta/2 (the rest of delta goes to omega).
+ *   The sum runs over calibration counts c (vertices with equal counts have
+ *   equal terms): sum_c #{x : cal(x) = c} * exp(-C eps^2 n_cal / c). */
+static double balanced_sum(const int64_t *hist, uint32_t cmax, int64_t n_cal, double eps, double C)
 {
+    /* sum over vertices with a calibration count c > 0 of exp(-C eps^2 / bhat),
+     * bhat = c / n_cal, grouped by c in ascending order */
     double sum = 0.0;
-    for (int64_t x = 0; x < n; x++) {
-        if (cal[x] == 0) continue;
-        double bhat = (double)cal[x] / (double)n_cal;
-        sum += exp(-((C * (eps * eps)) / bhat));
+    for (uint32_t c = 1; c <= cmax; c++) {
+        if (hist[c] == 0) continue;
+        double bhat = (double)c / (double)n_cal;
+        sum += (double)hist[c] * exp(-((C * (eps * eps)) / bhat));
     }
     return sum;
 }
@@ -462,14 +466,19 @@ void orc_calibrate_L(int64_t n, const uint32_t *cal, int64_t n_cal, double eps, 
         if (C_out) *C_out = 0.0;
         return;
     }
+    uint32_t cmax = 0;
+    for (int64_t x = 0; x < n; x++) if (cal[x] > cmax) cmax = cal[x];
+    int64_t *hist = (int64_t *)calloc((size_t)cmax + 1, sizeof(int64_t));
+    for (int64_t x = 0; x < n; x++) hist[cal[x]]++;
     double budget = (1.0 - beta) * delta / 4.0;
     double lo = 0.0;
     double hi = log(4.0 * (double)n / ((1.0 - beta) * delta)) / (eps * eps);
     while (hi - lo > eps / 10.0) {
         double mid = (lo + hi) / 2.0;
-        if (balanced_sum(n, cal, n_cal, eps, mid) <= budget) hi = mid;
+        if (balanced_sum(hist, cmax, n_cal, eps, mid) <= budget) hi = mid;
         else lo = mid;
     }
+    free(hist);
     double C = hi;
     double floor_term = beta * delta / (4.0 * (double)n);
     for (int64_t x = 0; x < n; x++) {
