@@ -160,10 +160,14 @@ def algorithmic_bytes(ls, offset_bytes):
             + 4 * ls.interior)
 
 
+KERNEL_SOURCES = ("sample_kernel.cu", "philox.cuh", "stop_math.cuh")
+
+
 def kernel_digest():
+    """Digest of the sources the sampling kernels are compiled from."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1910_11039_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
+    for name in KERNEL_SOURCES:
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(name.encode() + f.read())
     return h.hexdigest()[:16]

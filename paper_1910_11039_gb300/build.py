@@ -32,6 +32,7 @@ UNITS = [
     ("sample_kernel.cu", "nvcc", []),
     ("check_kernel.cu", "nvcc", ["-fmad=false"]),
     ("sample_static.cu", "nvcc", []),
+    ("graph_kernels.cu", "nvcc", []),
     ("kadabra_api.cpp", "cxx", []),
 ]
 

@@ -1,0 +1,254 @@
+// Graph-wide kernels of the diameter phase (arXiv 1910.11039, Section III-A:
+// the diameter is the main ingredient of omega).
+//
+// The vertex-diameter bound used for omega is, per connected component,
+// 2 * ecc(smallest vertex id) + 1, maximised over components.  On the device:
+//   1. components by union-find: every edge links the larger of its two roots
+//      under the smaller (CAS), so each component's root is its smallest id;
+//   2. one breadth-first search from all roots at once: a vertex's level is its
+//      distance from its own component's root, so the largest level is the
+//      largest eccentricity and the bound is 2 * (largest level) + 1.
+// The search runs in one cooperative launch (all CTAs resident) with a grid
+// barrier between levels; every wait in it is bounded and reports an error
+// flag instead of hanging.
+
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "kadabra_internal.h"
+
+namespace kadabra {
+namespace {
+
+constexpr unsigned int kUnvisited = 0xffffffffu;
+constexpr unsigned long long kSpinLimit = 1ULL << 26;
+
+__device__ __forceinline__ unsigned int find_root(unsigned int *parent, unsigned int x)
+{
+    // path halving; parents only ever decrease, so racing writes are benign
+    unsigned int p = __ldcg(parent + x);
+    while (p != x) {
+        const unsigned int gp = __ldcg(parent + p);
+        if (gp != p) __stcg(parent + x, gp);
+        x = p;
+        p = gp;
+    }
+    return x;
+}
+
+template <typename OffT>
+__global__ void cc_hook_kernel(long long n, const OffT *off, const uint2 *adj, unsigned int *parent, unsigned int *err)
+{
+    // one warp per vertex, lanes stride its adjacency
+    const int lane = threadIdx.x & 31;
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long u = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); u < n; u += warps) {
+        const long long b = (long long)__ldg(off + u), e = (long long)__ldg(off + u + 1);
+        for (long long i = b + lane; i < e; i += 32) {
+            const unsigned int v = __ldg(&adj[i].x);
+            if (v <= (unsigned int)u) continue;   // each undirected edge once
+            unsigned long long tries = 0;
+            for (;;) {
+                unsigned int ru = find_root(parent, (unsigned int)u), rv = find_root(parent, v);
+                if (ru == rv) break;
+                const unsigned int big = ru > rv ? ru : rv, small = ru > rv ? rv : ru;
+                if (atomicCAS(parent + big, big, small) == big) break;
+                if (++tries > kSpinLimit) {
+                    atomicOr(err, 1u);
+                    break;
+                }
+            }
+        }
+    }
+}
+
+__global__ void cc_init_kernel(long long n, unsigned int *parent, unsigned int *dist, unsigned int *queue,
+                               unsigned int *qlen)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        parent[v] = (unsigned int)v;
+        dist[v] = kUnvisited;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *qlen = 0;
+    (void)queue;
+}
+
+// roots (parent[v] == v after hooking) start the search at level 0
+__global__ void roots_kernel(long long n, unsigned int *parent, unsigned int *dist, unsigned int *queue,
+                             unsigned int *qlen)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        if (find_root(parent, (unsigned int)v) == (unsigned int)v) {
+            dist[v] = 0;
+            queue[atomicAdd(qlen, 1u)] = (unsigned int)v;
+        }
+    }
+}
+
+struct BfsState {
+    unsigned int len[2];       // frontier sizes of the two queues
+    unsigned int arrive;       // grid barrier arrivals
+    unsigned int gen;          // grid barrier generation
+    unsigned int level;        // largest level reached
+    unsigned int err;
+};
+
+__device__ bool grid_barrier(BfsState *s)
+{
+    __syncthreads();
+    __shared__ int ok;
+    if (threadIdx.x == 0) {
+        ok = 1;
+        volatile unsigned int *gen = &s->gen;
+        const unsigned int g = *gen;
+        __threadfence();
+        if (atomicAdd(&s->arrive, 1u) == gridDim.x - 1) {
+            s->arrive = 0;
+            __threadfence();
+            atomicAdd(&s->gen, 1u);
+        } else {
+            unsigned long long spins = 0;
+            while (*gen == g) {
+                if (++spins > kSpinLimit) {
+                    atomicOr(&s->err, 2u);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+template <typename OffT>
+__global__ void msbfs_kernel(long long n, const OffT *off, const uint2 *adj, unsigned int *dist, unsigned int *q0,
+                             unsigned int *q1, BfsState *s)
+{
+    unsigned int *q[2] = {q0, q1};
+    int cur = 0;
+    for (unsigned int level = 0;; ++level) {
+        const unsigned int len = *reinterpret_cast<volatile unsigned int *>(&s->len[cur]);
+        if (len == 0) break;
+        if (blockIdx.x == 0 && threadIdx.x == 0) s->level = level;
+        unsigned int *nextq = q[cur ^ 1];
+        // one warp per frontier vertex: lanes stride its adjacency
+        const int lane = threadIdx.x & 31;
+        const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+        for (long long i = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < len; i += warps) {
+            const unsigned int u = __ldcg(q[cur] + i);
+            const long long b = (long long)__ldg(off + u), e = (long long)__ldg(off + u + 1);
+            for (long long k = b + lane; k < e; k += 32) {
+                const unsigned int w = __ldg(&adj[k].x);
+                if (__ldcg(dist + w) == kUnvisited && atomicCAS(dist + w, kUnvisited, level + 1) == kUnvisited)
+                    __stcg(nextq + atomicAdd(&s->len[cur ^ 1], 1u), w);
+            }
+        }
+        if (!grid_barrier(s)) return;
+        // every CTA has read len[cur]; one clears it for reuse two levels on
+        if (blockIdx.x == 0 && threadIdx.x == 0) s->len[cur] = 0;
+        if (!grid_barrier(s)) return;
+        cur ^= 1;
+    }
+}
+
+__global__ void max_degree_kernel_i32(long long n, const int *off, unsigned long long *out)
+{
+    unsigned long long m = 0;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        const unsigned long long d = (unsigned long long)((long long)off[v + 1] - (long long)off[v]);
+        m = d > m ? d : m;
+    }
+    atomicMax(out, m);
+}
+
+__global__ void max_degree_kernel_i64(long long n, const long long *off, unsigned long long *out)
+{
+    unsigned long long m = 0;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        const unsigned long long d = (unsigned long long)(off[v + 1] - off[v]);
+        m = d > m ? d : m;
+    }
+    atomicMax(out, m);
+}
+
+int sm_count()
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 1;
+}
+
+template <typename OffT>
+cudaError_t vd_bound_t(int64_t n, const OffT *off, const uint2 *adj, unsigned int *scratch, cudaStream_t st,
+                       int64_t *vd)
+{
+    // scratch: parent[n], dist[n], q0[n], q1[n] (4n u32) followed by BfsState
+    unsigned int *parent = scratch;
+    unsigned int *dist = scratch + n;
+    unsigned int *q0 = scratch + 2 * n;
+    unsigned int *q1 = scratch + 3 * n;
+    BfsState *s = reinterpret_cast<BfsState *>(scratch + 4 * n);
+    const int sms = sm_count();
+    const int grid = (int)((n + 255) / 256 < (int64_t)sms * 8 ? (n + 255) / 256 : (int64_t)sms * 8);
+    cudaError_t e = cudaMemsetAsync(s, 0, sizeof(BfsState), st);
+    if (e != cudaSuccess) return e;
+    cc_init_kernel<<<grid, 256, 0, st>>>((long long)n, parent, dist, q0, &s->len[0]);
+    cc_hook_kernel<OffT><<<grid, 256, 0, st>>>((long long)n, off, adj, parent, &s->err);
+    roots_kernel<<<grid, 256, 0, st>>>((long long)n, parent, dist, q0, &s->len[0]);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // cooperative launch: every CTA is resident, so the grid barrier is safe
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, msbfs_kernel<OffT>, 256, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    const int bgrid = sms * (per_sm < 4 ? per_sm : 4);
+    long long nn = (long long)n;
+    void *args[] = {&nn, (void *)&off, (void *)&adj, &dist, &q0, &q1, &s};
+    e = cudaLaunchCooperativeKernel((const void *)msbfs_kernel<OffT>, dim3(bgrid), dim3(256), args, 0, st);
+    if (e != cudaSuccess) return e;
+    BfsState hs;
+    e = cudaMemcpyAsync(&hs, s, sizeof(hs), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return e;
+    if (hs.err) return cudaErrorLaunchTimeout;
+    *vd = 2 * (int64_t)hs.level + 1;
+    return cudaSuccess;
+}
+
+}  // namespace
+
+size_t vd_bound_scratch_bytes(int64_t n) { return (size_t)n * 16 + 64; }
+
+cudaError_t launch_vd_bound(int64_t n, const void *off, int off64, const uint2 *adj, void *scratch, cudaStream_t st,
+                            int64_t *vd)
+{
+    if (n < 1) return cudaErrorInvalidValue;
+    if (off64)
+        return vd_bound_t<long long>(n, static_cast<const long long *>(off), adj, static_cast<unsigned int *>(scratch),
+                                     st, vd);
+    return vd_bound_t<int>(n, static_cast<const int *>(off), adj, static_cast<unsigned int *>(scratch), st, vd);
+}
+
+cudaError_t launch_max_degree(int64_t n, const void *off, int off64, unsigned long long *out, cudaStream_t st)
+{
+    const int sms = sm_count();
+    const int grid = (int)((n + 255) / 256 < (int64_t)sms * 4 ? (n + 255) / 256 : (int64_t)sms * 4);
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    if (off64)
+        max_degree_kernel_i64<<<grid > 0 ? grid : 1, 256, 0, st>>>((long long)n, static_cast<const long long *>(off), out);
+    else
+        max_degree_kernel_i32<<<grid > 0 ? grid : 1, 256, 0, st>>>((long long)n, static_cast<const int *>(off), out);
+    return cudaGetLastError();
+}
+
+}  // namespace kadabra

@@ -61,8 +61,6 @@ struct kadabra_graph {
     int off64 = 0;
     void *d_off = nullptr;
     uint2 *d_adj = nullptr;       // (neighbour, neighbour degree) per adjacency entry
-    std::vector<int64_t> h_off;   // host copy for the diameter phase
-    std::vector<int32_t> h_col;
     // sampling scratch shared by the graph's queries
     kadabra::SlotRec *d_recs = nullptr;
     uint32_t *d_queues = nullptr;
@@ -239,83 +237,61 @@ extern "C" int kadabra_sigma_bits(int64_t n, int64_t max_degree)
     return a < b ? a : b;
 }
 
-// Vertex-diameter upper bound: per component, 2 * ecc(smallest id) + 1.
-static int64_t vd_bound(const kadabra_graph *g)
-{
-    const int64_t n = g->n;
-    std::vector<int32_t> dist((size_t)n, -1);
-    std::vector<int32_t> q((size_t)n);
-    int64_t best = 1;
-    for (int64_t r = 0; r < n; ++r) {
-        if (dist[(size_t)r] != -1) continue;
-        int64_t head = 0, tail = 0, ecc = 0;
-        dist[(size_t)r] = 0;
-        q[(size_t)tail++] = (int32_t)r;
-        while (head < tail) {
-            const int32_t u = q[(size_t)head++];
-            const int32_t du = dist[(size_t)u];
-            if (du > ecc) ecc = du;
-            for (int64_t i = g->h_off[(size_t)u]; i < g->h_off[(size_t)u + 1]; ++i) {
-                const int32_t w = g->h_col[(size_t)i];
-                if (dist[(size_t)w] == -1) {
-                    dist[(size_t)w] = du + 1;
-                    q[(size_t)tail++] = w;
-                }
-            }
-        }
-        if (2 * ecc + 1 > best) best = 2 * ecc + 1;
-    }
-    return best;
-}
-
 // delta_L / delta_U -> L = -ln(delta).  Balanced rule: bisection for C with
 // sum_x exp(-C eps^2 / bhat(x)) <= (1 - beta) delta / 4 (bhat = cal / n_cal),
-// delta_L = delta_U = exp(-C eps^2 / bhat) + beta delta / (4n).  The per-vertex
-// sum runs in vertex order; exp is evaluated once per distinct count value
-// (identical arguments give identical results).
+// delta_L = delta_U = exp(-C eps^2 / bhat) + beta delta / (4n).  Vertices with
+// equal calibration counts have equal terms: the sum runs over the distinct
+// counts in ascending order, weighted by how many vertices have each.  Both
+// rules make the budgets a function of the calibration count, so the budget
+// classes (equal (L_L, L_U)) are the distinct counts present (one class for
+// the uniform rule); cls[x] receives the class of every vertex.
 static void budgets(int64_t n, const std::vector<uint32_t> &cal, int64_t n_cal, double eps, double delta, int rule,
-                    double beta, std::vector<double> &LL, std::vector<double> &LU, double *C_out)
+                    double beta, std::vector<double2> &Lx, std::vector<uint32_t> &cls, std::vector<double2> &Ltab,
+                    double *C_out)
 {
-    LL.assign((size_t)n, 0.0);
-    LU.assign((size_t)n, 0.0);
+    Lx.assign((size_t)n, make_double2(0.0, 0.0));
+    cls.assign((size_t)n, 0u);
+    Ltab.clear();
     if (rule == KADABRA_DELTA_UNIFORM) {
         const double dl = delta / (4.0 * (double)n);
-        for (int64_t x = 0; x < n; ++x) {
-            LL[(size_t)x] = -std::log(dl);
-            LU[(size_t)x] = -std::log(dl);
-        }
+        const double2 L = make_double2(-std::log(dl), -std::log(dl));
+        for (int64_t x = 0; x < n; ++x) Lx[(size_t)x] = L;
+        Ltab.push_back(L);
         *C_out = 0.0;
         return;
     }
     uint32_t cmax = 0;
     for (uint32_t c : cal) cmax = c > cmax ? c : cmax;
-    std::vector<double> term((size_t)cmax + 1, 0.0);
-    auto fill_terms = [&](double C) {
-        for (uint32_t c = 1; c <= cmax; ++c) {
-            const double bhat = (double)c / (double)n_cal;
-            term[c] = std::exp(-((C * (eps * eps)) / bhat));
-        }
+    std::vector<int64_t> hist((size_t)cmax + 1, 0);
+    for (uint32_t c : cal) ++hist[c];
+    auto term = [&](double C, uint32_t c) {
+        const double bhat = (double)c / (double)n_cal;
+        return std::exp(-((C * (eps * eps)) / bhat));
     };
     const double budget = (1.0 - beta) * delta / 4.0;
     double lo = 0.0;
     double hi = std::log(4.0 * (double)n / ((1.0 - beta) * delta)) / (eps * eps);
     while (hi - lo > eps / 10.0) {
         const double mid = (lo + hi) / 2.0;
-        fill_terms(mid);
         double sum = 0.0;
-        for (int64_t x = 0; x < n; ++x)
-            if (cal[(size_t)x] != 0) sum += term[cal[(size_t)x]];
+        for (uint32_t c = 1; c <= cmax; ++c)
+            if (hist[c]) sum += (double)hist[c] * term(mid, c);
         if (sum <= budget) hi = mid;
         else lo = mid;
     }
     const double C = hi;
-    fill_terms(C);
     const double floor_term = beta * delta / (4.0 * (double)n);
+    std::vector<int32_t> class_of((size_t)cmax + 1, -1);
+    for (uint32_t c = 0; c <= cmax; ++c) {
+        if (!hist[c]) continue;
+        const double dl = c == 0 ? floor_term : term(C, c) + floor_term;
+        class_of[c] = (int32_t)Ltab.size();
+        Ltab.push_back(make_double2(-std::log(dl), -std::log(dl)));
+    }
     for (int64_t x = 0; x < n; ++x) {
-        const uint32_t c = cal[(size_t)x];
-        const double dl = c == 0 ? floor_term : term[c] + floor_term;
-        LL[(size_t)x] = -std::log(dl);
-        LU[(size_t)x] = -std::log(dl);
+        const uint32_t k = (uint32_t)class_of[cal[(size_t)x]];
+        cls[(size_t)x] = k;
+        Lx[(size_t)x] = Ltab[k];
     }
     *C_out = C;
 }
@@ -354,40 +330,42 @@ extern "C" kadabra_status kadabra_graph_load(int64_t n, int64_t nnz, const void 
     g->n = n;
     g->nnz = nnz;
     g->off64 = offsets_is_64 ? 1 : 0;
-    g->h_off.resize((size_t)n + 1);
-    g->h_col.resize((size_t)nnz);
-    // host copy (diameter phase, degree statistics)
-    std::vector<unsigned char> off_raw;
-    const void *hoff = offsets;
-    const int32_t *hcol = cols;
-    if (dev) {
-        off_raw.resize(ob);
-        cudaError_t e = cudaMemcpyAsync(off_raw.data(), offsets, ob, cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess && cb) e = cudaMemcpyAsync(g->h_col.data(), cols, cb, cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) {
-            delete g;
-            return cuda_fail(e, "copy CSR to host");
-        }
-        hoff = off_raw.data();
-        hcol = g->h_col.data();
-    }
+    // host-side checks (host inputs are read in place; device inputs are
+    // copied to the host only when they are to be validated)
     if (!(flags & KADABRA_GRAPH_SKIP_VALIDATE)) {
+        std::vector<unsigned char> off_raw;
+        std::vector<int32_t> col_raw;
+        const void *hoff = offsets;
+        const int32_t *hcol = cols;
+        if (dev) {
+            off_raw.resize(ob);
+            col_raw.resize((size_t)nnz);
+            cudaError_t e = cudaMemcpyAsync(off_raw.data(), offsets, ob, cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess && cb) e = cudaMemcpyAsync(col_raw.data(), cols, cb, cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) {
+                delete g;
+                return cuda_fail(e, "copy CSR to host for validation");
+            }
+            hoff = off_raw.data();
+            hcol = col_raw.data();
+        }
         kadabra_status s = kadabra_validate_csr(n, nnz, hoff, offsets_is_64, hcol);
         if (s != KADABRA_OK) {
             delete g;
             return s;
         }
     }
-    for (int64_t v = 0; v <= n; ++v)
-        g->h_off[(size_t)v] = offsets_is_64 ? static_cast<const int64_t *>(hoff)[v] : static_cast<const int32_t *>(hoff)[v];
-    if (!dev && cb) std::memcpy(g->h_col.data(), cols, cb);
-    int64_t md = 0;
-    for (int64_t v = 0; v < n; ++v) {
-        const int64_t d = g->h_off[(size_t)v + 1] - g->h_off[(size_t)v];
-        md = d > md ? d : md;
+    if (!dev) {
+        int64_t md = 0;
+        for (int64_t v = 0; v < n; ++v) {
+            const int64_t d = offsets_is_64 ? static_cast<const int64_t *>(offsets)[v + 1] - static_cast<const int64_t *>(offsets)[v]
+                                            : (int64_t)static_cast<const int32_t *>(offsets)[v + 1] -
+                                                  (int64_t)static_cast<const int32_t *>(offsets)[v];
+            md = d > md ? d : md;
+        }
+        g->max_degree = md;
     }
-    g->max_degree = md;
 
     // device copy: offsets, and the adjacency as (neighbour, neighbour degree)
     // pairs built on the device from a temporary copy of the columns
@@ -400,7 +378,14 @@ extern "C" kadabra_status kadabra_graph_load(int64_t n, int64_t nnz, const void 
     if (e == cudaSuccess && !dev && cb) e = cudaMemcpyAsync(d_cols_tmp, cols, cb, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
         e = kadabra::launch_build_adj(nnz, g->d_off, g->off64, dev ? cols : d_cols_tmp, g->d_adj, st);
+    unsigned long long *d_md = nullptr;
+    unsigned long long md = 0;
+    if (e == cudaSuccess && dev) e = cudaMalloc(reinterpret_cast<void **>(&d_md), sizeof(unsigned long long));
+    if (e == cudaSuccess && dev) e = kadabra::launch_max_degree(n, g->d_off, g->off64, d_md, st);
+    if (e == cudaSuccess && dev) e = cudaMemcpyAsync(&md, d_md, sizeof(md), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (dev) g->max_degree = (int64_t)md;
+    cudaFree(d_md);
     cudaFree(d_cols_tmp);
     if (e != cudaSuccess) {
         free_graph_device(g);
@@ -560,7 +545,22 @@ extern "C" kadabra_status kadabra_calibrate(kadabra_graph *g, const kadabra_para
     q->threads = p.threads;
     q->K = kadabra_sigma_bits(g->n, g->max_degree);
     // phase 1: diameter -> omega
-    q->vd = p.vertex_diameter > 0 ? p.vertex_diameter : vd_bound(g);
+    if (p.vertex_diameter > 0) {
+        q->vd = p.vertex_diameter;
+    } else {
+        // vertex-diameter bound on the device (union-find components, then one
+        // breadth-first search from every component's smallest vertex)
+        void *scratch = nullptr;
+        cudaError_t e = cudaMalloc(&scratch, kadabra::vd_bound_scratch_bytes(g->n));
+        if (e == cudaSuccess) e = kadabra::launch_vd_bound(g->n, g->d_off, g->off64, g->d_adj, scratch, st, &q->vd);
+        cudaFree(scratch);
+        if (e != cudaSuccess) {
+            delete q;
+            if (e == cudaErrorLaunchTimeout)
+                return fail(KADABRA_ERR_TIMEOUT, "diameter phase: a bounded device wait gave up");
+            return cuda_fail(e, "diameter phase");
+        }
+    }
     kadabra_omega(p.eps, p.delta, q->vd, &q->omega);
     q->omega_ceil = (uint64_t)std::ceil(q->omega);
     if (q->omega_ceil >= (uint64_t(1) << 32)) {
@@ -635,33 +635,10 @@ extern "C" kadabra_status kadabra_calibrate(kadabra_graph *g, const kadabra_para
         delete q;
         return s;
     }
-    std::vector<double> LL, LU;
-    budgets(g->n, cal, q->n_calib, p.eps, p.delta, p.delta_rule, p.beta, LL, LU, &q->balance_C);
-    std::vector<double2> L(n);
-    for (size_t x = 0; x < n; ++x) L[x] = make_double2(LL[x], LU[x]);
-    // budget classes (distinct (L_L, L_U) pairs, numbered in order of first appearance)
-    std::vector<uint32_t> cls(n);
+    std::vector<double2> L;
+    std::vector<uint32_t> cls;
     std::vector<double2> Ltab;
-    {
-        struct PairHash {
-            size_t operator()(const std::pair<uint64_t, uint64_t> &k) const
-            {
-                return std::hash<uint64_t>()(k.first * 0x9E3779B97F4A7C15ULL ^ k.second);
-            }
-        };
-        std::unordered_map<std::pair<uint64_t, uint64_t>, uint32_t, PairHash> ids;
-        for (size_t x = 0; x < n; ++x) {
-            uint64_t a, b;
-            std::memcpy(&a, &LL[x], 8);
-            std::memcpy(&b, &LU[x], 8);
-            auto it = ids.find({a, b});
-            if (it == ids.end()) {
-                it = ids.emplace(std::make_pair(a, b), (uint32_t)Ltab.size()).first;
-                Ltab.push_back(L[x]);
-            }
-            cls[x] = it->second;
-        }
-    }
+    budgets(g->n, cal, q->n_calib, p.eps, p.delta, p.delta_rule, p.beta, L, cls, Ltab, &q->balance_C);
     q->nclass = (int)Ltab.size();
     e = cudaMemcpyAsync(q->d_L, L.data(), n * sizeof(double2), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&q->d_cls), n * 4);

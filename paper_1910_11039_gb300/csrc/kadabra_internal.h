@@ -93,6 +93,11 @@ struct SampleLaunch {
 cudaError_t launch_sample(const SampleLaunch &a, cudaStream_t st);
 cudaError_t launch_build_adj(int64_t nnz, const void *off, int off64, const int32_t *col, uint2 *adj,
                              cudaStream_t st);
+// diameter phase (graph_kernels.cu)
+size_t vd_bound_scratch_bytes(int64_t n);
+cudaError_t launch_vd_bound(int64_t n, const void *off, int off64, const uint2 *adj, void *scratch, cudaStream_t st,
+                            int64_t *vd);
+cudaError_t launch_max_degree(int64_t n, const void *off, int off64, unsigned long long *out, cudaStream_t st);
 cudaError_t sample_occupancy(int threads, int off64, int *ctas_per_sm);
 
 // Pipelined adaptive phase (one persistent launch): epochs rotate through F

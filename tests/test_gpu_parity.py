@@ -297,6 +297,26 @@ def test_disconnected_pairs_count_but_add_nothing(K, orc):
     assert q.info().connected == st.connected
 
 
+@pytest.mark.parametrize("name", ["er2000", "rmat14", "grid64", "grid256", "path", "star", "disjoint", "edgeless",
+                                  "rmat12_raw"])
+def test_vertex_diameter_bound_matches_oracle(K, orc, name):
+    if name == "disjoint":
+        src = np.concatenate([np.arange(49), np.arange(50, 70), [80, 81]])
+        g = I.csr_from_edges(100, src, src + 1)
+    elif name == "edgeless":
+        g = I.csr_from_edges(5, np.zeros(0, dtype=np.int64), np.zeros(0, dtype=np.int64))
+    elif name == "rmat12_raw":
+        g = I.rmat_graph(12, 4, seed=77)        # many components and isolated vertices
+    else:
+        g = GRAPHS[name]() if name in GRAPHS else I.config_graph(name)
+    G = K.Graph.from_inputs(g)
+    q = K.Query(G, eps=0.05, delta=0.1, seed=1, n_calib=10)
+    assert q.info().vertex_diameter == orc.vertex_diameter_bound(g)
+    if name == "edgeless":
+        q.sample_epoch(50)
+        assert q.result(btilde=False)["counts"].sum() == 0 and q.info().connected == 0
+
+
 @pytest.mark.slow
 def test_rmat20_full_size_epoch_and_trace(K, orc):
     """R-MAT scale 20 (the measured workload) at full size, in the launch
@@ -312,6 +332,7 @@ def test_rmat20_full_size_epoch_and_trace(K, orc):
     assert np.array_equal(res["counts"], want)
     info = q.info()
     assert info.e_scan == st.e_scan and info.connected == st.connected
+    assert info.vertex_diameter == orc.vertex_diameter_bound(g)
     recs, paths = q.sample_trace(1, 123456, 64, path_cap=64)
     compare_trace(recs, paths, oracle_trace(orc, g, 1, 1, 123456, 64), 64)
     # calibration counts and budgets at full size
