@@ -234,6 +234,19 @@ kadabra_status kadabra_run(kadabra_query *q, int64_t epoch_len, int64_t max_epoc
  *   the true one) ends the launch with KADABRA_ERR_INVALID_ARG. */
 kadabra_status kadabra_run_pipelined(kadabra_query *q, int64_t epoch_len, int frames, void *cuda_stream);
 
+/* Sharded sampling (several ranks, one GPU each; Section I-A: samples are
+ * independent, so a rank can take any subset of an epoch's sample indices).
+ * kadabra_sample_range takes sample indices [first, first + count) of stream
+ * `tag` (0 calibration, 1 adaptive) with the query's seed and adds the
+ * interior vertices of each sampled path to counts[n] (device pointer,
+ * caller-owned, accumulated); the query's tau and c~ are not touched (async).
+ * kadabra_absorb is the epoch aggregate: it adds delta[n] (device pointer,
+ * e.g. the sum of every rank's counts for one epoch) to c~ and advances tau by
+ * `samples` (async); kadabra_check_stop then checks the new snapshot. */
+kadabra_status kadabra_sample_range(kadabra_query *q, int tag, uint64_t first, int64_t count, uint32_t *counts,
+                                    void *cuda_stream);
+kadabra_status kadabra_absorb(kadabra_query *q, const uint32_t *delta, uint64_t samples, void *cuda_stream);
+
 /* Restart phase 3 (tau = 0, c~ = 0, not stopped) keeping omega and the
  * calibrated budgets (async). */
 kadabra_status kadabra_query_reset(kadabra_query *q, void *cuda_stream);

@@ -96,6 +96,21 @@ __global__ void result_kernel(long long n, const uint32_t *counts, const Job *jo
         btilde[x] = __ddiv_rn((double)__ldg(counts + x), tau_d);
 }
 
+// c~ += delta, tau += samples (one thread block strides, then the tau update)
+__global__ void absorb_kernel(long long n, uint32_t *counts, const uint32_t *delta, Job *job,
+                              unsigned long long samples)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += stride) {
+        const unsigned int d = __ldg(delta + x);
+        if (d) {
+            const unsigned int old = atomicAdd(counts + x, d);
+            if (old + d < old) atomicOr(&job->error, kErrCounterOverflow);
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&job->tau, samples);
+}
+
 __global__ void reset_job_kernel(Job *job)
 {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
@@ -132,6 +147,13 @@ cudaError_t launch_check(const CheckLaunch &a, cudaStream_t st)
 cudaError_t launch_result(int64_t n, const uint32_t *counts, const Job *job, double *btilde, cudaStream_t st)
 {
     result_kernel<<<grid_for(n, 256), 256, 0, st>>>((long long)n, counts, job, btilde);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_absorb(int64_t n, uint32_t *counts, const uint32_t *delta, Job *job, uint64_t samples,
+                          cudaStream_t st)
+{
+    absorb_kernel<<<grid_for(n, 256), 256, 0, st>>>((long long)n, counts, delta, job, (unsigned long long)samples);
     return cudaGetLastError();
 }
 

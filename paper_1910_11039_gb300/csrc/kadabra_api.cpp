@@ -812,6 +812,37 @@ extern "C" kadabra_status kadabra_run(kadabra_query *q, int64_t epoch_len, int64
     return KADABRA_OK;
 }
 
+extern "C" kadabra_status kadabra_sample_range(kadabra_query *q, int tag, uint64_t first, int64_t count,
+                                               uint32_t *counts, void *cuda_stream)
+{
+    if (!q || !counts) return fail(KADABRA_ERR_INVALID_ARG, "query or counts is null");
+    if (tag != 0 && tag != 1) return fail(KADABRA_ERR_INVALID_ARG, "tag must be 0 or 1");
+    if (count < 0 || count >= (int64_t(1) << 32)) return fail(KADABRA_ERR_INVALID_ARG, "count must be in [0, 2^32)");
+    if (count == 0) return KADABRA_OK;
+    cudaStream_t st = as_stream(cuda_stream);
+    kadabra::SampleLaunch a = base_launch(q);
+    a.counts = counts;
+    a.job = q->d_trace_job;
+    a.tag = (uint32_t)tag;
+    a.use_stop = 0;
+    a.epoch_len = count;
+    a.clip = 0;
+    a.grid = clamp_grid(q, count);
+    const unsigned long long tau0 = first;
+    KCUDA(kadabra::launch_reset_job(q->d_trace_job, st), "reset range state");
+    KCUDA(cudaMemcpyAsync(&q->d_trace_job->tau, &tau0, 8, cudaMemcpyHostToDevice, st), "set range start");
+    KCUDA(kadabra::launch_sample(a, st), "sampling kernel launch");
+    return KADABRA_OK;
+}
+
+extern "C" kadabra_status kadabra_absorb(kadabra_query *q, const uint32_t *delta, uint64_t samples, void *cuda_stream)
+{
+    if (!q || !delta) return fail(KADABRA_ERR_INVALID_ARG, "query or delta is null");
+    KCUDA(kadabra::launch_absorb(q->g->n, q->d_counts, delta, q->d_job, samples, as_stream(cuda_stream)),
+          "absorb kernel launch");
+    return KADABRA_OK;
+}
+
 extern "C" kadabra_status kadabra_query_reset(kadabra_query *q, void *cuda_stream)
 {
     if (!q) return fail(KADABRA_ERR_INVALID_ARG, "query is null");

@@ -163,5 +163,7 @@ cudaError_t launch_static_job_init(Job *job, unsigned long long first, cudaStrea
 cudaError_t launch_result(int64_t n, const uint32_t *counts, const Job *job, double *btilde,
                           cudaStream_t st);
 cudaError_t launch_reset_job(Job *job, cudaStream_t st);
+cudaError_t launch_absorb(int64_t n, uint32_t *counts, const uint32_t *delta, Job *job, uint64_t samples,
+                          cudaStream_t st);
 
 }  // namespace kadabra

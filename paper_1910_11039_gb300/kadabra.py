@@ -106,6 +106,8 @@ SIGNATURES = {
     "kadabra_last_launch": (_ST, [_P, C.POINTER(LaunchStats)]),
     "kadabra_launch_log": (_ST, [_P, _I64, _P, C.POINTER(_I64)]),
     "kadabra_sample_static": (_ST, [_P, _U64, C.c_int, _U64, _I64, _P, _P]),
+    "kadabra_sample_range": (_ST, [_P, C.c_int, _U64, _I64, _P, _P]),
+    "kadabra_absorb": (_ST, [_P, _P, _U64, _P]),
 }
 
 _lock = threading.Lock()
@@ -268,6 +270,16 @@ class Query:
     def run_pipelined(self, epoch_len, frames=8, stream=None):
         """Whole adaptive phase as one persistent launch (async)."""
         _check(load().kadabra_run_pipelined(self.handle, epoch_len, frames, _stream(stream)))
+
+    def sample_range(self, tag, first, count, counts_device_ptr, stream=None):
+        """Add the interior vertices of samples [first, first+count) to a
+        caller-owned device counter array (the query's own state is untouched)."""
+        _check(load().kadabra_sample_range(self.handle, tag, first, count, C.c_void_p(int(counts_device_ptr)),
+                                           _stream(stream)))
+
+    def absorb(self, delta_device_ptr, samples, stream=None):
+        """c~ += delta, tau += samples (the epoch aggregate of a sharded run)."""
+        _check(load().kadabra_absorb(self.handle, C.c_void_p(int(delta_device_ptr)), samples, _stream(stream)))
 
     def reset(self, stream=None):
         _check(load().kadabra_query_reset(self.handle, _stream(stream)))

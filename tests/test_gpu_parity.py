@@ -207,6 +207,61 @@ def test_pipelined_run_after_reset_and_until_omega(K, orc):
     assert q.info().tau == R.tau and np.array_equal(q.result()["counts"], counts)
 
 
+def test_sharded_epochs_on_one_gpu(K, orc):
+    """Two ranks' shares of every epoch sampled into separate device arrays,
+    summed and absorbed (the sharded epoch aggregate), equal a single run."""
+    import torch
+    from paper_1910_11039_gb300.distributed import epoch_share
+    g = GRAPHS["rmat14"]()
+    G = K.Graph.from_inputs(g)
+    q = K.Query(G, eps=0.03, delta=0.1, seed=1)
+    E, tau, epochs = 500, 0, 0
+    omega_ceil = q.info().omega_ceil
+    d = [torch.zeros(g.n, dtype=torch.int32, device="cuda") for _ in range(2)]
+    while True:
+        m = min(E, omega_ceil - tau)
+        for r in range(2):
+            d[r].zero_()
+            first, count = epoch_share(tau, m, 2, r)
+            q.sample_range(1, first, count, d[r].data_ptr())
+        d[0] += d[1]
+        q.absorb(d[0].data_ptr(), m)
+        tau += m
+        epochs += 1
+        stopped, mf, mg = q.check_stop()
+        if stopped:
+            break
+    counts, cal, LL, LU, R = orc.kadabra(g, 0.03, 0.1, seed=1, epoch_len=E)
+    res = q.result()
+    assert res["tau"] == R.tau == tau and res["stop_epoch"] == R.stop_epoch == epochs - 1
+    assert np.array_equal(res["counts"], counts)
+    assert math.isclose(mf, R.max_f, rel_tol=REL, abs_tol=0)
+
+
+def test_sharded_run_driver_single_rank(K, orc):
+    import torch
+    import torch.distributed as dist
+    from paper_1910_11039_gb300.distributed import LibraryShard, ShardedRun
+    import os
+    import socket
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    os.environ["MASTER_ADDR"], os.environ["MASTER_PORT"] = "127.0.0.1", str(port)
+    dist.init_process_group("nccl", rank=0, world_size=1)
+    try:
+        g = GRAPHS["er2000"]()
+        G = K.Graph.from_inputs(g)
+        q = K.Query(G, eps=0.05, delta=0.1, seed=1)
+        shard = LibraryShard(q)
+        stopped, tau, epochs = ShardedRun(shard, shard, q.info().omega_ceil, dist).run(100)
+        counts, cal, LL, LU, R = orc.kadabra(g, 0.05, 0.1, seed=1, epoch_len=100)
+        assert stopped and tau == R.tau and epochs == R.stop_epoch + 1
+        assert np.array_equal(q.result()["counts"], counts)
+    finally:
+        dist.destroy_process_group()
+
+
 def test_reset_reproduces(K):
     g = GRAPHS["rmat12"]()
     G = K.Graph.from_inputs(g)
