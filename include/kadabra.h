@@ -234,6 +234,31 @@ kadabra_status kadabra_run(kadabra_query *q, int64_t epoch_len, int64_t max_epoc
  *   the true one) ends the launch with KADABRA_ERR_INVALID_ARG. */
 kadabra_status kadabra_run_pipelined(kadabra_query *q, int64_t epoch_len, int frames, void *cuda_stream);
 
+/* The pipelined phase in steps, and many queries in one launch.
+ * kadabra_pipeline_begin prepares a query's pipelined adaptive phase from its
+ * current tau (epoch logs, per-query pipeline state; async);
+ * kadabra_run_pipelined = begin + one launch run to the end.
+ * A kadabra_batch holds sampling scratch for `slots` samples in flight (0 =
+ * fill the GPU) on graphs of up to max_n vertices, all with the same offset
+ * width.  kadabra_batch_step is one persistent launch over `count` begun
+ * queries, possibly on different graphs (async): CTAs take the next sample
+ * of the running queries in round robin and check each query's epochs in
+ * order exactly as kadabra_run_pipelined does, so every query's tau, c~ and
+ * stop epoch are those it has alone.  The launch ends when every query has
+ * stopped or reached ceil(omega), or after `sample_budget` samples were
+ * handed out (0 = no limit); pipeline state persists, so a later step (with
+ * the same or other begun queries) continues where this one ended.  A batch
+ * must not be stepped on two streams at once. */
+typedef struct kadabra_batch kadabra_batch;
+kadabra_status kadabra_pipeline_begin(kadabra_query *q, int64_t epoch_len, int frames, void *cuda_stream);
+kadabra_status kadabra_batch_create(int64_t max_n, int32_t slots, int32_t threads, int offsets_is_64,
+                                    kadabra_batch **out);
+kadabra_status kadabra_batch_free(kadabra_batch *b);
+kadabra_status kadabra_batch_step(kadabra_batch *b, kadabra_query *const *qs, int64_t count, uint64_t sample_budget,
+                                  void *cuda_stream);
+/* Device time (ms) of the most recent step (CUDA events on its stream).  Synchronises. */
+kadabra_status kadabra_batch_last_ms(kadabra_batch *b, float *ms);
+
 /* Sharded sampling (several ranks, one GPU each; Section I-A: samples are
  * independent, so a rank can take any subset of an epoch's sample indices).
  * kadabra_sample_range takes sample indices [first, first + count) of stream

@@ -101,6 +101,24 @@ struct kadabra_query {
     uint32_t *d_logs = nullptr;              // epoch logs of interior vertices
     size_t logs_alloc = 0;                   // entries allocated
     kadabra::PipeState *d_pipe = nullptr;
+    kadabra::QueryDesc *d_desc = nullptr;    // descriptor for single-query launches
+    kadabra::BatchState *d_bs = nullptr;
+    bool pipe_begun = false;
+    int64_t pipe_E = 0;
+    int pipe_F = 0;
+    unsigned int pipe_cap = 0;
+};
+
+struct kadabra_batch {
+    int64_t max_n = 0;
+    int slots = 0, threads = 0, off64 = 0;
+    kadabra::SlotRec *d_recs = nullptr;
+    uint32_t *d_queues = nullptr;
+    kadabra::QueryDesc *d_descs = nullptr;
+    int64_t descs_cap = 0;
+    kadabra::BatchState *d_bs = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    bool have_step = false;
 };
 
 namespace kadabra {
@@ -474,6 +492,8 @@ static void free_query_device(kadabra_query *q)
     cudaFree(q->d_cmax);
     cudaFree(q->d_logs);
     cudaFree(q->d_pipe);
+    cudaFree(q->d_desc);
+    cudaFree(q->d_bs);
     for (int i = 0; i < kadabra::kLaunchLog; ++i) {
         if (q->ev0[i]) cudaEventDestroy(q->ev0[i]);
         if (q->ev1[i]) cudaEventDestroy(q->ev1[i]);
@@ -692,14 +712,13 @@ extern "C" kadabra_status kadabra_sample_epoch(kadabra_query *q, int64_t n_sampl
     return KADABRA_OK;
 }
 
-extern "C" kadabra_status kadabra_run_pipelined(kadabra_query *q, int64_t epoch_len, int frames, void *cuda_stream)
+extern "C" kadabra_status kadabra_pipeline_begin(kadabra_query *q, int64_t epoch_len, int frames, void *cuda_stream)
 {
     if (!q) return fail(KADABRA_ERR_INVALID_ARG, "query is null");
     if (epoch_len <= 0 || epoch_len >= (int64_t(1) << 40)) return fail(KADABRA_ERR_INVALID_ARG, "epoch_len out of range");
     if (frames <= 0) frames = 8;
     if (frames > kadabra::kMaxFrames) return fail(KADABRA_ERR_INVALID_ARG, "frames must be <= 16");
     cudaStream_t st = as_stream(cuda_stream);
-    const size_t n = (size_t)q->g->n;
     // an epoch logs at most (VD - 2) interior vertices per sample
     const uint64_t per_sample = q->vd > 3 ? (uint64_t)(q->vd - 2) : 1ULL;
     const uint64_t cap = (uint64_t)epoch_len * per_sample;
@@ -713,40 +732,184 @@ extern "C" kadabra_status kadabra_run_pipelined(kadabra_query *q, int64_t epoch_
         q->logs_alloc = need;
     }
     if (!q->d_pipe) KCUDA(cudaMalloc(reinterpret_cast<void **>(&q->d_pipe), sizeof(kadabra::PipeState)), "allocate pipeline state");
-    KCUDA(cudaMemsetAsync(q->d_pipe, 0, sizeof(kadabra::PipeState), st), "clear pipeline state");
-    // per-class maxima of the counters the run starts from
+    KCUDA(kadabra::launch_pipe_begin(q->d_pipe, q->d_job, q->omega_ceil, epoch_len, st), "begin pipeline");
+    // per-class maxima of the counters the pipeline starts from
     KCUDA(cudaMemsetAsync(q->d_cmax, 0, (size_t)q->nclass * 4, st), "clear class maxima");
     KCUDA(kadabra::launch_class_max(q->g->n, q->d_counts, q->d_cls, q->d_cmax, st), "class maxima");
-    (void)n;
-    kadabra::PipeLaunch P{};
-    P.s = base_launch(q);
-    P.s.counts = q->d_counts;
-    P.s.job = q->d_job;
-    P.s.tag = 1;
-    P.s.use_stop = 1;
-    P.s.epoch_len = epoch_len;
-    P.s.clip = q->omega_ceil;
-    P.s.grid = clamp_grid(q, int64_t(1) << 40);
-    P.logs = q->d_logs;
-    P.log_cap = (unsigned int)cap;
-    P.F = frames;
-    P.E = epoch_len;
-    P.cls = q->d_cls;
-    P.Ltab = q->d_Ltab;
-    P.cmax = q->d_cmax;
-    P.nclass = q->nclass;
-    P.omega = q->omega;
-    P.eps = q->p.eps;
-    P.ps = q->d_pipe;
-    P.spin_limit = 1ULL << 24;
+    q->pipe_begun = true;
+    q->pipe_E = epoch_len;
+    q->pipe_F = frames;
+    q->pipe_cap = (unsigned int)cap;
+    return KADABRA_OK;
+}
+
+static kadabra::QueryDesc make_desc(const kadabra_query *q, kadabra::Counters *launch_ctr)
+{
+    kadabra::QueryDesc d{};
+    d.n = q->g->n;
+    d.off = q->g->d_off;
+    d.adj = q->g->d_adj;
+    d.K = q->K;
+    d.strict = (q->p.flags & KADABRA_STRICT_SIGMA) ? 1 : 0;
+    d.seed = q->p.seed;
+    d.E = q->pipe_E;
+    d.F = q->pipe_F;
+    d.log_cap = q->pipe_cap;
+    d.logs = q->d_logs;
+    d.cls = q->d_cls;
+    d.Ltab = q->d_Ltab;
+    d.cmax = q->d_cmax;
+    d.nclass = q->nclass;
+    d.omega = q->omega;
+    d.eps = q->p.eps;
+    d.counts = q->d_counts;
+    d.job = q->d_job;
+    d.ps = q->d_pipe;
+    d.launch_ctr = launch_ctr;
+    return d;
+}
+
+extern "C" kadabra_status kadabra_run_pipelined(kadabra_query *q, int64_t epoch_len, int frames, void *cuda_stream)
+{
+    kadabra_status s = kadabra_pipeline_begin(q, epoch_len, frames, cuda_stream);
+    if (s != KADABRA_OK) return s;
+    cudaStream_t st = as_stream(cuda_stream);
+    if (!q->d_desc) KCUDA(cudaMalloc(reinterpret_cast<void **>(&q->d_desc), sizeof(kadabra::QueryDesc)), "allocate descriptor");
+    if (!q->d_bs) KCUDA(cudaMalloc(reinterpret_cast<void **>(&q->d_bs), sizeof(kadabra::BatchState)), "allocate launch state");
     const int slot = (int)(q->launches % kadabra::kLaunchLog);
-    P.s.launch_ctr = q->d_launch + slot;
-    KCUDA(cudaMemsetAsync(P.s.launch_ctr, 0, sizeof(kadabra::Counters), st), "reset launch counters");
+    kadabra::Counters *ctr = q->d_launch + slot;
+    const kadabra::QueryDesc d = make_desc(q, ctr);
+    KCUDA(cudaMemcpyAsync(q->d_desc, &d, sizeof(d), cudaMemcpyHostToDevice, st), "upload descriptor");
+    KCUDA(cudaMemsetAsync(q->d_bs, 0, sizeof(kadabra::BatchState), st), "clear launch state");
+    KCUDA(cudaMemsetAsync(ctr, 0, sizeof(kadabra::Counters), st), "reset launch counters");
+    kadabra::BatchLaunch B{};
+    B.queries = q->d_desc;
+    B.nq = 1;
+    B.recs = q->g->d_recs;
+    B.queues = q->g->d_queues;
+    B.stride = q->g->n;
+    B.bs = q->d_bs;
+    B.budget = 0;
+    B.spin_limit = 1ULL << 24;
+    B.grid = clamp_grid(q, int64_t(1) << 40);
+    B.threads = q->threads;
+    B.off64 = q->g->off64;
     KCUDA(cudaEventRecord(q->ev0[slot], st), "event");
-    KCUDA(kadabra::launch_pipe(P, st), "pipelined kernel launch");
+    KCUDA(kadabra::launch_batch(B, st), "pipelined kernel launch");
     KCUDA(cudaEventRecord(q->ev1[slot], st), "event");
-    q->grid_log[slot] = P.s.grid;
+    q->grid_log[slot] = B.grid;
     ++q->launches;
+    return KADABRA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// batches: many queries in one persistent launch
+// ---------------------------------------------------------------------------
+
+extern "C" kadabra_status kadabra_batch_create(int64_t max_n, int32_t slots, int32_t threads, int offsets_is_64,
+                                               kadabra_batch **out)
+{
+    if (!out) return fail(KADABRA_ERR_INVALID_ARG, "out is null");
+    if (max_n < 2 || max_n >= (int64_t(1) << 31)) return fail(KADABRA_ERR_INVALID_ARG, "max_n must be in [2, 2^31)");
+    if (threads == 0) threads = 1024;
+    if (threads != 128 && threads != 256 && threads != 512 && threads != 1024)
+        return fail(KADABRA_ERR_INVALID_ARG, "threads must be 128, 256, 512 or 1024");
+    int dev = 0, sms = 0, per_sm = 0;
+    KCUDA(cudaGetDevice(&dev), "cudaGetDevice");
+    KCUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
+    KCUDA(kadabra::sample_occupancy(threads, offsets_is_64 ? 1 : 0, &per_sm), "occupancy");
+    if (per_sm < 1) per_sm = 1;
+    if (slots <= 0 || slots > sms * per_sm) slots = sms * per_sm;
+    kadabra_batch *b = new kadabra_batch();
+    b->max_n = max_n;
+    b->slots = slots;
+    b->threads = threads;
+    b->off64 = offsets_is_64 ? 1 : 0;
+    const size_t nrec = (size_t)slots * (size_t)max_n;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&b->d_recs), nrec * sizeof(kadabra::SlotRec));
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&b->d_queues), nrec * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMemset(b->d_recs, 0, nrec * sizeof(kadabra::SlotRec));
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&b->d_bs), sizeof(kadabra::BatchState));
+    if (e == cudaSuccess) e = cudaEventCreate(&b->ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&b->ev1);
+    if (e != cudaSuccess) {
+        cudaFree(b->d_recs);
+        cudaFree(b->d_queues);
+        cudaFree(b->d_bs);
+        delete b;
+        return cuda_fail(e, "allocate batch scratch");
+    }
+    *out = b;
+    return KADABRA_OK;
+}
+
+extern "C" kadabra_status kadabra_batch_free(kadabra_batch *b)
+{
+    if (!b) return KADABRA_OK;
+    cudaDeviceSynchronize();
+    cudaFree(b->d_recs);
+    cudaFree(b->d_queues);
+    cudaFree(b->d_descs);
+    cudaFree(b->d_bs);
+    if (b->ev0) cudaEventDestroy(b->ev0);
+    if (b->ev1) cudaEventDestroy(b->ev1);
+    delete b;
+    return KADABRA_OK;
+}
+
+extern "C" kadabra_status kadabra_batch_step(kadabra_batch *b, kadabra_query *const *qs, int64_t count,
+                                             uint64_t sample_budget, void *cuda_stream)
+{
+    if (!b || (!qs && count > 0)) return fail(KADABRA_ERR_INVALID_ARG, "batch or queries is null");
+    if (count < 0 || count > (int64_t(1) << 20)) return fail(KADABRA_ERR_INVALID_ARG, "count out of range");
+    if (count == 0) return KADABRA_OK;
+    cudaStream_t st = as_stream(cuda_stream);
+    std::vector<kadabra::QueryDesc> descs((size_t)count);
+    for (int64_t i = 0; i < count; ++i) {
+        const kadabra_query *q = qs[i];
+        if (!q) return fail(KADABRA_ERR_INVALID_ARG, "null query in batch");
+        if (!q->pipe_begun) return fail(KADABRA_ERR_STATE, "query not begun (kadabra_pipeline_begin)");
+        if (q->g->n > b->max_n) return fail(KADABRA_ERR_INVALID_ARG, "query graph larger than the batch's max_n");
+        if (q->g->off64 != b->off64) return fail(KADABRA_ERR_INVALID_ARG, "query offset width differs from the batch's");
+        descs[(size_t)i] = make_desc(q, nullptr);
+    }
+    if (b->descs_cap < count) {
+        cudaStreamSynchronize(st);
+        cudaFree(b->d_descs);
+        b->d_descs = nullptr;
+        b->descs_cap = 0;
+        KCUDA(cudaMalloc(reinterpret_cast<void **>(&b->d_descs), (size_t)count * sizeof(kadabra::QueryDesc)),
+              "allocate descriptors");
+        b->descs_cap = count;
+    }
+    KCUDA(cudaMemcpyAsync(b->d_descs, descs.data(), (size_t)count * sizeof(kadabra::QueryDesc), cudaMemcpyHostToDevice, st),
+          "upload descriptors");
+    KCUDA(cudaMemsetAsync(b->d_bs, 0, sizeof(kadabra::BatchState), st), "clear launch state");
+    kadabra::BatchLaunch B{};
+    B.queries = b->d_descs;
+    B.nq = (int)count;
+    B.recs = b->d_recs;
+    B.queues = b->d_queues;
+    B.stride = b->max_n;
+    B.bs = b->d_bs;
+    B.budget = sample_budget;
+    B.spin_limit = 1ULL << 24;
+    B.grid = b->slots;
+    B.threads = b->threads;
+    B.off64 = b->off64;
+    KCUDA(cudaEventRecord(b->ev0, st), "event");
+    KCUDA(kadabra::launch_batch(B, st), "batch kernel launch");
+    KCUDA(cudaEventRecord(b->ev1, st), "event");
+    b->have_step = true;
+    return KADABRA_OK;
+}
+
+extern "C" kadabra_status kadabra_batch_last_ms(kadabra_batch *b, float *ms)
+{
+    if (!b || !ms) return fail(KADABRA_ERR_INVALID_ARG, "batch or ms is null");
+    if (!b->have_step) return fail(KADABRA_ERR_STATE, "no batch step yet");
+    KCUDA(cudaEventSynchronize(b->ev1), "event sync");
+    KCUDA(cudaEventElapsedTime(ms, b->ev0, b->ev1), "event time");
     return KADABRA_OK;
 }
 

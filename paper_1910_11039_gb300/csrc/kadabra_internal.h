@@ -100,37 +100,68 @@ cudaError_t launch_vd_bound(int64_t n, const void *off, int off64, const uint2 *
 cudaError_t launch_max_degree(int64_t n, const void *off, int off64, unsigned long long *out, cudaStream_t st);
 cudaError_t sample_occupancy(int threads, int off64, int *ctas_per_sm);
 
-// Pipelined adaptive phase (one persistent launch): epochs rotate through F
-// counter frames; see pipe_kernel in sample_kernel.cu.
+// Pipelined adaptive phase: epochs rotate through F epoch logs; one persistent
+// launch serves one or many queries (see batch_kernel in sample_kernel.cu).
 constexpr int kMaxFrames = 16;
 
+// Per-query pipeline state; persists across launches until the query is
+// begun again.
 struct PipeState {
-    unsigned long long next_idx;        // next sample (relative to the launch's base tau) to hand out
-    long long next_check;               // next epoch (relative) to fold into c~ and check
+    unsigned long long next_idx;        // next sample (relative to base) to hand out
+    long long next_check;               // next epoch to fold into c~ and check
     unsigned int done[kMaxFrames];      // finished samples of the epoch each frame holds
     unsigned int log_len[kMaxFrames];   // interior vertices logged by the epoch each frame holds
-    int checker;                        // 1 while a CTA folds and checks
+    int checker;                        // 1 while a CTA folds and checks this query
     int abort;                          // set when a bounded wait gave up
-    unsigned int exited;                // CTAs that left the launch
-    unsigned int pad;
+    unsigned long long base;            // tau when the pipeline began
+    unsigned long long R;               // samples the pipeline may take (ceil(omega) - base)
+    long long nE;                       // epochs in R
 };
 
-struct PipeLaunch {
-    SampleLaunch s;            // graph, scratch, seed, K, job (tag 1, no trace)
-    uint32_t *logs;            // F logs of log_cap interior-vertex ids
-    unsigned int log_cap;
-    int F;                     // frames (epoch logs) in rotation (1..kMaxFrames)
+// One query of a pipelined launch (device memory, written by the host).
+struct QueryDesc {
+    long long n;
+    const void *off;           // offsets (the launch's offset width)
+    const uint2 *adj;
+    int K;
+    int strict;
+    unsigned long long seed;
     long long E;               // samples per epoch
+    int F;                     // epoch logs in rotation
+    unsigned int log_cap;      // entries per log
+    uint32_t *logs;            // F logs
     const uint32_t *cls;       // budget class of every vertex
     const double2 *Ltab;       // (L_L, L_U) of every class
-    unsigned int *cmax;        // largest c~ in every class (kept current by the folds)
+    unsigned int *cmax;        // largest c~ in every class
     int nclass;
+    int pad;
     double omega, eps;
+    uint32_t *counts;          // c~
+    Job *job;
     PipeState *ps;
-    unsigned long long spin_limit;   // polls of a frame wait before giving up
+    Counters *launch_ctr;      // this launch's counters for the query (may be null)
 };
 
-cudaError_t launch_pipe(const PipeLaunch &a, cudaStream_t st);
+struct BatchState {
+    unsigned int ticket;                // round-robin start for query selection
+    unsigned int abort;
+    unsigned long long taken;           // samples handed out by this launch
+};
+
+struct BatchLaunch {
+    QueryDesc *queries;        // device array
+    int nq;
+    SlotRec *recs;             // slots * stride
+    uint32_t *queues;          // slots * stride
+    long long stride;          // largest n the scratch serves
+    BatchState *bs;
+    unsigned long long budget; // samples this launch may hand out (0 = no limit)
+    unsigned long long spin_limit;
+    int grid, threads, off64;
+};
+
+cudaError_t launch_batch(const BatchLaunch &a, cudaStream_t st);
+cudaError_t launch_pipe_begin(PipeState *ps, const Job *job, unsigned long long clip, long long E, cudaStream_t st);
 cudaError_t launch_class_max(int64_t n, const uint32_t *counts, const uint32_t *cls, unsigned int *cmax,
                              cudaStream_t st);
 

@@ -938,7 +938,7 @@ __global__ void __launch_bounds__(NT, (2048 / NT / 2) > 0 ? (2048 / NT / 2) : 1)
     }
 }
 
-// ---- pipelined adaptive phase ---------------------------------------------
+// ---- pipelined adaptive phase (one or many queries) -------------------------
 //
 // The paper's epoch framework (Section IV-A/B, Algorithm 2) lets every thread
 // keep sampling across an epoch transition: samples are written to the state
@@ -979,7 +979,7 @@ struct PipeSmem {
 // (counters only grow), so the check evaluates f and g once per class and
 // obtains exactly the per-vertex maxima.  Returns error bits.
 template <int NT>
-__device__ unsigned int fold_and_check(const PipeLaunch &P, uint32_t *counts, const uint32_t *log, unsigned int len,
+__device__ unsigned int fold_and_check(const QueryDesc &P, uint32_t *counts, const uint32_t *log, unsigned int len,
                                        unsigned long long tau, PipeSmem<NT> &ps, double &Mf, double &Mg)
 {
     unsigned int err = 0;
@@ -1021,82 +1021,157 @@ __device__ unsigned int fold_and_check(const PipeLaunch &P, uint32_t *counts, co
     return err;
 }
 
+// Sets up a query's pipeline: base = current tau, R samples up to ceil(omega).
+__global__ void pipe_begin_kernel(PipeState *ps, const Job *job, unsigned long long clip, long long E)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        PipeState z;
+        unsigned char *p = reinterpret_cast<unsigned char *>(&z);
+        for (size_t i = 0; i < sizeof(PipeState); ++i) p[i] = 0;
+        z.base = job->tau;
+        z.R = clip > z.base ? clip - z.base : 0ULL;
+        z.nE = (long long)((z.R + (unsigned long long)E - 1) / (unsigned long long)E);
+        *ps = z;
+    }
+}
+
+__device__ __forceinline__ unsigned long long epoch_size(const PipeState *st, long long E, long long e)
+{
+    const unsigned long long lo = (unsigned long long)e * (unsigned long long)E;
+    const unsigned long long R = st->R;
+    return R - lo < (unsigned long long)E ? R - lo : (unsigned long long)E;
+}
+
+// One persistent launch over the queries of a batch (one query for
+// kadabra_run_pipelined).  A CTA repeatedly takes the next sample index of
+// some running query (round robin, skipping queries whose epoch logs are all
+// in use), runs the sample in its slot, and, if that sample completed the
+// query's oldest unchecked epoch, folds and checks that query's complete
+// epochs in order.  The launch ends when every query has stopped or reached
+// ceil(omega), or once `budget` samples have been handed out; the pipeline
+// state persists, so the next launch continues where this one ended.
 template <int NT, typename OffT>
-__global__ void __launch_bounds__(NT, (2048 / NT / 2) > 0 ? (2048 / NT / 2) : 1) pipe_kernel(PipeLaunch P)
+__global__ void __launch_bounds__(NT, (2048 / NT / 2) > 0 ? (2048 / NT / 2) : 1) batch_kernel(BatchLaunch B)
 {
     __shared__ Smem<NT> sh;
     __shared__ PipeSmem<NT> pm;
-    const SampleLaunch &a = P.s;
+    __shared__ QueryDesc qd;
+    __shared__ SampleLaunch sa;
+    __shared__ int s_qi;
     const int tid = threadIdx.x;
-    GraphRef<OffT> G{reinterpret_cast<const OffT *>(a.off), a.adj, (long long)a.n};
-    SlotRec *rec = a.recs + (size_t)blockIdx.x * (size_t)a.n;
-    uint32_t *queue = a.queues + (size_t)blockIdx.x * (size_t)a.n;
-    Job *job = a.job;
-    PipeState *st = P.ps;
-    volatile PipeState *vst = P.ps;
-    volatile Job *vjob = a.job;
+    SlotRec *rec = B.recs + (size_t)blockIdx.x * (size_t)B.stride;
+    uint32_t *queue = B.queues + (size_t)blockIdx.x * (size_t)B.stride;
+    volatile BatchState *vbs = B.bs;
 
-    __shared__ unsigned long long s_base, s_R;
-    if (tid == 0) {
-        s_base = vjob->tau;
-        s_R = a.clip > s_base ? a.clip - s_base : 0ULL;
-    }
-    __syncthreads();
-    const unsigned long long base = s_base, R = s_R;
-    const unsigned long long E = (unsigned long long)P.E;
-    const long long nE = (long long)((R + E - 1) / E);     // epochs up to the cap
-    auto epoch_size = [&](long long e) -> unsigned long long {
-        const unsigned long long lo = (unsigned long long)e * E;
-        return R - lo < E ? R - lo : E;
-    };
-
-    LocalStats ls = {0, 0, 0, 0, 0, 0, 0, 0};
     for (;;) {
         if (tid == 0) {
             pm.take = 0;
-            if (!vst->abort && !vjob->stopped) {
-                const unsigned long long i = atomicAdd(&st->next_idx, 1ULL);
-                if (i < R) {
-                    const long long e = (long long)(i / E);
-                    // wait until epoch e - F has been folded (bounded)
-                    unsigned long long polls = 0;
-                    bool ok = true;
-                    while (e >= vst->next_check + P.F) {
-                        if (vjob->stopped || vst->abort) {
-                            ok = false;
-                            break;
+            s_qi = -1;
+            bool stop_launch = vbs->abort != 0;
+            if (!stop_launch && B.budget && atomicAdd(&B.bs->taken, 0ULL) >= B.budget) stop_launch = true;
+            if (!stop_launch) {
+                const unsigned int start = atomicAdd(&B.bs->ticket, 1u) % (unsigned int)B.nq;
+                unsigned long long polls = 0;
+                for (;;) {
+                    bool all_done = true;
+                    for (int k = 0; k < B.nq && !pm.take; ++k) {
+                        const int qi = (int)((start + (unsigned int)k) % (unsigned int)B.nq);
+                        QueryDesc *Q = B.queries + qi;
+                        PipeState *st = Q->ps;
+                        volatile PipeState *vst = st;
+                        volatile Job *vjob = Q->job;
+                        if (vjob->stopped || vst->abort) continue;
+                        const unsigned long long R = vst->R;
+                        const unsigned long long nx = vst->next_idx;
+                        if (nx >= R) continue;
+                        all_done = false;
+                        const long long E = Q->E;
+                        const int F = Q->F;
+                        if ((long long)(nx / (unsigned long long)E) >= vst->next_check + F) continue;   // logs all in use
+                        const unsigned long long i = atomicAdd(&st->next_idx, 1ULL);
+                        if (i >= R) continue;
+                        const long long e = (long long)(i / (unsigned long long)E);
+                        // rare: another CTA took the indices in between; wait (bounded) for the log
+                        unsigned long long w = 0;
+                        bool ok = true;
+                        while (e >= vst->next_check + F) {
+                            if (vjob->stopped || vst->abort) {
+                                ok = false;
+                                break;
+                            }
+                            if (++w > B.spin_limit) {
+                                atomicOr(&Q->job->error, kErrTimeout);
+                                vst->abort = 1;
+                                ok = false;
+                                break;
+                            }
+                            __nanosleep(256);
                         }
-                        if (++polls > P.spin_limit) {
-                            atomicOr(&job->error, kErrTimeout);
-                            vst->abort = 1;
-                            ok = false;
-                            break;
-                        }
-                        __nanosleep(256);
-                    }
-                    __threadfence();
-                    if (ok) {
+                        __threadfence();
+                        if (!ok) continue;
                         pm.take = 1;
                         pm.epoch = e;
                         pm.idx = i;
+                        s_qi = qi;
                     }
+                    if (pm.take || all_done) break;
+                    // every running query waits for an epoch check: back off (bounded)
+                    if (++polls > B.spin_limit) {
+                        atomicOr(&B.bs->abort, 1u);
+                        for (int k = 0; k < B.nq; ++k) atomicOr(&B.queries[k].job->error, kErrTimeout);
+                        break;
+                    }
+                    __nanosleep(512);
                 }
+                if (pm.take && B.budget) atomicAdd(&B.bs->taken, 1ULL);
+            }
+            if (pm.take) {
+                qd = B.queries[s_qi];
+                SampleLaunch t{};
+                t.n = qd.n;
+                t.off = qd.off;
+                t.adj = qd.adj;
+                t.job = qd.job;
+                t.seed = qd.seed;
+                t.tag = 1;
+                t.K = qd.K;
+                t.strict = qd.strict;
+                sa = t;
             }
         }
         __syncthreads();
         if (!pm.take) break;
         const long long e = pm.epoch;
-        const int f = (int)(e % P.F);
-        run_sample<NT, OffT>(a, G, rec, queue, sh, base + pm.idx, pm.idx, ls,
-                             CountSink{nullptr, P.logs + (size_t)f * P.log_cap, &st->log_len[f], P.log_cap});
+        const int f = (int)(e % qd.F);
+        PipeState *st = qd.ps;
+        volatile PipeState *vst = st;
+        volatile Job *vjob = qd.job;
+        Job *job = qd.job;
+        GraphRef<OffT> G{reinterpret_cast<const OffT *>(qd.off), qd.adj, qd.n};
+        LocalStats ls = {0, 0, 0, 0, 0, 0, 0, 0};
+        run_sample<NT, OffT>(sa, G, rec, queue, sh, st->base + pm.idx, pm.idx, ls,
+                             CountSink{nullptr, qd.logs + (size_t)f * qd.log_cap, &st->log_len[f], qd.log_cap});
         if (tid == 0) {
-            __threadfence();    // this sample's counter updates before its completion
-            const unsigned int d = atomicAdd(&st->done[e % P.F], 1u) + 1u;
-            pm.try_check = (d == epoch_size(e)) ? 1 : 0;
+            Counters *cs[2] = {&job->total, qd.launch_ctr};
+            for (int c = 0; c < 2; ++c) {
+                if (!cs[c]) continue;
+                atomicAdd(&cs[c]->samples, ls.samples);
+                atomicAdd(&cs[c]->connected, ls.connected);
+                atomicAdd(&cs[c]->e_scan, ls.e_scan);
+                atomicAdd(&cs[c]->expanded, ls.expanded);
+                atomicAdd(&cs[c]->touched, ls.touched);
+                atomicAdd(&cs[c]->interior, ls.interior);
+                atomicAdd(&cs[c]->walk_scan, ls.walk_scan);
+                atomicAdd(&cs[c]->scaled, ls.scaled);
+            }
+            __threadfence();    // this sample's log entries before its completion
+            const unsigned int d = atomicAdd(&st->done[f], 1u) + 1u;
+            pm.try_check = (d == epoch_size(st, qd.E, e)) ? 1 : 0;
         }
         __syncthreads();
         if (!pm.try_check) continue;
-        // this CTA completed an epoch: fold and check every complete epoch in order
+        // this CTA completed an epoch of the query: fold and check its complete epochs in order
+        const long long nE = st->nE;
         for (;;) {
             if (tid == 0) pm.acquired = atomicCAS(&st->checker, 0, 1) == 0;
             __syncthreads();
@@ -1104,23 +1179,24 @@ __global__ void __launch_bounds__(NT, (2048 / NT / 2) > 0 ? (2048 / NT / 2) : 1)
             for (;;) {
                 if (tid == 0) {
                     const long long ce = vst->next_check;
-                    pm.go = ce < nE && !vjob->stopped && vst->done[ce % P.F] == epoch_size(ce);
+                    pm.go = ce < nE && !vjob->stopped && vst->done[ce % qd.F] == epoch_size(st, qd.E, ce);
                     pm.chk_epoch = ce;
                     __threadfence();
                 }
                 __syncthreads();
                 if (!pm.go) break;
                 const long long ce = pm.chk_epoch;
-                const unsigned long long tau = base + (unsigned long long)ce * E + epoch_size(ce);
+                const unsigned long long tau = st->base + (unsigned long long)ce * (unsigned long long)qd.E +
+                                               epoch_size(st, qd.E, ce);
                 double Mf, Mg;
-                const int cf = (int)(ce % P.F);
+                const int cf = (int)(ce % qd.F);
                 const unsigned int llen = vst->log_len[cf];
                 unsigned int ferr = 0;
-                if (llen > P.log_cap) {
+                if (llen > qd.log_cap) {
                     ferr = kErrLogOverflow;
                     Mf = Mg = 0.0;
                 } else {
-                    ferr = fold_and_check<NT>(P, a.counts, P.logs + (size_t)cf * P.log_cap, llen, tau, pm, Mf, Mg);
+                    ferr = fold_and_check<NT>(qd, qd.counts, qd.logs + (size_t)cf * qd.log_cap, llen, tau, pm, Mf, Mg);
                 }
                 if (ferr) {
                     atomicOr(&job->error, ferr);
@@ -1129,7 +1205,7 @@ __global__ void __launch_bounds__(NT, (2048 / NT / 2) > 0 ? (2048 / NT / 2) : 1)
                     break;
                 }
                 if (tid == 0) {
-                    const int stop = ((double)tau >= P.omega) || (Mf < P.eps && Mg < P.eps);
+                    const int stop = ((double)tau >= qd.omega) || (Mf < qd.eps && Mg < qd.eps);
                     job->tau = tau;
                     job->last_maxf = Mf;
                     job->last_maxg = Mg;
@@ -1138,10 +1214,10 @@ __global__ void __launch_bounds__(NT, (2048 / NT / 2) > 0 ? (2048 / NT / 2) : 1)
                         job->stopped = 1;
                     }
                     job->epoch += 1;
-                    st->done[ce % P.F] = 0u;
-                    st->log_len[ce % P.F] = 0u;
+                    st->done[cf] = 0u;
+                    st->log_len[cf] = 0u;
                     __threadfence();
-                    st->next_check = ce + 1;     // frees the frame for epoch ce + F
+                    st->next_check = ce + 1;     // frees the log for epoch ce + F
                     __threadfence();
                 }
                 __syncthreads();
@@ -1153,31 +1229,10 @@ __global__ void __launch_bounds__(NT, (2048 / NT / 2) > 0 ? (2048 / NT / 2) : 1)
                 atomicExch(&st->checker, 0);
                 __threadfence();
                 const long long ce = vst->next_check;
-                pm.again = ce < nE && !vjob->stopped && vst->done[ce % P.F] == epoch_size(ce);
+                pm.again = ce < nE && !vjob->stopped && vst->done[ce % qd.F] == epoch_size(st, qd.E, ce);
             }
             __syncthreads();
             if (!pm.again) break;
-        }
-    }
-
-    if (tid == 0) {
-        atomicAdd(&job->total.samples, ls.samples);
-        atomicAdd(&job->total.connected, ls.connected);
-        atomicAdd(&job->total.e_scan, ls.e_scan);
-        atomicAdd(&job->total.expanded, ls.expanded);
-        atomicAdd(&job->total.touched, ls.touched);
-        atomicAdd(&job->total.interior, ls.interior);
-        atomicAdd(&job->total.walk_scan, ls.walk_scan);
-        atomicAdd(&job->total.scaled, ls.scaled);
-        if (a.launch_ctr) {
-            atomicAdd(&a.launch_ctr->samples, ls.samples);
-            atomicAdd(&a.launch_ctr->connected, ls.connected);
-            atomicAdd(&a.launch_ctr->e_scan, ls.e_scan);
-            atomicAdd(&a.launch_ctr->expanded, ls.expanded);
-            atomicAdd(&a.launch_ctr->touched, ls.touched);
-            atomicAdd(&a.launch_ctr->interior, ls.interior);
-            atomicAdd(&a.launch_ctr->walk_scan, ls.walk_scan);
-            atomicAdd(&a.launch_ctr->scaled, ls.scaled);
         }
     }
 }
@@ -1250,26 +1305,31 @@ cudaError_t launch_build_adj(int64_t nnz, const void *off, int off64, const int3
 }
 
 template <int NT>
-cudaError_t launch_pipe_nt(const PipeLaunch &a, cudaStream_t st)
+cudaError_t launch_batch_nt(const BatchLaunch &a, cudaStream_t st)
 {
-    if (a.s.off64)
-        pipe_kernel<NT, long long><<<a.s.grid, NT, 0, st>>>(a);
+    if (a.off64)
+        batch_kernel<NT, long long><<<a.grid, NT, 0, st>>>(a);
     else
-        pipe_kernel<NT, int><<<a.s.grid, NT, 0, st>>>(a);
+        batch_kernel<NT, int><<<a.grid, NT, 0, st>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_pipe(const PipeLaunch &a, cudaStream_t st)
+cudaError_t launch_batch(const BatchLaunch &a, cudaStream_t st)
 {
-    if (a.s.grid <= 0) return cudaSuccess;
-    if (a.F < 1 || a.F > kMaxFrames || a.E < 1) return cudaErrorInvalidValue;
-    switch (a.s.threads) {
-    case 128: return launch_pipe_nt<128>(a, st);
-    case 256: return launch_pipe_nt<256>(a, st);
-    case 512: return launch_pipe_nt<512>(a, st);
-    case 1024: return launch_pipe_nt<1024>(a, st);
+    if (a.grid <= 0 || a.nq <= 0) return cudaSuccess;
+    switch (a.threads) {
+    case 128: return launch_batch_nt<128>(a, st);
+    case 256: return launch_batch_nt<256>(a, st);
+    case 512: return launch_batch_nt<512>(a, st);
+    case 1024: return launch_batch_nt<1024>(a, st);
     default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_pipe_begin(PipeState *ps, const Job *job, unsigned long long clip, long long E, cudaStream_t st)
+{
+    pipe_begin_kernel<<<1, 32, 0, st>>>(ps, job, clip, E);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_class_max(int64_t n, const uint32_t *counts, const uint32_t *cls, unsigned int *cmax,

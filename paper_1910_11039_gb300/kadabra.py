@@ -108,6 +108,11 @@ SIGNATURES = {
     "kadabra_sample_static": (_ST, [_P, _U64, C.c_int, _U64, _I64, _P, _P]),
     "kadabra_sample_range": (_ST, [_P, C.c_int, _U64, _I64, _P, _P]),
     "kadabra_absorb": (_ST, [_P, _P, _U64, _P]),
+    "kadabra_pipeline_begin": (_ST, [_P, _I64, C.c_int, _P]),
+    "kadabra_batch_create": (_ST, [_I64, C.c_int32, C.c_int32, C.c_int, C.POINTER(_P)]),
+    "kadabra_batch_free": (_ST, [_P]),
+    "kadabra_batch_step": (_ST, [_P, _P, _I64, _U64, _P]),
+    "kadabra_batch_last_ms": (_ST, [_P, C.POINTER(C.c_float)]),
 }
 
 _lock = threading.Lock()
@@ -281,6 +286,9 @@ class Query:
         """c~ += delta, tau += samples (the epoch aggregate of a sharded run)."""
         _check(load().kadabra_absorb(self.handle, C.c_void_p(int(delta_device_ptr)), samples, _stream(stream)))
 
+    def pipeline_begin(self, epoch_len, frames=8, stream=None):
+        _check(load().kadabra_pipeline_begin(self.handle, epoch_len, frames, _stream(stream)))
+
     def reset(self, stream=None):
         _check(load().kadabra_query_reset(self.handle, _stream(stream)))
 
@@ -348,6 +356,36 @@ def sample_static(graph: Graph, seed, tag, first, count, counts_device_ptr, stre
     device array."""
     _check(load().kadabra_sample_static(graph.handle, seed, tag, first, count, C.c_void_p(int(counts_device_ptr)),
                                         _stream(stream)))
+
+
+class Batch:
+    """Sampling scratch shared by many queries stepped in one launch."""
+
+    def __init__(self, max_n, slots=0, threads=1024, offsets_64=False):
+        self.handle = C.c_void_p()
+        _check(load().kadabra_batch_create(max_n, slots, threads, int(bool(offsets_64)), C.byref(self.handle)))
+        self.max_n = max_n
+
+    def step(self, queries, sample_budget=0, stream=None):
+        arr = (C.c_void_p * len(queries))(*[q.handle.value for q in queries])
+        _check(load().kadabra_batch_step(self.handle, C.cast(arr, C.c_void_p), len(queries), sample_budget,
+                                         _stream(stream)))
+
+    def last_ms(self) -> float:
+        ms = C.c_float()
+        _check(load().kadabra_batch_last_ms(self.handle, C.byref(ms)))
+        return ms.value
+
+    def free(self):
+        if self.handle:
+            load().kadabra_batch_free(self.handle)
+            self.handle = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
 
 
 # C-ABI names, for callers that prefer the flat interface
