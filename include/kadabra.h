@@ -106,6 +106,7 @@ typedef struct kadabra_query_info {
     int32_t threads;            /* threads per sampling CTA                                */
     int32_t offsets_64;         /* 1 if the graph uses int64 offsets                       */
     int32_t budget_classes;     /* distinct (L_L, L_U) pairs                               */
+    uint64_t stop_ns;           /* device global timer (ns) when the stop was decided, or 0 */
 } kadabra_query_info;
 
 /* Per-sample record written by kadabra_sample_trace (one per sample index). */
@@ -159,6 +160,10 @@ kadabra_status kadabra_omega(double eps, double delta, int64_t vertex_diameter, 
  * within 128 bits.  The paper does not say how counts beyond a machine word
  * are handled; this is the library's reading. */
 int kadabra_sigma_bits(int64_t n, int64_t max_degree);
+
+/* Device global timer (ns; the clock of kadabra_query_info.stop_ns), read by a
+ * one-thread kernel on `cuda_stream`.  Synchronises. */
+kadabra_status kadabra_device_clock(uint64_t *ns, void *cuda_stream);
 
 /* ---- graph ------------------------------------------------------------- */
 
@@ -271,6 +276,16 @@ kadabra_status kadabra_batch_last_ms(kadabra_batch *b, float *ms);
 kadabra_status kadabra_sample_range(kadabra_query *q, int tag, uint64_t first, int64_t count, uint32_t *counts,
                                     void *cuda_stream);
 kadabra_status kadabra_absorb(kadabra_query *q, const uint32_t *delta, uint64_t samples, void *cuda_stream);
+
+/* The stream-ordered epochs of kadabra_run as a CUDA graph: the first call
+ * for a given (epoch_len, epochs_per_graph) captures epochs_per_graph epochs
+ * (sampling launch + stop-check launch each) on a private stream and
+ * instantiates the graph; every call then launches the graph on `cuda_stream`
+ * until the query stops, max_epochs epochs ran, or tau reaches ceil(omega),
+ * reading the device stop flag once per graph launch.  Results equal
+ * kadabra_run with the same epoch_len.  Writes *stopped. */
+kadabra_status kadabra_run_graph(kadabra_query *q, int64_t epoch_len, int epochs_per_graph, int64_t max_epochs,
+                                 void *cuda_stream, int *stopped);
 
 /* Restart phase 3 (tau = 0, c~ = 0, not stopped) keeping omega and the
  * calibrated budgets (async). */

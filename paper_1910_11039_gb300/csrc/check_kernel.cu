@@ -76,6 +76,9 @@ __global__ void __launch_bounds__(kCheckThreads) check_kernel(CheckLaunch a)
             job->last_maxf = Mf;
             job->last_maxg = Mg;
             if (stop) {
+                unsigned long long now;
+                asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
+                job->stop_ns = now;
                 job->stopped = 1;
                 job->stop_epoch = job->epoch;
             }
@@ -109,6 +112,13 @@ __global__ void absorb_kernel(long long n, uint32_t *counts, const uint32_t *del
         }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&job->tau, samples);
+}
+
+__global__ void clock_kernel(unsigned long long *out)
+{
+    unsigned long long now;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
+    *out = now;
 }
 
 __global__ void reset_job_kernel(Job *job)
@@ -155,6 +165,19 @@ cudaError_t launch_absorb(int64_t n, uint32_t *counts, const uint32_t *delta, Jo
 {
     absorb_kernel<<<grid_for(n, 256), 256, 0, st>>>((long long)n, counts, delta, job, (unsigned long long)samples);
     return cudaGetLastError();
+}
+
+cudaError_t read_device_clock(unsigned long long *ns, cudaStream_t st)
+{
+    unsigned long long *d = nullptr;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&d), sizeof(unsigned long long));
+    if (e != cudaSuccess) return e;
+    clock_kernel<<<1, 1, 0, st>>>(d);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ns, d, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(d);
+    return e;
 }
 
 cudaError_t launch_reset_job(Job *job, cudaStream_t st)

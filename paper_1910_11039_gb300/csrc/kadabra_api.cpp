@@ -107,6 +107,11 @@ struct kadabra_query {
     int64_t pipe_E = 0;
     int pipe_F = 0;
     unsigned int pipe_cap = 0;
+    // captured epochs (kadabra_run_graph)
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    int64_t graph_E = 0;
+    int graph_k = 0;
 };
 
 struct kadabra_batch {
@@ -223,6 +228,15 @@ static kadabra_status validate(int64_t n, int64_t nnz, const OffT *off, const in
                                                          std::to_string(w) + " has no reverse");
         }
     }
+    return KADABRA_OK;
+}
+
+extern "C" kadabra_status kadabra_device_clock(uint64_t *ns, void *cuda_stream)
+{
+    if (!ns) return fail(KADABRA_ERR_INVALID_ARG, "ns is null");
+    unsigned long long v = 0;
+    KCUDA(kadabra::read_device_clock(&v, as_stream(cuda_stream)), "device clock");
+    *ns = v;
     return KADABRA_OK;
 }
 
@@ -494,6 +508,8 @@ static void free_query_device(kadabra_query *q)
     cudaFree(q->d_pipe);
     cudaFree(q->d_desc);
     cudaFree(q->d_bs);
+    if (q->graph_exec) cudaGraphExecDestroy(q->graph_exec);
+    if (q->cap_stream) cudaStreamDestroy(q->cap_stream);
     for (int i = 0; i < kadabra::kLaunchLog; ++i) {
         if (q->ev0[i]) cudaEventDestroy(q->ev0[i]);
         if (q->ev1[i]) cudaEventDestroy(q->ev1[i]);
@@ -1006,6 +1022,64 @@ extern "C" kadabra_status kadabra_absorb(kadabra_query *q, const uint32_t *delta
     return KADABRA_OK;
 }
 
+extern "C" kadabra_status kadabra_run_graph(kadabra_query *q, int64_t epoch_len, int epochs_per_graph, int64_t max_epochs,
+                                            void *cuda_stream, int *stopped)
+{
+    if (!q) return fail(KADABRA_ERR_INVALID_ARG, "query is null");
+    if (epoch_len <= 0 || epoch_len >= (int64_t(1) << 32) || epochs_per_graph <= 0 || epochs_per_graph > 4096 ||
+        max_epochs <= 0)
+        return fail(KADABRA_ERR_INVALID_ARG, "epoch_len, epochs_per_graph or max_epochs out of range");
+    cudaStream_t st = as_stream(cuda_stream);
+    if (!q->graph_exec || q->graph_E != epoch_len || q->graph_k != epochs_per_graph) {
+        if (q->graph_exec) cudaGraphExecDestroy(q->graph_exec);
+        q->graph_exec = nullptr;
+        if (!q->cap_stream) KCUDA(cudaStreamCreateWithFlags(&q->cap_stream, cudaStreamNonBlocking), "capture stream");
+        kadabra::SampleLaunch a = base_launch(q);
+        a.counts = q->d_counts;
+        a.job = q->d_job;
+        a.tag = 1;
+        a.use_stop = 1;
+        a.epoch_len = epoch_len;
+        a.clip = q->omega_ceil;
+        a.grid = clamp_grid(q, epoch_len);
+        kadabra::CheckLaunch c{};
+        c.n = q->g->n;
+        c.counts = q->d_counts;
+        c.L = q->d_L;
+        c.job = q->d_job;
+        c.omega = q->omega;
+        c.eps = q->p.eps;
+        KCUDA(cudaStreamBeginCapture(q->cap_stream, cudaStreamCaptureModeRelaxed), "begin capture");
+        cudaError_t e = cudaSuccess;
+        for (int k = 0; k < epochs_per_graph && e == cudaSuccess; ++k) {
+            e = kadabra::launch_sample(a, q->cap_stream);
+            if (e == cudaSuccess) e = kadabra::launch_check(c, q->cap_stream);
+        }
+        cudaGraph_t graph = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(q->cap_stream, &graph);
+        if (e == cudaSuccess) e = e2;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&q->graph_exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            q->graph_exec = nullptr;
+            return cuda_fail(e, "capture epochs");
+        }
+        q->graph_E = epoch_len;
+        q->graph_k = epochs_per_graph;
+    }
+    Job j{};
+    for (int64_t done = 0; done < max_epochs; done += epochs_per_graph) {
+        KCUDA(cudaGraphLaunch(q->graph_exec, st), "graph launch");
+        kadabra_status s = read_job(q, &j, st);
+        if (s != KADABRA_OK) return s;
+        s = device_error_status(j);
+        if (s != KADABRA_OK) return s;
+        if (j.stopped || j.tau >= q->omega_ceil) break;
+    }
+    if (stopped) *stopped = j.stopped;
+    return KADABRA_OK;
+}
+
 extern "C" kadabra_status kadabra_query_reset(kadabra_query *q, void *cuda_stream)
 {
     if (!q) return fail(KADABRA_ERR_INVALID_ARG, "query is null");
@@ -1071,6 +1145,7 @@ extern "C" kadabra_status kadabra_query_get_info(kadabra_query *q, kadabra_query
     I.threads = q->threads;
     I.offsets_64 = q->g->off64;
     I.budget_classes = q->nclass;
+    I.stop_ns = j.stopped ? j.stop_ns : 0ULL;
     *out = I;
     return KADABRA_OK;
 }

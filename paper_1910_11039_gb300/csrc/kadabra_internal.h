@@ -41,6 +41,7 @@ struct Job {
     unsigned int check_done;       // CTAs that finished the running check
     unsigned int error;            // sticky error bits (kErr*)
     double last_maxf, last_maxg;   // maxima of the last completed check
+    unsigned long long stop_ns;    // device global timer when the stop was decided (0: not stopped)
     Counters total;                // since the query started (reset with the query)
 };
 
@@ -194,6 +195,7 @@ cudaError_t launch_static_job_init(Job *job, unsigned long long first, cudaStrea
 cudaError_t launch_result(int64_t n, const uint32_t *counts, const Job *job, double *btilde,
                           cudaStream_t st);
 cudaError_t launch_reset_job(Job *job, cudaStream_t st);
+cudaError_t read_device_clock(unsigned long long *ns, cudaStream_t st);
 cudaError_t launch_absorb(int64_t n, uint32_t *counts, const uint32_t *delta, Job *job, uint64_t samples,
                           cudaStream_t st);
 

@@ -1210,6 +1210,7 @@ __global__ void __launch_bounds__(NT, (2048 / NT / 2) > 0 ? (2048 / NT / 2) : 1)
                     job->last_maxf = Mf;
                     job->last_maxg = Mg;
                     if (stop) {
+                        job->stop_ns = global_ns();
                         job->stop_epoch = job->epoch;
                         job->stopped = 1;
                     }

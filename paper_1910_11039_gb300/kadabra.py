@@ -53,7 +53,7 @@ class QueryInfo(C.Structure):
                 ("expanded", C.c_uint64), ("touched", C.c_uint64), ("interior", C.c_uint64),
                 ("walk_scan", C.c_uint64), ("scaled", C.c_uint64), ("device_error", C.c_uint32),
                 ("slots", C.c_int32), ("threads", C.c_int32), ("offsets_64", C.c_int32),
-                ("budget_classes", C.c_int32)]
+                ("budget_classes", C.c_int32), ("stop_ns", C.c_uint64)]
 
 
 class TraceRec(C.Structure):
@@ -109,6 +109,8 @@ SIGNATURES = {
     "kadabra_sample_range": (_ST, [_P, C.c_int, _U64, _I64, _P, _P]),
     "kadabra_absorb": (_ST, [_P, _P, _U64, _P]),
     "kadabra_pipeline_begin": (_ST, [_P, _I64, C.c_int, _P]),
+    "kadabra_run_graph": (_ST, [_P, _I64, C.c_int, _I64, _P, C.POINTER(C.c_int)]),
+    "kadabra_device_clock": (_ST, [C.POINTER(_U64), _P]),
     "kadabra_batch_create": (_ST, [_I64, C.c_int32, C.c_int32, C.c_int, C.POINTER(_P)]),
     "kadabra_batch_free": (_ST, [_P]),
     "kadabra_batch_step": (_ST, [_P, _P, _I64, _U64, _P]),
@@ -185,6 +187,13 @@ def omega(eps, delta, vertex_diameter) -> float:
     out = C.c_double()
     _check(load().kadabra_omega(eps, delta, vertex_diameter, C.byref(out)))
     return out.value
+
+
+def device_clock(stream=None) -> int:
+    """Device global timer in ns (the clock of QueryInfo.stop_ns)."""
+    v = _U64()
+    _check(load().kadabra_device_clock(C.byref(v), _stream(stream)))
+    return v.value
 
 
 def sigma_bits(n, max_degree) -> int:
@@ -285,6 +294,13 @@ class Query:
     def absorb(self, delta_device_ptr, samples, stream=None):
         """c~ += delta, tau += samples (the epoch aggregate of a sharded run)."""
         _check(load().kadabra_absorb(self.handle, C.c_void_p(int(delta_device_ptr)), samples, _stream(stream)))
+
+    def run_graph(self, epoch_len, epochs_per_graph=4, max_epochs=1 << 30, stream=None) -> bool:
+        """Stream-ordered epochs replayed from a captured CUDA graph."""
+        st = C.c_int()
+        _check(load().kadabra_run_graph(self.handle, epoch_len, epochs_per_graph, max_epochs, _stream(stream),
+                                        C.byref(st)))
+        return bool(st.value)
 
     def pipeline_begin(self, epoch_len, frames=8, stream=None):
         _check(load().kadabra_pipeline_begin(self.handle, epoch_len, frames, _stream(stream)))

@@ -262,6 +262,25 @@ def test_sharded_run_driver_single_rank(K, orc):
         dist.destroy_process_group()
 
 
+@pytest.mark.parametrize("name,eps,E,k", [("er2000", 0.05, 100, 4), ("rmat14", 0.03, 500, 1), ("grid64", 0.05, 250, 7)])
+def test_graph_epochs_match_oracle(K, orc, name, eps, E, k):
+    g = GRAPHS[name]()
+    G = K.Graph.from_inputs(g)
+    q = K.Query(G, eps=eps, delta=0.1, seed=1)
+    assert q.run_graph(E, epochs_per_graph=k)
+    res = q.result()
+    counts, cal, LL, LU, R = orc.kadabra(g, eps, 0.1, seed=1, epoch_len=E)
+    assert res["tau"] == R.tau and res["stop_epoch"] == R.stop_epoch
+    assert np.array_equal(res["counts"], counts)
+    stop_ns = q.info().stop_ns
+    assert 0 < stop_ns <= K.device_clock()
+    # the instantiated graph is reused after a reset
+    q.reset()
+    assert q.info().stop_ns == 0
+    assert q.run_graph(E, epochs_per_graph=k)
+    assert np.array_equal(q.result()["counts"], counts)
+
+
 def test_reset_reproduces(K):
     g = GRAPHS["rmat12"]()
     G = K.Graph.from_inputs(g)
