@@ -263,6 +263,15 @@ kadabra_status kadabra_batch_step(kadabra_batch *b, kadabra_query *const *qs, in
                                   void *cuda_stream);
 /* Device time (ms) of the most recent step (CUDA events on its stream).  Synchronises. */
 kadabra_status kadabra_batch_last_ms(kadabra_batch *b, float *ms);
+/* Which running query a CTA serves next.  ROUND_ROBIN (default): each pick
+ * starts the scan at the next query in turn, so running queries take samples
+ * at equal rates.  IN_ORDER: the first query in the array passed to
+ * kadabra_batch_step that can take a sample gets it, so earlier queries run
+ * at full width and later ones fill the slots they leave (a priority order,
+ * e.g. shortest expected work first or arrival order).  Results do not
+ * depend on the policy. */
+enum { KADABRA_BATCH_ROUND_ROBIN = 0, KADABRA_BATCH_IN_ORDER = 1 };
+kadabra_status kadabra_batch_set_policy(kadabra_batch *b, int policy);
 
 /* Sharded sampling (several ranks, one GPU each; Section I-A: samples are
  * independent, so a rank can take any subset of an epoch's sample indices).

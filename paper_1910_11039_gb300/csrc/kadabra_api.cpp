@@ -124,6 +124,7 @@ struct kadabra_batch {
     kadabra::BatchState *d_bs = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     bool have_step = false;
+    int policy = 0;
 };
 
 namespace kadabra {
@@ -913,10 +914,20 @@ extern "C" kadabra_status kadabra_batch_step(kadabra_batch *b, kadabra_query *co
     B.grid = b->slots;
     B.threads = b->threads;
     B.off64 = b->off64;
+    B.policy = b->policy;
     KCUDA(cudaEventRecord(b->ev0, st), "event");
     KCUDA(kadabra::launch_batch(B, st), "batch kernel launch");
     KCUDA(cudaEventRecord(b->ev1, st), "event");
     b->have_step = true;
+    return KADABRA_OK;
+}
+
+extern "C" kadabra_status kadabra_batch_set_policy(kadabra_batch *b, int policy)
+{
+    if (!b) return fail(KADABRA_ERR_INVALID_ARG, "batch is null");
+    if (policy != KADABRA_BATCH_ROUND_ROBIN && policy != KADABRA_BATCH_IN_ORDER)
+        return fail(KADABRA_ERR_INVALID_ARG, "unknown batch policy");
+    b->policy = policy;
     return KADABRA_OK;
 }
 

@@ -159,6 +159,7 @@ struct BatchLaunch {
     unsigned long long budget; // samples this launch may hand out (0 = no limit)
     unsigned long long spin_limit;
     int grid, threads, off64;
+    int policy;                // 0: round robin over the queries; 1: first in array order
 };
 
 cudaError_t launch_batch(const BatchLaunch &a, cudaStream_t st);

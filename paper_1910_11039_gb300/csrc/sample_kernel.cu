@@ -1064,68 +1064,107 @@ __global__ void __launch_bounds__(NT, (2048 / NT / 2) > 0 ? (2048 / NT / 2) : 1)
     volatile BatchState *vbs = B.bs;
 
     for (;;) {
-        if (tid == 0) {
-            pm.take = 0;
-            s_qi = -1;
-            bool stop_launch = vbs->abort != 0;
-            if (!stop_launch && B.budget && atomicAdd(&B.bs->taken, 0ULL) >= B.budget) stop_launch = true;
+        // Warp 0 picks the next sample: its lanes read the state of 32
+        // queries at a time and the first eligible one in scan order (round
+        // robin from a per-pick ticket, or array order) is tried.
+        if (tid < 32) {
+            const int lane = tid;
+            int take = 0;
+            bool stop_launch = false;
+            if (lane == 0) {
+                pm.take = 0;
+                s_qi = -1;
+                stop_launch = vbs->abort != 0;
+                if (!stop_launch && B.budget && atomicAdd(&B.bs->taken, 0ULL) >= B.budget) stop_launch = true;
+            }
+            stop_launch = __shfl_sync(0xffffffffu, stop_launch ? 1 : 0, 0) != 0;
             if (!stop_launch) {
-                const unsigned int start = atomicAdd(&B.bs->ticket, 1u) % (unsigned int)B.nq;
+                unsigned int start = 0;
+                if (B.policy == 0 && lane == 0) start = atomicAdd(&B.bs->ticket, 1u) % (unsigned int)B.nq;
+                start = __shfl_sync(0xffffffffu, start, 0);
                 unsigned long long polls = 0;
                 for (;;) {
-                    bool all_done = true;
-                    for (int k = 0; k < B.nq && !pm.take; ++k) {
-                        const int qi = (int)((start + (unsigned int)k) % (unsigned int)B.nq);
-                        QueryDesc *Q = B.queries + qi;
-                        PipeState *st = Q->ps;
-                        volatile PipeState *vst = st;
-                        volatile Job *vjob = Q->job;
-                        if (vjob->stopped || vst->abort) continue;
-                        const unsigned long long R = vst->R;
-                        const unsigned long long nx = vst->next_idx;
-                        if (nx >= R) continue;
-                        all_done = false;
-                        const long long E = Q->E;
-                        const int F = Q->F;
-                        if ((long long)(nx / (unsigned long long)E) >= vst->next_check + F) continue;   // logs all in use
-                        const unsigned long long i = atomicAdd(&st->next_idx, 1ULL);
-                        if (i >= R) continue;
-                        const long long e = (long long)(i / (unsigned long long)E);
-                        // rare: another CTA took the indices in between; wait (bounded) for the log
-                        unsigned long long w = 0;
-                        bool ok = true;
-                        while (e >= vst->next_check + F) {
-                            if (vjob->stopped || vst->abort) {
-                                ok = false;
-                                break;
+                    bool any_running = false;
+                    for (int base = 0; base < B.nq && !take; base += 32) {
+                        const int k = base + lane;
+                        int qi = -1;
+                        bool running = false, eligible = false;
+                        if (k < B.nq) {
+                            qi = (int)((start + (unsigned int)k) % (unsigned int)B.nq);
+                            const QueryDesc *Q = B.queries + qi;
+                            volatile PipeState *vst = Q->ps;
+                            volatile Job *vjob = Q->job;
+                            if (!vjob->stopped && !vst->abort) {
+                                const unsigned long long nx = vst->next_idx;
+                                if (nx < vst->R) {
+                                    running = true;
+                                    eligible = (long long)(nx / (unsigned long long)Q->E) < vst->next_check + Q->F;
+                                }
                             }
-                            if (++w > B.spin_limit) {
-                                atomicOr(&Q->job->error, kErrTimeout);
-                                vst->abort = 1;
-                                ok = false;
-                                break;
-                            }
-                            __nanosleep(256);
                         }
-                        __threadfence();
-                        if (!ok) continue;
-                        pm.take = 1;
-                        pm.epoch = e;
-                        pm.idx = i;
-                        s_qi = qi;
+                        any_running |= __any_sync(0xffffffffu, running);
+                        unsigned int mask = __ballot_sync(0xffffffffu, eligible);
+                        while (mask && !take) {
+                            const int leader = __ffs(mask) - 1;
+                            int got = 0;
+                            if (lane == leader) {
+                                QueryDesc *Q = B.queries + qi;
+                                PipeState *st = Q->ps;
+                                volatile PipeState *vst = st;
+                                volatile Job *vjob = Q->job;
+                                const unsigned long long R = vst->R;
+                                const unsigned long long i = atomicAdd(&st->next_idx, 1ULL);
+                                if (i < R) {
+                                    const long long E = Q->E;
+                                    const int F = Q->F;
+                                    const long long e = (long long)(i / (unsigned long long)E);
+                                    // rare: another CTA took the indices in between; wait (bounded) for the log
+                                    unsigned long long w = 0;
+                                    bool ok = true;
+                                    while (e >= vst->next_check + F) {
+                                        if (vjob->stopped || vst->abort) {
+                                            ok = false;
+                                            break;
+                                        }
+                                        if (++w > B.spin_limit) {
+                                            atomicOr(&Q->job->error, kErrTimeout);
+                                            vst->abort = 1;
+                                            ok = false;
+                                            break;
+                                        }
+                                        __nanosleep(256);
+                                    }
+                                    __threadfence();
+                                    if (ok) {
+                                        got = 1;
+                                        pm.epoch = e;
+                                        pm.idx = i;
+                                        s_qi = qi;
+                                    }
+                                }
+                            }
+                            take = __shfl_sync(0xffffffffu, got, leader);
+                            mask &= ~(1u << leader);
+                        }
                     }
-                    if (pm.take || all_done) break;
+                    if (take || !any_running) break;
                     // every running query waits for an epoch check: back off (bounded)
                     if (++polls > B.spin_limit) {
-                        atomicOr(&B.bs->abort, 1u);
-                        for (int k = 0; k < B.nq; ++k) atomicOr(&B.queries[k].job->error, kErrTimeout);
+                        if (lane == 0) {
+                            atomicOr(&B.bs->abort, 1u);
+                            for (int k = 0; k < B.nq; ++k) atomicOr(&B.queries[k].job->error, kErrTimeout);
+                        }
                         break;
                     }
                     __nanosleep(512);
                 }
-                if (pm.take && B.budget) atomicAdd(&B.bs->taken, 1ULL);
+                if (lane == 0 && take) {
+                    pm.take = 1;
+                    if (B.budget) atomicAdd(&B.bs->taken, 1ULL);
+                }
             }
-            if (pm.take) {
+            __syncwarp();
+            if (lane == 0 && take) {
                 qd = B.queries[s_qi];
                 SampleLaunch t{};
                 t.n = qd.n;

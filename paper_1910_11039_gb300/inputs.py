@@ -29,6 +29,7 @@ __all__ = [
     "Graph", "csr_from_edges", "largest_component", "er_graph", "rmat_graph",
     "grid_graph", "rgg_graph", "path_graph", "star_graph", "cycle_graph",
     "complete_graph", "full_grid_graph", "config_graph", "CONFIGS",
+    "graph_from_spec", "batched_specs",
 ]
 
 
@@ -235,10 +236,9 @@ CONFIGS = {
 }
 
 
-@functools.lru_cache(maxsize=8)
-def config_graph(name: str) -> Graph:
-    """Build a named workload graph (cached per process)."""
-    cfg = dict(CONFIGS[name])
+def graph_from_spec(spec: dict, name: str = "") -> Graph:
+    """Build a graph from a generator spec ``dict(kind=..., **arguments)``."""
+    cfg = dict(spec)
     kind = cfg.pop("kind")
     if kind == "er":
         g = er_graph(**cfg)
@@ -250,4 +250,31 @@ def config_graph(name: str) -> Graph:
         g = rgg_graph(**cfg)
     else:
         raise KeyError(kind)
-    return dataclasses.replace(g, name=name)
+    return dataclasses.replace(g, name=name or g.name)
+
+
+@functools.lru_cache(maxsize=8)
+def config_graph(name: str) -> Graph:
+    """Build a named workload graph (cached per process)."""
+    return graph_from_spec(CONFIGS[name], name)
+
+
+def batched_specs(count: int = 64, n_rgg: int = 8, seed0: int = 1000,
+                  scales=(12, 18), edge_factors=(8, 32), rgg_n=(50_000, 500_000)) -> list[dict]:
+    """The many-graphs-of-uneven-size workload: ``count - n_rgg`` R-MAT graphs
+    (scale uniform in scales, edge factor uniform in edge_factors, both
+    inclusive) followed by ``n_rgg`` random geometric graphs (n uniform in
+    rgg_n, average degree 10).  Graph i draws its sizes from a generator
+    seeded seed0 + i and its edges with seed seed0 + i.  No largest-component
+    restriction: a pair in different components counts as a sample with an
+    empty path."""
+    specs = []
+    for i in range(count):
+        rng = np.random.default_rng(seed0 + i)
+        if i < count - n_rgg:
+            specs.append(dict(kind="rmat", scale=int(rng.integers(scales[0], scales[1] + 1)),
+                              edge_factor=int(rng.integers(edge_factors[0], edge_factors[1] + 1)), seed=seed0 + i))
+        else:
+            specs.append(dict(kind="rgg", n=int(rng.integers(rgg_n[0], rgg_n[1] + 1)), avg_degree=10,
+                              seed=seed0 + i))
+    return specs

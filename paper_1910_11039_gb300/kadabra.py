@@ -110,6 +110,7 @@ SIGNATURES = {
     "kadabra_absorb": (_ST, [_P, _P, _U64, _P]),
     "kadabra_pipeline_begin": (_ST, [_P, _I64, C.c_int, _P]),
     "kadabra_run_graph": (_ST, [_P, _I64, C.c_int, _I64, _P, C.POINTER(C.c_int)]),
+    "kadabra_batch_set_policy": (_ST, [_P, C.c_int]),
     "kadabra_device_clock": (_ST, [C.POINTER(_U64), _P]),
     "kadabra_batch_create": (_ST, [_I64, C.c_int32, C.c_int32, C.c_int, C.POINTER(_P)]),
     "kadabra_batch_free": (_ST, [_P]),
@@ -377,10 +378,19 @@ def sample_static(graph: Graph, seed, tag, first, count, counts_device_ptr, stre
 class Batch:
     """Sampling scratch shared by many queries stepped in one launch."""
 
-    def __init__(self, max_n, slots=0, threads=1024, offsets_64=False):
+    ROUND_ROBIN, IN_ORDER = 0, 1
+
+    def __init__(self, max_n, slots=0, threads=1024, offsets_64=False, policy=0):
         self.handle = C.c_void_p()
         _check(load().kadabra_batch_create(max_n, slots, threads, int(bool(offsets_64)), C.byref(self.handle)))
         self.max_n = max_n
+        self.threads = threads
+        if policy:
+            self.set_policy(policy)
+
+    def set_policy(self, policy):
+        _check(load().kadabra_batch_set_policy(self.handle, int(policy)))
+        self.policy = policy
 
     def step(self, queries, sample_budget=0, stream=None):
         arr = (C.c_void_p * len(queries))(*[q.handle.value for q in queries])

@@ -68,9 +68,10 @@ def check_all(K, orc, qs, specs=SPECS):
         assert np.array_equal(res["counts"], counts), name
 
 
-def test_batch_one_launch_matches_alone(K, orc, graphs):
+@pytest.mark.parametrize("policy", [0, 1])
+def test_batch_one_launch_matches_alone(K, orc, graphs, policy):
     qs = make_queries(K, graphs)
-    b = K.Batch(max(g.n for g, _ in graphs.values()))
+    b = K.Batch(max(g.n for g, _ in graphs.values()), policy=policy)
     for q, E, F, g in qs:
         q.pipeline_begin(E, frames=F)
     b.step([q for q, *_ in qs])
@@ -78,10 +79,10 @@ def test_batch_one_launch_matches_alone(K, orc, graphs):
     check_all(K, orc, qs)
 
 
-@pytest.mark.parametrize("budget", [1, 97, 1000])
-def test_batch_in_small_steps_matches_alone(K, orc, graphs, budget):
+@pytest.mark.parametrize("budget,policy", [(1, 0), (97, 0), (1000, 0), (97, 1)])
+def test_batch_in_small_steps_matches_alone(K, orc, graphs, budget, policy):
     qs = make_queries(K, graphs)
-    b = K.Batch(max(g.n for g, _ in graphs.values()), slots=64)
+    b = K.Batch(max(g.n for g, _ in graphs.values()), slots=64, policy=policy)
     for q, E, F, g in qs:
         q.pipeline_begin(E, frames=F)
     for _ in range(100000):
@@ -119,3 +120,27 @@ def test_batch_rejects_unbegun_and_oversized(K, graphs):
     with pytest.raises(K.KadabraError) as ei:
         b.step([q])
     assert ei.value.status == 1
+    with pytest.raises(K.KadabraError) as ei:
+        b.set_policy(2)
+    assert ei.value.status == 1
+
+
+def test_autotuned_schedule_matches_oracle(K, orc, graphs):
+    """Every trial of the tuner is a full run; the chosen schedule's results
+    are those of each query alone with the schedule's epoch length."""
+    from paper_1910_11039_gb300 import autotune as AT
+    qs = make_queries(K, graphs)
+    Q = [q for q, *_ in qs]
+    pool = AT.BatchPool(max(g.n for g, _ in graphs.values()))
+    best, trials, secs = AT.autotune(Q, pool, threads=(256, 1024), divisors=(16, 64), frames=(4,))
+    assert len(trials) == 5 and secs > 0          # base, one thread count, two divisors, one frame count
+    assert best.threads in (256, 1024) and best.divisor in (16, 32, 64) and best.frames in (4, 8)
+    r = AT.run_mix(pool.get(best.threads), Q, best)
+    assert all(r["stopped"])
+    for (q, _, _, g), (name, eps, seed, _, _), E in zip(qs, SPECS, r["epoch_lens"]):
+        counts, R = expected(orc, g, eps, seed, E)
+        res = q.result()
+        assert res["tau"] == R.tau and res["stop_epoch"] == R.stop_epoch, name
+        assert np.array_equal(res["counts"], counts), name
+    # time-to-stop is measured from the launch's submission on the device clock
+    assert all(0 < t <= r["ms"] + 5.0 for t in r["tts_ms"])

@@ -1,0 +1,36 @@
+"""Host-side logic that needs no GPU: workload specs and schedule rules."""
+import math
+
+from paper_1910_11039_gb300 import inputs as I
+
+
+def test_batched_specs_follow_the_recipe():
+    sp = I.batched_specs()
+    assert len(sp) == 64
+    rmat, rgg = sp[:56], sp[56:]
+    assert all(d["kind"] == "rmat" for d in rmat) and all(d["kind"] == "rgg" for d in rgg)
+    assert all(12 <= d["scale"] <= 18 and 8 <= d["edge_factor"] <= 32 for d in rmat)
+    assert all(50_000 <= d["n"] <= 500_000 and d["avg_degree"] == 10 for d in rgg)
+    assert [d["seed"] for d in sp] == list(range(1000, 1064))
+    assert sp == I.batched_specs()                     # deterministic
+    # the draws cover the ranges (both ends of the scale range appear)
+    scales = {d["scale"] for d in rmat}
+    assert 12 in scales and 18 in scales
+
+
+def test_graph_from_spec_matches_config_graph():
+    g1 = I.config_graph("rmat12")
+    g2 = I.graph_from_spec(I.CONFIGS["rmat12"], "rmat12")
+    assert (g1.offsets == g2.offsets).all() and (g1.cols == g2.cols).all()
+
+
+def test_schedule_epoch_rule():
+    from paper_1910_11039_gb300.autotune import Schedule
+    s = Schedule(divisor=32, min_epoch=32, max_epoch=4096)
+    for omega in (1, 10, 1000, 5000, 17_500, 35_000, 10**6, 10**9):
+        E = s.epoch_len(omega)
+        assert 32 <= E <= 4096 and E & (E - 1) == 0
+        if 32 * 32 <= omega <= 4096 * 32:
+            # nearest power of two to omega / divisor (in log scale)
+            assert abs(math.log2(E) - math.log2(omega / 32)) <= 0.5 + 1e-12
+    assert Schedule(divisor=8).epoch_len(8192) == 1024
