@@ -107,6 +107,10 @@ typedef struct kadabra_query_info {
     int32_t offsets_64;         /* 1 if the graph uses int64 offsets                       */
     int32_t budget_classes;     /* distinct (L_L, L_U) pairs                               */
     uint64_t stop_ns;           /* device global timer (ns) when the stop was decided, or 0 */
+    int32_t phase;              /* 0 created, 1 calibrating in a batch, 2 calibrated        */
+    int32_t pad0;
+    uint64_t cal_done;          /* calibration samples completed (phase 1), else n_calib    */
+    uint64_t device_bytes;      /* device memory the query holds (not the graph's)          */
 } kadabra_query_info;
 
 /* Per-sample record written by kadabra_sample_trace (one per sample index). */
@@ -183,6 +187,24 @@ kadabra_status kadabra_graph_info(const kadabra_graph *g, int64_t *n, int64_t *n
                                   int64_t *max_degree, int *offsets_is_64);
 
 /* ---- query: the three phases (Section III-A) --------------------------- */
+
+/* Phase 1 alone: VD and omega, and the query's device state (counters,
+ * budgets, calibration counts), without calibration samples.  Synchronises.
+ * The query then takes its calibration samples inside a batch
+ * (kadabra_calibration_begin, kadabra_batch_step until
+ * kadabra_query_info.cal_done == n_calib, kadabra_calibration_finish); no
+ * other sampling call accepts it before that.  The calibration samples are
+ * the same ones kadabra_calibrate takes, so the budgets are identical. */
+kadabra_status kadabra_query_create(kadabra_graph *g, const kadabra_params *p, void *cuda_stream,
+                                    kadabra_query **out);
+/* Hand out calibration sample indices [0, n_calib) (stream tag 0) to the
+ * next batch steps that include the query (async).  KADABRA_ERR_STATE unless
+ * the query came from kadabra_query_create and has not begun calibrating. */
+kadabra_status kadabra_calibration_begin(kadabra_query *q, void *cuda_stream);
+/* Phase 2 on the host once all calibration samples completed: delta_L,
+ * delta_U and the budget classes, uploaded to the device.  Synchronises.
+ * KADABRA_ERR_STATE while samples are outstanding. */
+kadabra_status kadabra_calibration_finish(kadabra_query *q, void *cuda_stream);
 
 /* Phases 1 and 2.  Computes VD (or takes it from `p`) and omega, runs the
  * calibration samples on the device (stream tag 0, sample indices

@@ -66,6 +66,7 @@ struct kadabra_graph {
     uint32_t *d_queues = nullptr;
     int ws_slots = 0;
     int ws_threads = 0;
+    int ws_req = 0;               // slots requested when the scratch was sized
 };
 
 struct kadabra_query {
@@ -104,6 +105,7 @@ struct kadabra_query {
     kadabra::QueryDesc *d_desc = nullptr;    // descriptor for single-query launches
     kadabra::BatchState *d_bs = nullptr;
     bool pipe_begun = false;
+    int phase = 0;                           // 0 created, 1 calibrating in a batch, 2 calibrated
     int64_t pipe_E = 0;
     int pipe_F = 0;
     unsigned int pipe_cap = 0;
@@ -459,7 +461,8 @@ static kadabra_status ensure_workspace(kadabra_graph *g, int want_slots, int thr
     if (per_sm < 1) per_sm = 1;
     int slots = want_slots > 0 ? want_slots : sms * per_sm;
     const size_t per_slot = (size_t)g->n * (sizeof(kadabra::SlotRec) + sizeof(uint32_t));
-    if (g->d_recs && g->ws_slots >= slots && g->ws_threads == threads) return KADABRA_OK;
+    if (g->d_recs && g->ws_threads == threads && (g->ws_slots >= slots || g->ws_req == slots)) return KADABRA_OK;
+    const int requested = slots;
     cudaDeviceSynchronize();
     cudaFree(g->d_recs);
     cudaFree(g->d_queues);
@@ -485,6 +488,7 @@ static kadabra_status ensure_workspace(kadabra_graph *g, int want_slots, int thr
     }
     g->ws_slots = slots;
     g->ws_threads = threads;
+    g->ws_req = requested;
     return KADABRA_OK;
 }
 
@@ -558,8 +562,8 @@ static int clamp_grid(const kadabra_query *q, int64_t count)
     return (int)g;
 }
 
-extern "C" kadabra_status kadabra_calibrate(kadabra_graph *g, const kadabra_params *pin, void *cuda_stream,
-                                            kadabra_query **out)
+// Phase 1 and the query's device state; no sampling yet.
+static kadabra_status create_query(kadabra_graph *g, const kadabra_params *pin, cudaStream_t st, kadabra_query **out)
 {
     if (!g || !out) return fail(KADABRA_ERR_INVALID_ARG, "graph or out is null");
     kadabra_params p;
@@ -574,7 +578,6 @@ extern "C" kadabra_status kadabra_calibrate(kadabra_graph *g, const kadabra_para
     if (p.threads != 128 && p.threads != 256 && p.threads != 512 && p.threads != 1024)
         return fail(KADABRA_ERR_INVALID_ARG, "threads must be 128, 256, 512 or 1024");
     if (g->n < 2) return fail(KADABRA_ERR_INVALID_ARG, "sampling pairs needs n >= 2");
-    cudaStream_t st = as_stream(cuda_stream);
 
     kadabra_query *q = new kadabra_query();
     q->g = g;
@@ -614,13 +617,6 @@ extern "C" kadabra_status kadabra_calibrate(kadabra_graph *g, const kadabra_para
         return fail(KADABRA_ERR_INVALID_ARG, "n_calib must be < 2^32");
     }
 
-    kadabra_status s = ensure_workspace(g, p.slots, p.threads, p.scratch_fraction);
-    if (s != KADABRA_OK) {
-        delete q;
-        return s;
-    }
-    q->slots = p.slots > 0 && p.slots < g->ws_slots ? p.slots : g->ws_slots;
-
     const size_t n = (size_t)g->n;
     cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&q->d_counts), n * 4);
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&q->d_cal), n * 4);
@@ -629,6 +625,7 @@ extern "C" kadabra_status kadabra_calibrate(kadabra_graph *g, const kadabra_para
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&q->d_job), sizeof(Job));
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&q->d_cal_job), sizeof(Job));
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&q->d_trace_job), sizeof(Job));
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&q->d_cls), n * 4);
     if (e == cudaSuccess)
         e = cudaMalloc(reinterpret_cast<void **>(&q->d_launch), sizeof(kadabra::Counters) * kadabra::kLaunchLog);
     for (int i = 0; i < kadabra::kLaunchLog && e == cudaSuccess; ++i) {
@@ -645,7 +642,66 @@ extern "C" kadabra_status kadabra_calibrate(kadabra_graph *g, const kadabra_para
         delete q;
         return cuda_fail(e, "allocate query state");
     }
+    *out = q;
+    return KADABRA_OK;
+}
 
+// Sampling scratch of the graph for launches that serve this query alone.
+static kadabra_status ready_workspace(kadabra_query *q)
+{
+    kadabra_status s = ensure_workspace(q->g, q->p.slots, q->p.threads, q->p.scratch_fraction);
+    if (s != KADABRA_OK) return s;
+    q->slots = q->p.slots > 0 && q->p.slots < q->g->ws_slots ? q->p.slots : q->g->ws_slots;
+    return KADABRA_OK;
+}
+
+// Phase 2 on the host: budgets from the calibration counts.  Synchronises.
+static kadabra_status finish_calibration(kadabra_query *q, cudaStream_t st)
+{
+    const size_t n = (size_t)q->g->n;
+    std::vector<uint32_t> cal(n);
+    Job cj{};
+    cudaError_t e = cudaMemcpyAsync(cal.data(), q->d_cal, n * 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&cj, q->d_cal_job, sizeof(Job), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "calibration samples");
+    kadabra_status s = device_error_status(cj);
+    if (s != KADABRA_OK) return s;
+    std::vector<double2> L;
+    std::vector<uint32_t> cls;
+    std::vector<double2> Ltab;
+    budgets(q->g->n, cal, q->n_calib, q->p.eps, q->p.delta, q->p.delta_rule, q->p.beta, L, cls, Ltab, &q->balance_C);
+    cudaFree(q->d_Ltab);
+    cudaFree(q->d_cmax);
+    q->d_Ltab = nullptr;
+    q->d_cmax = nullptr;
+    q->nclass = (int)Ltab.size();
+    e = cudaMemcpyAsync(q->d_L, L.data(), n * sizeof(double2), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&q->d_Ltab), Ltab.size() * sizeof(double2));
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&q->d_cmax), Ltab.size() * 4);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(q->d_cls, cls.data(), n * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(q->d_Ltab, Ltab.data(), Ltab.size() * sizeof(double2), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "upload budgets");
+    q->phase = 2;
+    q->pipe_begun = false;
+    return KADABRA_OK;
+}
+
+extern "C" kadabra_status kadabra_calibrate(kadabra_graph *g, const kadabra_params *pin, void *cuda_stream,
+                                            kadabra_query **out)
+{
+    cudaStream_t st = as_stream(cuda_stream);
+    kadabra_query *q = nullptr;
+    kadabra_status s = create_query(g, pin, st, &q);
+    if (s != KADABRA_OK) return s;
+    s = ready_workspace(q);
+    if (s != KADABRA_OK) {
+        free_query_device(q);
+        delete q;
+        return s;
+    }
     // phase 2: calibration samples (stream tag 0) on the device
     kadabra::SampleLaunch a = base_launch(q);
     a.counts = q->d_cal;
@@ -655,43 +711,61 @@ extern "C" kadabra_status kadabra_calibrate(kadabra_graph *g, const kadabra_para
     a.epoch_len = q->n_calib;
     a.clip = 0;
     a.grid = clamp_grid(q, q->n_calib);
-    e = kadabra::launch_sample(a, st);
-    std::vector<uint32_t> cal(n);
-    Job cj{};
-    if (e == cudaSuccess) e = cudaMemcpyAsync(cal.data(), q->d_cal, n * 4, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&cj, q->d_cal_job, sizeof(Job), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaError_t e = kadabra::launch_sample(a, st);
     if (e != cudaSuccess) {
         free_query_device(q);
         delete q;
         return cuda_fail(e, "calibration samples");
     }
-    s = device_error_status(cj);
+    s = finish_calibration(q, st);
     if (s != KADABRA_OK) {
         free_query_device(q);
         delete q;
         return s;
     }
-    std::vector<double2> L;
-    std::vector<uint32_t> cls;
-    std::vector<double2> Ltab;
-    budgets(g->n, cal, q->n_calib, p.eps, p.delta, p.delta_rule, p.beta, L, cls, Ltab, &q->balance_C);
-    q->nclass = (int)Ltab.size();
-    e = cudaMemcpyAsync(q->d_L, L.data(), n * sizeof(double2), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&q->d_cls), n * 4);
-    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&q->d_Ltab), Ltab.size() * sizeof(double2));
-    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&q->d_cmax), Ltab.size() * 4);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(q->d_cls, cls.data(), n * 4, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(q->d_Ltab, Ltab.data(), Ltab.size() * sizeof(double2), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) {
-        free_query_device(q);
-        delete q;
-        return cuda_fail(e, "upload budgets");
-    }
     *out = q;
     return KADABRA_OK;
+}
+
+extern "C" kadabra_status kadabra_query_create(kadabra_graph *g, const kadabra_params *p, void *cuda_stream,
+                                               kadabra_query **out)
+{
+    return create_query(g, p, as_stream(cuda_stream), out);
+}
+
+static kadabra_status ensure_pipe_state(kadabra_query *q)
+{
+    if (!q->d_pipe) KCUDA(cudaMalloc(reinterpret_cast<void **>(&q->d_pipe), sizeof(kadabra::PipeState)), "allocate pipeline state");
+    return KADABRA_OK;
+}
+
+extern "C" kadabra_status kadabra_calibration_begin(kadabra_query *q, void *cuda_stream)
+{
+    if (!q) return fail(KADABRA_ERR_INVALID_ARG, "query is null");
+    if (q->phase != 0) return fail(KADABRA_ERR_STATE, "query is already calibrating or calibrated");
+    cudaStream_t st = as_stream(cuda_stream);
+    kadabra_status s = ensure_pipe_state(q);
+    if (s != KADABRA_OK) return s;
+    KCUDA(cudaMemsetAsync(q->d_cal, 0, (size_t)q->g->n * 4, st), "clear calibration counts");
+    KCUDA(kadabra::launch_reset_job(q->d_cal_job, st), "reset calibration state");
+    // one epoch of n_calib samples, no check: the pipeline state only hands
+    // out indices [0, n_calib) and counts completions
+    KCUDA(kadabra::launch_pipe_begin(q->d_pipe, q->d_cal_job, (unsigned long long)q->n_calib, q->n_calib, st),
+          "begin calibration");
+    q->phase = 1;
+    return KADABRA_OK;
+}
+
+extern "C" kadabra_status kadabra_calibration_finish(kadabra_query *q, void *cuda_stream)
+{
+    if (!q) return fail(KADABRA_ERR_INVALID_ARG, "query is null");
+    if (q->phase != 1) return fail(KADABRA_ERR_STATE, "query is not calibrating (kadabra_calibration_begin)");
+    cudaStream_t st = as_stream(cuda_stream);
+    kadabra::PipeState ps{};
+    KCUDA(cudaMemcpyAsync(&ps, q->d_pipe, sizeof(ps), cudaMemcpyDeviceToHost, st), "read calibration progress");
+    KCUDA(cudaStreamSynchronize(st), "synchronise");
+    if (ps.done[0] < (unsigned int)q->n_calib) return fail(KADABRA_ERR_STATE, "calibration samples not complete");
+    return finish_calibration(q, st);
 }
 
 extern "C" kadabra_status kadabra_query_free(kadabra_query *q)
@@ -703,9 +777,23 @@ extern "C" kadabra_status kadabra_query_free(kadabra_query *q)
     return KADABRA_OK;
 }
 
-extern "C" kadabra_status kadabra_sample_epoch(kadabra_query *q, int64_t n_samples, void *cuda_stream)
+static kadabra_status need_calibrated(kadabra_query *q)
 {
     if (!q) return fail(KADABRA_ERR_INVALID_ARG, "query is null");
+    if (q->phase != 2) return fail(KADABRA_ERR_STATE, "query is not calibrated");
+    return KADABRA_OK;
+}
+
+#define KREADY(q)                                          \
+    do {                                                   \
+        kadabra_status s_ = need_calibrated(q);            \
+        if (s_ == KADABRA_OK) s_ = ready_workspace(q);     \
+        if (s_ != KADABRA_OK) return s_;                   \
+    } while (0)
+
+extern "C" kadabra_status kadabra_sample_epoch(kadabra_query *q, int64_t n_samples, void *cuda_stream)
+{
+    KREADY(q);
     if (n_samples < 0 || n_samples >= (int64_t(1) << 32))
         return fail(KADABRA_ERR_INVALID_ARG, "n_samples must be in [0, 2^32)");
     if (n_samples == 0) return KADABRA_OK;
@@ -731,7 +819,10 @@ extern "C" kadabra_status kadabra_sample_epoch(kadabra_query *q, int64_t n_sampl
 
 extern "C" kadabra_status kadabra_pipeline_begin(kadabra_query *q, int64_t epoch_len, int frames, void *cuda_stream)
 {
-    if (!q) return fail(KADABRA_ERR_INVALID_ARG, "query is null");
+    {
+        kadabra_status s = need_calibrated(q);
+        if (s != KADABRA_OK) return s;
+    }
     if (epoch_len <= 0 || epoch_len >= (int64_t(1) << 40)) return fail(KADABRA_ERR_INVALID_ARG, "epoch_len out of range");
     if (frames <= 0) frames = 8;
     if (frames > kadabra::kMaxFrames) return fail(KADABRA_ERR_INVALID_ARG, "frames must be <= 16");
@@ -748,7 +839,10 @@ extern "C" kadabra_status kadabra_pipeline_begin(kadabra_query *q, int64_t epoch
         KCUDA(cudaMalloc(reinterpret_cast<void **>(&q->d_logs), need * 4), "allocate epoch logs");
         q->logs_alloc = need;
     }
-    if (!q->d_pipe) KCUDA(cudaMalloc(reinterpret_cast<void **>(&q->d_pipe), sizeof(kadabra::PipeState)), "allocate pipeline state");
+    {
+        kadabra_status s = ensure_pipe_state(q);
+        if (s != KADABRA_OK) return s;
+    }
     KCUDA(kadabra::launch_pipe_begin(q->d_pipe, q->d_job, q->omega_ceil, epoch_len, st), "begin pipeline");
     // per-class maxima of the counters the pipeline starts from
     KCUDA(cudaMemsetAsync(q->d_cmax, 0, (size_t)q->nclass * 4, st), "clear class maxima");
@@ -783,11 +877,24 @@ static kadabra::QueryDesc make_desc(const kadabra_query *q, kadabra::Counters *l
     d.job = q->d_job;
     d.ps = q->d_pipe;
     d.launch_ctr = launch_ctr;
+    d.tag = 1;
+    if (q->phase == 1) {
+        // calibration samples: one epoch of n_calib samples counted into the
+        // calibration counters, no logs and no check
+        d.tag = 0;
+        d.E = q->n_calib;
+        d.F = 1;
+        d.log_cap = 0;
+        d.logs = nullptr;
+        d.counts = q->d_cal;
+        d.job = q->d_cal_job;
+    }
     return d;
 }
 
 extern "C" kadabra_status kadabra_run_pipelined(kadabra_query *q, int64_t epoch_len, int frames, void *cuda_stream)
 {
+    KREADY(q);
     kadabra_status s = kadabra_pipeline_begin(q, epoch_len, frames, cuda_stream);
     if (s != KADABRA_OK) return s;
     cudaStream_t st = as_stream(cuda_stream);
@@ -885,7 +992,8 @@ extern "C" kadabra_status kadabra_batch_step(kadabra_batch *b, kadabra_query *co
     for (int64_t i = 0; i < count; ++i) {
         const kadabra_query *q = qs[i];
         if (!q) return fail(KADABRA_ERR_INVALID_ARG, "null query in batch");
-        if (!q->pipe_begun) return fail(KADABRA_ERR_STATE, "query not begun (kadabra_pipeline_begin)");
+        if (q->phase == 0 || (q->phase == 2 && !q->pipe_begun))
+            return fail(KADABRA_ERR_STATE, "query not begun (kadabra_pipeline_begin or kadabra_calibration_begin)");
         if (q->g->n > b->max_n) return fail(KADABRA_ERR_INVALID_ARG, "query graph larger than the batch's max_n");
         if (q->g->off64 != b->off64) return fail(KADABRA_ERR_INVALID_ARG, "query offset width differs from the batch's");
         descs[(size_t)i] = make_desc(q, nullptr);
@@ -942,7 +1050,10 @@ extern "C" kadabra_status kadabra_batch_last_ms(kadabra_batch *b, float *ms)
 
 extern "C" kadabra_status kadabra_check_stop_async(kadabra_query *q, void *cuda_stream)
 {
-    if (!q) return fail(KADABRA_ERR_INVALID_ARG, "query is null");
+    {
+        kadabra_status s = need_calibrated(q);
+        if (s != KADABRA_OK) return s;
+    }
     kadabra::CheckLaunch c{};
     c.n = q->g->n;
     c.counts = q->d_counts;
@@ -1005,6 +1116,7 @@ extern "C" kadabra_status kadabra_run(kadabra_query *q, int64_t epoch_len, int64
 extern "C" kadabra_status kadabra_sample_range(kadabra_query *q, int tag, uint64_t first, int64_t count,
                                                uint32_t *counts, void *cuda_stream)
 {
+    KREADY(q);
     if (!q || !counts) return fail(KADABRA_ERR_INVALID_ARG, "query or counts is null");
     if (tag != 0 && tag != 1) return fail(KADABRA_ERR_INVALID_ARG, "tag must be 0 or 1");
     if (count < 0 || count >= (int64_t(1) << 32)) return fail(KADABRA_ERR_INVALID_ARG, "count must be in [0, 2^32)");
@@ -1027,6 +1139,10 @@ extern "C" kadabra_status kadabra_sample_range(kadabra_query *q, int tag, uint64
 
 extern "C" kadabra_status kadabra_absorb(kadabra_query *q, const uint32_t *delta, uint64_t samples, void *cuda_stream)
 {
+    {
+        kadabra_status s = need_calibrated(q);
+        if (s != KADABRA_OK) return s;
+    }
     if (!q || !delta) return fail(KADABRA_ERR_INVALID_ARG, "query or delta is null");
     KCUDA(kadabra::launch_absorb(q->g->n, q->d_counts, delta, q->d_job, samples, as_stream(cuda_stream)),
           "absorb kernel launch");
@@ -1036,6 +1152,7 @@ extern "C" kadabra_status kadabra_absorb(kadabra_query *q, const uint32_t *delta
 extern "C" kadabra_status kadabra_run_graph(kadabra_query *q, int64_t epoch_len, int epochs_per_graph, int64_t max_epochs,
                                             void *cuda_stream, int *stopped)
 {
+    KREADY(q);
     if (!q) return fail(KADABRA_ERR_INVALID_ARG, "query is null");
     if (epoch_len <= 0 || epoch_len >= (int64_t(1) << 32) || epochs_per_graph <= 0 || epochs_per_graph > 4096 ||
         max_epochs <= 0)
@@ -1093,6 +1210,10 @@ extern "C" kadabra_status kadabra_run_graph(kadabra_query *q, int64_t epoch_len,
 
 extern "C" kadabra_status kadabra_query_reset(kadabra_query *q, void *cuda_stream)
 {
+    {
+        kadabra_status s = need_calibrated(q);
+        if (s != KADABRA_OK) return s;
+    }
     if (!q) return fail(KADABRA_ERR_INVALID_ARG, "query is null");
     cudaStream_t st = as_stream(cuda_stream);
     KCUDA(cudaMemsetAsync(q->d_counts, 0, (size_t)q->g->n * 4, st), "reset counters");
@@ -1157,6 +1278,19 @@ extern "C" kadabra_status kadabra_query_get_info(kadabra_query *q, kadabra_query
     I.offsets_64 = q->g->off64;
     I.budget_classes = q->nclass;
     I.stop_ns = j.stopped ? j.stop_ns : 0ULL;
+    I.phase = q->phase;
+    I.cal_done = q->phase == 2 ? (uint64_t)q->n_calib : 0ULL;
+    if (q->phase == 1) {
+        kadabra::PipeState ps{};
+        cudaStream_t st = as_stream(cuda_stream);
+        KCUDA(cudaMemcpyAsync(&ps, q->d_pipe, sizeof(ps), cudaMemcpyDeviceToHost, st), "read calibration progress");
+        KCUDA(cudaStreamSynchronize(st), "synchronise");
+        I.cal_done = ps.done[0];
+    }
+    const uint64_t n = (uint64_t)q->g->n;
+    I.device_bytes = n * (4 + 4 + 16 + 8 + 4) + 3 * sizeof(Job) +
+                     sizeof(kadabra::Counters) * kadabra::kLaunchLog + (uint64_t)q->nclass * (16 + 4) +
+                     (uint64_t)q->logs_alloc * 4 + (q->d_pipe ? sizeof(kadabra::PipeState) : 0);
     *out = I;
     return KADABRA_OK;
 }
@@ -1164,7 +1298,10 @@ extern "C" kadabra_status kadabra_query_get_info(kadabra_query *q, kadabra_query
 extern "C" kadabra_status kadabra_query_budgets(kadabra_query *q, double *L_L, double *L_U, uint32_t *cal,
                                                 void *cuda_stream)
 {
-    if (!q) return fail(KADABRA_ERR_INVALID_ARG, "query is null");
+    {
+        kadabra_status s = need_calibrated(q);
+        if (s != KADABRA_OK) return s;
+    }
     cudaStream_t st = as_stream(cuda_stream);
     const size_t n = (size_t)q->g->n;
     std::vector<double2> L(n);
@@ -1187,6 +1324,10 @@ extern "C" kadabra_status kadabra_sample_trace(kadabra_query *q, int tag, uint64
     if (count <= 0 || count >= (int64_t(1) << 31)) return fail(KADABRA_ERR_INVALID_ARG, "count out of range");
     if (interior && path_cap <= 0) return fail(KADABRA_ERR_INVALID_ARG, "path_cap must be > 0");
     static_assert(sizeof(kadabra::TraceRec) == sizeof(kadabra_trace_rec), "trace record layout");
+    {
+        kadabra_status s = ready_workspace(q);
+        if (s != KADABRA_OK) return s;
+    }
     cudaStream_t st = as_stream(cuda_stream);
     kadabra::TraceRec *d_tr = nullptr;
     int32_t *d_path = nullptr;

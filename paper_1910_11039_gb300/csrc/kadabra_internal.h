@@ -135,7 +135,8 @@ struct QueryDesc {
     const double2 *Ltab;       // (L_L, L_U) of every class
     unsigned int *cmax;        // largest c~ in every class
     int nclass;
-    int pad;
+    int tag;                   // 1: adaptive phase (epochs, logs, checks); 0: calibration samples
+                               //    counted straight into `counts` (E = n_calib, F = 1, no check)
     double omega, eps;
     uint32_t *counts;          // c~
     Job *job;

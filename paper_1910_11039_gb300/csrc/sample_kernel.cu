@@ -58,6 +58,9 @@ constexpr int kMaxLayers = 64;     // BFS layers whose queue ranges are remember
 #define KADABRA_UNROLL 2
 #endif
 constexpr int kUnroll = KADABRA_UNROLL;   // adjacency entries in flight per thread
+#ifndef KADABRA_CLAIM_FIRST
+#define KADABRA_CLAIM_FIRST 0             // 1: claim targets without reading their record first
+#endif
 constexpr unsigned int kNone = 0xffffffffu;
 
 __device__ __forceinline__ unsigned int ldcg(const unsigned int *p) { return __ldcg(p); }
@@ -117,6 +120,9 @@ struct Smem {
     // per-layer accumulators
     unsigned int new_count;
     unsigned int meet_count;
+    unsigned long long lmax;         // largest path count of the new layer
+    unsigned long long ldeg;         // degree sum of the new frontier
+    int shv;                         // shift that scales the new layer (> 0: scale)
     unsigned long long e_scan;       // this sample
     unsigned long long expanded;
     // selection and walk
@@ -429,21 +435,19 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
         sh.e_scan = 0;
         sh.expanded = 0;
         sh.meet_count = 0;
+        sh.new_count = 0;
+        sh.lmax = 0;
+        sh.ldeg = 0;
+        sh.shv = 0;
         sh.chosen = -1;
+        sh.X = (sh.fdeg[0] <= sh.fdeg[1]) ? 0 : 1;
     }
     __syncthreads();
 
-    // A2: balanced bidirectional BFS, one whole layer per step
+    // A2: balanced bidirectional BFS, one whole layer per step.  The side of
+    // the next layer is chosen, and the layer accumulators cleared, by thread
+    // 0 at the end of the previous layer, inside that layer's last barrier.
     for (;;) {
-        if (tid == 0) {
-            const int Xs = (sh.fdeg[0] <= sh.fdeg[1]) ? 0 : 1;
-            sh.X = Xs;
-            sh.new_count = 0;
-            sh.meet_count = 0;
-            if (sh.layer[Xs] + 2u > 0xffffu) sh.status = 4;   // levels are 16-bit
-        }
-        __syncthreads();
-        if (sh.status != 0) break;
         const int X = sh.X;
         const unsigned int nl = sh.layer[X] + 2;    // level code of the new layer
         const unsigned int fb = sh.fbeg[X], fe = sh.fend[X];
@@ -497,6 +501,31 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
                         dw[j] = c.y;
                     }
                 }
+#if KADABRA_CLAIM_FIRST
+                // phase 2+3: claim every target with one compare-and-swap
+                // (the old value gives its level when it was seen before);
+                // claimed targets then read the other side's word
+                unsigned int lx[kUnroll];
+                unsigned int ymask = 0;
+                unsigned int cmask = 0;
+#pragma unroll
+                for (int j = 0; j < kUnroll; ++j) {
+                    lx[j] = 1u;
+                    if (w[j] != kNone) {
+                        const unsigned long long su = sh.u.ex.csig[own[j]];
+                        const unsigned long long old = atomicCAS(&rec[w[j]].w[X], 0ULL, pack(nl, su));
+                        if (old == 0) {
+                            cmask |= 1u << j;
+                            my_max = su > my_max ? su : my_max;
+                        }
+                        lx[j] = old == 0 ? nl : lvl_of(old);
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < kUnroll; ++j) {
+                    if ((cmask >> j) & 1u) ymask |= (lvl_of(ldcg(&rec[w[j]].w[1 - X])) != 0 ? 1u : 0u) << j;
+                }
+#else
                 // phase 2: (level_s, level_t) of every target, one 8-byte load each
                 unsigned int lx[kUnroll];
                 unsigned int ymask = 0;
@@ -525,6 +554,7 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
                         lx[j] = old == 0 ? nl : lvl_of(old);
                     }
                 }
+#endif
                 // phase 4: path counts of targets in the new layer; the additions
                 // return their old value, so a thread has waited for all of them
                 // before the layer's closing barrier and every count is complete
@@ -562,12 +592,23 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
                     }
                 }
             }
+            // largest new path count (every count's final value is the largest
+            // value its additions returned) and the new frontier's degree sum,
+            // folded per warp into shared memory before the chunk's barrier
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long om = __shfl_xor_sync(0xffffffffu, my_max, o);
+                my_max = om > my_max ? om : my_max;
+                my_deg += __shfl_xor_sync(0xffffffffu, my_deg, o);
+            }
+            if (lane == 0) {
+                if (my_max) atomicMax(&sh.lmax, my_max);
+                if (my_deg) atomicAdd(&sh.ldeg, my_deg);
+            }
+            my_max = 0;
+            my_deg = 0;
             __syncthreads();
         }
-        // largest new path count (every count's final value is the largest
-        // value its additions returned) and the new frontier's degree sum
-        const unsigned long long lmax = block_max<NT>(my_max, sh);
-        const unsigned long long ldeg = block_sum<NT>(my_deg, sh);
         if (tid == 0) {
             sh.e_scan += my_scan;
             sh.expanded += fe - fb;
@@ -585,21 +626,31 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
             } else {
                 sh.fbeg[X] = qbase;
                 sh.fend[X] = qbase + sh.new_count;
-                sh.fdeg[X] = ldeg;
+                sh.fdeg[X] = sh.ldeg;
+                // keep the new layer's counts <= 2^K, rounding up so that they stay >= 1
+                const int shv = bitlen64(sh.lmax) - a.K;
+                sh.shv = shv > 0 ? shv : 0;
+                if (shv > 0) {
+                    sh.scaled = 1;
+                    if (a.strict) sh.status = 3;
+                }
+                // the next layer: side with the smaller frontier degree sum (ties: s)
+                const int Xn = (sh.fdeg[0] <= sh.fdeg[1]) ? 0 : 1;
+                if (sh.status == 0 && sh.layer[Xn] + 2u > 0xffffu) sh.status = 4;   // levels are 16-bit
+                if (sh.status == 0) {
+                    sh.X = Xn;
+                    sh.new_count = 0;
+                    sh.meet_count = 0;
+                    sh.lmax = 0;
+                    sh.ldeg = 0;
+                }
             }
         }
         __syncthreads();
         if (sh.status != 0) break;
-        {
-            // keep the new layer's counts <= 2^K, rounding up so that they stay >= 1
-            const int shv = bitlen64(lmax) - a.K;
-            if (shv > 0) {
-                if (tid == 0) sh.scaled = 1;
-                if (a.strict) {
-                    if (tid == 0) sh.status = 3;
-                    __syncthreads();
-                    break;
-                }
+        if (sh.shv > 0) {
+            const int shv = sh.shv;
+            {
                 for (unsigned int i = sh.fbeg[X] + tid; i < sh.fend[X]; i += NT) {
                     const unsigned int v = qget(queue, n, X, i);
                     const unsigned long long wv = ldcg(&rec[v].w[X]);
@@ -1172,7 +1223,7 @@ __global__ void __launch_bounds__(NT, (2048 / NT / 2) > 0 ? (2048 / NT / 2) : 1)
                 t.adj = qd.adj;
                 t.job = qd.job;
                 t.seed = qd.seed;
-                t.tag = 1;
+                t.tag = qd.tag;
                 t.K = qd.K;
                 t.strict = qd.strict;
                 sa = t;
@@ -1189,7 +1240,9 @@ __global__ void __launch_bounds__(NT, (2048 / NT / 2) > 0 ? (2048 / NT / 2) : 1)
         GraphRef<OffT> G{reinterpret_cast<const OffT *>(qd.off), qd.adj, qd.n};
         LocalStats ls = {0, 0, 0, 0, 0, 0, 0, 0};
         run_sample<NT, OffT>(sa, G, rec, queue, sh, st->base + pm.idx, pm.idx, ls,
-                             CountSink{nullptr, qd.logs + (size_t)f * qd.log_cap, &st->log_len[f], qd.log_cap});
+                             qd.tag == 0 ? CountSink{qd.counts, nullptr, nullptr, 0u}
+                                         : CountSink{nullptr, qd.logs + (size_t)f * qd.log_cap, &st->log_len[f],
+                                                     qd.log_cap});
         if (tid == 0) {
             Counters *cs[2] = {&job->total, qd.launch_ctr};
             for (int c = 0; c < 2; ++c) {
@@ -1205,7 +1258,7 @@ __global__ void __launch_bounds__(NT, (2048 / NT / 2) > 0 ? (2048 / NT / 2) : 1)
             }
             __threadfence();    // this sample's log entries before its completion
             const unsigned int d = atomicAdd(&st->done[f], 1u) + 1u;
-            pm.try_check = (d == epoch_size(st, qd.E, e)) ? 1 : 0;
+            pm.try_check = (qd.tag != 0 && d == epoch_size(st, qd.E, e)) ? 1 : 0;
         }
         __syncthreads();
         if (!pm.try_check) continue;

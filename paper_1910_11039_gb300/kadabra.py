@@ -53,7 +53,8 @@ class QueryInfo(C.Structure):
                 ("expanded", C.c_uint64), ("touched", C.c_uint64), ("interior", C.c_uint64),
                 ("walk_scan", C.c_uint64), ("scaled", C.c_uint64), ("device_error", C.c_uint32),
                 ("slots", C.c_int32), ("threads", C.c_int32), ("offsets_64", C.c_int32),
-                ("budget_classes", C.c_int32), ("stop_ns", C.c_uint64)]
+                ("budget_classes", C.c_int32), ("stop_ns", C.c_uint64), ("phase", C.c_int32),
+                ("pad0", C.c_int32), ("cal_done", C.c_uint64), ("device_bytes", C.c_uint64)]
 
 
 class TraceRec(C.Structure):
@@ -111,6 +112,9 @@ SIGNATURES = {
     "kadabra_pipeline_begin": (_ST, [_P, _I64, C.c_int, _P]),
     "kadabra_run_graph": (_ST, [_P, _I64, C.c_int, _I64, _P, C.POINTER(C.c_int)]),
     "kadabra_batch_set_policy": (_ST, [_P, C.c_int]),
+    "kadabra_query_create": (_ST, [_P, _P, _P, _P]),
+    "kadabra_calibration_begin": (_ST, [_P, _P]),
+    "kadabra_calibration_finish": (_ST, [_P, _P]),
     "kadabra_device_clock": (_ST, [C.POINTER(_U64), _P]),
     "kadabra_batch_create": (_ST, [_I64, C.c_int32, C.c_int32, C.c_int, C.POINTER(_P)]),
     "kadabra_batch_free": (_ST, [_P]),
@@ -257,14 +261,24 @@ class Graph:
 class Query:
     """One betweenness query: kadabra_calibrate and the calls on its result."""
 
-    def __init__(self, graph: Graph, params: Params | None = None, stream=None, **kw):
+    def __init__(self, graph: Graph, params: Params | None = None, stream=None, calibrate=True, **kw):
+        """calibrate=True: kadabra_calibrate (phases 1 and 2 now);
+        calibrate=False: kadabra_query_create (phase 1 only; calibrate in a
+        batch with calibration_begin / Batch.step / calibration_finish)."""
         self.graph = graph
         p = params if params is not None else params_default()
         for k, v in kw.items():
             setattr(p, k, v)
         self.params = p
         self.handle = C.c_void_p()
-        _check(load().kadabra_calibrate(graph.handle, C.byref(p), _stream(stream), C.byref(self.handle)))
+        fn = load().kadabra_calibrate if calibrate else load().kadabra_query_create
+        _check(fn(graph.handle, C.byref(p), _stream(stream), C.byref(self.handle)))
+
+    def calibration_begin(self, stream=None):
+        _check(load().kadabra_calibration_begin(self.handle, _stream(stream)))
+
+    def calibration_finish(self, stream=None):
+        _check(load().kadabra_calibration_finish(self.handle, _stream(stream)))
 
     def sample_epoch(self, n_samples, stream=None):
         _check(load().kadabra_sample_epoch(self.handle, n_samples, _stream(stream)))

@@ -1,0 +1,221 @@
+"""Continuous-batching betweenness server on one GPU.
+
+Requests (graph, eps, delta, seed) arrive over time.  The server keeps the
+graphs resident and runs every admitted query inside one shared persistent
+launch per step (kadabra_batch_step with a sample budget, so a step lasts
+about `step_ms`).  Between steps it
+
+  * admits arrived requests while their device state fits the memory budget
+    (query state: counters, budgets, calibration counts, epoch logs; the
+    graphs and the batch's sampling scratch are reserved up front),
+  * starts each new query's calibration samples, which then run in the next
+    steps beside the other queries' adaptive samples (the paper's phase 2,
+    Section III-A, done inside the batch),
+  * turns a query whose calibration completed into an adaptive query
+    (budgets on the host, epoch logs on the device),
+  * retires queries whose stopping condition held (or that reached omega),
+    reading their counters and freeing their state.
+
+A query's state stays on the device for its whole life; its samples are
+indexed by (seed, stream tag, sample index), so its result does not depend
+on what else shares the launch: the same request alone and in any mix gives
+the same tau, stop epoch and counters.
+
+Time-to-stop is measured on the device clock: the stop check records the
+global timer when it decides the stop, and the server maps that timer onto
+the run's host clock once at start.
+"""
+from __future__ import annotations
+
+import dataclasses
+import time
+from collections import deque
+
+import numpy as np
+
+from . import kadabra as K
+from .autotune import Schedule
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    graph: str
+    eps: float
+    delta: float = 0.1
+    seed: int = 1
+    arrival: float = 0.0          # seconds after the start of the run
+    # filled in by the server
+    admitted: float | None = None  # host time of admission (run clock)
+    calibrated: float | None = None
+    seen_done: float | None = None  # host time the completion was observed
+    stop_time: float | None = None  # device time of the stop decision (run clock)
+    tau: int = 0
+    stop_epoch: int = -1
+    epoch_len: int = 0
+    omega_ceil: int = 0
+    device_bytes: int = 0
+    counts: np.ndarray | None = None
+
+    @property
+    def time_to_stop(self) -> float | None:
+        return None if self.stop_time is None else self.stop_time - self.arrival
+
+
+class _Active:
+    __slots__ = ("req", "q", "phase", "bytes")
+
+    def __init__(self, req, q, nbytes):
+        self.req, self.q, self.phase, self.bytes = req, q, 1, nbytes
+
+
+class Server:
+    """policy "fifo": earlier arrivals take samples first (the batch's
+    IN_ORDER policy over the active list in arrival order); "round_robin":
+    every active query takes samples at the same rate."""
+
+    def __init__(self, graphs: dict, threads: int = 1024, slots: int = 0, schedule: Schedule | None = None,
+                 memory_budget: int | None = None, step_ms: float = 20.0, policy: str = "fifo",
+                 keep_results: bool = True, log=None):
+        import torch
+
+        self.torch = torch
+        self.graphs = {}
+        for key, g in graphs.items():
+            self.graphs[key] = g if isinstance(g, K.Graph) else K.Graph.from_inputs(g, skip_validate=True)
+        infos = {k: G.info() for k, G in self.graphs.items()}
+        off64 = {bool(i["offsets_64"]) for i in infos.values()}
+        if len(off64) > 1:
+            raise ValueError("all graphs of a server must use the same offset width")
+        self.n = {k: int(i["n"]) for k, i in infos.items()}
+        self.max_n = max(self.n.values())
+        self.schedule = schedule or Schedule(threads=threads)
+        self.batch = K.Batch(self.max_n, slots=slots, threads=self.schedule.threads,
+                             offsets_64=off64.pop() if off64 else False)
+        if policy not in ("fifo", "round_robin"):
+            raise ValueError("policy must be 'fifo' or 'round_robin'")
+        self.policy = policy
+        self.batch.set_policy(K.Batch.IN_ORDER if policy == "fifo" else K.Batch.ROUND_ROBIN)
+        torch.cuda.synchronize()
+        free, _ = torch.cuda.mem_get_info()
+        self.memory_budget = int(memory_budget if memory_budget is not None else 0.8 * free)
+        self.step_ms = step_ms
+        self.keep_results = keep_results
+        self.log = log
+        self.used = 0
+        self.stats = {"steps": 0, "step_ms": 0.0, "samples": 0, "cal_samples": 0, "admit_waits": 0,
+                      "max_active": 0, "peak_bytes": 0}
+
+    # -- helpers -----------------------------------------------------------
+
+    def _state_bytes_estimate(self, key: str) -> int:
+        """Device bytes of a query before its epoch logs are known."""
+        return 40 * self.n[key] + (1 << 20)
+
+    def _log_bytes(self, vd: int, E: int) -> int:
+        return 4 * self.schedule.frames * E * max(1, vd - 2)
+
+    def close(self):
+        self.batch.free()
+        for G in self.graphs.values():
+            G.free()
+        self.graphs = {}
+
+    # -- the loop ----------------------------------------------------------
+
+    def run(self, requests, realtime: bool = True, clock=time.perf_counter):
+        """Serve `requests` (any order; each has an arrival time in seconds).
+        With realtime=False every request is taken as already arrived.
+        Returns the requests with their results and timings."""
+        future = deque(sorted(requests, key=lambda r: (r.arrival, r.rid)))
+        pending: deque[Request] = deque()
+        active: list[_Active] = []
+        done: list[Request] = []
+        budget = 4096
+        t0 = clock()
+        dev0 = K.device_clock()
+        t_dev = clock()
+        t0 = 0.5 * (t0 + t_dev)          # host time matching dev0
+
+        def now():
+            return clock() - t0
+
+        while future or pending or active:
+            t = now()
+            while future and (not realtime or future[0].arrival <= t):
+                pending.append(future.popleft())
+            # admission by device memory
+            while pending:
+                r = pending[0]
+                est = self._state_bytes_estimate(r.graph)
+                if active and self.used + est > self.memory_budget:
+                    self.stats["admit_waits"] += 1
+                    break
+                pending.popleft()
+                q = K.Query(self.graphs[r.graph], calibrate=False, eps=r.eps, delta=r.delta, seed=r.seed,
+                            threads=self.schedule.threads)
+                inf = q.info()
+                r.omega_ceil = int(inf.omega_ceil)
+                r.epoch_len = self.schedule.epoch_len(r.omega_ceil)
+                nbytes = int(inf.device_bytes) + self._log_bytes(int(inf.vertex_diameter), r.epoch_len)
+                r.device_bytes = nbytes
+                self.used += nbytes
+                q.calibration_begin()
+                r.admitted = now()
+                active.append(_Active(r, q, nbytes))
+            self.stats["max_active"] = max(self.stats["max_active"], len(active))
+            self.stats["peak_bytes"] = max(self.stats["peak_bytes"], self.used)
+            if not active:
+                if future and realtime:
+                    time.sleep(max(0.0, min(0.05, future[0].arrival - now())))
+                continue
+            # one step over every active query (arrival order = priority under "fifo")
+            self.batch.step([a.q for a in active], sample_budget=budget)
+            ms = self.batch.last_ms()
+            self.stats["steps"] += 1
+            self.stats["step_ms"] += ms
+            budget = int(min(1 << 22, max(256, budget * self.step_ms / max(ms, 1e-3))))
+            still = []
+            for a in active:
+                inf = a.q.info()
+                if a.phase == 1:
+                    if inf.cal_done >= inf.n_calib:
+                        a.q.calibration_finish()
+                        a.q.pipeline_begin(a.req.epoch_len, frames=self.schedule.frames)
+                        a.phase = 2
+                        a.req.calibrated = now()
+                        self.stats["cal_samples"] += int(inf.n_calib)
+                    still.append(a)
+                    continue
+                if not inf.stopped:
+                    still.append(a)
+                    continue
+                r = a.req
+                r.seen_done = now()
+                r.stop_time = (int(inf.stop_ns) - dev0) / 1e9
+                r.tau = int(inf.tau)
+                r.stop_epoch = int(inf.stop_epoch)
+                self.stats["samples"] += int(inf.samples)
+                self.stats["tau"] = self.stats.get("tau", 0) + r.tau
+                if self.keep_results:
+                    r.counts = a.q.result(btilde=False)["counts"]
+                a.q.free()
+                self.used -= a.bytes
+                done.append(r)
+            active = still
+        self.stats["wall_s"] = now()
+        return done
+
+    def summary(self, done) -> dict:
+        tts = sorted(r.time_to_stop for r in done)
+        wall = self.stats["wall_s"]
+        pct = lambda p: tts[min(len(tts) - 1, max(0, int(round(p / 100.0 * (len(tts) - 1)))))] if tts else None
+        return {"queries": len(done), "tts_p50_s": pct(50), "tts_p99_s": pct(99), "tts_max_s": tts[-1] if tts else None,
+                "samples": self.stats["samples"], "cal_samples": self.stats["cal_samples"],
+                "tau_total": self.stats.get("tau", 0),
+                "samples_per_s": (self.stats["samples"] + self.stats["cal_samples"]) / wall if wall else None,
+                "adaptive_samples_per_s": self.stats["samples"] / wall if wall else None,
+                "wall_s": wall, "steps": self.stats["steps"],
+                "gpu_busy_frac": self.stats["step_ms"] / 1e3 / wall if wall else None,
+                "max_active": self.stats["max_active"], "peak_state_bytes": self.stats["peak_bytes"],
+                "admission_waits": self.stats["admit_waits"], "memory_budget": self.memory_budget}

@@ -4,6 +4,8 @@ Each query in a batch must end with exactly the tau, counters and stop epoch
 it has when run alone, whatever else shares the launch, however the work is
 split into steps, and when queries join between steps.
 """
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -144,3 +146,72 @@ def test_autotuned_schedule_matches_oracle(K, orc, graphs):
         assert np.array_equal(res["counts"], counts), name
     # time-to-stop is measured from the launch's submission on the device clock
     assert all(0 < t <= r["ms"] + 5.0 for t in r["tts_ms"])
+
+
+def test_calibration_inside_batch_matches_calibrate(K, orc, graphs):
+    """Queries created without calibration take their calibration samples in
+    batch steps beside running queries; budgets and results equal those of
+    kadabra_calibrate and of the oracle."""
+    qs = make_queries(K, graphs)                       # calibrated the usual way
+    fresh = []
+    for name, eps, seed, E, F in SPECS:
+        g, G = graphs[name]
+        fresh.append((K.Query(G, eps=eps, delta=0.1, seed=seed, calibrate=False), E, F, g))
+    for (q, *_), (p, *_) in zip(qs, fresh):
+        assert p.info().phase == 0 and q.info().phase == 2
+        with pytest.raises(K.KadabraError) as ei:
+            p.sample_epoch(10)
+        assert ei.value.status == 7
+    b = K.Batch(max(g.n for g, _ in graphs.values()), slots=96, policy=1)
+    for q, E, F, g in qs[:3]:                          # some adaptive queries already running
+        q.pipeline_begin(E, frames=F)
+    active = [q for q, *_ in qs[:3]]
+    for p, *_ in fresh:
+        p.calibration_begin()
+        active.append(p)
+    with pytest.raises(K.KadabraError) as ei:
+        fresh[0][0].calibration_finish()               # nothing sampled yet
+    assert ei.value.status == 7
+    phase = {id(p): 1 for p, *_ in fresh}
+    for _ in range(100000):
+        b.step(active, sample_budget=257)
+        for p, E, F, g in fresh:
+            if phase[id(p)] == 1 and p.info().cal_done >= p.info().n_calib:
+                p.calibration_finish()
+                p.pipeline_begin(E, frames=F)
+                phase[id(p)] = 2
+        active = [q for q in active if not (q.info().phase == 2 and q.info().stopped)]
+        if not active:
+            break
+    for (q, *_), (p, E, F, g), (name, eps, seed, *_) in zip(qs, fresh, SPECS):
+        a, c = q.budgets(), p.budgets()
+        for x, y in zip(a, c):
+            assert np.array_equal(x, y), name
+        counts, R = expected(orc, g, eps, seed, E)
+        res = p.result()
+        assert res["tau"] == R.tau and res["stop_epoch"] == R.stop_epoch, name
+        assert np.array_equal(res["counts"], counts), name
+
+
+def test_server_results_equal_alone_and_in_mix(K, orc, graphs):
+    """Requests served together (continuous batching, arrivals while others
+    run) give the results each gives alone, and those of the oracle."""
+    from paper_1910_11039_gb300.autotune import Schedule
+    from paper_1910_11039_gb300.server import Request, Server
+    sched = Schedule(threads=256, divisor=32, frames=4)
+    reqs = [Request(i, name, eps, 0.1, seed, arrival=0.002 * i) for i, (name, eps, seed, _, _) in enumerate(SPECS)]
+    reqs += [Request(10 + i, name, eps, 0.1, seed + 100, arrival=0.001 * i)
+             for i, (name, eps, seed, _, _) in enumerate(SPECS[:3])]
+    srv = Server({k: v[1] for k, v in graphs.items()}, schedule=sched, step_ms=2.0)
+    mixed = {r.rid: r for r in srv.run([dataclasses.replace(r) for r in reqs])}
+    assert len(mixed) == len(reqs)
+    s = srv.summary(list(mixed.values()))
+    assert s["queries"] == len(reqs) and s["tts_p50_s"] > 0 and s["steps"] > 1
+    for r in reqs:
+        alone = Server({r.graph: graphs[r.graph][1]}, schedule=sched, step_ms=2.0).run([dataclasses.replace(r)])[0]
+        m = mixed[r.rid]
+        assert (m.tau, m.stop_epoch) == (alone.tau, alone.stop_epoch), r
+        assert np.array_equal(m.counts, alone.counts), r
+        counts, R = expected(orc, graphs[r.graph][0], r.eps, r.seed, sched.epoch_len(m.omega_ceil))
+        assert m.tau == R.tau and m.stop_epoch == R.stop_epoch
+        assert np.array_equal(m.counts, counts)
