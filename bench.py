@@ -277,6 +277,7 @@ def run_gpu(args, wl, g, rank, world, local_rank, cpu_baseline):
     if dist:
         torch.distributed.barrier()
     torch.cuda.synchronize()
+    launches0 = q.info().launches
     clocks = ClockSampler(local_rank)
     clocks.start()
     t_wall0 = time.perf_counter()
@@ -307,17 +308,18 @@ def run_gpu(args, wl, g, rank, world, local_rank, cpu_baseline):
     gteps = all_escan / (total_ms_max / 1e3) / 1e9
 
     # roofline of the sampling kernel over the timed steps' launches
-    launches = [ls for ls in q.launch_log(256) if ls.samples > 0]
+    timed = min(256, q.info().launches - launches0)
+    launches = [ls for ls in q.launch_log(timed) if ls.samples > 0]
     ob = 4  # int32 offsets
     peak, peak_kind = measured_peak_hbm()
     tot_b = sum(algorithmic_bytes(ls, ob) for ls in launches)
     tot_ms = sum(ls.ms for ls in launches)
     achieved = tot_b / (tot_ms / 1e3) / 1e9 if tot_ms > 0 else 0.0
-    per_sample = profiled_traffic(args.workload, "pipe_kernel" if args.mode == "pipelined" else "sample_kernel")
+    per_sample = profiled_traffic(args.workload, "batch_kernel" if args.mode == "pipelined" else "sample_kernel")
     mean_samples = sum(ls.samples for ls in launches) / max(1, len(launches))
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": per_sample * mean_samples if per_sample else None,
-                "kernel": "pipe_kernel" if args.mode == "pipelined" else "sample_kernel", "peak_source": f"{peak_kind} hbm_gbs",
+                "kernel": "batch_kernel" if args.mode == "pipelined" else "sample_kernel", "peak_source": f"{peak_kind} hbm_gbs",
                 "launches": len(launches), "avg_launch_ms": tot_ms / max(1, len(launches)),
                 "algorithmic_bytes_per_launch": tot_b / max(1, len(launches)),
                 "per_sample": {k: sum(getattr(ls, k) for ls in launches) / max(1, sum(ls.samples for ls in launches))
@@ -546,6 +548,70 @@ def run_batched(args, local_rank):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# serving: a Poisson stream of queries, continuous batching vs one at a time
+# ---------------------------------------------------------------------------
+
+def run_serve(args, local_rank):
+    import torch
+
+    from paper_1910_11039_gb300 import build as B
+    from paper_1910_11039_gb300 import inputs
+    from paper_1910_11039_gb300 import kadabra as K
+    from paper_1910_11039_gb300.autotune import Schedule
+    from paper_1910_11039_gb300.server import Request, Server
+
+    pool = [k for k in inputs.SERVING_POOL if args.serve_pool == "full" or k.startswith("rmat")]
+    reqs = inputs.serving_requests(count=args.serve_queries, rate=args.serve_rate, pool=pool)
+    used = sorted({r["graph"] for r in reqs})
+    t0 = time.perf_counter()
+    host_graphs = {k: inputs.graph_from_spec(inputs.SERVING_POOL[k], k) for k in used}
+    gen_s = time.perf_counter() - t0
+    log(f"generated {len(used)} graphs in {gen_s:.1f} s")
+    B.build()
+    K.load()
+    torch.cuda.set_device(local_rank)
+    sched = Schedule(threads=args.threads, divisor=args.divisor, frames=args.frames)
+    srv = Server(host_graphs, schedule=sched, step_ms=args.step_ms, policy=args.serve_policy,
+                 keep_results=False)
+    del host_graphs
+    # warm-up: a few requests of the stream, served at once and discarded
+    warm = [Request(**dict(r, arrival=0.0)) for r in reqs[:max(8, 4 * args.warmup)]]
+    srv.run(warm, realtime=False)
+    srv.run_one_at_a_time([Request(**dict(r, arrival=0.0)) for r in reqs[:4]], realtime=False)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    done = srv.run([Request(**r) for r in reqs])
+    clk = clocks.stop()
+    s_batched = srv.summary(done)
+    log("continuous batching", json.dumps(s_batched))
+    done1 = srv.run_one_at_a_time([Request(**r) for r in reqs])
+    s_plain = srv.summary(done1)
+    log("one at a time", json.dumps(s_plain))
+    a = {r.rid: (r.tau, r.stop_epoch) for r in done}
+    b = {r.rid: (r.tau, r.stop_epoch) for r in done1}
+    same = sum(1 for k in a if a[k] == b.get(k))
+    line = {
+        "metric": "time-to-(eps,delta) stop p50/p99 and samples/sec under a Poisson query stream",
+        "value": s_batched["samples_per_s"], "unit": "samples/s", "n_gpus": 1, "steps": 1, "warmup": args.warmup,
+        "ms_per_step": 1e3 * s_batched["wall_s"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": f"Poisson stream, rate {args.serve_rate}/s, {args.serve_queries} queries, graphs "
+                               f"uniform over {pool}, eps uniform over {{0.01, 0.005}}, delta 0.1, stream seed 5",
+                   "pool": args.serve_pool, "graphs_used": used, "schedule": dataclasses.asdict(sched),
+                   "step_ms": args.step_ms, "policy": args.serve_policy, "generation_s": gen_s},
+        "tts_p50_s": s_batched["tts_p50_s"], "tts_p99_s": s_batched["tts_p99_s"],
+        "continuous_batching": s_batched,
+        "one_query_at_a_time": s_plain,
+        "results_identical": {"compared": len(a), "same_tau_and_stop_epoch": same},
+        "gpu_launches": s_batched["steps"],
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -554,8 +620,15 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default="rmat20", choices=list(WORKLOADS))
     ap.add_argument("--epoch", type=int, default=1024)
-    ap.add_argument("--mode", default="pipelined", choices=["pipelined", "epochs", "batched"],
-                    help="pipelined/epochs: one query on --workload; batched: 64 queries of uneven size")
+    ap.add_argument("--mode", default="pipelined", choices=["pipelined", "epochs", "batched", "serve"],
+                    help="pipelined/epochs: one query on --workload; batched: 64 queries of uneven size; "
+                         "serve: a Poisson stream of queries")
+    ap.add_argument("--serve-queries", type=int, default=2000)
+    ap.add_argument("--serve-rate", type=float, default=20.0)
+    ap.add_argument("--serve-pool", default="rmat", choices=["rmat", "full"],
+                    help="rmat: R-MAT scale 14-24; full: also the perturbed grids 1024^2-4096^2")
+    ap.add_argument("--serve-policy", default="fifo", choices=["fifo", "round_robin"])
+    ap.add_argument("--step-ms", type=float, default=20.0, help="serve mode: target length of a batch step")
     ap.add_argument("--autotune", action="store_true", help="batched mode: search the schedule first")
     ap.add_argument("--divisor", type=int, default=32, help="batched mode: epoch length = omega / divisor")
     ap.add_argument("--graph-epochs", type=int, default=4, help="epochs per CUDA graph (graph_epochs form)")
@@ -575,13 +648,13 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     wl = WORKLOADS[args.workload]
-    if args.mode == "batched":
+    if args.mode in ("batched", "serve"):
         if args.impl == "reference":
-            print(json.dumps({"impl": "reference", "unavailable": "the batched mode has no CPU form; the oracle "
-                              "arm runs on the single-query workloads"}), flush=True)
+            print(json.dumps({"impl": "reference", "unavailable": f"the {args.mode} mode has no CPU form; the "
+                              "oracle arm runs on the single-query workloads"}), flush=True)
             return
         if rank == 0:
-            run_batched(args, local_rank)
+            (run_batched if args.mode == "batched" else run_serve)(args, local_rank)
         return
 
     from paper_1910_11039_gb300 import inputs

@@ -111,6 +111,7 @@ typedef struct kadabra_query_info {
     int32_t pad0;
     uint64_t cal_done;          /* calibration samples completed (phase 1), else n_calib    */
     uint64_t device_bytes;      /* device memory the query holds (not the graph's)          */
+    int64_t launches;           /* sampling launches logged (kadabra_launch_log), ever      */
 } kadabra_query_info;
 
 /* Per-sample record written by kadabra_sample_trace (one per sample index). */
@@ -293,6 +294,12 @@ kadabra_status kadabra_batch_last_ms(kadabra_batch *b, float *ms);
  * e.g. shortest expected work first or arrival order).  Results do not
  * depend on the policy. */
 enum { KADABRA_BATCH_ROUND_ROBIN = 0, KADABRA_BATCH_IN_ORDER = 1 };
+/* After a step: the state of each of its `count` queries (in the order they
+ * were passed) into states[] (host): 0 running, 1 calibration samples
+ * complete (kadabra_calibration_finish may run), 2 stopped or at ceil(omega).
+ * One small kernel and one copy on `cuda_stream`.  Synchronises.
+ * KADABRA_ERR_INVALID_ARG if count differs from the last step's. */
+kadabra_status kadabra_batch_poll(kadabra_batch *b, int32_t *states, int64_t count, void *cuda_stream);
 kadabra_status kadabra_batch_set_policy(kadabra_batch *b, int policy);
 
 /* Sharded sampling (several ranks, one GPU each; Section I-A: samples are

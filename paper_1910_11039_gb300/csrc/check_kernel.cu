@@ -180,6 +180,109 @@ cudaError_t read_device_clock(unsigned long long *ns, cudaStream_t st)
     return e;
 }
 
+// ---- budgets from calibration counts (Section III-A, phase 2) -----------
+//
+// The budget rule depends on a vertex only through its calibration count, so
+// the host needs just the number of vertices with each count; every vertex
+// then takes the (L_L, L_U) pair of its count's class.
+
+__global__ void cal_max_kernel(long long n, const uint32_t *cal, unsigned int *mx)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    unsigned int m = 0;
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        const unsigned int c = cal[v];
+        m = c > m ? c : m;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned int y = __shfl_xor_sync(0xffffffffu, m, o);
+        m = y > m ? y : m;
+    }
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(mx, m);
+}
+
+constexpr int kHistSmem = 4096;
+
+__global__ void cal_hist_kernel(long long n, const uint32_t *cal, unsigned int cmax, unsigned long long *hist)
+{
+    __shared__ unsigned int h[kHistSmem];
+    const unsigned int nb = cmax + 1u < (unsigned int)kHistSmem ? cmax + 1u : (unsigned int)kHistSmem;
+    for (unsigned int i = threadIdx.x; i < nb; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long n_round = (n + 31) & ~31LL;   // whole warps stay in the loop
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n_round; v += stride) {
+        const bool in = v < n;
+        const unsigned int c = in ? cal[v] : 0xffffffffu;
+        const unsigned int peers = __match_any_sync(0xffffffffu, c);
+        if (in && (threadIdx.x & 31) == __ffs(peers) - 1) {
+            if (c < nb) atomicAdd(&h[c], (unsigned int)__popc(peers));
+            else atomicAdd(&hist[c], (unsigned long long)__popc(peers));
+        }
+    }
+    __syncthreads();
+    for (unsigned int i = threadIdx.x; i < nb; i += blockDim.x)
+        if (h[i]) atomicAdd(&hist[i], (unsigned long long)h[i]);
+}
+
+__global__ void fill_budgets_kernel(long long n, const uint32_t *cal, const int *class_of, const double2 *Ltab,
+                                    uint32_t *cls, double2 *L)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        const int k = class_of[cal[v]];
+        cls[v] = (uint32_t)k;
+        L[v] = Ltab[k];
+    }
+}
+
+cudaError_t launch_cal_max(int64_t n, const uint32_t *cal, unsigned int *mx, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(mx, 0, sizeof(unsigned int), st);
+    if (e != cudaSuccess) return e;
+    cal_max_kernel<<<grid_for(n, 256), 256, 0, st>>>((long long)n, cal, mx);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cal_hist(int64_t n, const uint32_t *cal, unsigned int cmax, unsigned long long *hist,
+                            cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(hist, 0, ((size_t)cmax + 1) * sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    cal_hist_kernel<<<grid_for(n, 256), 256, 0, st>>>((long long)n, cal, cmax, hist);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill_budgets(int64_t n, const uint32_t *cal, const int *class_of, const double2 *Ltab,
+                                uint32_t *cls, double2 *L, cudaStream_t st)
+{
+    fill_budgets_kernel<<<grid_for(n, 256), 256, 0, st>>>((long long)n, cal, class_of, Ltab, cls, L);
+    return cudaGetLastError();
+}
+
+// State of every query of a batch step: 0 running, 1 calibration samples
+// complete, 2 stopped (or at its sample cap).
+__global__ void batch_poll_kernel(const QueryDesc *d, int nq, int *out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nq) return;
+    const QueryDesc &q = d[i];
+    const volatile PipeState *ps = q.ps;
+    const volatile Job *job = q.job;
+    int r = 0;
+    if (q.tag == 0) r = ps->done[0] >= (unsigned int)q.E ? 1 : 0;
+    else r = job->stopped ? 2 : 0;
+    out[i] = r;
+}
+
+cudaError_t launch_batch_poll(const QueryDesc *d, int nq, int *out, cudaStream_t st)
+{
+    if (nq <= 0) return cudaSuccess;
+    batch_poll_kernel<<<(nq + 255) / 256, 256, 0, st>>>(d, nq, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_reset_job(Job *job, cudaStream_t st)
 {
     reset_job_kernel<<<1, 32, 0, st>>>(job);

@@ -3,8 +3,14 @@
 //
 // The vertex-diameter bound used for omega is, per connected component,
 // 2 * ecc(smallest vertex id) + 1, maximised over components.  On the device:
-//   1. components by union-find: every edge links the larger of its two roots
-//      under the smaller (CAS), so each component's root is its smallest id;
+//   1. components by union-find: an edge links the larger of its two roots
+//      under the smaller (CAS), so each component's root is its smallest id.
+//      Edges are taken in the order of subgraph sampling (Sutton, Ben-Nun and
+//      Barak, IPDPS 2018): every vertex first links along its first two
+//      adjacency entries; the root that most sampled vertices then share is
+//      that of the largest component, whose vertices skip their remaining
+//      edges (each such edge is also an edge of its other endpoint, which
+//      either lies in the same component or links along it itself);
 //   2. one breadth-first search from all roots at once: a vertex's level is its
 //      distance from its own component's root, so the largest level is the
 //      largest eccentricity and the bound is 2 * (largest level) + 1.
@@ -12,6 +18,7 @@
 // barrier between levels; every wait in it is bounded and reports an error
 // flag instead of hanging.
 
+#include <algorithm>
 #include <cstdint>
 
 #include <cuda_runtime.h>
@@ -37,29 +44,66 @@ __device__ __forceinline__ unsigned int find_root(unsigned int *parent, unsigned
     return x;
 }
 
-template <typename OffT>
-__global__ void cc_hook_kernel(long long n, const OffT *off, const uint2 *adj, unsigned int *parent, unsigned int *err)
+// Link the trees of u and v: the larger root goes under the smaller one.
+__device__ __forceinline__ void hook(unsigned int *parent, unsigned int u, unsigned int v, unsigned int *err)
 {
-    // one warp per vertex, lanes stride its adjacency
+    unsigned long long tries = 0;
+    for (;;) {
+        const unsigned int ru = find_root(parent, u), rv = find_root(parent, v);
+        if (ru == rv) return;
+        const unsigned int big = ru > rv ? ru : rv, small = ru > rv ? rv : ru;
+        if (atomicCAS(parent + big, big, small) == big) return;
+        if (++tries > kSpinLimit) {
+            atomicOr(err, 1u);
+            return;
+        }
+    }
+}
+
+// Round r of the sampling phase: every vertex links along adjacency entry r.
+template <typename OffT>
+__global__ void cc_link_round_kernel(long long n, const OffT *off, const uint2 *adj, unsigned int *parent, int r,
+                                     unsigned int *err)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += stride) {
+        const long long b = (long long)__ldg(off + u), e = (long long)__ldg(off + u + 1);
+        if (b + r < e) hook(parent, (unsigned int)u, __ldg(&adj[b + r].x), err);
+    }
+}
+
+__global__ void cc_compress_kernel(long long n, unsigned int *parent)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
+        __stcg(parent + v, find_root(parent, (unsigned int)v));
+}
+
+// Roots of m spread-out vertices (a fixed multiplicative stride through the ids).
+__global__ void cc_sample_kernel(long long n, unsigned int *parent, unsigned int *out, int m)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const unsigned long long v = ((unsigned long long)i * 2654435761ULL + 40503ULL) % (unsigned long long)n;
+    out[i] = find_root(parent, (unsigned int)v);
+}
+
+// The remaining adjacency entries (from entry r0 on) of every vertex outside
+// the tree rooted at `skip`; one warp per vertex, lanes stride its entries.
+template <typename OffT>
+__global__ void cc_rest_kernel(long long n, const OffT *off, const uint2 *adj, unsigned int *parent, unsigned int skip,
+                               int r0, unsigned int *err)
+{
     const int lane = threadIdx.x & 31;
     const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
     for (long long u = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); u < n; u += warps) {
         const long long b = (long long)__ldg(off + u), e = (long long)__ldg(off + u + 1);
-        for (long long i = b + lane; i < e; i += 32) {
-            const unsigned int v = __ldg(&adj[i].x);
-            if (v <= (unsigned int)u) continue;   // each undirected edge once
-            unsigned long long tries = 0;
-            for (;;) {
-                unsigned int ru = find_root(parent, (unsigned int)u), rv = find_root(parent, v);
-                if (ru == rv) break;
-                const unsigned int big = ru > rv ? ru : rv, small = ru > rv ? rv : ru;
-                if (atomicCAS(parent + big, big, small) == big) break;
-                if (++tries > kSpinLimit) {
-                    atomicOr(err, 1u);
-                    break;
-                }
-            }
-        }
+        if (b + r0 >= e) continue;
+        unsigned int ru = 0;
+        if (lane == 0) ru = find_root(parent, (unsigned int)u);
+        ru = __shfl_sync(0xffffffffu, ru, 0);
+        if (ru == skip) continue;
+        for (long long i = b + r0 + lane; i < e; i += 32) hook(parent, (unsigned int)u, __ldg(&adj[i].x), err);
     }
 }
 
@@ -202,7 +246,32 @@ cudaError_t vd_bound_t(int64_t n, const OffT *off, const uint2 *adj, unsigned in
     cudaError_t e = cudaMemsetAsync(s, 0, sizeof(BfsState), st);
     if (e != cudaSuccess) return e;
     cc_init_kernel<<<grid, 256, 0, st>>>((long long)n, parent, dist, q0, &s->len[0]);
-    cc_hook_kernel<OffT><<<grid, 256, 0, st>>>((long long)n, off, adj, parent, &s->err);
+    constexpr int kRounds = 2, kSamples = 1024;
+    for (int r = 0; r < kRounds; ++r) {
+        cc_link_round_kernel<OffT><<<grid, 256, 0, st>>>((long long)n, off, adj, parent, r, &s->err);
+        cc_compress_kernel<<<grid, 256, 0, st>>>((long long)n, parent);
+    }
+    // the most frequent root among the sampled vertices (q1, n entries, holds the samples)
+    const int m = n < kSamples ? (int)n : kSamples;
+    cc_sample_kernel<<<(m + 255) / 256, 256, 0, st>>>((long long)n, parent, q1, m);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    unsigned int roots[kSamples];
+    e = cudaMemcpyAsync(roots, q1, (size_t)m * sizeof(unsigned int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return e;
+    std::sort(roots, roots + m);
+    unsigned int best = roots[0];
+    int best_run = 0;
+    for (int i = 0; i < m;) {
+        int j = i;
+        while (j < m && roots[j] == roots[i]) ++j;
+        if (j - i > best_run) {
+            best_run = j - i;
+            best = roots[i];
+        }
+        i = j;
+    }
+    cc_rest_kernel<OffT><<<grid, 256, 0, st>>>((long long)n, off, adj, parent, best, kRounds, &s->err);
     roots_kernel<<<grid, 256, 0, st>>>((long long)n, parent, dist, q0, &s->len[0]);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // cooperative launch: every CTA is resident, so the grid barrier is safe

@@ -127,6 +127,8 @@ struct kadabra_batch {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     bool have_step = false;
     int policy = 0;
+    int64_t last_count = 0;       // queries of the most recent step
+    int *d_states = nullptr;      // descs_cap entries
 };
 
 namespace kadabra {
@@ -280,25 +282,26 @@ extern "C" int kadabra_sigma_bits(int64_t n, int64_t max_degree)
 // rules make the budgets a function of the calibration count, so the budget
 // classes (equal (L_L, L_U)) are the distinct counts present (one class for
 // the uniform rule); cls[x] receives the class of every vertex.
-static void budgets(int64_t n, const std::vector<uint32_t> &cal, int64_t n_cal, double eps, double delta, int rule,
-                    double beta, std::vector<double2> &Lx, std::vector<uint32_t> &cls, std::vector<double2> &Ltab,
-                    double *C_out)
+// Budget table from the number of vertices with each calibration count:
+// class_of[c] (-1 where no vertex has count c) and (L_L, L_U) per class.
+// Uniform rule: delta_L = delta_U = delta / (4n) for every vertex.  Balanced
+// rule: delta_L = delta_U = exp(-C eps^2 / bhat) + beta delta / (4n) with
+// bhat = c / n_cal, C found by bisection so that the variable terms sum to at
+// most (1 - beta) delta / 4 (zero counts get the floor term alone).
+static void budget_table(int64_t n, const std::vector<unsigned long long> &hist, int64_t n_cal, double eps,
+                         double delta, int rule, double beta, std::vector<int32_t> &class_of,
+                         std::vector<double2> &Ltab, double *C_out)
 {
-    Lx.assign((size_t)n, make_double2(0.0, 0.0));
-    cls.assign((size_t)n, 0u);
+    const uint32_t cmax = (uint32_t)(hist.size() - 1);
+    class_of.assign((size_t)cmax + 1, -1);
     Ltab.clear();
     if (rule == KADABRA_DELTA_UNIFORM) {
         const double dl = delta / (4.0 * (double)n);
-        const double2 L = make_double2(-std::log(dl), -std::log(dl));
-        for (int64_t x = 0; x < n; ++x) Lx[(size_t)x] = L;
-        Ltab.push_back(L);
+        Ltab.push_back(make_double2(-std::log(dl), -std::log(dl)));
+        for (auto &k : class_of) k = 0;
         *C_out = 0.0;
         return;
     }
-    uint32_t cmax = 0;
-    for (uint32_t c : cal) cmax = c > cmax ? c : cmax;
-    std::vector<int64_t> hist((size_t)cmax + 1, 0);
-    for (uint32_t c : cal) ++hist[c];
     auto term = [&](double C, uint32_t c) {
         const double bhat = (double)c / (double)n_cal;
         return std::exp(-((C * (eps * eps)) / bhat));
@@ -316,17 +319,11 @@ static void budgets(int64_t n, const std::vector<uint32_t> &cal, int64_t n_cal, 
     }
     const double C = hi;
     const double floor_term = beta * delta / (4.0 * (double)n);
-    std::vector<int32_t> class_of((size_t)cmax + 1, -1);
     for (uint32_t c = 0; c <= cmax; ++c) {
         if (!hist[c]) continue;
         const double dl = c == 0 ? floor_term : term(C, c) + floor_term;
         class_of[c] = (int32_t)Ltab.size();
         Ltab.push_back(make_double2(-std::log(dl), -std::log(dl)));
-    }
-    for (int64_t x = 0; x < n; ++x) {
-        const uint32_t k = (uint32_t)class_of[cal[(size_t)x]];
-        cls[(size_t)x] = k;
-        Lx[(size_t)x] = Ltab[k];
     }
     *C_out = C;
 }
@@ -628,10 +625,6 @@ static kadabra_status create_query(kadabra_graph *g, const kadabra_params *pin, 
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&q->d_cls), n * 4);
     if (e == cudaSuccess)
         e = cudaMalloc(reinterpret_cast<void **>(&q->d_launch), sizeof(kadabra::Counters) * kadabra::kLaunchLog);
-    for (int i = 0; i < kadabra::kLaunchLog && e == cudaSuccess; ++i) {
-        e = cudaEventCreate(&q->ev0[i]);
-        if (e == cudaSuccess) e = cudaEventCreate(&q->ev1[i]);
-    }
     if (e == cudaSuccess) e = cudaMemsetAsync(q->d_counts, 0, n * 4, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(q->d_cal, 0, n * 4, st);
     if (e == cudaSuccess) e = kadabra::launch_reset_job(q->d_job, st);
@@ -646,6 +639,14 @@ static kadabra_status create_query(kadabra_graph *g, const kadabra_params *pin, 
     return KADABRA_OK;
 }
 
+// Event pair of launch-log slot `slot`, created on first use.
+static kadabra_status slot_events(kadabra_query *q, int slot)
+{
+    if (!q->ev0[slot]) KCUDA(cudaEventCreate(&q->ev0[slot]), "create event");
+    if (!q->ev1[slot]) KCUDA(cudaEventCreate(&q->ev1[slot]), "create event");
+    return KADABRA_OK;
+}
+
 // Sampling scratch of the graph for launches that serve this query alone.
 static kadabra_status ready_workspace(kadabra_query *q)
 {
@@ -655,35 +656,54 @@ static kadabra_status ready_workspace(kadabra_query *q)
     return KADABRA_OK;
 }
 
-// Phase 2 on the host: budgets from the calibration counts.  Synchronises.
+// Phase 2: budgets from the calibration counts.  The device reduces the
+// counts to a histogram, the host runs the budget rule on it, the device
+// gives every vertex its class's budgets.  Synchronises.
 static kadabra_status finish_calibration(kadabra_query *q, cudaStream_t st)
 {
-    const size_t n = (size_t)q->g->n;
-    std::vector<uint32_t> cal(n);
+    const int64_t n = q->g->n;
     Job cj{};
-    cudaError_t e = cudaMemcpyAsync(cal.data(), q->d_cal, n * 4, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&cj, q->d_cal_job, sizeof(Job), cudaMemcpyDeviceToHost, st);
+    KCUDA(cudaMemcpyAsync(&cj, q->d_cal_job, sizeof(Job), cudaMemcpyDeviceToHost, st), "read calibration state");
+    unsigned int *d_mx = nullptr;
+    KCUDA(cudaMalloc(reinterpret_cast<void **>(&d_mx), sizeof(unsigned int)), "allocate");
+    unsigned int cmax = 0;
+    cudaError_t e = kadabra::launch_cal_max(n, q->d_cal, d_mx, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&cmax, d_mx, sizeof(cmax), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return cuda_fail(e, "calibration samples");
+    cudaFree(d_mx);
+    if (e != cudaSuccess) return cuda_fail(e, "calibration counts");
     kadabra_status s = device_error_status(cj);
     if (s != KADABRA_OK) return s;
-    std::vector<double2> L;
-    std::vector<uint32_t> cls;
+    std::vector<unsigned long long> hist((size_t)cmax + 1, 0ULL);
+    unsigned long long *d_hist = nullptr;
+    KCUDA(cudaMalloc(reinterpret_cast<void **>(&d_hist), hist.size() * sizeof(unsigned long long)), "allocate");
+    e = kadabra::launch_cal_hist(n, q->d_cal, cmax, d_hist, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(hist.data(), d_hist, hist.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(d_hist);
+    if (e != cudaSuccess) return cuda_fail(e, "calibration histogram");
+    std::vector<int32_t> class_of;
     std::vector<double2> Ltab;
-    budgets(q->g->n, cal, q->n_calib, q->p.eps, q->p.delta, q->p.delta_rule, q->p.beta, L, cls, Ltab, &q->balance_C);
+    budget_table(n, hist, q->n_calib, q->p.eps, q->p.delta, q->p.delta_rule, q->p.beta, class_of, Ltab,
+                 &q->balance_C);
     cudaFree(q->d_Ltab);
     cudaFree(q->d_cmax);
     q->d_Ltab = nullptr;
     q->d_cmax = nullptr;
     q->nclass = (int)Ltab.size();
-    e = cudaMemcpyAsync(q->d_L, L.data(), n * sizeof(double2), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&q->d_Ltab), Ltab.size() * sizeof(double2));
+    int *d_class_of = nullptr;
+    e = cudaMalloc(reinterpret_cast<void **>(&q->d_Ltab), Ltab.size() * sizeof(double2));
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&q->d_cmax), Ltab.size() * 4);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(q->d_cls, cls.data(), n * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&d_class_of), class_of.size() * sizeof(int32_t));
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(q->d_Ltab, Ltab.data(), Ltab.size() * sizeof(double2), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_class_of, class_of.data(), class_of.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = kadabra::launch_fill_budgets(n, q->d_cal, d_class_of, q->d_Ltab, q->d_cls, q->d_L, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return cuda_fail(e, "upload budgets");
+    cudaFree(d_class_of);
+    if (e != cudaSuccess) return cuda_fail(e, "budgets");
     q->phase = 2;
     q->pipe_begun = false;
     return KADABRA_OK;
@@ -711,7 +731,18 @@ extern "C" kadabra_status kadabra_calibrate(kadabra_graph *g, const kadabra_para
     a.epoch_len = q->n_calib;
     a.clip = 0;
     a.grid = clamp_grid(q, q->n_calib);
-    cudaError_t e = kadabra::launch_sample(a, st);
+    const int slot = (int)(q->launches % kadabra::kLaunchLog);
+    a.launch_ctr = q->d_launch + slot;
+    s = slot_events(q, slot);
+    cudaError_t e = s == KADABRA_OK ? cudaSuccess : cudaErrorMemoryAllocation;
+    if (e == cudaSuccess) e = cudaMemsetAsync(a.launch_ctr, 0, sizeof(kadabra::Counters), st);
+    if (e == cudaSuccess) e = cudaEventRecord(q->ev0[slot], st);
+    if (e == cudaSuccess) e = kadabra::launch_sample(a, st);
+    if (e == cudaSuccess) e = cudaEventRecord(q->ev1[slot], st);
+    if (e == cudaSuccess) {
+        q->grid_log[slot] = a.grid;
+        ++q->launches;
+    }
     if (e != cudaSuccess) {
         free_query_device(q);
         delete q;
@@ -809,6 +840,10 @@ extern "C" kadabra_status kadabra_sample_epoch(kadabra_query *q, int64_t n_sampl
     const int slot = (int)(q->launches % kadabra::kLaunchLog);
     a.launch_ctr = q->d_launch + slot;
     KCUDA(cudaMemsetAsync(a.launch_ctr, 0, sizeof(kadabra::Counters), st), "reset launch counters");
+    {
+        kadabra_status se = slot_events(q, slot);
+        if (se != KADABRA_OK) return se;
+    }
     KCUDA(cudaEventRecord(q->ev0[slot], st), "event");
     KCUDA(kadabra::launch_sample(a, st), "sampling kernel launch");
     KCUDA(cudaEventRecord(q->ev1[slot], st), "event");
@@ -918,6 +953,10 @@ extern "C" kadabra_status kadabra_run_pipelined(kadabra_query *q, int64_t epoch_
     B.grid = clamp_grid(q, int64_t(1) << 40);
     B.threads = q->threads;
     B.off64 = q->g->off64;
+    {
+        kadabra_status se = slot_events(q, slot);
+        if (se != KADABRA_OK) return se;
+    }
     KCUDA(cudaEventRecord(q->ev0[slot], st), "event");
     KCUDA(kadabra::launch_batch(B, st), "pipelined kernel launch");
     KCUDA(cudaEventRecord(q->ev1[slot], st), "event");
@@ -974,6 +1013,7 @@ extern "C" kadabra_status kadabra_batch_free(kadabra_batch *b)
     cudaFree(b->d_recs);
     cudaFree(b->d_queues);
     cudaFree(b->d_descs);
+    cudaFree(b->d_states);
     cudaFree(b->d_bs);
     if (b->ev0) cudaEventDestroy(b->ev0);
     if (b->ev1) cudaEventDestroy(b->ev1);
@@ -1003,8 +1043,11 @@ extern "C" kadabra_status kadabra_batch_step(kadabra_batch *b, kadabra_query *co
         cudaFree(b->d_descs);
         b->d_descs = nullptr;
         b->descs_cap = 0;
+        cudaFree(b->d_states);
+        b->d_states = nullptr;
         KCUDA(cudaMalloc(reinterpret_cast<void **>(&b->d_descs), (size_t)count * sizeof(kadabra::QueryDesc)),
               "allocate descriptors");
+        KCUDA(cudaMalloc(reinterpret_cast<void **>(&b->d_states), (size_t)count * sizeof(int)), "allocate states");
         b->descs_cap = count;
     }
     KCUDA(cudaMemcpyAsync(b->d_descs, descs.data(), (size_t)count * sizeof(kadabra::QueryDesc), cudaMemcpyHostToDevice, st),
@@ -1027,6 +1070,21 @@ extern "C" kadabra_status kadabra_batch_step(kadabra_batch *b, kadabra_query *co
     KCUDA(kadabra::launch_batch(B, st), "batch kernel launch");
     KCUDA(cudaEventRecord(b->ev1, st), "event");
     b->have_step = true;
+    b->last_count = count;
+    return KADABRA_OK;
+}
+
+extern "C" kadabra_status kadabra_batch_poll(kadabra_batch *b, int32_t *states, int64_t count, void *cuda_stream)
+{
+    if (!b || (!states && count > 0)) return fail(KADABRA_ERR_INVALID_ARG, "batch or states is null");
+    if (!b->have_step) return fail(KADABRA_ERR_STATE, "no batch step yet");
+    if (count != b->last_count) return fail(KADABRA_ERR_INVALID_ARG, "count differs from the last step's");
+    if (count == 0) return KADABRA_OK;
+    cudaStream_t st = as_stream(cuda_stream);
+    KCUDA(kadabra::launch_batch_poll(b->d_descs, (int)count, b->d_states, st), "poll kernel launch");
+    KCUDA(cudaMemcpyAsync(states, b->d_states, (size_t)count * sizeof(int32_t), cudaMemcpyDeviceToHost, st),
+          "read states");
+    KCUDA(cudaStreamSynchronize(st), "synchronise");
     return KADABRA_OK;
 }
 
@@ -1279,6 +1337,7 @@ extern "C" kadabra_status kadabra_query_get_info(kadabra_query *q, kadabra_query
     I.budget_classes = q->nclass;
     I.stop_ns = j.stopped ? j.stop_ns : 0ULL;
     I.phase = q->phase;
+    I.launches = q->launches;
     I.cal_done = q->phase == 2 ? (uint64_t)q->n_calib : 0ULL;
     if (q->phase == 1) {
         kadabra::PipeState ps{};

@@ -198,6 +198,12 @@ cudaError_t launch_result(int64_t n, const uint32_t *counts, const Job *job, dou
                           cudaStream_t st);
 cudaError_t launch_reset_job(Job *job, cudaStream_t st);
 cudaError_t read_device_clock(unsigned long long *ns, cudaStream_t st);
+cudaError_t launch_batch_poll(const QueryDesc *d, int nq, int *out, cudaStream_t st);
+cudaError_t launch_cal_max(int64_t n, const uint32_t *cal, unsigned int *mx, cudaStream_t st);
+cudaError_t launch_cal_hist(int64_t n, const uint32_t *cal, unsigned int cmax, unsigned long long *hist,
+                            cudaStream_t st);
+cudaError_t launch_fill_budgets(int64_t n, const uint32_t *cal, const int *class_of, const double2 *Ltab,
+                                uint32_t *cls, double2 *L, cudaStream_t st);
 cudaError_t launch_absorb(int64_t n, uint32_t *counts, const uint32_t *delta, Job *job, uint64_t samples,
                           cudaStream_t st);
 

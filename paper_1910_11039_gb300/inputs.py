@@ -29,7 +29,7 @@ __all__ = [
     "Graph", "csr_from_edges", "largest_component", "er_graph", "rmat_graph",
     "grid_graph", "rgg_graph", "path_graph", "star_graph", "cycle_graph",
     "complete_graph", "full_grid_graph", "config_graph", "CONFIGS",
-    "graph_from_spec", "batched_specs",
+    "graph_from_spec", "batched_specs", "SERVING_POOL", "serving_requests",
 ]
 
 
@@ -278,3 +278,25 @@ def batched_specs(count: int = 64, n_rgg: int = 8, seed0: int = 1000,
             specs.append(dict(kind="rgg", n=int(rng.integers(rgg_n[0], rgg_n[1] + 1)), avg_degree=10,
                               seed=seed0 + i))
     return specs
+
+
+# Graphs a query stream draws from: R-MAT scale 14..24 (edge factor 16) and
+# perturbed grids 1024^2..4096^2 (10% of the edges deleted, largest component).
+SERVING_POOL = {f"rmat{s}": dict(kind="rmat", scale=s, edge_factor=16, seed=100 + s) for s in range(14, 25)}
+SERVING_POOL.update({f"grid{k}": dict(kind="grid", k=k, delete_p=0.1, seed=3, lcc=True)
+                     for k in (1024, 2048, 3072, 4096)})
+
+
+def serving_requests(count: int = 2000, rate: float = 20.0, seed: int = 5, pool=None,
+                     eps_choices=(0.01, 0.005), delta: float = 0.1) -> list[dict]:
+    """A Poisson query stream: exponential inter-arrival gaps with mean
+    1/rate seconds, each request's graph uniform over `pool` (names of
+    SERVING_POOL) and its eps uniform over eps_choices; request i samples
+    with seed `seed` * 1_000_000 + i."""
+    pool = list(pool if pool is not None else SERVING_POOL)
+    rng = np.random.default_rng(seed)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, count))
+    gi = rng.integers(0, len(pool), count)
+    ei = rng.integers(0, len(eps_choices), count)
+    return [dict(rid=i, graph=pool[int(gi[i])], eps=float(eps_choices[int(ei[i])]), delta=delta,
+                 seed=seed * 1_000_000 + i, arrival=float(arrivals[i])) for i in range(count)]

@@ -54,7 +54,8 @@ class QueryInfo(C.Structure):
                 ("walk_scan", C.c_uint64), ("scaled", C.c_uint64), ("device_error", C.c_uint32),
                 ("slots", C.c_int32), ("threads", C.c_int32), ("offsets_64", C.c_int32),
                 ("budget_classes", C.c_int32), ("stop_ns", C.c_uint64), ("phase", C.c_int32),
-                ("pad0", C.c_int32), ("cal_done", C.c_uint64), ("device_bytes", C.c_uint64)]
+                ("pad0", C.c_int32), ("cal_done", C.c_uint64), ("device_bytes", C.c_uint64),
+                ("launches", C.c_int64)]
 
 
 class TraceRec(C.Structure):
@@ -112,6 +113,7 @@ SIGNATURES = {
     "kadabra_pipeline_begin": (_ST, [_P, _I64, C.c_int, _P]),
     "kadabra_run_graph": (_ST, [_P, _I64, C.c_int, _I64, _P, C.POINTER(C.c_int)]),
     "kadabra_batch_set_policy": (_ST, [_P, C.c_int]),
+    "kadabra_batch_poll": (_ST, [_P, _P, _I64, _P]),
     "kadabra_query_create": (_ST, [_P, _P, _P, _P]),
     "kadabra_calibration_begin": (_ST, [_P, _P]),
     "kadabra_calibration_finish": (_ST, [_P, _P]),
@@ -410,6 +412,13 @@ class Batch:
         arr = (C.c_void_p * len(queries))(*[q.handle.value for q in queries])
         _check(load().kadabra_batch_step(self.handle, C.cast(arr, C.c_void_p), len(queries), sample_budget,
                                          _stream(stream)))
+
+    def poll(self, count, stream=None) -> np.ndarray:
+        """States of the last step's queries: 0 running, 1 calibration
+        complete, 2 stopped."""
+        out = np.zeros(count, dtype=np.int32)
+        _check(load().kadabra_batch_poll(self.handle, _ptr(out), count, _stream(stream)))
+        return out
 
     def last_ms(self) -> float:
         ms = C.c_float()

@@ -103,6 +103,7 @@ class Server:
         self.keep_results = keep_results
         self.log = log
         self.used = 0
+        self.vd: dict[str, int] = {}      # vertex-diameter bound per graph, computed by its first query
         self.stats = {"steps": 0, "step_ms": 0.0, "samples": 0, "cal_samples": 0, "admit_waits": 0,
                       "max_active": 0, "peak_bytes": 0}
 
@@ -111,6 +112,15 @@ class Server:
     def _state_bytes_estimate(self, key: str) -> int:
         """Device bytes of a query before its epoch logs are known."""
         return 40 * self.n[key] + (1 << 20)
+
+    def _create(self, r: "Request"):
+        """Phase 1 of a request's query (the graph's vertex-diameter bound is
+        computed once, by its first query, and reused)."""
+        q = K.Query(self.graphs[r.graph], calibrate=False, eps=r.eps, delta=r.delta, seed=r.seed,
+                    threads=self.schedule.threads, vertex_diameter=self.vd.get(r.graph, 0))
+        if r.graph not in self.vd:
+            self.vd[r.graph] = int(q.info().vertex_diameter)
+        return q
 
     def _log_bytes(self, vd: int, E: int) -> int:
         return 4 * self.schedule.frames * E * max(1, vd - 2)
@@ -127,6 +137,8 @@ class Server:
         """Serve `requests` (any order; each has an arrival time in seconds).
         With realtime=False every request is taken as already arrived.
         Returns the requests with their results and timings."""
+        self.stats = {"steps": 0, "step_ms": 0.0, "samples": 0, "cal_samples": 0, "admit_waits": 0,
+                      "max_active": 0, "peak_bytes": 0, "tau": 0}
         future = deque(sorted(requests, key=lambda r: (r.arrival, r.rid)))
         pending: deque[Request] = deque()
         active: list[_Active] = []
@@ -152,8 +164,7 @@ class Server:
                     self.stats["admit_waits"] += 1
                     break
                 pending.popleft()
-                q = K.Query(self.graphs[r.graph], calibrate=False, eps=r.eps, delta=r.delta, seed=r.seed,
-                            threads=self.schedule.threads)
+                q = self._create(r)
                 inf = q.info()
                 r.omega_ceil = int(inf.omega_ceil)
                 r.epoch_len = self.schedule.epoch_len(r.omega_ceil)
@@ -175,28 +186,29 @@ class Server:
             self.stats["steps"] += 1
             self.stats["step_ms"] += ms
             budget = int(min(1 << 22, max(256, budget * self.step_ms / max(ms, 1e-3))))
+            states = self.batch.poll(len(active))
             still = []
-            for a in active:
-                inf = a.q.info()
+            for a, state in zip(active, states):
                 if a.phase == 1:
-                    if inf.cal_done >= inf.n_calib:
+                    if state == 1:
                         a.q.calibration_finish()
                         a.q.pipeline_begin(a.req.epoch_len, frames=self.schedule.frames)
                         a.phase = 2
                         a.req.calibrated = now()
-                        self.stats["cal_samples"] += int(inf.n_calib)
                     still.append(a)
                     continue
-                if not inf.stopped:
+                if state != 2:
                     still.append(a)
                     continue
+                inf = a.q.info()
+                self.stats["cal_samples"] += int(inf.n_calib)
                 r = a.req
                 r.seen_done = now()
                 r.stop_time = (int(inf.stop_ns) - dev0) / 1e9
                 r.tau = int(inf.tau)
                 r.stop_epoch = int(inf.stop_epoch)
                 self.stats["samples"] += int(inf.samples)
-                self.stats["tau"] = self.stats.get("tau", 0) + r.tau
+                self.stats["tau"] += r.tau
                 if self.keep_results:
                     r.counts = a.q.result(btilde=False)["counts"]
                 a.q.free()
@@ -204,6 +216,54 @@ class Server:
                 done.append(r)
             active = still
         self.stats["wall_s"] = now()
+        return done
+
+    def run_one_at_a_time(self, requests, realtime: bool = True, clock=time.perf_counter):
+        """The same stream served the plain way: one query at a time in
+        arrival order, its calibration in one launch and its adaptive phase
+        in one more launch (same kernels, scratch and schedule, no sharing)."""
+        future = deque(sorted(requests, key=lambda r: (r.arrival, r.rid)))
+        done: list[Request] = []
+        self.batch.set_policy(K.Batch.IN_ORDER)
+        t0 = clock()
+        dev0 = K.device_clock()
+        t0 = 0.5 * (t0 + clock())
+        steps, step_ms, samples, cal = 0, 0.0, 0, 0
+
+        def now():
+            return clock() - t0
+
+        while future:
+            r = future.popleft()
+            if realtime and r.arrival > now():
+                time.sleep(r.arrival - now())
+            q = self._create(r)
+            r.admitted = now()
+            inf = q.info()
+            r.omega_ceil = int(inf.omega_ceil)
+            r.epoch_len = self.schedule.epoch_len(r.omega_ceil)
+            q.calibration_begin()
+            self.batch.step([q])
+            step_ms += self.batch.last_ms()
+            q.calibration_finish()
+            r.calibrated = now()
+            q.pipeline_begin(r.epoch_len, frames=self.schedule.frames)
+            self.batch.step([q])
+            step_ms += self.batch.last_ms()
+            steps += 2
+            inf = q.info()
+            r.seen_done = now()
+            r.stop_time = (int(inf.stop_ns) - dev0) / 1e9
+            r.tau, r.stop_epoch = int(inf.tau), int(inf.stop_epoch)
+            samples += int(inf.samples)
+            cal += int(inf.n_calib)
+            if self.keep_results:
+                r.counts = q.result(btilde=False)["counts"]
+            q.free()
+            done.append(r)
+        self.batch.set_policy(K.Batch.IN_ORDER if self.policy == "fifo" else K.Batch.ROUND_ROBIN)
+        self.stats.update(steps=steps, step_ms=step_ms, samples=samples, cal_samples=cal, wall_s=now(),
+                          tau=sum(r.tau for r in done), max_active=1, peak_bytes=0, admit_waits=0)
         return done
 
     def summary(self, done) -> dict:

@@ -92,6 +92,8 @@ def test_batch_in_small_steps_matches_alone(K, orc, graphs, budget, policy):
         if not running:
             break
         b.step(running, sample_budget=budget)
+        states = b.poll(len(running))
+        assert [int(x) for x in states] == [2 if q.info().stopped else 0 for q in running]
     check_all(K, orc, qs)
 
 
@@ -175,6 +177,11 @@ def test_calibration_inside_batch_matches_calibrate(K, orc, graphs):
     phase = {id(p): 1 for p, *_ in fresh}
     for _ in range(100000):
         b.step(active, sample_budget=257)
+        states = b.poll(len(active))
+        for q, st in zip(active, states):
+            inf = q.info()
+            want = (1 if inf.cal_done >= inf.n_calib else 0) if inf.phase == 1 else (2 if inf.stopped else 0)
+            assert st == want
         for p, E, F, g in fresh:
             if phase[id(p)] == 1 and p.info().cal_done >= p.info().n_calib:
                 p.calibration_finish()

@@ -372,7 +372,7 @@ def test_disconnected_pairs_count_but_add_nothing(K, orc):
 
 
 @pytest.mark.parametrize("name", ["er2000", "rmat14", "grid64", "grid256", "path", "star", "disjoint", "edgeless",
-                                  "rmat12_raw"])
+                                  "rmat12_raw", "rgg5k_raw", "big_second"])
 def test_vertex_diameter_bound_matches_oracle(K, orc, name):
     if name == "disjoint":
         src = np.concatenate([np.arange(49), np.arange(50, 70), [80, 81]])
@@ -381,6 +381,12 @@ def test_vertex_diameter_bound_matches_oracle(K, orc, name):
         g = I.csr_from_edges(5, np.zeros(0, dtype=np.int64), np.zeros(0, dtype=np.int64))
     elif name == "rmat12_raw":
         g = I.rmat_graph(12, 4, seed=77)        # many components and isolated vertices
+    elif name == "rgg5k_raw":
+        g = I.rgg_graph(5000, 4, seed=3)        # sparse: many components of all sizes
+    elif name == "big_second":
+        # a short path on the low ids, a long path (the largest component) after it
+        src = np.concatenate([np.arange(0, 9), np.arange(10, 299)])
+        g = I.csr_from_edges(300, src, src + 1)
     else:
         g = GRAPHS[name]() if name in GRAPHS else I.config_graph(name)
     G = K.Graph.from_inputs(g)
