@@ -627,7 +627,7 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=20.0)
     ap.add_argument("--serve-pool", default="rmat", choices=["rmat", "full"],
                     help="rmat: R-MAT scale 14-24; full: also the perturbed grids 1024^2-4096^2")
-    ap.add_argument("--serve-policy", default="fifo", choices=["fifo", "round_robin"])
+    ap.add_argument("--serve-policy", default="fifo", choices=["fifo", "shortest", "round_robin"])
     ap.add_argument("--step-ms", type=float, default=20.0, help="serve mode: target length of a batch step")
     ap.add_argument("--autotune", action="store_true", help="batched mode: search the schedule first")
     ap.add_argument("--divisor", type=int, default=32, help="batched mode: epoch length = omega / divisor")

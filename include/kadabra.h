@@ -385,8 +385,8 @@ kadabra_status kadabra_launch_log(kadabra_query *q, int64_t max_entries, kadabra
  * do, and adds each sampled path's interior vertices to counts[n] (device
  * pointer, caller-owned, accumulated, not cleared).  The scratch lives in a
  * fixed array of KADABRA_STATIC_SCRATCH_BYTES inside the library; nothing is
- * allocated.  Graphs need n * 20 bytes per in-flight sample, so n must satisfy
- * n * 20 <= KADABRA_STATIC_SCRATCH_BYTES - 256 (else KADABRA_ERR_INVALID_ARG),
+ * allocated.  Graphs need n * 36 bytes per in-flight sample, so n must satisfy
+ * n * 36 <= KADABRA_STATIC_SCRATCH_BYTES - 256 (else KADABRA_ERR_INVALID_ARG),
  * and fewer samples run in parallel as n grows.
  * The first call on a device looks up the array's device address (make that
  * first call before any stream capture).  All calls share the array: calls

@@ -17,10 +17,14 @@ namespace kadabra {
 // A first discovery claims the vertex and sets its count with one CAS.
 // Invariant between samples: every record of a slot is all-zero (the sample
 // that touched a record clears it before the slot takes its next sample).
-struct alignas(16) SlotRec {
+// A record fills one 32-byte sector (16 bytes of padding): records of
+// different vertices never share a sector, and the clearing store writes the
+// whole sector, so the cache does not read the sector back from DRAM first.
+struct alignas(32) SlotRec {
     unsigned long long w[2];
+    unsigned long long pad[2];
 };
-static_assert(sizeof(SlotRec) == 16, "SlotRec is two 64-bit words");
+static_assert(sizeof(SlotRec) == 32, "SlotRec fills a 32-byte sector");
 
 // Counters a launch accumulates (one atomicAdd per CTA at exit).
 struct Counters {

@@ -19,8 +19,9 @@
 //   the last CTA of the launch advances tau (A5: stream order makes the
 //   counter vector at the next kernel a consistent snapshot).
 //
-// Layout in HBM (per slot): SlotRec[n] (16 B per vertex: for each side one
-// word holding the path count and the BFS level) and a uint32 queue of n entries shared by
+// Layout in HBM (per slot): SlotRec[n] (32 B per vertex, one sector: for each
+// side one word holding the path count and the BFS level, then padding) and a
+// uint32 queue of n entries shared by
 // both sides (s-side grows from the front, t-side from the back; the balls
 // are disjoint until they meet, so n entries always suffice).  Records are
 // cleared by the sample that set them, so no per-sample O(n) reset is needed.
@@ -674,69 +675,126 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
         const bool in_smem = mcnt <= (unsigned int)kMeetCap;
         // weights sigma_s(w) * sigma_t(w) and their 128-bit total
         unsigned long long tlo = 0, thi = 0;
-        if (in_smem) {
-            for (unsigned int i = tid; i < mcnt; i += NT) {
-                const unsigned int w = sh.cand[i];
-                unsigned long long w0, w1;
-                load_rec(rec + w, w0, w1);
-                const unsigned long long p = sig_of(w0), q = sig_of(w1);
-                const unsigned long long lo = p * q, hi = __umul64hi(p, q);
-                sh.wlo[i] = lo;
-                sh.whi[i] = hi;
-                add128(tlo, thi, lo, hi);
-            }
-        } else {
-            for (unsigned int i = sh.fbeg[Y] + tid; i < sh.fend[Y]; i += NT) {
-                const unsigned int w = qget(queue, n, Y, i);
-                unsigned long long w0, w1;
-                load_rec(rec + w, w0, w1);
-                if (lvl_of(X ? w1 : w0) != nl) continue;
-                const unsigned long long p = sig_of(w0), q = sig_of(w1);
-                add128(tlo, thi, p * q, __umul64hi(p, q));
-            }
-        }
-        block_sum128<NT>(tlo, thi, sh);
-        if (tid == 0) {
-            sh.sig_lo = tlo;
-            sh.sig_hi = thi;
-            if (in_smem && mcnt == 1) {
-                sh.chosen = sh.cand[0];
-            } else {
-                const U64x4 x = sample_draw(a.seed, a.tag, idx, 1);
-                const unsigned __int128 R = ((unsigned __int128)x.v[1] << 64) | x.v[0];
-                const unsigned __int128 T = ((unsigned __int128)thi << 64) | tlo;
-                const unsigned __int128 r = R % T;
-                sh.r_lo = (unsigned long long)r;
-                sh.r_hi = (unsigned long long)(r >> 64);
-                sh.chosen = -1;
-            }
-        }
-        __syncthreads();
-        if (sh.chosen < 0) {
-            long long c;
-            if (in_smem) {
-                c = radix_choose<NT>(sh, npass, [&](auto &&add) {
-                    for (unsigned int i = tid; i < mcnt; i += NT) add(sh.cand[i], sh.wlo[i], sh.whi[i]);
-                });
-            } else {
-                const unsigned int yb = sh.fbeg[Y], ye = sh.fend[Y];
-                c = radix_choose<NT>(sh, npass, [&](auto &&add) {
-                    for (unsigned int i = yb + tid; i < ye; i += NT) {
-                        const unsigned int w = qget(queue, n, Y, i);
-                        unsigned long long w0, w1;
-                        load_rec(rec + w, w0, w1);
-                        if (lvl_of(X ? w1 : w0) != nl) continue;
-                        const unsigned long long p = sig_of(w0), q = sig_of(w1);
-                        add(w, p * q, __umul64hi(p, q));
+        if (mcnt <= 32u) {
+            // small meeting set: warp 0 alone weighs the candidates, orders
+            // them by id and picks the one whose prefix interval holds r
+            if (tid < 32) {
+                const int lane = tid;
+                const bool have = (unsigned int)lane < mcnt;
+                const unsigned int id = have ? sh.cand[lane] : 0xffffffffu;
+                unsigned long long lo = 0, hi = 0;
+                if (have) {
+                    unsigned long long w0, w1;
+                    load_rec(rec + id, w0, w1);
+                    const unsigned long long p = sig_of(w0), q = sig_of(w1);
+                    lo = p * q;
+                    hi = __umul64hi(p, q);
+                }
+                // exclusive prefix of the weights in ascending id order, and the total
+                unsigned long long plo = 0, phi = 0, alo = 0, ahi = 0;
+                for (int j = 0; j < 32; ++j) {
+                    const unsigned int idj = __shfl_sync(0xffffffffu, id, j);
+                    const unsigned long long ljo = __shfl_sync(0xffffffffu, lo, j);
+                    const unsigned long long hjo = __shfl_sync(0xffffffffu, hi, j);
+                    add128(alo, ahi, ljo, hjo);
+                    if (idj < id) add128(plo, phi, ljo, hjo);
+                }
+                long long chosen = -1;
+                unsigned long long rlo = 0, rhi = 0;
+                if (mcnt == 1) {
+                    chosen = sh.cand[0];
+                } else {
+                    if (lane == 0) {
+                        const U64x4 x = sample_draw(a.seed, a.tag, idx, 1);
+                        const unsigned __int128 R = ((unsigned __int128)x.v[1] << 64) | x.v[0];
+                        const unsigned __int128 T = ((unsigned __int128)ahi << 64) | alo;
+                        const unsigned __int128 r = R % T;
+                        rlo = (unsigned long long)r;
+                        rhi = (unsigned long long)(r >> 64);
                     }
-                });
-            }
-            if (tid == 0) {
-                const bool ok = c >= 0 && c < n && lvl_of(ldcg(&rec[c].w[X])) == nl && lvl_of(ldcg(&rec[c].w[Y])) != 0;
-                sh.chosen = ok ? c : -1;
-                if (!ok) sh.err |= kErrSelect;
+                    rlo = __shfl_sync(0xffffffffu, rlo, 0);
+                    rhi = __shfl_sync(0xffffffffu, rhi, 0);
+                    unsigned long long elo = plo, ehi = phi;
+                    add128(elo, ehi, lo, hi);
+                    const bool mine = have && !less128(rlo, rhi, plo, phi) && less128(rlo, rhi, elo, ehi);
+                    const unsigned int m = __ballot_sync(0xffffffffu, mine);
+                    chosen = m ? (long long)__shfl_sync(0xffffffffu, id, __ffs(m) - 1) : -1;
+                }
+                if (lane == 0) {
+                    sh.sig_lo = alo;
+                    sh.sig_hi = ahi;
+                    const bool ok = chosen >= 0 && chosen < n && lvl_of(ldcg(&rec[chosen].w[X])) == nl &&
+                                    lvl_of(ldcg(&rec[chosen].w[Y])) != 0;
+                    sh.chosen = ok ? chosen : -1;
+                    if (!ok) sh.err |= kErrSelect;
+                }
             }
             __syncthreads();
+        } else {
+            if (in_smem) {
+                for (unsigned int i = tid; i < mcnt; i += NT) {
+                    const unsigned int w = sh.cand[i];
+                    unsigned long long w0, w1;
+                    load_rec(rec + w, w0, w1);
+                    const unsigned long long p = sig_of(w0), q = sig_of(w1);
+                    const unsigned long long lo = p * q, hi = __umul64hi(p, q);
+                    sh.wlo[i] = lo;
+                    sh.whi[i] = hi;
+                    add128(tlo, thi, lo, hi);
+                }
+            } else {
+                for (unsigned int i = sh.fbeg[Y] + tid; i < sh.fend[Y]; i += NT) {
+                    const unsigned int w = qget(queue, n, Y, i);
+                    unsigned long long w0, w1;
+                    load_rec(rec + w, w0, w1);
+                    if (lvl_of(X ? w1 : w0) != nl) continue;
+                    const unsigned long long p = sig_of(w0), q = sig_of(w1);
+                    add128(tlo, thi, p * q, __umul64hi(p, q));
+                }
+            }
+            block_sum128<NT>(tlo, thi, sh);
+            if (tid == 0) {
+                sh.sig_lo = tlo;
+                sh.sig_hi = thi;
+                if (in_smem && mcnt == 1) {
+                    sh.chosen = sh.cand[0];
+                } else {
+                    const U64x4 x = sample_draw(a.seed, a.tag, idx, 1);
+                    const unsigned __int128 R = ((unsigned __int128)x.v[1] << 64) | x.v[0];
+                    const unsigned __int128 T = ((unsigned __int128)thi << 64) | tlo;
+                    const unsigned __int128 r = R % T;
+                    sh.r_lo = (unsigned long long)r;
+                    sh.r_hi = (unsigned long long)(r >> 64);
+                    sh.chosen = -1;
+                }
+            }
+            __syncthreads();
+            if (sh.chosen < 0) {
+                long long c;
+                if (in_smem) {
+                    c = radix_choose<NT>(sh, npass, [&](auto &&add) {
+                        for (unsigned int i = tid; i < mcnt; i += NT) add(sh.cand[i], sh.wlo[i], sh.whi[i]);
+                    });
+                } else {
+                    const unsigned int yb = sh.fbeg[Y], ye = sh.fend[Y];
+                    c = radix_choose<NT>(sh, npass, [&](auto &&add) {
+                        for (unsigned int i = yb + tid; i < ye; i += NT) {
+                            const unsigned int w = qget(queue, n, Y, i);
+                            unsigned long long w0, w1;
+                            load_rec(rec + w, w0, w1);
+                            if (lvl_of(X ? w1 : w0) != nl) continue;
+                            const unsigned long long p = sig_of(w0), q = sig_of(w1);
+                            add(w, p * q, __umul64hi(p, q));
+                        }
+                    });
+                }
+                if (tid == 0) {
+                    const bool ok = c >= 0 && c < n && lvl_of(ldcg(&rec[c].w[X])) == nl && lvl_of(ldcg(&rec[c].w[Y])) != 0;
+                    sh.chosen = ok ? c : -1;
+                    if (!ok) sh.err |= kErrSelect;
+                }
+                __syncthreads();
+            }
         }
 
         const long long w = sh.chosen;
@@ -804,6 +862,30 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
                                 for (unsigned int i = tid; i < pc; i += NT) add(sh.cand[i], sh.wlo[i], 0ULL);
                             });
                             if (tid == 0) sh.next_v = c;
+                        }
+                        __syncthreads();
+                    } else if (d <= 32) {
+                        // few neighbours: warp 0 alone scans them in adjacency order
+                        walk_scan += (unsigned long long)d;
+                        if (tid < 32) {
+                            long long u = -1;
+                            unsigned long long wt = 0;
+                            if (tid < d) {
+                                u = G.col(b + tid);
+                                const unsigned long long wu = ldcg(&rec[u].w[Z]);
+                                if (lvl_of(wu) == target) wt = sig_of(wu);
+                            }
+                            unsigned long long incl = wt;
+#pragma unroll
+                            for (int o = 1; o < 32; o <<= 1) {
+                                const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
+                                if (tid >= o) incl += y;
+                            }
+                            const unsigned long long total = __shfl_sync(0xffffffffu, incl, 31);
+                            const unsigned long long ex = incl - wt;
+                            const unsigned long long r = __umul64hi(x.v[0], total);
+                            __syncwarp();
+                            if (wt > 0 && ex <= r && r < ex + wt) sh.next_v = u;
                         }
                         __syncthreads();
                     } else if (d <= NT) {
@@ -916,12 +998,21 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
     // clear every record this sample touched (meeting vertices sit in the
     // other side's queue), restoring the all-zero invariant
     __syncthreads();
-    const uint4 z = make_uint4(0u, 0u, 0u, 0u);
     for (int side = 0; side < 2; ++side) {
         const unsigned int len = sh.qlen[side];
-        for (unsigned int i = tid; i < len; i += NT) {
-            const unsigned int v = qget(queue, n, side, i);
-            __stcg(reinterpret_cast<uint4 *>(rec + v), z);
+        for (unsigned int i0 = tid; i0 < len; i0 += 4 * NT) {
+            unsigned int v[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const unsigned int i = i0 + (unsigned int)j * NT;
+                v[j] = i < len ? qget(queue, n, side, i) : kNone;
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (v[j] == kNone) continue;
+                // one 32-byte store clears the record's whole sector
+                asm volatile("st.global.cg.v4.u64 [%0], {%1, %1, %1, %1};" ::"l"(rec + v[j]), "l"(0ULL) : "memory");
+            }
         }
     }
     __syncthreads();

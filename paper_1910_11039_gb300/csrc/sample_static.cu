@@ -105,7 +105,7 @@ extern "C" kadabra_status kadabra_sample_static(const kadabra_graph *g, uint64_t
     const size_t max_slots = (kStaticScratchBytes - kStaticJobBytes) / per_slot;
     if (max_slots < 1)
         return static_fail(KADABRA_ERR_INVALID_ARG,
-                           "graph too large for the static scratch: n * 20 bytes must fit in "
+                           "graph too large for the static scratch: n * 36 bytes must fit in "
                            "KADABRA_STATIC_SCRATCH_BYTES - 256");
     if (count == 0) return KADABRA_OK;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);

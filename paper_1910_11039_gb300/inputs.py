@@ -226,6 +226,8 @@ CONFIGS = {
     "rmat20": dict(kind="rmat", scale=20, edge_factor=16, seed=2),
     # 4096 x 4096 grid with 10% of the edges deleted (seed 3), largest component
     "grid4096": dict(kind="grid", k=4096, delete_p=0.1, seed=3, lcc=True),
+    # R-MAT scale 26, edge factor 16 (~1.07B edge draws; int64 offsets), generator seed 4
+    "rmat26": dict(kind="rmat", scale=26, edge_factor=16, seed=4),
     # small members of the same families
     "rmat12": dict(kind="rmat", scale=12, edge_factor=16, seed=12),
     "rmat14": dict(kind="rmat", scale=14, edge_factor=16, seed=14),

@@ -63,16 +63,19 @@ class Request:
 
 
 class _Active:
-    __slots__ = ("req", "q", "phase", "bytes")
+    __slots__ = ("req", "q", "phase", "bytes", "n_calib")
 
-    def __init__(self, req, q, nbytes):
-        self.req, self.q, self.phase, self.bytes = req, q, 1, nbytes
+    def __init__(self, req, q, nbytes, n_calib):
+        self.req, self.q, self.phase, self.bytes, self.n_calib = req, q, 1, nbytes, n_calib
 
 
 class Server:
     """policy "fifo": earlier arrivals take samples first (the batch's
-    IN_ORDER policy over the active list in arrival order); "round_robin":
-    every active query takes samples at the same rate."""
+    IN_ORDER policy over the active list in arrival order); "shortest": the
+    query with the least expected work left goes first (IN_ORDER over the
+    active list sorted by samples left times graph size, a proxy for the cost
+    of a sample); "round_robin": every active query takes samples at the same
+    rate."""
 
     def __init__(self, graphs: dict, threads: int = 1024, slots: int = 0, schedule: Schedule | None = None,
                  memory_budget: int | None = None, step_ms: float = 20.0, policy: str = "fifo",
@@ -92,10 +95,10 @@ class Server:
         self.schedule = schedule or Schedule(threads=threads)
         self.batch = K.Batch(self.max_n, slots=slots, threads=self.schedule.threads,
                              offsets_64=off64.pop() if off64 else False)
-        if policy not in ("fifo", "round_robin"):
-            raise ValueError("policy must be 'fifo' or 'round_robin'")
+        if policy not in ("fifo", "shortest", "round_robin"):
+            raise ValueError("policy must be 'fifo', 'shortest' or 'round_robin'")
         self.policy = policy
-        self.batch.set_policy(K.Batch.IN_ORDER if policy == "fifo" else K.Batch.ROUND_ROBIN)
+        self.batch.set_policy(K.Batch.ROUND_ROBIN if policy == "round_robin" else K.Batch.IN_ORDER)
         torch.cuda.synchronize()
         free, _ = torch.cuda.mem_get_info()
         self.memory_budget = int(memory_budget if memory_budget is not None else 0.8 * free)
@@ -121,6 +124,13 @@ class Server:
         if r.graph not in self.vd:
             self.vd[r.graph] = int(q.info().vertex_diameter)
         return q
+
+    def _work_left(self, a: "_Active") -> float:
+        """Expected work of an active query: samples it may still take (its
+        calibration samples, or omega, as an upper bound known without a
+        device read) times its graph's vertex count."""
+        left = a.n_calib if a.phase == 1 else a.req.omega_ceil
+        return float(left) * self.n[a.req.graph]
 
     def _log_bytes(self, vd: int, E: int) -> int:
         return 4 * self.schedule.frames * E * max(1, vd - 2)
@@ -173,14 +183,16 @@ class Server:
                 self.used += nbytes
                 q.calibration_begin()
                 r.admitted = now()
-                active.append(_Active(r, q, nbytes))
+                active.append(_Active(r, q, nbytes, int(inf.n_calib)))
             self.stats["max_active"] = max(self.stats["max_active"], len(active))
             self.stats["peak_bytes"] = max(self.stats["peak_bytes"], self.used)
             if not active:
                 if future and realtime:
                     time.sleep(max(0.0, min(0.05, future[0].arrival - now())))
                 continue
-            # one step over every active query (arrival order = priority under "fifo")
+            # one step over every active query (list order = priority under IN_ORDER)
+            if self.policy == "shortest":
+                active.sort(key=self._work_left)
             self.batch.step([a.q for a in active], sample_budget=budget)
             ms = self.batch.last_ms()
             self.stats["steps"] += 1
@@ -261,7 +273,7 @@ class Server:
                 r.counts = q.result(btilde=False)["counts"]
             q.free()
             done.append(r)
-        self.batch.set_policy(K.Batch.IN_ORDER if self.policy == "fifo" else K.Batch.ROUND_ROBIN)
+        self.batch.set_policy(K.Batch.ROUND_ROBIN if self.policy == "round_robin" else K.Batch.IN_ORDER)
         self.stats.update(steps=steps, step_ms=step_ms, samples=samples, cal_samples=cal, wall_s=now(),
                           tau=sum(r.tau for r in done), max_active=1, peak_bytes=0, admit_waits=0)
         return done

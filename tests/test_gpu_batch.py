@@ -200,7 +200,8 @@ def test_calibration_inside_batch_matches_calibrate(K, orc, graphs):
         assert np.array_equal(res["counts"], counts), name
 
 
-def test_server_results_equal_alone_and_in_mix(K, orc, graphs):
+@pytest.mark.parametrize("policy", ["fifo", "shortest"])
+def test_server_results_equal_alone_and_in_mix(K, orc, graphs, policy):
     """Requests served together (continuous batching, arrivals while others
     run) give the results each gives alone, and those of the oracle."""
     from paper_1910_11039_gb300.autotune import Schedule
@@ -209,7 +210,7 @@ def test_server_results_equal_alone_and_in_mix(K, orc, graphs):
     reqs = [Request(i, name, eps, 0.1, seed, arrival=0.002 * i) for i, (name, eps, seed, _, _) in enumerate(SPECS)]
     reqs += [Request(10 + i, name, eps, 0.1, seed + 100, arrival=0.001 * i)
              for i, (name, eps, seed, _, _) in enumerate(SPECS[:3])]
-    srv = Server({k: v[1] for k, v in graphs.items()}, schedule=sched, step_ms=2.0)
+    srv = Server({k: v[1] for k, v in graphs.items()}, schedule=sched, step_ms=2.0, policy=policy)
     mixed = {r.rid: r for r in srv.run([dataclasses.replace(r) for r in reqs])}
     assert len(mixed) == len(reqs)
     s = srv.summary(list(mixed.values()))

@@ -6,6 +6,7 @@ must agree to 1e-12 relative (both sides use the same IEEE operation
 sequence, so they are expected to be identical).
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -421,3 +422,46 @@ def test_rmat20_full_size_epoch_and_trace(K, orc):
     assert np.array_equal(cal, want_cal)
     wLL, wLU, _ = orc.calibrate_L(want_cal, info.n_calib, 0.01, 0.1)
     np.testing.assert_allclose(LL, wLL, rtol=REL, atol=0)
+
+
+@pytest.mark.slow
+def test_grid4096_full_size_sampled(K, orc):
+    """The 4096 x 4096 grid with 10% of the edges deleted (the high-diameter
+    workload) at full size: vertex-diameter bound, and per-sample records of
+    sampled indices (paths thousands of layers long, scaled path counts)."""
+    g = I.config_graph("grid4096")
+    G = K.Graph.from_inputs(g, skip_validate=True)
+    q = K.Query(G, eps=0.01, delta=0.1, seed=1, n_calib=64)
+    info = q.info()
+    assert info.vertex_diameter == orc.vertex_diameter_bound(g)
+    assert info.omega == orc.omega(0.01, 0.1, info.vertex_diameter)
+    cap = 12000
+    recs, paths = q.sample_trace(1, 777, 6, path_cap=cap)
+    compare_trace(recs, paths, oracle_trace(orc, g, 1, 1, 777, 6), cap)
+    assert all(r.scaled for r in recs)
+    assert max(r.d for r in recs) > 1000
+
+
+@pytest.mark.slow
+@pytest.mark.skipif(not os.environ.get("KADABRA_FULL_SIZE"),
+                    reason="R-MAT scale 26 takes minutes and ~70 GB of host memory to generate; "
+                           "set KADABRA_FULL_SIZE=1")
+def test_rmat26_full_size_sampled(K, orc):
+    """R-MAT scale 26, edge factor 16 (int64 offsets) at full size: the
+    vertex-diameter bound, one epoch of counters bit-exact, and per-sample
+    records of a sampled index range."""
+    g = I.config_graph("rmat26")
+    assert g.nnz > (1 << 31)                       # needs 64-bit offsets
+    G = K.Graph.from_inputs(g, offsets_64=True, skip_validate=True)
+    q = K.Query(G, eps=0.01, delta=0.1, seed=1, n_calib=256)
+    info = q.info()
+    assert info.offsets_64 == 1
+    assert info.vertex_diameter == orc.vertex_diameter_bound(g)
+    E = 512
+    q.sample_epoch(E)
+    res = q.result(btilde=False)
+    want, st = orc.run_samples(g, 1, 1, 0, E)
+    assert np.array_equal(res["counts"], want)
+    assert q.info().e_scan == st.e_scan
+    recs, paths = q.sample_trace(1, 5_000_000, 32, path_cap=64)
+    compare_trace(recs, paths, oracle_trace(orc, g, 1, 1, 5_000_000, 32), 64)

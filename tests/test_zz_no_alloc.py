@@ -71,7 +71,7 @@ def test_static_sampling_calibration_stream(K, orc):
 
 def test_static_sampling_rejects_graphs_beyond_the_array(K):
     import torch
-    # a path of 3.5M vertices needs 70 MB per in-flight sample: more than the array
+    # a path of 3.5M vertices needs 126 MB per in-flight sample: more than the array
     n = 3_500_000
     deg = np.full(n, 2, dtype=np.int64)
     deg[0] = deg[-1] = 1
