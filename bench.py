@@ -45,6 +45,13 @@ WORKLOADS = {
     "rmat20": dict(graph="rmat20", eps=0.01, delta=0.1, seed=1,
                    desc="R-MAT scale 20, edge factor 16, (a,b,c,d)=(0.57,0.19,0.19,0.05), symmetrised, "
                         "no self-loops/duplicates, int32 CSR; eps=0.01 delta=0.1 seed=1"),
+    "rhg20": dict(graph="rhg20", eps=0.01, delta=0.1, seed=1, steps=5, cpu_samples=4800, ref_samples=1600,
+                  desc="random hyperbolic graph, n=2^20, power-law exponent 3, average degree 60 (|E| = 30|V|), "
+                       "seed 20, int32 CSR; eps=0.01 delta=0.1 seed=1"),
+    "grid4096": dict(graph="grid4096", eps=0.01, delta=0.1, seed=1, steps=1, e2e_steps=1, cpu_samples=48,
+                     ref_samples=16,
+                     desc="4096x4096 grid, 10% of the edges deleted (seed 3), largest component, int32 CSR; "
+                          "eps=0.01 delta=0.1 seed=1"),
     "er2000": dict(graph="er2000", eps=0.05, delta=0.1, seed=1,
                    desc="Erdos-Renyi G(n=2000, avg degree 8) seed 1, largest component, int32 CSR; "
                         "eps=0.05 delta=0.1 seed=1"),
@@ -615,7 +622,7 @@ def run_serve(args, local_rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=None, help="timed steps (default: per workload, 20 for rmat20)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default="rmat20", choices=list(WORKLOADS))
@@ -633,12 +640,12 @@ def main():
     ap.add_argument("--divisor", type=int, default=32, help="batched mode: epoch length = omega / divisor")
     ap.add_argument("--graph-epochs", type=int, default=4, help="epochs per CUDA graph (graph_epochs form)")
     ap.add_argument("--frames", type=int, default=8, help="epoch frames in flight (pipelined mode)")
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--slots", type=int, default=0, help="samples in flight (0 = fill the GPU)")
     ap.add_argument("--threads", type=int, default=1024, help="threads per sampling CTA")
-    ap.add_argument("--cpu-samples", type=int, default=48000,
+    ap.add_argument("--cpu-samples", type=int, default=None,
                     help="oracle samples for the CPU baseline (split over host cores)")
-    ap.add_argument("--ref-samples", type=int, default=16000, help="oracle samples per reference step")
+    ap.add_argument("--ref-samples", type=int, default=None, help="oracle samples per reference step")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
     assert args.warmup >= 3 or args.impl == "reference" or os.environ.get("KADABRA_BENCH_ALLOW_SHORT"), \
@@ -648,6 +655,12 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     wl = WORKLOADS[args.workload]
+    # defaults sized so that each workload's run ends within minutes
+    if args.mode in ("batched", "serve") and args.steps is None:
+        args.steps = 2
+    for key, default in (("steps", 20), ("e2e_steps", 3), ("cpu_samples", 48000), ("ref_samples", 16000)):
+        if getattr(args, key) is None:
+            setattr(args, key, wl.get(key, default))
     if args.mode in ("batched", "serve"):
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": f"the {args.mode} mode has no CPU form; the "

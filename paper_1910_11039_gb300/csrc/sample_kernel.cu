@@ -345,6 +345,28 @@ __device__ long long radix_choose(Smem<NT> &sh, int npass, Each each)
     return (long long)sh.prefix;
 }
 
+// Warp 0 picks among cnt <= 32 candidates (sh.cand, 64-bit weights sh.wlo)
+// the one whose interval, in ascending id order, holds r; sh.next_v.
+template <int NT>
+__device__ __forceinline__ void warp_pick64(Smem<NT> &sh, unsigned int cnt, unsigned long long r)
+{
+    if (threadIdx.x >= 32) return;
+    const unsigned int lane = threadIdx.x;
+    const bool have = lane < cnt;
+    const unsigned int id = have ? sh.cand[lane] : 0xffffffffu;
+    const unsigned long long wt = have ? sh.wlo[lane] : 0ULL;
+    unsigned long long pre = 0;
+    for (int j = 0; j < 32; ++j) {
+        const unsigned int idj = __shfl_sync(0xffffffffu, id, j);
+        const unsigned long long wj = __shfl_sync(0xffffffffu, wt, j);
+        if (idj < id) pre += wj;
+    }
+    const bool mine = have && pre <= r && r < pre + wt;
+    const unsigned int m = __ballot_sync(0xffffffffu, mine);
+    const unsigned int pick = m ? __shfl_sync(0xffffffffu, id, __ffs(m) - 1) : 0u;
+    if (lane == 0) sh.next_v = m ? (long long)pick : -1;
+}
+
 // ---- queue of one side ---------------------------------------------------
 
 __device__ __forceinline__ unsigned int qget(const uint32_t *q, long long n, int side, unsigned int i)
@@ -810,22 +832,28 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
         // walk towards s (side 0), then towards t (side 1); draws 2, 3, ...
         unsigned long long k = 2;
         bool walk_ok = w >= 0;
+        unsigned long long ww0 = 0, ww1 = 0;
+        if (walk_ok) load_rec(rec + w, ww0, ww1);
         for (int Z = 0; Z < 2 && walk_ok; ++Z) {
             long long v = w;
             const long long src = Z == 0 ? sh.s : sh.t;
+            unsigned int lz = lvl_of(Z == 0 ? ww0 : ww1);   // level code of v on side Z
             for (;;) {
-                const unsigned int lz = lvl_of(ldcg(&rec[v].w[Z]));
                 if (lz <= 1) break;      // reached the source of side Z
                 const unsigned int target = lz - 1;      // level code of the predecessors
                 const unsigned int P = lz - 2;           // their layer index
-                const long long b = G.begin(v);
-                const long long d = G.end(v) - b;
-                const U64x4 x = sample_draw(a.seed, a.tag, idx, k);
-                ++k;
+                const unsigned long long draw = k++;     // every step owns a draw index
                 if (P == 0) {
-                    // the only vertex one layer closer is the source itself
+                    // the only vertex one layer closer is the source itself:
+                    // no draw is evaluated, nothing is counted, no barrier
                     v = src;
-                } else {
+                    lz = target;
+                    continue;
+                }
+                {
+                    const long long b = G.begin(v);
+                    const long long d = G.end(v) - b;
+                    const U64x4 x = sample_draw(a.seed, a.tag, idx, draw);
                     const unsigned int lsz = P < (unsigned int)kMaxLayers ? sh.lend[Z][P] - sh.lbeg[Z][P] : 0xffffffffu;
                     if (tid == 0) sh.next_v = -1;
                     if (d > 2 * NT && lsz <= (unsigned int)kMeetCap && (unsigned long long)lsz * 8ULL < (unsigned long long)d) {
@@ -852,6 +880,8 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
                         const unsigned long long total = block_sum<NT>(part, sh);
                         if (pc == 1) {
                             if (tid == 0) sh.next_v = sh.cand[0];
+                        } else if (pc > 1 && pc <= 32) {
+                            warp_pick64<NT>(sh, pc, __umul64hi(x.v[0], total));
                         } else if (pc > 1) {
                             if (tid == 0) {
                                 sh.r_lo = __umul64hi(x.v[0], total);
@@ -904,15 +934,46 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
                         if (wt > 0 && ex <= r && r < ex + wt) sh.next_v = u;
                         __syncthreads();
                     } else {
+                        // one pass over the adjacency collects the candidates
+                        // (up to kMeetCap) with their weights; more than that
+                        // falls back to a second, ordered pass
                         walk_scan += (unsigned long long)d;
+                        if (tid == 0) sh.pcnt = 0;
+                        __syncthreads();
                         unsigned long long part = 0;
                         for (long long j = tid; j < d; j += NT) {
                             const long long u = G.col(b + j);
                             const unsigned long long wu = ldcg(&rec[u].w[Z]);
-                            if (lvl_of(wu) == target) part += sig_of(wu);
+                            if (lvl_of(wu) == target) {
+                                part += sig_of(wu);
+                                const unsigned int p = atomicAdd(&sh.pcnt, 1u);
+                                if (p < (unsigned int)kMeetCap) {
+                                    sh.cand[p] = (unsigned int)u;
+                                    sh.wlo[p] = sig_of(wu);
+                                }
+                            }
                         }
                         const unsigned long long total = block_sum<NT>(part, sh);
                         const unsigned long long r = __umul64hi(x.v[0], total);
+                        const unsigned int pc = sh.pcnt;
+                        if (pc <= (unsigned int)kMeetCap) {
+                            if (pc == 1) {
+                                if (tid == 0) sh.next_v = sh.cand[0];
+                            } else if (pc <= 32) {
+                                warp_pick64<NT>(sh, pc, r);
+                            } else {
+                                if (tid == 0) {
+                                    sh.r_lo = r;
+                                    sh.r_hi = 0;
+                                }
+                                __syncthreads();
+                                const long long c = radix_choose<NT>(sh, npass, [&](auto &&add) {
+                                    for (unsigned int i = tid; i < pc; i += NT) add(sh.cand[i], sh.wlo[i], 0ULL);
+                                });
+                                if (tid == 0) sh.next_v = c;
+                            }
+                            __syncthreads();
+                        } else {
                         unsigned long long carry = 0;
                         if (tid == 0) sh.found = 0;
                         __syncthreads();
@@ -935,6 +996,7 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
                             __syncthreads();
                             if (sh.found) break;
                         }
+                        }
                     }
                     v = sh.next_v;
                     if (v < 0 || v >= n || lvl_of(ldcg(&rec[v].w[Z])) != target) {
@@ -944,6 +1006,7 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
                         __syncthreads();
                         break;
                     }
+                    lz = target;
                 }
                 if (tid == 0 && v != src) {
                     sh.err |= sink.add(v);

@@ -27,7 +27,7 @@ import numpy as np
 
 __all__ = [
     "Graph", "csr_from_edges", "largest_component", "er_graph", "rmat_graph",
-    "grid_graph", "rgg_graph", "path_graph", "star_graph", "cycle_graph",
+    "grid_graph", "rgg_graph", "rhg_graph", "path_graph", "star_graph", "cycle_graph",
     "complete_graph", "full_grid_graph", "config_graph", "CONFIGS",
     "graph_from_spec", "batched_specs", "SERVING_POOL", "serving_requests",
 ]
@@ -181,6 +181,78 @@ def rgg_graph(n: int, avg_degree: float, seed: int, lcc: bool = False) -> Graph:
     return largest_component(g) if lcc else g
 
 
+def rhg_graph(n: int, avg_degree: float, gamma: float = 3.0, seed: int = 0, lcc: bool = False,
+              bands: int = 32) -> Graph:
+    """Random hyperbolic graph, threshold model (Krioukov et al. 2010): n
+    points in a hyperbolic disk of radius R with uniform angles and radial
+    density alpha sinh(alpha r) / (cosh(alpha R) - 1), alpha = (gamma - 1) / 2
+    (degree power law with exponent gamma); two points are adjacent when
+    their hyperbolic distance is at most R.  R = 2 ln(2 xi^2 n / (pi k)) with
+    xi = alpha / (alpha - 1/2) gives expected average degree k (Gugelmann,
+    Panagiotou and Peter 2012).
+    Neighbours are found band by band (points sorted by angle within radial
+    bands of equal size): a point at radius r can only reach a band whose
+    lowest radius is b within the angle acos((cosh r cosh b - cosh R) /
+    (sinh r sinh b)); it searches only bands whose largest radius is at least
+    r (the other endpoint of a pair searches the rest), and every candidate
+    pair is confirmed with cosh d = cosh(r1 - r2) + 2 sin^2(dtheta / 2)
+    sinh r1 sinh r2."""
+    rng = np.random.default_rng(seed)
+    alpha = (gamma - 1.0) / 2.0
+    xi = alpha / (alpha - 0.5)
+    R = 2.0 * np.log(2.0 * xi * xi * n / (np.pi * avg_degree))
+    theta = rng.random(n) * (2.0 * np.pi)
+    u = rng.random(n)
+    r = np.arccosh(1.0 + u * (np.cosh(alpha * R) - 1.0)) / alpha
+    cosh_R = np.cosh(R)
+    ch, sh = np.cosh(r), np.sinh(r)
+    by_r = np.argsort(r, kind="stable")
+    srcs, dsts = [], []
+    for band in np.array_split(by_r, bands):
+        if band.size == 0:
+            continue
+        b = float(r[band].min())
+        top = float(r[band].max())
+        order = band[np.argsort(theta[band], kind="stable")]
+        th = theta[order]
+        ext_th = np.concatenate([th - 2 * np.pi, th, th + 2 * np.pi])
+        ext_id = np.concatenate([order, order, order])
+        # widest angle at which each point can reach this band
+        if b <= 0.0:
+            dmax = np.full(n, np.pi)
+        else:
+            arg = (ch * np.cosh(b) - cosh_R) / (sh * np.sinh(b))
+            dmax = np.where(arg <= -1.0, np.pi, np.arccos(np.clip(arg, -1.0, 1.0)))
+            dmax = np.where(arg > 1.0, -1.0, dmax)
+        # a pair is searched from its endpoint of smaller radius (the other
+        # endpoint's band), so only points not above this band search it
+        searchers = np.nonzero(r <= top)[0]
+        for lo_p in range(0, searchers.size, 1 << 16):
+            pts = searchers[lo_p:lo_p + (1 << 16)]
+            d = dmax[pts]
+            ok = d >= 0.0
+            pts, d = pts[ok], d[ok]
+            lo = np.searchsorted(ext_th, theta[pts] - d, side="left")
+            hi = np.searchsorted(ext_th, theta[pts] + d, side="right")
+            cnt = hi - lo
+            if cnt.sum() == 0:
+                continue
+            p_rep = np.repeat(pts, cnt)
+            start = np.repeat(lo - np.concatenate([[0], np.cumsum(cnt)[:-1]]), cnt)
+            q = ext_id[np.arange(cnt.sum()) + start]
+            keep = p_rep != q
+            p_rep, q = p_rep[keep], q[keep]
+            dth = theta[p_rep] - theta[q]
+            coshd = np.cosh(r[p_rep] - r[q]) + 2.0 * np.sin(dth / 2.0) ** 2 * sh[p_rep] * sh[q]
+            adj = coshd <= cosh_R
+            srcs.append(p_rep[adj])
+            dsts.append(q[adj])
+    src = np.concatenate(srcs) if srcs else np.zeros(0, dtype=np.int64)
+    dst = np.concatenate(dsts) if dsts else np.zeros(0, dtype=np.int64)
+    g = csr_from_edges(n, src, dst, name=f"rhg{n}")
+    return largest_component(g) if lcc else g
+
+
 def _from_pairs(n, pairs, name):
     pairs = np.asarray(pairs, dtype=np.int64).reshape(-1, 2)
     return csr_from_edges(n, pairs[:, 0], pairs[:, 1], name=name)
@@ -235,6 +307,9 @@ CONFIGS = {
     "grid64": dict(kind="grid", k=64, delete_p=0.1, seed=3, lcc=True),
     "grid256": dict(kind="grid", k=256, delete_p=0.1, seed=3, lcc=True),
     "rgg5k": dict(kind="rgg", n=5000, avg_degree=10, seed=7, lcc=True),
+    # random hyperbolic graphs, power-law exponent 3, |E| = 30 |V| (average degree 60)
+    "rhg20": dict(kind="rhg", n=1 << 20, avg_degree=60, gamma=3.0, seed=20),
+    "rhg4k": dict(kind="rhg", n=4096, avg_degree=60, gamma=3.0, seed=12),
 }
 
 
@@ -250,6 +325,8 @@ def graph_from_spec(spec: dict, name: str = "") -> Graph:
         g = grid_graph(**cfg)
     elif kind == "rgg":
         g = rgg_graph(**cfg)
+    elif kind == "rhg":
+        g = rhg_graph(**cfg)
     else:
         raise KeyError(kind)
     return dataclasses.replace(g, name=name or g.name)

@@ -55,6 +55,7 @@ GRAPHS = {
     "path": lambda: I.path_graph(300),
     "edge": lambda: I.path_graph(2),
     "layered": lambda: layered_graph(700),              # meeting sets larger than shared memory
+    "rhg4k": lambda: I.config_graph("rhg4k"),           # random hyperbolic, power-law exponent 3
 }
 
 
@@ -111,7 +112,7 @@ def test_calibration_matches_oracle(K, orc, name, rule):
 
 @pytest.mark.parametrize("name,E,epochs", [
     ("er2000", 97, 5), ("rmat12", 500, 3), ("rmat14", 1000, 2), ("grid64", 300, 3),
-    ("rgg5k", 256, 2), ("fullgrid64", 200, 2), ("star", 64, 3), ("layered", 400, 2),
+    ("rgg5k", 256, 2), ("fullgrid64", 200, 2), ("star", 64, 3), ("layered", 400, 2), ("rhg4k", 300, 2),
 ])
 def test_epoch_counters_bit_exact(K, orc, name, E, epochs):
     g = GRAPHS[name]()
@@ -131,7 +132,7 @@ def test_epoch_counters_bit_exact(K, orc, name, E, epochs):
 
 @pytest.mark.parametrize("name,eps,E", [
     ("er2000", 0.05, 100), ("grid64", 0.05, 250), ("rmat14", 0.03, 500), ("rgg5k", 0.05, 300),
-    ("star", 0.05, 50), ("path", 0.05, 200),
+    ("star", 0.05, 50), ("path", 0.05, 200), ("rhg4k", 0.03, 256),
 ])
 @pytest.mark.parametrize("rule", [0, 1])
 def test_full_run_matches_oracle(K, orc, name, eps, E, rule):
@@ -173,7 +174,7 @@ def test_run_loop_matches_manual_epochs(K, orc):
 @pytest.mark.parametrize("name,eps,E,frames", [
     ("er2000", 0.05, 100, 8), ("er2000", 0.05, 7, 1), ("grid64", 0.05, 250, 2), ("rmat14", 0.03, 500, 8),
     ("rmat14", 0.03, 64, 3), ("rgg5k", 0.05, 300, 16), ("star", 0.05, 50, 4), ("path", 0.05, 200, 8),
-    ("fullgrid64", 0.05, 150, 4),
+    ("fullgrid64", 0.05, 150, 4), ("rhg4k", 0.03, 128, 8),
 ])
 def test_pipelined_run_matches_oracle(K, orc, name, eps, E, frames):
     g = GRAPHS[name]()

@@ -50,3 +50,46 @@ def test_small_families():
         assert_valid_csr(g)
     assert I.cycle_graph(7).nnz == 14 and I.complete_graph(5).nnz == 20
     assert I.full_grid_graph(3, 4).nnz == 2 * (3 * 3 + 2 * 4)
+
+
+def _rhg_brute(n, k, seed):
+    """Adjacency of the random hyperbolic graph by the definition: every pair's
+    hyperbolic distance against R (same draws as the generator)."""
+    rng = np.random.default_rng(seed)
+    alpha, xi = 1.0, 2.0
+    R = 2 * np.log(2 * xi * xi * n / (np.pi * k))
+    theta = rng.random(n) * 2 * np.pi
+    u = rng.random(n)
+    r = np.arccosh(1 + u * (np.cosh(alpha * R) - 1)) / alpha
+    # hyperbolic law of cosines
+    coshd = (np.cosh(r[:, None]) * np.cosh(r[None, :])
+             - np.sinh(r[:, None]) * np.sinh(r[None, :]) * np.cos(theta[:, None] - theta[None, :]))
+    adj = coshd <= np.cosh(R)
+    np.fill_diagonal(adj, False)
+    return adj, coshd, np.cosh(R)
+
+
+@pytest.mark.parametrize("n,k,seed", [(500, 20, 3), (1200, 60, 5)])
+def test_rhg_matches_the_definition(n, k, seed):
+    g = I.rhg_graph(n, k, seed=seed)
+    adj, coshd, coshR = _rhg_brute(n, k, seed)
+    got = np.zeros((n, n), dtype=bool)
+    rows = np.repeat(np.arange(n), np.diff(g.offsets))
+    got[rows, g.cols] = True
+    # pairs within rounding of the threshold may go either way between the
+    # two distance formulas; every other pair must agree
+    clear = np.abs(coshd - coshR) > 1e-9 * coshR
+    assert np.array_equal(got[clear], adj[clear])
+    assert (got != adj).sum() <= 2
+
+
+def test_rhg_degree_law():
+    g = I.rhg_graph(1 << 14, 60, seed=1)
+    deg = np.diff(g.offsets)
+    assert abs(deg.mean() - 60) < 0.15 * 60
+    # power law with exponent 3: the largest degree is far above the mean and
+    # the share of vertices of degree >= d falls roughly as d^-2
+    assert deg.max() > 20 * deg.mean()
+    f1 = (deg >= 120).mean()
+    f2 = (deg >= 480).mean()
+    assert 8 < f1 / max(f2, 1e-9) < 32
