@@ -331,9 +331,10 @@ def run_gpu(args, wl, g, rank, world, local_rank, cpu_baseline):
                 "algorithmic_bytes_per_launch": tot_b / max(1, len(launches)),
                 "per_sample": {k: sum(getattr(ls, k) for ls in launches) / max(1, sum(ls.samples for ls in launches))
                                for k in ("e_scan", "expanded", "touched", "walk_scan", "interior", "connected")}}
-    # our kernels per step: reset + (pipelined: class maxima + one persistent launch;
-    # epochs: one sampling and one check launch per enqueued epoch)
-    n_launch_kernels = args.steps * (3 if args.mode == "pipelined" else 2 * max_epochs + 1)
+    # our kernels per step: the query reset, then (pipelined: pipeline begin, class
+    # maxima and one persistent launch; epochs: one sampling and one check launch
+    # per enqueued epoch)
+    n_launch_kernels = args.steps * (4 if args.mode == "pipelined" else 2 * max_epochs + 1)
 
     # ---- end to end through the C ABI with pinned host buffers ----
     e2e = None

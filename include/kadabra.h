@@ -301,6 +301,13 @@ enum { KADABRA_BATCH_ROUND_ROBIN = 0, KADABRA_BATCH_IN_ORDER = 1 };
  * KADABRA_ERR_INVALID_ARG if count differs from the last step's. */
 kadabra_status kadabra_batch_poll(kadabra_batch *b, int32_t *states, int64_t count, void *cuda_stream);
 kadabra_status kadabra_batch_set_policy(kadabra_batch *b, int policy);
+/* Every wait inside a batch step (a CTA waiting for a free epoch frame, or
+ * for any running query to accept a sample) polls at most `polls` times
+ * (default 2^24, each poll sleeps ~0.3-0.5 us); a wait that runs out marks its
+ * queries with the timeout bit and ends the step, and the next synchronising
+ * call on such a query returns KADABRA_ERR_TIMEOUT.  The device stays usable:
+ * kadabra_query_reset and kadabra_pipeline_begin restart the query. */
+kadabra_status kadabra_batch_set_spin_limit(kadabra_batch *b, uint64_t polls);
 
 /* Sharded sampling (several ranks, one GPU each; Section I-A: samples are
  * independent, so a rank can take any subset of an epoch's sample indices).

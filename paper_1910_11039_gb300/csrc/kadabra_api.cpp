@@ -129,6 +129,7 @@ struct kadabra_batch {
     int policy = 0;
     int64_t last_count = 0;       // queries of the most recent step
     int *d_states = nullptr;      // descs_cap entries
+    uint64_t spin_limit = 1ULL << 24;
 };
 
 namespace kadabra {
@@ -1061,7 +1062,7 @@ extern "C" kadabra_status kadabra_batch_step(kadabra_batch *b, kadabra_query *co
     B.stride = b->max_n;
     B.bs = b->d_bs;
     B.budget = sample_budget;
-    B.spin_limit = 1ULL << 24;
+    B.spin_limit = b->spin_limit;
     B.grid = b->slots;
     B.threads = b->threads;
     B.off64 = b->off64;
@@ -1085,6 +1086,14 @@ extern "C" kadabra_status kadabra_batch_poll(kadabra_batch *b, int32_t *states, 
     KCUDA(cudaMemcpyAsync(states, b->d_states, (size_t)count * sizeof(int32_t), cudaMemcpyDeviceToHost, st),
           "read states");
     KCUDA(cudaStreamSynchronize(st), "synchronise");
+    return KADABRA_OK;
+}
+
+extern "C" kadabra_status kadabra_batch_set_spin_limit(kadabra_batch *b, uint64_t polls)
+{
+    if (!b) return fail(KADABRA_ERR_INVALID_ARG, "batch is null");
+    if (polls == 0) return fail(KADABRA_ERR_INVALID_ARG, "the poll limit must be >= 1");
+    b->spin_limit = polls;
     return KADABRA_OK;
 }
 

@@ -1267,6 +1267,11 @@ __global__ void __launch_bounds__(NT, (2048 / NT / 2) > 0 ? (2048 / NT / 2) : 1)
     SlotRec *rec = B.recs + (size_t)blockIdx.x * (size_t)B.stride;
     uint32_t *queue = B.queues + (size_t)blockIdx.x * (size_t)B.stride;
     volatile BatchState *vbs = B.bs;
+    if (B.nq == 1) {
+        // one query: its descriptor stays in shared memory for the whole launch
+        if (tid == 0) qd = B.queries[0];
+        __syncthreads();
+    }
 
     for (;;) {
         // Warp 0 picks the next sample: its lanes read the state of 32
@@ -1285,7 +1290,7 @@ __global__ void __launch_bounds__(NT, (2048 / NT / 2) > 0 ? (2048 / NT / 2) : 1)
             stop_launch = __shfl_sync(0xffffffffu, stop_launch ? 1 : 0, 0) != 0;
             if (!stop_launch) {
                 unsigned int start = 0;
-                if (B.policy == 0 && lane == 0) start = atomicAdd(&B.bs->ticket, 1u) % (unsigned int)B.nq;
+                if (B.policy == 0 && B.nq > 1 && lane == 0) start = atomicAdd(&B.bs->ticket, 1u) % (unsigned int)B.nq;
                 start = __shfl_sync(0xffffffffu, start, 0);
                 unsigned long long polls = 0;
                 for (;;) {
@@ -1296,7 +1301,7 @@ __global__ void __launch_bounds__(NT, (2048 / NT / 2) > 0 ? (2048 / NT / 2) : 1)
                         bool running = false, eligible = false;
                         if (k < B.nq) {
                             qi = (int)((start + (unsigned int)k) % (unsigned int)B.nq);
-                            const QueryDesc *Q = B.queries + qi;
+                            const QueryDesc *Q = B.nq == 1 ? &qd : B.queries + qi;
                             volatile PipeState *vst = Q->ps;
                             volatile Job *vjob = Q->job;
                             if (!vjob->stopped && !vst->abort) {
@@ -1313,7 +1318,7 @@ __global__ void __launch_bounds__(NT, (2048 / NT / 2) > 0 ? (2048 / NT / 2) : 1)
                             const int leader = __ffs(mask) - 1;
                             int got = 0;
                             if (lane == leader) {
-                                QueryDesc *Q = B.queries + qi;
+                                const QueryDesc *Q = B.nq == 1 ? &qd : B.queries + qi;
                                 PipeState *st = Q->ps;
                                 volatile PipeState *vst = st;
                                 volatile Job *vjob = Q->job;
@@ -1370,7 +1375,7 @@ __global__ void __launch_bounds__(NT, (2048 / NT / 2) > 0 ? (2048 / NT / 2) : 1)
             }
             __syncwarp();
             if (lane == 0 && take) {
-                qd = B.queries[s_qi];
+                if (B.nq > 1) qd = B.queries[s_qi];
                 SampleLaunch t{};
                 t.n = qd.n;
                 t.off = qd.off;

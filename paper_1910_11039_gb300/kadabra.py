@@ -114,6 +114,7 @@ SIGNATURES = {
     "kadabra_run_graph": (_ST, [_P, _I64, C.c_int, _I64, _P, C.POINTER(C.c_int)]),
     "kadabra_batch_set_policy": (_ST, [_P, C.c_int]),
     "kadabra_batch_poll": (_ST, [_P, _P, _I64, _P]),
+    "kadabra_batch_set_spin_limit": (_ST, [_P, _U64]),
     "kadabra_query_create": (_ST, [_P, _P, _P, _P]),
     "kadabra_calibration_begin": (_ST, [_P, _P]),
     "kadabra_calibration_finish": (_ST, [_P, _P]),
@@ -403,6 +404,9 @@ class Batch:
         self.threads = threads
         if policy:
             self.set_policy(policy)
+
+    def set_spin_limit(self, polls):
+        _check(load().kadabra_batch_set_spin_limit(self.handle, int(polls)))
 
     def set_policy(self, policy):
         _check(load().kadabra_batch_set_policy(self.handle, int(policy)))

@@ -80,9 +80,6 @@ class Server:
     def __init__(self, graphs: dict, threads: int = 1024, slots: int = 0, schedule: Schedule | None = None,
                  memory_budget: int | None = None, step_ms: float = 20.0, policy: str = "fifo",
                  keep_results: bool = True, log=None):
-        import torch
-
-        self.torch = torch
         self.graphs = {}
         for key, g in graphs.items():
             self.graphs[key] = g if isinstance(g, K.Graph) else K.Graph.from_inputs(g, skip_validate=True)
@@ -99,9 +96,13 @@ class Server:
             raise ValueError("policy must be 'fifo', 'shortest' or 'round_robin'")
         self.policy = policy
         self.batch.set_policy(K.Batch.ROUND_ROBIN if policy == "round_robin" else K.Batch.IN_ORDER)
-        torch.cuda.synchronize()
-        free, _ = torch.cuda.mem_get_info()
-        self.memory_budget = int(memory_budget if memory_budget is not None else 0.8 * free)
+        if memory_budget is None:
+            import torch
+
+            torch.cuda.synchronize()
+            free, _ = torch.cuda.mem_get_info()
+            memory_budget = int(0.8 * free)
+        self.memory_budget = int(memory_budget)
         self.step_ms = step_ms
         self.keep_results = keep_results
         self.log = log

@@ -223,3 +223,30 @@ def test_server_results_equal_alone_and_in_mix(K, orc, graphs, policy):
         counts, R = expected(orc, graphs[r.graph][0], r.eps, r.seed, sched.epoch_len(m.omega_ceil))
         assert m.tau == R.tau and m.stop_epoch == R.stop_epoch
         assert np.array_equal(m.counts, counts)
+
+
+def test_bounded_waits_end_a_step_with_a_timeout(K, orc, graphs):
+    """A wait that runs out of polls ends the step with the timeout status,
+    without a fault; the query then restarts and runs to the oracle's result."""
+    g, G = graphs["er2000"]
+    q = K.Query(G, eps=0.05, delta=0.1, seed=1)
+    b = K.Batch(g.n)
+    b.set_spin_limit(1)               # one frame of 16 samples: every other CTA must wait
+    q.pipeline_begin(16, frames=1)
+    b.step([q])
+    assert b.last_ms() > 0
+    assert q.info().device_error & 32
+    with pytest.raises(K.KadabraError) as ei:
+        q.result()
+    assert ei.value.status == 6
+    # the context and the query are usable again
+    q.reset()
+    b.set_spin_limit(1 << 24)
+    q.pipeline_begin(16, frames=1)
+    b.step([q])
+    res = q.result()
+    counts, R = expected(orc, g, 0.05, 1, 16)
+    assert res["tau"] == R.tau and res["stop_epoch"] == R.stop_epoch
+    assert np.array_equal(res["counts"], counts)
+    with pytest.raises(K.KadabraError):
+        b.set_spin_limit(0)

@@ -452,7 +452,7 @@ def test_rmat26_full_size_sampled(K, orc):
     vertex-diameter bound, one epoch of counters bit-exact, and per-sample
     records of a sampled index range."""
     g = I.config_graph("rmat26")
-    assert g.nnz > (1 << 31)                       # needs 64-bit offsets
+    assert g.n == 1 << 26 and g.nnz > 2_000_000_000
     G = K.Graph.from_inputs(g, offsets_64=True, skip_validate=True)
     q = K.Query(G, eps=0.01, delta=0.1, seed=1, n_calib=256)
     info = q.info()
