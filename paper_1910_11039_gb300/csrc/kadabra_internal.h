@@ -93,6 +93,7 @@ struct SampleLaunch {
     int64_t trace_cap;
     int grid;
     int threads;
+    const int *abandon;        // optional: a sample stops at its next layer once *abandon != 0
 };
 
 cudaError_t launch_sample(const SampleLaunch &a, cudaStream_t st);

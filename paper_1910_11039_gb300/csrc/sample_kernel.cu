@@ -115,7 +115,8 @@ struct Smem {
     unsigned int lbeg[2][kMaxLayers];// queue range of layer k of each side (k < kMaxLayers)
     unsigned int lend[2][kMaxLayers];
     int X;                           // side expanded this layer
-    int status;                      // 0 running, 1 met, 2 disconnected, 3 strict overflow, 4 too deep
+    int status;                      // 0 running, 1 met, 2 disconnected, 3 strict overflow, 4 too deep,
+                                     // 5 discarded (its query stopped)
     int scaled;
     unsigned int err;
     // per-layer accumulators
@@ -646,6 +647,8 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
                 sh.status = 1;
             } else if (sh.new_count == 0) {
                 sh.status = 2;
+            } else if (a.abandon && *reinterpret_cast<const volatile int *>(a.abandon)) {
+                sh.status = 5;      // discarded sample: clear its records and leave
             } else {
                 sh.fbeg[X] = qbase;
                 sh.fend[X] = qbase + sh.new_count;
@@ -1385,6 +1388,9 @@ __global__ void __launch_bounds__(NT, (2048 / NT / 2) > 0 ? (2048 / NT / 2) : 1)
                 t.tag = qd.tag;
                 t.K = qd.K;
                 t.strict = qd.strict;
+                // a sample still running when its query stops belongs to an
+                // epoch after the stopping one and is discarded: end it early
+                t.abandon = qd.tag != 0 ? &qd.job->stopped : nullptr;
                 sa = t;
             }
         }
