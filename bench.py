@@ -52,6 +52,9 @@ WORKLOADS = {
                      ref_samples=16,
                      desc="4096x4096 grid, 10% of the edges deleted (seed 3), largest component, int32 CSR; "
                           "eps=0.01 delta=0.1 seed=1"),
+    "grid512": dict(graph="grid512", eps=0.05, delta=0.1, seed=1, steps=5, cpu_samples=1600, ref_samples=800,
+                    desc="512x512 grid, 10% of the edges deleted (seed 3), largest component, int32 CSR; "
+                         "eps=0.05 delta=0.1 seed=1 (small high-diameter case for profiles)"),
     "er2000": dict(graph="er2000", eps=0.05, delta=0.1, seed=1,
                    desc="Erdos-Renyi G(n=2000, avg degree 8) seed 1, largest component, int32 CSR; "
                         "eps=0.05 delta=0.1 seed=1"),

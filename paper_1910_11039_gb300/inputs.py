@@ -306,6 +306,7 @@ CONFIGS = {
     "rmat16": dict(kind="rmat", scale=16, edge_factor=16, seed=16),
     "grid64": dict(kind="grid", k=64, delete_p=0.1, seed=3, lcc=True),
     "grid256": dict(kind="grid", k=256, delete_p=0.1, seed=3, lcc=True),
+    "grid512": dict(kind="grid", k=512, delete_p=0.1, seed=3, lcc=True),
     "rgg5k": dict(kind="rgg", n=5000, avg_degree=10, seed=7, lcc=True),
     # random hyperbolic graphs, power-law exponent 3, |E| = 30 |V| (average degree 60)
     "rhg20": dict(kind="rhg", n=1 << 20, avg_degree=60, gamma=3.0, seed=20),

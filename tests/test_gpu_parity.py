@@ -466,3 +466,32 @@ def test_rmat26_full_size_sampled(K, orc):
     assert q.info().e_scan == st.e_scan
     recs, paths = q.sample_trace(1, 5_000_000, 32, path_cap=64)
     compare_trace(recs, paths, oracle_trace(orc, g, 1, 1, 5_000_000, 32), 64)
+
+
+@pytest.mark.slow
+def test_batched_mix_members_match_oracle(K, orc):
+    """Members of the 64-graph mix (R-MAT scale 12 members and the smallest
+    random geometric graph) run together in one persistent launch with the
+    schedule the autotuner picks for the mix: the R-MAT members bit-exact
+    against full oracle runs, the random geometric member by sampled
+    per-sample records."""
+    from paper_1910_11039_gb300.autotune import Schedule, run_mix
+    specs = I.batched_specs()
+    idx = [7, 46, 47, 51]
+    assert all(specs[i]["kind"] == "rmat" and specs[i]["scale"] == 12 for i in idx)
+    gs = [I.graph_from_spec(specs[i], f"mix{i}") for i in idx]
+    rgg = I.graph_from_spec(specs[60], "mix60")
+    Gs = [K.Graph.from_inputs(g) for g in gs] + [K.Graph.from_inputs(rgg)]
+    seeds = [1000 + i for i in idx] + [1060]
+    Qs = [K.Query(G, eps=0.02, delta=0.1, seed=s) for G, s in zip(Gs, seeds)]
+    sched = Schedule(threads=256, divisor=128, frames=4)
+    b = K.Batch(rgg.n, threads=256)
+    r = run_mix(b, Qs, sched)
+    assert all(r["stopped"])
+    for q, g, s, E in zip(Qs[:4], gs, seeds, r["epoch_lens"]):
+        counts, cal, LL, LU, R = orc.kadabra(g, 0.02, 0.1, seed=s, epoch_len=E)
+        res = q.result()
+        assert res["tau"] == R.tau and res["stop_epoch"] == R.stop_epoch
+        assert np.array_equal(res["counts"], counts)
+    recs, paths = Qs[4].sample_trace(1, 12345, 8, path_cap=4000)
+    compare_trace(recs, paths, oracle_trace(orc, rgg, 1060, 1, 12345, 8), 4000)
