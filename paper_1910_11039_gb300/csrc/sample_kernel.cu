@@ -55,6 +55,7 @@ namespace {
 constexpr int kMeetCap = 512;      // candidates kept in shared memory (meeting set, predecessors)
 constexpr int kBuckets = 256;      // radix-select digit width: 8 bits
 constexpr int kMaxLayers = 64;     // BFS layers whose queue ranges are remembered for the walk
+constexpr int kPathCap = 1024;     // path vertices buffered in shared memory before a flush
 #ifndef KADABRA_UNROLL
 #define KADABRA_UNROLL 2
 #endif
@@ -136,6 +137,15 @@ struct Smem {
     long long next_v;
     int found;
     unsigned int cur;                // work item taken by this CTA
+    // back-walk: vertices found so far (flushed to the sink by warp 0) and
+    // the state handed between warp 0's steps and the whole CTA's steps
+    unsigned int path[kPathCap];
+    unsigned int plen;               // entries in path[]
+    unsigned int pflushed;           // entries flushed before path[0]
+    long long wv;
+    unsigned int wl;
+    int wstate;
+    unsigned long long wk;
     unsigned long long tmp[NT / 32];
     unsigned long long tmp2[NT / 32];
     unsigned int cand[kMeetCap];     // candidate ids (meeting set or predecessors)
@@ -418,6 +428,29 @@ struct CountSink {
         return 0u;
     }
 };
+
+// Warp 0 hands the buffered path vertices path[0, cnt) to the sink (counter
+// increments, or one log reservation for all of them); returns error bits.
+__device__ __forceinline__ unsigned int sink_flush(const CountSink &sink, const unsigned int *path, unsigned int cnt)
+{
+    const unsigned int lane = threadIdx.x & 31;
+    unsigned int err = 0;
+    if (sink.counts) {
+        for (unsigned int i = lane; i < cnt; i += 32) {
+            const unsigned int old = atomicAdd(&sink.counts[path[i]], 1u);
+            if (old == 0xffffffffu) err |= kErrCounterOverflow;
+        }
+    } else if (sink.log && cnt) {
+        unsigned int p0 = 0;
+        if (lane == 0) p0 = atomicAdd(sink.len, cnt);
+        p0 = __shfl_sync(0xffffffffu, p0, 0);
+        for (unsigned int i = lane; i < cnt; i += 32) {
+            if (p0 + i >= sink.cap) err |= kErrLogOverflow;
+            else __stcg(sink.log + p0 + i, path[i]);
+        }
+    }
+    return __reduce_or_sync(0xffffffffu, err);
+}
 
 struct LocalStats {
     unsigned long long samples, connected, e_scan, expanded, touched, interior, walk_scan, scaled;
@@ -824,11 +857,11 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
 
         const long long w = sh.chosen;
         if (tid == 0 && a.trace) t_sel = global_ns();
-        if (tid == 0 && w >= 0) {
-            if (w != sh.s && w != sh.t) {
-                sh.err |= sink.add(w);
-                if (a.trace_path && (long long)path_len < a.trace_cap)
-                    a.trace_path[trace_i * a.trace_cap + path_len] = (int32_t)w;
+        if (tid == 0) {
+            sh.plen = 0;
+            sh.pflushed = 0;
+            if (w >= 0 && w != sh.s && w != sh.t) {
+                sh.path[sh.plen++] = (unsigned int)w;
                 ++path_len;
             }
         }
@@ -842,17 +875,99 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
             const long long src = Z == 0 ? sh.s : sh.t;
             unsigned int lz = lvl_of(Z == 0 ? ww0 : ww1);   // level code of v on side Z
             for (;;) {
-                if (lz <= 1) break;      // reached the source of side Z
-                const unsigned int target = lz - 1;      // level code of the predecessors
-                const unsigned int P = lz - 2;           // their layer index
-                const unsigned long long draw = k++;     // every step owns a draw index
-                if (P == 0) {
-                    // the only vertex one layer closer is the source itself:
-                    // no draw is evaluated, nothing is counted, no barrier
-                    v = src;
-                    lz = target;
-                    continue;
+                // Warp 0 alone takes every step from a vertex of degree <= 32
+                // (lanes hold its neighbours) and every step whose predecessor
+                // is the side's source, without block barriers; the CTA joins
+                // for a step from a larger vertex.  Every step owns one draw
+                // index, in path order.
+                if (tid < 32) {
+                    long long vv = v;
+                    unsigned int ll = lz;
+                    unsigned long long kk = k;
+                    int state = 0;        // 0: a large step at vv, 1: source reached, 2: broken invariant
+                    unsigned long long scan = 0;
+                    for (;;) {
+                        if (ll <= 1) {
+                            state = 1;
+                            break;
+                        }
+                        const unsigned int tg = ll - 1;
+                        if (ll == 2) {
+                            vv = src;
+                            ll = tg;
+                            ++kk;
+                            continue;
+                        }
+                        const long long bb = G.begin(vv);
+                        const long long dd = G.end(vv) - bb;
+                        if (dd > 32) break;
+                        const U64x4 xx = sample_draw(a.seed, a.tag, idx, kk);
+                        ++kk;
+                        long long u = -1;
+                        unsigned long long wt = 0;
+                        if (tid < dd) {
+                            u = G.col(bb + tid);
+                            const unsigned long long wu = ldcg(&rec[u].w[Z]);
+                            if (lvl_of(wu) == tg) wt = sig_of(wu);
+                        }
+                        unsigned long long incl = wt;
+#pragma unroll
+                        for (int o = 1; o < 32; o <<= 1) {
+                            const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
+                            if (tid >= o) incl += y;
+                        }
+                        const unsigned long long total = __shfl_sync(0xffffffffu, incl, 31);
+                        const unsigned long long ex = incl - wt;
+                        const unsigned long long r = __umul64hi(xx.v[0], total);
+                        const unsigned int m = __ballot_sync(0xffffffffu, wt > 0 && ex <= r && r < ex + wt);
+                        scan += (unsigned long long)dd;
+                        if (!m) {
+                            state = 2;
+                            break;
+                        }
+                        vv = __shfl_sync(0xffffffffu, u, __ffs(m) - 1);
+                        ll = tg;
+                        if (tid == 0) sh.path[sh.plen++] = (unsigned int)vv;
+                        __syncwarp();
+                        if (sh.plen >= (unsigned int)kPathCap) {
+                            const unsigned int fe = sink_flush(sink, sh.path, sh.plen);
+                            if (tid == 0) sh.err |= fe;
+                            __syncwarp();
+                            if (tid == 0) {
+                                if (a.trace_path)
+                                    for (unsigned int i = 0; i < sh.plen; ++i)
+                                        if ((long long)(sh.pflushed + i) < a.trace_cap)
+                                            a.trace_path[trace_i * a.trace_cap + sh.pflushed + i] = (int32_t)sh.path[i];
+                                sh.pflushed += sh.plen;
+                                sh.plen = 0;
+                            }
+                            __syncwarp();
+                        }
+                    }
+                    if (tid == 0) {
+                        sh.wv = vv;
+                        sh.wl = ll;
+                        sh.wk = kk;
+                        sh.wstate = state;
+                        walk_scan += scan;
+                        path_len = sh.pflushed + sh.plen;
+                    }
                 }
+                __syncthreads();
+                v = sh.wv;
+                lz = sh.wl;
+                k = sh.wk;
+                const int wstate = sh.wstate;
+                __syncthreads();   // sh.w* are rewritten by the next warp phase
+                if (wstate == 1) break;
+                if (wstate == 2) {
+                    if (tid == 0) sh.err |= kErrSelect;
+                    walk_ok = false;
+                    break;
+                }
+                const unsigned int target = lz - 1;      // level code of the predecessors
+                const unsigned int P = lz - 2;           // their layer index (>= 1 here)
+                const unsigned long long draw = k++;
                 {
                     const long long b = G.begin(v);
                     const long long d = G.end(v) - b;
@@ -895,30 +1010,6 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
                                 for (unsigned int i = tid; i < pc; i += NT) add(sh.cand[i], sh.wlo[i], 0ULL);
                             });
                             if (tid == 0) sh.next_v = c;
-                        }
-                        __syncthreads();
-                    } else if (d <= 32) {
-                        // few neighbours: warp 0 alone scans them in adjacency order
-                        walk_scan += (unsigned long long)d;
-                        if (tid < 32) {
-                            long long u = -1;
-                            unsigned long long wt = 0;
-                            if (tid < d) {
-                                u = G.col(b + tid);
-                                const unsigned long long wu = ldcg(&rec[u].w[Z]);
-                                if (lvl_of(wu) == target) wt = sig_of(wu);
-                            }
-                            unsigned long long incl = wt;
-#pragma unroll
-                            for (int o = 1; o < 32; o <<= 1) {
-                                const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
-                                if (tid >= o) incl += y;
-                            }
-                            const unsigned long long total = __shfl_sync(0xffffffffu, incl, 31);
-                            const unsigned long long ex = incl - wt;
-                            const unsigned long long r = __umul64hi(x.v[0], total);
-                            __syncwarp();
-                            if (wt > 0 && ex <= r && r < ex + wt) sh.next_v = u;
                         }
                         __syncthreads();
                     } else if (d <= NT) {
@@ -1011,15 +1102,40 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
                     }
                     lz = target;
                 }
-                if (tid == 0 && v != src) {
-                    sh.err |= sink.add(v);
-                    if (a.trace_path && (long long)path_len < a.trace_cap)
-                        a.trace_path[trace_i * a.trace_cap + path_len] = (int32_t)v;
+                if (tid == 0) {
+                    sh.path[sh.plen++] = (unsigned int)v;    // P >= 1: v is interior
                     ++path_len;
                 }
                 __syncthreads();   // sh.next_v is rewritten by the next step
+                if (sh.plen >= (unsigned int)kPathCap - 1u) {
+                    if (tid < 32) {
+                        const unsigned int fe = sink_flush(sink, sh.path, sh.plen);
+                        if (tid == 0) sh.err |= fe;
+                        __syncwarp();
+                        if (tid == 0) {
+                            if (a.trace_path)
+                                for (unsigned int i = 0; i < sh.plen; ++i)
+                                    if ((long long)(sh.pflushed + i) < a.trace_cap)
+                                        a.trace_path[trace_i * a.trace_cap + sh.pflushed + i] = (int32_t)sh.path[i];
+                            sh.pflushed += sh.plen;
+                            sh.plen = 0;
+                        }
+                    }
+                    __syncthreads();
+                }
             }
         }
+        // the path's interior vertices still buffered go to the sink
+        if (tid < 32) {
+            const unsigned int cnt = sh.plen;
+            const unsigned int fe = sink_flush(sink, sh.path, cnt);
+            if (tid == 0) sh.err |= fe;
+            if (a.trace_path)
+                for (unsigned int i = tid; i < cnt; i += 32)
+                    if ((long long)(sh.pflushed + i) < a.trace_cap)
+                        a.trace_path[trace_i * a.trace_cap + sh.pflushed + i] = (int32_t)sh.path[i];
+        }
+        __syncthreads();
     }
 
     // per-sample bookkeeping (thread 0)
