@@ -886,6 +886,10 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
                     unsigned long long kk = k;
                     int state = 0;        // 0: a large step at vv, 1: source reached, 2: broken invariant
                     unsigned long long scan = 0;
+                    // row of vv, when already known (each lane reads its
+                    // candidate's row with its record, so the chosen
+                    // predecessor's row comes with the choice)
+                    long long bb = -1, be = -1;
                     for (;;) {
                         if (ll <= 1) {
                             state = 1;
@@ -898,16 +902,21 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
                             ++kk;
                             continue;
                         }
-                        const long long bb = G.begin(vv);
-                        const long long dd = G.end(vv) - bb;
+                        if (bb < 0) {
+                            bb = G.begin(vv);
+                            be = G.end(vv);
+                        }
+                        const long long dd = be - bb;
                         if (dd > 32) break;
                         const U64x4 xx = sample_draw(a.seed, a.tag, idx, kk);
                         ++kk;
-                        long long u = -1;
+                        long long u = -1, ub = -1, ue = -1;
                         unsigned long long wt = 0;
                         if (tid < dd) {
                             u = G.col(bb + tid);
                             const unsigned long long wu = ldcg(&rec[u].w[Z]);
+                            ub = G.begin(u);
+                            ue = G.end(u);
                             if (lvl_of(wu) == tg) wt = sig_of(wu);
                         }
                         unsigned long long incl = wt;
@@ -925,7 +934,10 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
                             state = 2;
                             break;
                         }
-                        vv = __shfl_sync(0xffffffffu, u, __ffs(m) - 1);
+                        const int pick = __ffs(m) - 1;
+                        vv = __shfl_sync(0xffffffffu, u, pick);
+                        bb = __shfl_sync(0xffffffffu, ub, pick);
+                        be = __shfl_sync(0xffffffffu, ue, pick);
                         ll = tg;
                         if (tid == 0) sh.path[sh.plen++] = (unsigned int)vv;
                         __syncwarp();
