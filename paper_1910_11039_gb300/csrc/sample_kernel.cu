@@ -60,9 +60,6 @@ constexpr int kPathCap = 1024;     // path vertices buffered in shared memory be
 #define KADABRA_UNROLL 2
 #endif
 constexpr int kUnroll = KADABRA_UNROLL;   // adjacency entries in flight per thread
-#ifndef KADABRA_CLAIM_FIRST
-#define KADABRA_CLAIM_FIRST 0             // 1: claim targets without reading their record first
-#endif
 constexpr unsigned int kNone = 0xffffffffu;
 
 __device__ __forceinline__ unsigned int ldcg(const unsigned int *p) { return __ldcg(p); }
@@ -123,6 +120,7 @@ struct Smem {
     // per-layer accumulators
     unsigned int new_count;
     unsigned int meet_count;
+    int meets;                       // a target of this layer is on the other side: it is the last
     unsigned long long lmax;         // largest path count of the new layer
     unsigned long long ldeg;         // degree sum of the new frontier
     int shv;                         // shift that scales the new layer (> 0: scale)
@@ -493,6 +491,7 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
         sh.expanded = 0;
         sh.meet_count = 0;
         sh.new_count = 0;
+        sh.meets = 0;
         sh.lmax = 0;
         sh.ldeg = 0;
         sh.shv = 0;
@@ -558,31 +557,6 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
                         dw[j] = c.y;
                     }
                 }
-#if KADABRA_CLAIM_FIRST
-                // phase 2+3: claim every target with one compare-and-swap
-                // (the old value gives its level when it was seen before);
-                // claimed targets then read the other side's word
-                unsigned int lx[kUnroll];
-                unsigned int ymask = 0;
-                unsigned int cmask = 0;
-#pragma unroll
-                for (int j = 0; j < kUnroll; ++j) {
-                    lx[j] = 1u;
-                    if (w[j] != kNone) {
-                        const unsigned long long su = sh.u.ex.csig[own[j]];
-                        const unsigned long long old = atomicCAS(&rec[w[j]].w[X], 0ULL, pack(nl, su));
-                        if (old == 0) {
-                            cmask |= 1u << j;
-                            my_max = su > my_max ? su : my_max;
-                        }
-                        lx[j] = old == 0 ? nl : lvl_of(old);
-                    }
-                }
-#pragma unroll
-                for (int j = 0; j < kUnroll; ++j) {
-                    if ((cmask >> j) & 1u) ymask |= (lvl_of(ldcg(&rec[w[j]].w[1 - X])) != 0 ? 1u : 0u) << j;
-                }
-#else
                 // phase 2: (level_s, level_t) of every target, one 8-byte load each
                 unsigned int lx[kUnroll];
                 unsigned int ymask = 0;
@@ -596,12 +570,20 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
                         ymask |= (lvl_of(X ? w0 : w1) != 0 ? 1u : 0u) << j;
                     }
                 }
+                // an unseen target that the other side holds makes this layer
+                // the last one: from then on only meeting vertices need a record
+                // (their path counts); other targets of the last layer are never
+                // read again, so their claims are skipped
+#pragma unroll
+                for (int j = 0; j < kUnroll; ++j)
+                    if (w[j] != kNone && lx[j] == 0 && ((ymask >> j) & 1u)) *(volatile int *)&sh.meets = 1;
+                const bool last = *(volatile int *)&sh.meets != 0;
                 // phase 3: claim unseen targets for the new layer; the claim
                 // stores the level and the first path-count contribution at once
                 unsigned int cmask = 0;
 #pragma unroll
                 for (int j = 0; j < kUnroll; ++j) {
-                    if (w[j] != kNone && lx[j] == 0) {
+                    if (w[j] != kNone && lx[j] == 0 && (!last || ((ymask >> j) & 1u))) {
                         const unsigned long long su = sh.u.ex.csig[own[j]];
                         const unsigned long long old = atomicCAS(&rec[w[j]].w[X], 0ULL, pack(nl, su));
                         if (old == 0) {
@@ -611,7 +593,6 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
                         lx[j] = old == 0 ? nl : lvl_of(old);
                     }
                 }
-#endif
                 // phase 4: path counts of targets in the new layer; the additions
                 // return their old value, so a thread has waited for all of them
                 // before the layer's closing barrier and every count is complete
@@ -700,6 +681,7 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
                     sh.X = Xn;
                     sh.new_count = 0;
                     sh.meet_count = 0;
+                    sh.meets = 0;
                     sh.lmax = 0;
                     sh.ldeg = 0;
                 }
