@@ -64,6 +64,7 @@ struct kadabra_graph {
     // sampling scratch shared by the graph's queries
     kadabra::SlotRec *d_recs = nullptr;
     uint32_t *d_queues = nullptr;
+    uint32_t *d_bits = nullptr;   // reached-bit maps: 2 * ceil(n / 32) words per slot
     int ws_slots = 0;
     int ws_threads = 0;
     int ws_req = 0;               // slots requested when the scratch was sized
@@ -121,6 +122,7 @@ struct kadabra_batch {
     int slots = 0, threads = 0, off64 = 0;
     kadabra::SlotRec *d_recs = nullptr;
     uint32_t *d_queues = nullptr;
+    uint32_t *d_bits = nullptr;
     kadabra::QueryDesc *d_descs = nullptr;
     int64_t descs_cap = 0;
     kadabra::BatchState *d_bs = nullptr;
@@ -339,10 +341,12 @@ static void free_graph_device(kadabra_graph *g)
     cudaFree(g->d_adj);
     cudaFree(g->d_recs);
     cudaFree(g->d_queues);
+    cudaFree(g->d_bits);
     g->d_off = nullptr;
     g->d_adj = nullptr;
     g->d_recs = nullptr;
     g->d_queues = nullptr;
+    g->d_bits = nullptr;
 }
 
 extern "C" kadabra_status kadabra_graph_load(int64_t n, int64_t nnz, const void *offsets, int offsets_is_64,
@@ -458,14 +462,17 @@ static kadabra_status ensure_workspace(kadabra_graph *g, int want_slots, int thr
     KCUDA(kadabra::sample_occupancy(threads, g->off64, &per_sm), "occupancy");
     if (per_sm < 1) per_sm = 1;
     int slots = want_slots > 0 ? want_slots : sms * per_sm;
-    const size_t per_slot = (size_t)g->n * (sizeof(kadabra::SlotRec) + sizeof(uint32_t));
+    const size_t bits_per_slot = 2 * (size_t)kadabra::bit_words(g->n) * sizeof(uint32_t);
+    const size_t per_slot = (size_t)g->n * (sizeof(kadabra::SlotRec) + sizeof(uint32_t)) + bits_per_slot;
     if (g->d_recs && g->ws_threads == threads && (g->ws_slots >= slots || g->ws_req == slots)) return KADABRA_OK;
     const int requested = slots;
     cudaDeviceSynchronize();
     cudaFree(g->d_recs);
     cudaFree(g->d_queues);
+    cudaFree(g->d_bits);
     g->d_recs = nullptr;
     g->d_queues = nullptr;
+    g->d_bits = nullptr;
     g->ws_slots = 0;
     size_t free_b = 0, total_b = 0;
     KCUDA(cudaMemGetInfo(&free_b, &total_b), "cudaMemGetInfo");
@@ -477,11 +484,15 @@ static kadabra_status ensure_workspace(kadabra_graph *g, int want_slots, int thr
     cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&g->d_recs), (size_t)slots * (size_t)g->n * sizeof(kadabra::SlotRec));
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&g->d_queues), (size_t)slots * (size_t)g->n * sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMemset(g->d_recs, 0, (size_t)slots * (size_t)g->n * sizeof(kadabra::SlotRec));
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&g->d_bits), (size_t)slots * bits_per_slot);
+    if (e == cudaSuccess) e = cudaMemset(g->d_bits, 0, (size_t)slots * bits_per_slot);
     if (e != cudaSuccess) {
         cudaFree(g->d_recs);
         cudaFree(g->d_queues);
+        cudaFree(g->d_bits);
         g->d_recs = nullptr;
         g->d_queues = nullptr;
+        g->d_bits = nullptr;
         return cuda_fail(e, "allocate sampling scratch");
     }
     g->ws_slots = slots;
@@ -544,6 +555,7 @@ static kadabra::SampleLaunch base_launch(const kadabra_query *q)
     a.adj = q->g->d_adj;
     a.recs = q->g->d_recs;
     a.queues = q->g->d_queues;
+    a.bits = q->vd <= kadabra::kBitsMaxVD ? q->g->d_bits : nullptr;
     a.seed = q->p.seed;
     a.K = q->K;
     a.strict = (q->p.flags & KADABRA_STRICT_SIGMA) ? 1 : 0;
@@ -913,6 +925,7 @@ static kadabra::QueryDesc make_desc(const kadabra_query *q, kadabra::Counters *l
     d.job = q->d_job;
     d.ps = q->d_pipe;
     d.launch_ctr = launch_ctr;
+    d.use_bits = q->vd <= kadabra::kBitsMaxVD ? 1 : 0;
     d.tag = 1;
     if (q->phase == 1) {
         // calibration samples: one epoch of n_calib samples counted into the
@@ -947,6 +960,7 @@ extern "C" kadabra_status kadabra_run_pipelined(kadabra_query *q, int64_t epoch_
     B.nq = 1;
     B.recs = q->g->d_recs;
     B.queues = q->g->d_queues;
+    B.bits = q->g->d_bits;
     B.stride = q->g->n;
     B.bs = q->d_bs;
     B.budget = 0;
@@ -990,15 +1004,19 @@ extern "C" kadabra_status kadabra_batch_create(int64_t max_n, int32_t slots, int
     b->threads = threads;
     b->off64 = offsets_is_64 ? 1 : 0;
     const size_t nrec = (size_t)slots * (size_t)max_n;
+    const size_t nbits = (size_t)slots * 2 * (size_t)kadabra::bit_words(max_n);
     cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&b->d_recs), nrec * sizeof(kadabra::SlotRec));
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&b->d_queues), nrec * sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMemset(b->d_recs, 0, nrec * sizeof(kadabra::SlotRec));
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&b->d_bits), nbits * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMemset(b->d_bits, 0, nbits * sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&b->d_bs), sizeof(kadabra::BatchState));
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev1);
     if (e != cudaSuccess) {
         cudaFree(b->d_recs);
         cudaFree(b->d_queues);
+        cudaFree(b->d_bits);
         cudaFree(b->d_bs);
         delete b;
         return cuda_fail(e, "allocate batch scratch");
@@ -1013,6 +1031,7 @@ extern "C" kadabra_status kadabra_batch_free(kadabra_batch *b)
     cudaDeviceSynchronize();
     cudaFree(b->d_recs);
     cudaFree(b->d_queues);
+    cudaFree(b->d_bits);
     cudaFree(b->d_descs);
     cudaFree(b->d_states);
     cudaFree(b->d_bs);
@@ -1059,6 +1078,7 @@ extern "C" kadabra_status kadabra_batch_step(kadabra_batch *b, kadabra_query *co
     B.nq = (int)count;
     B.recs = b->d_recs;
     B.queues = b->d_queues;
+    B.bits = b->d_bits;
     B.stride = b->max_n;
     B.bs = b->d_bs;
     B.budget = sample_budget;

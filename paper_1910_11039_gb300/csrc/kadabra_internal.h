@@ -26,6 +26,14 @@ struct alignas(32) SlotRec {
 };
 static_assert(sizeof(SlotRec) == 32, "SlotRec fills a 32-byte sector");
 
+// words of one side's reached-bit map for n vertices
+inline __host__ __device__ long long bit_words(long long n) { return (n + 31) / 32; }
+// The reached-bit maps pay for their upkeep (one bit set per reached vertex)
+// only when the last BFS layer is a large share of a sample, i.e. on graphs
+// of small diameter; queries whose vertex-diameter bound exceeds this leave
+// them alone.
+constexpr long long kBitsMaxVD = 64;
+
 // Counters a launch accumulates (one atomicAdd per CTA at exit).
 struct Counters {
     unsigned long long samples, connected, e_scan, expanded, touched, interior, walk_scan, scaled;
@@ -94,6 +102,8 @@ struct SampleLaunch {
     int grid;
     int threads;
     const int *abandon;        // optional: a sample stops at its next layer once *abandon != 0
+    uint32_t *bits;            // optional: per slot, one bit per vertex and side (reached by
+                               // that side), 2 * ceil(n / 32) words per slot, zero at rest
 };
 
 cudaError_t launch_sample(const SampleLaunch &a, cudaStream_t st);
@@ -140,6 +150,7 @@ struct QueryDesc {
     const double2 *Ltab;       // (L_L, L_U) of every class
     unsigned int *cmax;        // largest c~ in every class
     int nclass;
+    int use_bits;              // the query uses the slots' reached-bit maps
     int tag;                   // 1: adaptive phase (epochs, logs, checks); 0: calibration samples
                                //    counted straight into `counts` (E = n_calib, F = 1, no check)
     double omega, eps;
@@ -160,6 +171,7 @@ struct BatchLaunch {
     int nq;
     SlotRec *recs;             // slots * stride
     uint32_t *queues;          // slots * stride
+    uint32_t *bits;            // slots * 2 * ceil(stride / 32) words (may be null)
     long long stride;          // largest n the scratch serves
     BatchState *bs;
     unsigned long long budget; // samples this launch may hand out (0 = no limit)

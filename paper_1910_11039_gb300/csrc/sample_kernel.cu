@@ -456,8 +456,8 @@ struct LocalStats {
 
 template <int NT, typename OffT>
 __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotRec *rec, uint32_t *queue,
-                           Smem<NT> &sh, unsigned long long idx, unsigned long long trace_i, LocalStats &ls,
-                           const CountSink &sink)
+                           uint32_t *bits, long long bw, Smem<NT> &sh, unsigned long long idx,
+                           unsigned long long trace_i, LocalStats &ls, const CountSink &sink)
 {
     const int tid = threadIdx.x;
     const long long n = G.n;
@@ -474,6 +474,10 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
         sh.t = (long long)t;
         __stcg(&rec[s].w[0], pack(1u, 1ULL));
         __stcg(&rec[t].w[1], pack(1u, 1ULL));
+        if (bits) {
+            atomicOr(&bits[s >> 5], 1u << (s & 31));
+            atomicOr(&bits[bw + (t >> 5)], 1u << (t & 31));
+        }
         qset(queue, n, 0, 0, (unsigned int)s);
         qset(queue, n, 1, 0, (unsigned int)t);
         sh.qlen[0] = sh.qlen[1] = 1;
@@ -557,17 +561,34 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
                         dw[j] = c.y;
                     }
                 }
-                // phase 2: (level_s, level_t) of every target, one 8-byte load each
+                // phase 2: (level_s, level_t) of every target, one 16-byte load
+                // each; once the layer is known to be the last, only the other
+                // side's reached bit (a dense map that stays in L2): targets
+                // without it are skipped, targets with it are claimed or counted
+                // (lx = 0 lets the claim decide; 1 is no level of this layer)
                 unsigned int lx[kUnroll];
                 unsigned int ymask = 0;
+                const bool fast = bits != nullptr && *(volatile int *)&sh.meets != 0;
+                if (fast) {
+                    const uint32_t *ybits = bits + (X ? 0 : bw);
 #pragma unroll
-                for (int j = 0; j < kUnroll; ++j) {
-                    lx[j] = 1u;
-                    if (w[j] != kNone) {
-                        unsigned long long w0, w1;
-                        load_rec(rec + w[j], w0, w1);
-                        lx[j] = lvl_of(X ? w1 : w0);
-                        ymask |= (lvl_of(X ? w0 : w1) != 0 ? 1u : 0u) << j;
+                    for (int j = 0; j < kUnroll; ++j) {
+                        lx[j] = 1u;
+                        if (w[j] != kNone && ((__ldcg(ybits + (w[j] >> 5)) >> (w[j] & 31)) & 1u)) {
+                            lx[j] = 0u;
+                            ymask |= 1u << j;
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < kUnroll; ++j) {
+                        lx[j] = 1u;
+                        if (w[j] != kNone) {
+                            unsigned long long w0, w1;
+                            load_rec(rec + w[j], w0, w1);
+                            lx[j] = lvl_of(X ? w1 : w0);
+                            ymask |= (lvl_of(X ? w0 : w1) != 0 ? 1u : 0u) << j;
+                        }
                     }
                 }
                 // an unseen target that the other side holds makes this layer
@@ -622,6 +643,7 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
                         if (joins) {
                             qset(queue, n, X, qbase + slot0 + __popc(m & ((1u << lane) - 1u)), w[j]);
                             my_deg += dw[j];
+                            if (bits) atomicOr(&bits[(X ? bw : 0) + (w[j] >> 5)], 1u << (w[j] & 31));
                         }
                     }
                     if (meets) {
@@ -1188,6 +1210,9 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
                 if (v[j] == kNone) continue;
                 // one 32-byte store clears the record's whole sector
                 asm volatile("st.global.cg.v4.u64 [%0], {%1, %1, %1, %1};" ::"l"(rec + v[j]), "l"(0ULL) : "memory");
+                // every set bit of this side's map belongs to a queued vertex of
+                // this sample, so the whole word can go
+                if (bits) __stcg(bits + (side ? bw : 0) + (v[j] >> 5), 0u);
             }
         }
     }
@@ -1205,6 +1230,8 @@ __global__ void __launch_bounds__(NT, (2048 / NT / 2) > 0 ? (2048 / NT / 2) : 1)
     GraphRef<OffT> G{reinterpret_cast<const OffT *>(a.off), a.adj, (long long)a.n};
     SlotRec *rec = a.recs + (size_t)blockIdx.x * (size_t)a.n;
     uint32_t *queue = a.queues + (size_t)blockIdx.x * (size_t)a.n;
+    const long long bw = bit_words(a.n);
+    uint32_t *bits = a.bits ? a.bits + (size_t)blockIdx.x * (size_t)(2 * bw) : nullptr;
     Job *job = a.job;
 
     if (tid == 0) {
@@ -1227,7 +1254,7 @@ __global__ void __launch_bounds__(NT, (2048 / NT / 2) > 0 ? (2048 / NT / 2) : 1)
         __syncthreads();
         const unsigned long long i = sh.cur;
         if (i >= count) break;
-        run_sample<NT, OffT>(a, G, rec, queue, sh, base + i, i, ls, CountSink{a.counts, nullptr, nullptr, 0u});
+        run_sample<NT, OffT>(a, G, rec, queue, bits, bw, sh, base + i, i, ls, CountSink{a.counts, nullptr, nullptr, 0u});
     }
 
     if (tid == 0) {
@@ -1379,6 +1406,8 @@ __global__ void __launch_bounds__(NT, (2048 / NT / 2) > 0 ? (2048 / NT / 2) : 1)
     const int tid = threadIdx.x;
     SlotRec *rec = B.recs + (size_t)blockIdx.x * (size_t)B.stride;
     uint32_t *queue = B.queues + (size_t)blockIdx.x * (size_t)B.stride;
+    const long long bw = bit_words(B.stride);
+    uint32_t *bits = B.bits ? B.bits + (size_t)blockIdx.x * (size_t)(2 * bw) : nullptr;
     volatile BatchState *vbs = B.bs;
     if (B.nq == 1) {
         // one query: its descriptor stays in shared memory for the whole launch
@@ -1514,7 +1543,7 @@ __global__ void __launch_bounds__(NT, (2048 / NT / 2) > 0 ? (2048 / NT / 2) : 1)
         Job *job = qd.job;
         GraphRef<OffT> G{reinterpret_cast<const OffT *>(qd.off), qd.adj, qd.n};
         LocalStats ls = {0, 0, 0, 0, 0, 0, 0, 0};
-        run_sample<NT, OffT>(sa, G, rec, queue, sh, st->base + pm.idx, pm.idx, ls,
+        run_sample<NT, OffT>(sa, G, rec, queue, qd.use_bits ? bits : nullptr, bw, sh, st->base + pm.idx, pm.idx, ls,
                              qd.tag == 0 ? CountSink{qd.counts, nullptr, nullptr, 0u}
                                          : CountSink{nullptr, qd.logs + (size_t)f * qd.log_cap, &st->log_len[f],
                                                      qd.log_cap});
