@@ -42,7 +42,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "shortest-path samples/sec and time-to-(eps,delta) stop; GTEPS and HBM fraction"
 WORKLOADS = {
-    "rmat20": dict(graph="rmat20", eps=0.01, delta=0.1, seed=1,
+    "rmat20": dict(graph="rmat20", eps=0.01, delta=0.1, seed=1, threads=512,
                    desc="R-MAT scale 20, edge factor 16, (a,b,c,d)=(0.57,0.19,0.19,0.05), symmetrised, "
                         "no self-loops/duplicates, int32 CSR; eps=0.01 delta=0.1 seed=1"),
     "rhg20": dict(graph="rhg20", eps=0.01, delta=0.1, seed=1, steps=5, cpu_samples=4800, ref_samples=1600,
@@ -646,7 +646,7 @@ def main():
     ap.add_argument("--frames", type=int, default=8, help="epoch frames in flight (pipelined mode)")
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--slots", type=int, default=0, help="samples in flight (0 = fill the GPU)")
-    ap.add_argument("--threads", type=int, default=1024, help="threads per sampling CTA")
+    ap.add_argument("--threads", type=int, default=None, help="threads per sampling CTA (default: per workload)")
     ap.add_argument("--cpu-samples", type=int, default=None,
                     help="oracle samples for the CPU baseline (split over host cores)")
     ap.add_argument("--ref-samples", type=int, default=None, help="oracle samples per reference step")
@@ -660,9 +660,13 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     wl = WORKLOADS[args.workload]
     # defaults sized so that each workload's run ends within minutes
-    if args.mode in ("batched", "serve") and args.steps is None:
-        args.steps = 2
-    for key, default in (("steps", 20), ("e2e_steps", 3), ("cpu_samples", 48000), ("ref_samples", 16000)):
+    if args.mode in ("batched", "serve"):
+        if args.steps is None:
+            args.steps = 2
+        if args.threads is None:
+            args.threads = 1024
+    for key, default in (("steps", 20), ("e2e_steps", 3), ("cpu_samples", 48000), ("ref_samples", 16000),
+                         ("threads", 1024)):
         if getattr(args, key) is None:
             setattr(args, key, wl.get(key, default))
     if args.mode in ("batched", "serve"):
