@@ -45,7 +45,7 @@ WORKLOADS = {
     "rmat20": dict(graph="rmat20", eps=0.01, delta=0.1, seed=1, threads=512,
                    desc="R-MAT scale 20, edge factor 16, (a,b,c,d)=(0.57,0.19,0.19,0.05), symmetrised, "
                         "no self-loops/duplicates, int32 CSR; eps=0.01 delta=0.1 seed=1"),
-    "rhg20": dict(graph="rhg20", eps=0.01, delta=0.1, seed=1, steps=5, cpu_samples=4800, ref_samples=1600,
+    "rhg20": dict(graph="rhg20", eps=0.01, delta=0.1, seed=1, steps=5, cpu_samples=4800, ref_samples=1600, threads=512,
                   desc="random hyperbolic graph, n=2^20, power-law exponent 3, average degree 60 (|E| = 30|V|), "
                        "seed 20, int32 CSR; eps=0.01 delta=0.1 seed=1"),
     "grid4096": dict(graph="grid4096", eps=0.01, delta=0.1, seed=1, steps=1, e2e_steps=1, cpu_samples=48,
