@@ -119,16 +119,43 @@ __global__ void cc_init_kernel(long long n, unsigned int *parent, unsigned int *
     (void)queue;
 }
 
+// Warp-aggregated append of the lanes' `take` vertices to queue q (length
+// *len), adding their degrees to *fdeg.
+__device__ __forceinline__ void warp_append(bool take, unsigned int v, unsigned long long deg, unsigned int *q,
+                                            unsigned int *len, unsigned long long *fdeg)
+{
+    const unsigned int lane = threadIdx.x & 31;
+    const unsigned int active = __activemask();
+    const unsigned int m = __ballot_sync(active, take);
+    if (!m) return;
+    unsigned long long dsum = take ? deg : 0ULL;
+    for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(active, dsum, o);
+    const int leader = __ffs(m) - 1;
+    unsigned int base = 0;
+    if ((int)lane == leader) {
+        base = atomicAdd(len, (unsigned int)__popc(m));
+        atomicAdd(fdeg, dsum);
+    }
+    base = __shfl_sync(active, base, leader);
+    if (take) __stcg(q + base + __popc(m & ((1u << lane) - 1u)), v);
+}
+
 // roots (parent[v] == v after hooking) start the search at level 0
-__global__ void roots_kernel(long long n, unsigned int *parent, unsigned int *dist, unsigned int *queue,
-                             unsigned int *qlen)
+template <typename OffT>
+__global__ void roots_kernel(long long n, const OffT *off, unsigned int *parent, unsigned int *dist,
+                             unsigned int *queue, unsigned int *qlen, unsigned long long *fdeg)
 {
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
-        if (find_root(parent, (unsigned int)v) == (unsigned int)v) {
+    const long long n_round = (n + 31) & ~31LL;
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n_round; v += stride) {
+        bool take = false;
+        unsigned long long d = 0;
+        if (v < n && find_root(parent, (unsigned int)v) == (unsigned int)v) {
             dist[v] = 0;
-            queue[atomicAdd(qlen, 1u)] = (unsigned int)v;
+            take = true;
+            d = (unsigned long long)((long long)off[v + 1] - (long long)off[v]);
         }
+        warp_append(take, (unsigned int)v, d, queue, qlen, fdeg);
     }
 }
 
@@ -138,6 +165,9 @@ struct BfsState {
     unsigned int gen;          // grid barrier generation
     unsigned int level;        // largest level reached
     unsigned int err;
+    unsigned long long fdeg[2];  // degree sums of the two queues' vertices
+    unsigned long long explored; // degree sum of every vertex reached so far
+    int bottom_up;             // direction of the current level
 };
 
 __device__ bool grid_barrier(BfsState *s)
@@ -170,32 +200,82 @@ __device__ bool grid_barrier(BfsState *s)
     return ok != 0;
 }
 
+// Multi-source breadth-first search, direction-optimising (Beamer, Asanovic
+// and Patterson, SC 2012): a level expands its frontier top-down (one warp per
+// frontier vertex) while the frontier's edges are few against the edges not
+// yet explored, and bottom-up (every unreached vertex looks for a neighbour in
+// the frontier) while the frontier is large.  Both give every vertex its exact
+// distance from its component's root.
 template <typename OffT>
 __global__ void msbfs_kernel(long long n, const OffT *off, const uint2 *adj, unsigned int *dist, unsigned int *q0,
-                             unsigned int *q1, BfsState *s)
+                             unsigned int *q1, BfsState *s, unsigned long long nnz)
 {
     unsigned int *q[2] = {q0, q1};
     int cur = 0;
+    const int lane = threadIdx.x & 31;
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    const long long threads = (long long)gridDim.x * blockDim.x;
+    int bottom_up = 0;
     for (unsigned int level = 0;; ++level) {
         const unsigned int len = *reinterpret_cast<volatile unsigned int *>(&s->len[cur]);
         if (len == 0) break;
         if (blockIdx.x == 0 && threadIdx.x == 0) s->level = level;
+        // direction of this level, decided alike by every CTA from the same state
+        const unsigned long long mf = *reinterpret_cast<volatile unsigned long long *>(&s->fdeg[cur]);
+        const unsigned long long ex = *reinterpret_cast<volatile unsigned long long *>(&s->explored);
+        const unsigned long long mu = nnz > ex ? nnz - ex : 0ULL;
+        if (!bottom_up && mf * 14ULL > mu) bottom_up = 1;
+        else if (bottom_up && (unsigned long long)len * 24ULL < (unsigned long long)n) bottom_up = 0;
         unsigned int *nextq = q[cur ^ 1];
-        // one warp per frontier vertex: lanes stride its adjacency
-        const int lane = threadIdx.x & 31;
-        const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
-        for (long long i = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < len; i += warps) {
-            const unsigned int u = __ldcg(q[cur] + i);
-            const long long b = (long long)__ldg(off + u), e = (long long)__ldg(off + u + 1);
-            for (long long k = b + lane; k < e; k += 32) {
-                const unsigned int w = __ldg(&adj[k].x);
-                if (__ldcg(dist + w) == kUnvisited && atomicCAS(dist + w, kUnvisited, level + 1) == kUnvisited)
-                    __stcg(nextq + atomicAdd(&s->len[cur ^ 1], 1u), w);
+        unsigned int *nlen = &s->len[cur ^ 1];
+        unsigned long long *nfdeg = &s->fdeg[cur ^ 1];
+        if (!bottom_up) {
+            // one warp per frontier vertex: lanes stride its adjacency
+            for (long long i = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < len; i += warps) {
+                const unsigned int u = __ldcg(q[cur] + i);
+                const long long b = (long long)__ldg(off + u), e = (long long)__ldg(off + u + 1);
+                for (long long k0 = b; k0 < e; k0 += 32) {
+                    const long long k = k0 + lane;
+                    bool take = false;
+                    unsigned int w = 0;
+                    unsigned long long dw = 0;
+                    if (k < e) {
+                        const uint2 c = __ldg(&adj[k]);
+                        w = c.x;
+                        dw = c.y;
+                        take = __ldcg(dist + w) == kUnvisited && atomicCAS(dist + w, kUnvisited, level + 1) == kUnvisited;
+                    }
+                    warp_append(take, w, dw, nextq, nlen, nfdeg);
+                }
+            }
+        } else {
+            // every unreached vertex looks for a neighbour at this level
+            const long long n_round = (n + 31) & ~31LL;
+            for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n_round; v += threads) {
+                bool take = false;
+                unsigned long long dv = 0;
+                if (v < n && __ldcg(dist + v) == kUnvisited) {
+                    const long long b = (long long)__ldg(off + v), e = (long long)__ldg(off + v + 1);
+                    dv = (unsigned long long)(e - b);
+                    for (long long k = b; k < e; ++k) {
+                        if (__ldcg(dist + __ldg(&adj[k].x)) == level) {
+                            take = true;
+                            break;
+                        }
+                    }
+                    if (take) __stcg(dist + v, level + 1);
+                }
+                warp_append(take, (unsigned int)v, dv, nextq, nlen, nfdeg);
             }
         }
         if (!grid_barrier(s)) return;
-        // every CTA has read len[cur]; one clears it for reuse two levels on
-        if (blockIdx.x == 0 && threadIdx.x == 0) s->len[cur] = 0;
+        // every CTA has read len[cur] and fdeg[cur]; one clears them for reuse
+        // two levels on and books the next frontier's edges as explored
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            s->len[cur] = 0;
+            s->fdeg[cur] = 0;
+            s->explored += s->fdeg[cur ^ 1];
+        }
         if (!grid_barrier(s)) return;
         cur ^= 1;
     }
@@ -272,7 +352,7 @@ cudaError_t vd_bound_t(int64_t n, const OffT *off, const uint2 *adj, unsigned in
         i = j;
     }
     cc_rest_kernel<OffT><<<grid, 256, 0, st>>>((long long)n, off, adj, parent, best, kRounds, &s->err);
-    roots_kernel<<<grid, 256, 0, st>>>((long long)n, parent, dist, q0, &s->len[0]);
+    roots_kernel<OffT><<<grid, 256, 0, st>>>((long long)n, off, parent, dist, q0, &s->len[0], &s->fdeg[0]);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // cooperative launch: every CTA is resident, so the grid barrier is safe
     int per_sm = 0;
@@ -281,7 +361,15 @@ cudaError_t vd_bound_t(int64_t n, const OffT *off, const uint2 *adj, unsigned in
     if (per_sm < 1) per_sm = 1;
     const int bgrid = sms * (per_sm < 4 ? per_sm : 4);
     long long nn = (long long)n;
-    void *args[] = {&nn, (void *)&off, (void *)&adj, &dist, &q0, &q1, &s};
+    unsigned long long nnz = 0;
+    {
+        OffT last = 0;
+        e = cudaMemcpyAsync(&last, off + n, sizeof(OffT), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return e;
+        nnz = (unsigned long long)last;
+    }
+    void *args[] = {&nn, (void *)&off, (void *)&adj, &dist, &q0, &q1, &s, &nnz};
     e = cudaLaunchCooperativeKernel((const void *)msbfs_kernel<OffT>, dim3(bgrid), dim3(256), args, 0, st);
     if (e != cudaSuccess) return e;
     BfsState hs;
