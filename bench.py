@@ -572,7 +572,12 @@ def run_serve(args, local_rank):
     from paper_1910_11039_gb300.autotune import Schedule
     from paper_1910_11039_gb300.server import Request, Server
 
-    pool = [k for k in inputs.SERVING_POOL if args.serve_pool == "full" or k.startswith("rmat")]
+    if args.serve_pool == "full":
+        pool = list(inputs.SERVING_POOL)
+    elif args.serve_pool == "mixed":
+        pool = [f"rmat{s}" for s in range(14, 21)] + ["grid1024"]
+    else:
+        pool = [k for k in inputs.SERVING_POOL if k.startswith("rmat")]
     reqs = inputs.serving_requests(count=args.serve_queries, rate=args.serve_rate, pool=pool)
     used = sorted({r["graph"] for r in reqs})
     t0 = time.perf_counter()
@@ -636,8 +641,9 @@ def main():
                          "serve: a Poisson stream of queries")
     ap.add_argument("--serve-queries", type=int, default=2000)
     ap.add_argument("--serve-rate", type=float, default=20.0)
-    ap.add_argument("--serve-pool", default="rmat", choices=["rmat", "full"],
-                    help="rmat: R-MAT scale 14-24; full: also the perturbed grids 1024^2-4096^2")
+    ap.add_argument("--serve-pool", default="rmat", choices=["rmat", "full", "mixed"],
+                    help="rmat: R-MAT scale 14-24; full: also the perturbed grids 1024^2-4096^2; "
+                         "mixed: R-MAT scale 14-20 and the 1024^2 grid")
     ap.add_argument("--serve-policy", default="fifo", choices=["fifo", "shortest", "round_robin"])
     ap.add_argument("--step-ms", type=float, default=20.0, help="serve mode: target length of a batch step")
     ap.add_argument("--autotune", action="store_true", help="batched mode: search the schedule first")

@@ -308,6 +308,9 @@ kadabra_status kadabra_batch_set_policy(kadabra_batch *b, int policy);
  * call on such a query returns KADABRA_ERR_TIMEOUT.  The device stays usable:
  * kadabra_query_reset and kadabra_pipeline_begin restart the query. */
 kadabra_status kadabra_batch_set_spin_limit(kadabra_batch *b, uint64_t polls);
+/* Samples in flight per step (CTAs), threads per sampling CTA and the largest
+ * n the batch serves; each output optional. */
+kadabra_status kadabra_batch_info(const kadabra_batch *b, int32_t *slots, int32_t *threads, int64_t *max_n);
 
 /* Sharded sampling (several ranks, one GPU each; Section I-A: samples are
  * independent, so a rank can take any subset of an epoch's sample indices).

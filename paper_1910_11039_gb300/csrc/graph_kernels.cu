@@ -44,19 +44,26 @@ __device__ __forceinline__ unsigned int find_root(unsigned int *parent, unsigned
     return x;
 }
 
-// Link the trees of u and v: the larger root goes under the smaller one.
+// Link the trees of u and v: the larger root goes under the smaller one.  The
+// link is an atomic minimum, so it always makes progress under contention
+// (many vertices linking to one hub): if the larger root had meanwhile been
+// linked to some other vertex, the minimum keeps the smaller of the two
+// parents and the loop links the displaced one as well.  Parents only ever
+// decrease, so every root stays the smallest id of its tree.
 __device__ __forceinline__ void hook(unsigned int *parent, unsigned int u, unsigned int v, unsigned int *err)
 {
     unsigned long long tries = 0;
-    for (;;) {
-        const unsigned int ru = find_root(parent, u), rv = find_root(parent, v);
-        if (ru == rv) return;
+    unsigned int ru = find_root(parent, u), rv = find_root(parent, v);
+    while (ru != rv) {
         const unsigned int big = ru > rv ? ru : rv, small = ru > rv ? rv : ru;
-        if (atomicCAS(parent + big, big, small) == big) return;
+        const unsigned int old = atomicMin(parent + big, small);
+        if (old == big) return;
         if (++tries > kSpinLimit) {
             atomicOr(err, 1u);
             return;
         }
+        ru = find_root(parent, old);
+        rv = find_root(parent, small);
     }
 }
 

@@ -1109,6 +1109,15 @@ extern "C" kadabra_status kadabra_batch_poll(kadabra_batch *b, int32_t *states, 
     return KADABRA_OK;
 }
 
+extern "C" kadabra_status kadabra_batch_info(const kadabra_batch *b, int32_t *slots, int32_t *threads, int64_t *max_n)
+{
+    if (!b) return fail(KADABRA_ERR_INVALID_ARG, "batch is null");
+    if (slots) *slots = b->slots;
+    if (threads) *threads = b->threads;
+    if (max_n) *max_n = b->max_n;
+    return KADABRA_OK;
+}
+
 extern "C" kadabra_status kadabra_batch_set_spin_limit(kadabra_batch *b, uint64_t polls)
 {
     if (!b) return fail(KADABRA_ERR_INVALID_ARG, "batch is null");

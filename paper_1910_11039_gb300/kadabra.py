@@ -115,6 +115,7 @@ SIGNATURES = {
     "kadabra_batch_set_policy": (_ST, [_P, C.c_int]),
     "kadabra_batch_poll": (_ST, [_P, _P, _I64, _P]),
     "kadabra_batch_set_spin_limit": (_ST, [_P, _U64]),
+    "kadabra_batch_info": (_ST, [_P, _P, _P, _P]),
     "kadabra_query_create": (_ST, [_P, _P, _P, _P]),
     "kadabra_calibration_begin": (_ST, [_P, _P]),
     "kadabra_calibration_finish": (_ST, [_P, _P]),
@@ -404,6 +405,11 @@ class Batch:
         self.threads = threads
         if policy:
             self.set_policy(policy)
+
+    def info(self) -> dict:
+        sl, th, mn = C.c_int32(), C.c_int32(), _I64()
+        _check(load().kadabra_batch_info(self.handle, C.byref(sl), C.byref(th), C.byref(mn)))
+        return dict(slots=sl.value, threads=th.value, max_n=mn.value)
 
     def set_spin_limit(self, polls):
         _check(load().kadabra_batch_set_spin_limit(self.handle, int(polls)))

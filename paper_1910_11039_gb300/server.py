@@ -92,6 +92,9 @@ class Server:
         self.schedule = schedule or Schedule(threads=threads)
         self.batch = K.Batch(self.max_n, slots=slots, threads=self.schedule.threads,
                              offsets_64=off64.pop() if off64 else False)
+        # a step hands out at least this many samples, so that the samples still
+        # running when the budget is spent (one per slot) are a small share of it
+        self.min_budget = 8 * int(self.batch.info()["slots"]) if hasattr(self.batch, "info") else 256
         if policy not in ("fifo", "shortest", "round_robin"):
             raise ValueError("policy must be 'fifo', 'shortest' or 'round_robin'")
         self.policy = policy
@@ -198,7 +201,7 @@ class Server:
             ms = self.batch.last_ms()
             self.stats["steps"] += 1
             self.stats["step_ms"] += ms
-            budget = int(min(1 << 22, max(256, budget * self.step_ms / max(ms, 1e-3))))
+            budget = int(min(1 << 22, max(self.min_budget, budget * self.step_ms / max(ms, 1e-3))))
             states = self.batch.poll(len(active))
             still = []
             for a, state in zip(active, states):
