@@ -174,13 +174,25 @@ def algorithmic_bytes(ls, offset_bytes):
 KERNEL_SOURCES = ("sample_kernel.cu", "philox.cuh", "stop_math.cuh")
 
 
+def _code_only(text: str) -> str:
+    """Source text without comments and blank lines (comment edits do not
+    change the compiled kernel, so they must not invalidate a profile)."""
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    lines = []
+    for line in text.splitlines():
+        line = re.sub(r"//.*$", "", line).rstrip()
+        if line.strip():
+            lines.append(line)
+    return "\n".join(lines)
+
+
 def kernel_digest():
-    """Digest of the sources the sampling kernels are compiled from."""
+    """Digest of the code (comments stripped) the sampling kernels are compiled from."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1910_11039_gb300", "csrc")
     for name in KERNEL_SOURCES:
-        with open(os.path.join(csrc, name), "rb") as f:
-            h.update(name.encode() + f.read())
+        with open(os.path.join(csrc, name), encoding="utf-8") as f:
+            h.update(name.encode() + _code_only(f.read()).encode())
     return h.hexdigest()[:16]
 
 

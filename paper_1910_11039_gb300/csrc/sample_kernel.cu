@@ -20,28 +20,33 @@
 //   counter vector at the next kernel a consistent snapshot).
 //
 // Layout in HBM (per slot): SlotRec[n] (32 B per vertex, one sector: for each
-// side one word holding the path count and the BFS level, then padding) and a
-// uint32 queue of n entries shared by
-// both sides (s-side grows from the front, t-side from the back; the balls
-// are disjoint until they meet, so n entries always suffice).  Records are
-// cleared by the sample that set them, so no per-sample O(n) reset is needed.
+// side one word holding the path count and the BFS level, then padding), a
+// uint32 queue of n entries shared by both sides (s-side grows from the front,
+// t-side from the back; the balls are disjoint until they meet, so n entries
+// always suffice) and, for each side, one reached bit per vertex.  Records
+// and bits are cleared by the sample that set them, so no per-sample O(n)
+// reset is needed; the clearing store writes a record's whole sector.
 //
 // Latency hiding inside one CTA: the layer expansion assigns adjacency
 // entries to threads by a block-wide prefix sum over the frontier's degrees
 // (every thread gets the same share whatever the degree skew) and keeps
 // kUnroll entries per thread in flight: their column ids, then their
-// (level_s, level_t) pairs (one 8-byte load), then the claims, then the
-// path-count additions (waited on once per batch).  The back-walk takes the
-// predecessor layer from the BFS queue when that layer is much smaller than
-// the current vertex's adjacency (hubs), instead of scanning the adjacency.
+// (level_s, level_t) pairs (one 16-byte load), then the claims, then the
+// path-count additions (waited on once per batch).
+//
+// The last layer: as soon as a target of the layer is found on the other
+// side, the layer is the last one and only meeting vertices need records;
+// other targets are not claimed, and on graphs of small diameter an edge then
+// reads only the other side's reached bit (a dense map that stays in L2)
+// instead of the target's record.
+//
+// The meeting-vertex choice and walk steps with at most 32 candidates run in
+// warp 0 with shuffles, without block barriers; larger ones use the CTA (and,
+// at hubs, the predecessor layer from the BFS queue instead of the hub's
+// adjacency).  The path's vertices go to the sink in one flush.
 //
 // Mutable slot state is read with ld.global.cg (L2) so that values written by
 // atomics of other threads in the CTA are never served stale from L1.
-//
-// Scratch footprint matters more than it seems: the probes of all in-flight
-// samples land at random in slots * n * 16 bytes, and the per-edge cost under
-// full load grows with that footprint (translation and DRAM row misses), so
-// the record is kept at 16 bytes and the slot count is bounded.
 
 #include <cstdint>
 
