@@ -92,9 +92,12 @@ class Server:
         self.schedule = schedule or Schedule(threads=threads)
         self.batch = K.Batch(self.max_n, slots=slots, threads=self.schedule.threads,
                              offsets_64=off64.pop() if off64 else False)
-        # a step hands out at least this many samples, so that the samples still
-        # running when the budget is spent (one per slot) are a small share of it
-        self.min_budget = 8 * int(self.batch.info()["slots"]) if hasattr(self.batch, "info") else 256
+        # a step hands out at least this many samples per slot, so that the
+        # samples still running when the budget is spent (one per slot) are a
+        # small share of it; long samples (high-diameter graphs) get more
+        self.slots = int(self.batch.info()["slots"]) if hasattr(self.batch, "info") else 32
+        self.min_budget = 8 * self.slots
+        self.min_budget_long = 32 * self.slots
         if policy not in ("fifo", "shortest", "round_robin"):
             raise ValueError("policy must be 'fifo', 'shortest' or 'round_robin'")
         self.policy = policy
@@ -201,7 +204,8 @@ class Server:
             ms = self.batch.last_ms()
             self.stats["steps"] += 1
             self.stats["step_ms"] += ms
-            budget = int(min(1 << 22, max(self.min_budget, budget * self.step_ms / max(ms, 1e-3))))
+            floor = self.min_budget_long if any(self.vd.get(a.req.graph, 0) > 64 for a in active) else self.min_budget
+            budget = int(min(1 << 22, max(floor, budget * self.step_ms / max(ms, 1e-3))))
             states = self.batch.poll(len(active))
             still = []
             for a, state in zip(active, states):
