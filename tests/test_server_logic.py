@@ -146,3 +146,36 @@ def test_graphs_must_share_offset_width(monkeypatch):
     monkeypatch.setattr(S, "K", fake)
     with pytest.raises(ValueError):
         S.Server({"a": FakeGraph(10), "b": G64(10)}, memory_budget=1 << 30)
+
+
+def test_step_budget_floor_grows_with_long_samples(monkeypatch):
+    """Steps hand out at least 8 samples per slot, 32 while a query of
+    diameter bound above 64 is active (its samples are long)."""
+    fake, log = make_fake({1: 3, 2: 3})
+    budgets = []
+
+    class BudgetBatch(fake.Batch):
+        def info(self):
+            return {"slots": 10, "threads": 256, "max_n": 1000}
+
+        def step(self, qs, sample_budget=0):
+            budgets.append(sample_budget)
+            super().step(qs, sample_budget)
+
+    fake.Batch = BudgetBatch
+
+    class LongQuery(fake.Query):
+        def info(self):
+            i = super().info()
+            i.vertex_diameter = 500 if self.g.n == 1000 else 7
+            return i
+
+    fake.Query = LongQuery
+    monkeypatch.setattr(S, "K", fake)
+    srv = S.Server({"grid": FakeGraph(1000), "rmat": FakeGraph(100)}, memory_budget=1 << 30, step_ms=1e-6)
+    assert srv.min_budget == 80 and srv.min_budget_long == 320
+    srv.run([S.Request(1, "rmat", 0.1, seed=1)], realtime=False)
+    assert min(budgets[1:]) == 80                  # short samples only: the small floor
+    budgets.clear()
+    srv.run([S.Request(2, "grid", 0.1, seed=2)], realtime=False)
+    assert min(budgets[1:]) == 320                 # a long-sample query is active
