@@ -34,3 +34,21 @@ def test_schedule_epoch_rule():
             # nearest power of two to omega / divisor (in log scale)
             assert abs(math.log2(E) - math.log2(omega / 32)) <= 0.5 + 1e-12
     assert Schedule(divisor=8).epoch_len(8192) == 1024
+
+
+def test_serving_stream_recipe():
+    reqs = I.serving_requests()
+    assert len(reqs) == 2000
+    arr = [r["arrival"] for r in reqs]
+    assert arr == sorted(arr) and arr[0] > 0
+    gaps = [b - a for a, b in zip([0.0] + arr[:-1], arr)]
+    mean_gap = sum(gaps) / len(gaps)
+    assert abs(mean_gap - 1 / 20.0) < 0.1 / 20.0            # Poisson at 20 per second
+    pool = set(I.SERVING_POOL)
+    assert {r["graph"] for r in reqs} == pool                # every pool graph is drawn
+    eps = [r["eps"] for r in reqs]
+    assert set(eps) == {0.01, 0.005} and 0.4 < eps.count(0.01) / len(eps) < 0.6
+    assert all(r["delta"] == 0.1 for r in reqs)
+    assert len({r["seed"] for r in reqs}) == len(reqs)
+    assert reqs == I.serving_requests()                       # deterministic
+    assert set(I.SERVING_POOL) >= {f"rmat{s}" for s in range(14, 25)} | {"grid1024", "grid4096"}
