@@ -495,3 +495,20 @@ def test_batched_mix_members_match_oracle(K, orc):
         assert np.array_equal(res["counts"], counts)
     recs, paths = Qs[4].sample_trace(1, 12345, 8, path_cap=4000)
     compare_trace(recs, paths, oracle_trace(orc, rgg, 1060, 1, 12345, 8), 4000)
+
+
+@pytest.mark.slow
+def test_rmat20_benchmarked_configuration_matches_oracle(K, orc):
+    """R-MAT scale 20 (the benchmarked workload) in exactly the benchmarked
+    launch configuration (pipelined, 512 threads per sample, E = 1024, 8
+    frames): the whole adaptive phase ends with the oracle's tau, stop epoch
+    and counters."""
+    g = I.config_graph("rmat20")
+    G = K.Graph.from_inputs(g, skip_validate=True)
+    q = K.Query(G, eps=0.01, delta=0.1, seed=1, threads=512)
+    q.run_pipelined(1024, frames=8)
+    res = q.result(btilde=False)
+    counts, cal, LL, LU, R = orc.kadabra(g, 0.01, 0.1, seed=1, epoch_len=1024)
+    assert R.stopped and q.info().stopped == 1
+    assert res["tau"] == R.tau and res["stop_epoch"] == R.stop_epoch
+    assert np.array_equal(res["counts"], counts)
