@@ -342,3 +342,46 @@ def test_kadabra_within_eps_of_brandes(orc, name, eps, rule):
     b = orc.brandes(g)
     err = np.abs(counts / R.tau - b).max()
     assert err <= eps, (name, err)
+
+
+def test_stop_functions_are_monotone_in_the_counter(orc):
+    """f and g, as computed in IEEE double (each step a correctly rounded
+    monotone operation), never decrease when the counter grows with the
+    budgets fixed.  The pipelined check evaluates one vertex per budget class
+    (the class's largest counter) on the strength of this property."""
+    rng = np.random.default_rng(11)
+    for _ in range(200):
+        omega = float(rng.uniform(1e3, 1e6))
+        tau = int(rng.integers(1, int(omega)))
+        LL = float(rng.uniform(0.5, 60.0))
+        LU = float(rng.uniform(0.5, 60.0))
+        cs = np.unique(np.concatenate([rng.integers(0, tau + 1, 64), [0, 1, tau]]))
+        prev_f = prev_g = -np.inf
+        for c in cs:
+            f, g = orc.stop_functions(int(c), tau, omega, LL, LU)
+            assert f >= prev_f and g >= prev_g, (c, tau, omega, LL, LU)
+            prev_f, prev_g = f, g
+
+
+def test_class_maxima_equal_vertex_maxima(orc):
+    """The maxima of f and g over vertices equal the maxima over budget
+    classes (vertices with equal (L_L, L_U)) evaluated at each class's largest
+    counter: the reduction the pipelined check is built on."""
+    rng = np.random.default_rng(5)
+    n = 5000
+    classes = rng.uniform(1.0, 40.0, size=(12, 2))
+    cls = rng.integers(0, len(classes), n)
+    LL = classes[cls, 0].copy()
+    LU = classes[cls, 1].copy()
+    omega, eps = 20000.0, 0.05
+    for tau in (50, 700, 9000):
+        counts = rng.integers(0, tau + 1, n).astype(np.uint32)
+        _, mf, mg = orc.check_stop(counts, tau, omega, eps, LL, LU)
+        bf = bg = -np.inf
+        for k in range(len(classes)):
+            members = cls == k
+            if not members.any():
+                continue
+            f, g = orc.stop_functions(int(counts[members].max()), tau, omega, classes[k, 0], classes[k, 1])
+            bf, bg = max(bf, f), max(bg, g)
+        assert mf == bf and mg == bg
