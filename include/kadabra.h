@@ -339,6 +339,19 @@ kadabra_status kadabra_run_graph(kadabra_query *q, int64_t epoch_len, int epochs
  * calibrated budgets (async). */
 kadabra_status kadabra_query_reset(kadabra_query *q, void *cuda_stream);
 
+/* Checkpoint and resume.  A query's adaptive state is its counters c~, tau
+ * and the number of epochs checked; samples are indexed by (seed, stream tag,
+ * sample index), so a query restored from that state continues exactly as the
+ * checkpointed one would have (same tau, stop epoch and counters at the end).
+ * A checkpoint is read with kadabra_result (counts, tau) and
+ * kadabra_query_get_info (epochs).  kadabra_query_restore sets c~ from
+ * counts[n] (host), tau and the epoch count, and clears the stop flag and
+ * error bits; the query must have been calibrated with the parameters of the
+ * checkpointed one (graph, eps, delta, seed, n_calib, delta rule, vertex
+ * diameter).  A pipelined phase must be begun again.  Synchronises. */
+kadabra_status kadabra_query_restore(kadabra_query *q, const uint32_t *counts, uint64_t tau, int64_t epochs,
+                                     void *cuda_stream);
+
 /* Result: b~(x) = c~(x) / tau, computed on the device.  Host outputs, each
  * optional: btilde[n] (double), counts[n] (uint32 c~), *tau, *stop_epoch.
  * Synchronises.  KADABRA_ERR_STATE if tau == 0 and btilde is requested. */

@@ -1317,6 +1317,30 @@ extern "C" kadabra_status kadabra_query_reset(kadabra_query *q, void *cuda_strea
     return KADABRA_OK;
 }
 
+extern "C" kadabra_status kadabra_query_restore(kadabra_query *q, const uint32_t *counts, uint64_t tau, int64_t epochs,
+                                              void *cuda_stream)
+{
+    {
+        kadabra_status s = need_calibrated(q);
+        if (s != KADABRA_OK) return s;
+    }
+    if (!counts) return fail(KADABRA_ERR_INVALID_ARG, "counts is null");
+    if (epochs < 0) return fail(KADABRA_ERR_INVALID_ARG, "epochs must be >= 0");
+    if (tau > q->omega_ceil) return fail(KADABRA_ERR_INVALID_ARG, "tau beyond ceil(omega)");
+    cudaStream_t st = as_stream(cuda_stream);
+    KCUDA(cudaMemcpyAsync(q->d_counts, counts, (size_t)q->g->n * 4, cudaMemcpyHostToDevice, st), "upload counters");
+    KCUDA(kadabra::launch_reset_job(q->d_job, st), "reset state");
+    Job j{};
+    KCUDA(cudaMemcpyAsync(&j, q->d_job, sizeof(Job), cudaMemcpyDeviceToHost, st), "read state");
+    KCUDA(cudaStreamSynchronize(st), "synchronise");
+    j.tau = tau;
+    j.epoch = epochs;
+    KCUDA(cudaMemcpyAsync(q->d_job, &j, sizeof(Job), cudaMemcpyHostToDevice, st), "write state");
+    KCUDA(cudaStreamSynchronize(st), "synchronise");
+    q->pipe_begun = false;
+    return KADABRA_OK;
+}
+
 extern "C" kadabra_status kadabra_result(kadabra_query *q, double *btilde, uint32_t *counts, uint64_t *tau,
                                          int64_t *stop_epoch, void *cuda_stream)
 {

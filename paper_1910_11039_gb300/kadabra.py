@@ -116,6 +116,7 @@ SIGNATURES = {
     "kadabra_batch_poll": (_ST, [_P, _P, _I64, _P]),
     "kadabra_batch_set_spin_limit": (_ST, [_P, _U64]),
     "kadabra_batch_info": (_ST, [_P, _P, _P, _P]),
+    "kadabra_query_restore": (_ST, [_P, _P, _U64, _I64, _P]),
     "kadabra_query_create": (_ST, [_P, _P, _P, _P]),
     "kadabra_calibration_begin": (_ST, [_P, _P]),
     "kadabra_calibration_finish": (_ST, [_P, _P]),
@@ -277,6 +278,30 @@ class Query:
         self.handle = C.c_void_p()
         fn = load().kadabra_calibrate if calibrate else load().kadabra_query_create
         _check(fn(graph.handle, C.byref(p), _stream(stream), C.byref(self.handle)))
+
+    def checkpoint(self, stream=None) -> dict:
+        """The query's adaptive state (counters, tau, epochs checked) and the
+        parameters a restored query must share."""
+        res = self.result(btilde=False, stream=stream)
+        inf = self.info(stream)
+        p = self.params
+        return {"counts": res["counts"].astype(np.uint32), "tau": int(res["tau"]), "epochs": int(inf.epochs),
+                "eps": p.eps, "delta": p.delta, "seed": int(p.seed), "n_calib": int(inf.n_calib),
+                "delta_rule": int(p.delta_rule), "vertex_diameter": int(inf.vertex_diameter)}
+
+    def restore(self, ckpt: dict, stream=None):
+        """Continue from a checkpoint taken on a query with the same parameters."""
+        inf = self.info(stream)
+        p = self.params
+        if (ckpt["eps"], ckpt["delta"], ckpt["seed"], ckpt["delta_rule"]) != (p.eps, p.delta, int(p.seed),
+                                                                              int(p.delta_rule)) \
+                or ckpt["n_calib"] != inf.n_calib or ckpt["vertex_diameter"] != inf.vertex_diameter:
+            raise ValueError("checkpoint taken with other query parameters")
+        counts = np.ascontiguousarray(ckpt["counts"], dtype=np.uint32)
+        if counts.shape != (self.graph.n,):
+            raise ValueError("checkpoint counters do not match the graph")
+        _check(load().kadabra_query_restore(self.handle, _ptr(counts), int(ckpt["tau"]), int(ckpt["epochs"]),
+                                            _stream(stream)))
 
     def calibration_begin(self, stream=None):
         _check(load().kadabra_calibration_begin(self.handle, _stream(stream)))
@@ -445,6 +470,21 @@ class Batch:
             self.free()
         except Exception:
             pass
+
+
+def save_checkpoint(path, ckpt: dict):
+    """Write a checkpoint (Query.checkpoint()) to an .npz file."""
+    np.savez(path, **{k: np.asarray(v) for k, v in ckpt.items()})
+
+
+def load_checkpoint(path) -> dict:
+    with np.load(path) as z:
+        out = {k: z[k] for k in z.files}
+    for k in ("tau", "epochs", "seed", "n_calib", "delta_rule", "vertex_diameter"):
+        out[k] = int(out[k])
+    for k in ("eps", "delta"):
+        out[k] = float(out[k])
+    return out
 
 
 # C-ABI names, for callers that prefer the flat interface

@@ -512,3 +512,35 @@ def test_rmat20_benchmarked_configuration_matches_oracle(K, orc):
     assert R.stopped and q.info().stopped == 1
     assert res["tau"] == R.tau and res["stop_epoch"] == R.stop_epoch
     assert np.array_equal(res["counts"], counts)
+
+
+def test_checkpoint_resume_is_bit_identical(K, orc, tmp_path):
+    """A query restored from a checkpoint (counters, tau, epochs) continues
+    exactly as the original: same tau, stop epoch and counters, in the
+    stream-ordered and the pipelined form; the checkpoint survives a file."""
+    g = GRAPHS["rmat14"]()
+    G = K.Graph.from_inputs(g)
+    eps, E = 0.03, 200
+    counts, cal, LL, LU, R = orc.kadabra(g, eps, 0.1, seed=4, epoch_len=E)
+    assert R.stop_epoch >= 3
+    a = K.Query(G, eps=eps, delta=0.1, seed=4)
+    for _ in range(2):
+        a.sample_epoch(E)
+        stopped, _, _ = a.check_stop()
+        assert not stopped
+    path = tmp_path / "ck.npz"
+    K.save_checkpoint(path, a.checkpoint())
+    ck = K.load_checkpoint(path)
+    assert ck["tau"] == 2 * E and ck["epochs"] == 2
+    for form in ("epochs", "pipelined"):
+        b = K.Query(G, eps=eps, delta=0.1, seed=4)
+        b.restore(ck)
+        if form == "epochs":
+            assert b.run(E)
+        else:
+            b.run_pipelined(E, frames=4)
+        res = b.result(btilde=False)
+        assert res["tau"] == R.tau and res["stop_epoch"] == R.stop_epoch, form
+        assert np.array_equal(res["counts"], counts), form
+    with pytest.raises(ValueError):
+        K.Query(G, eps=eps, delta=0.1, seed=5).restore(ck)

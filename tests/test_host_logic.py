@@ -52,3 +52,17 @@ def test_serving_stream_recipe():
     assert len({r["seed"] for r in reqs}) == len(reqs)
     assert reqs == I.serving_requests()                       # deterministic
     assert set(I.SERVING_POOL) >= {f"rmat{s}" for s in range(14, 25)} | {"grid1024", "grid4096"}
+
+
+def test_checkpoint_file_roundtrip(tmp_path):
+    import numpy as np
+    from paper_1910_11039_gb300 import kadabra as K
+    ck = {"counts": np.arange(10, dtype=np.uint32), "tau": 1234, "epochs": 7, "eps": 0.05, "delta": 0.1,
+          "seed": 9, "n_calib": 1000, "delta_rule": 1, "vertex_diameter": 13}
+    path = tmp_path / "ck.npz"
+    K.save_checkpoint(path, ck)
+    back = K.load_checkpoint(path)
+    assert set(back) == set(ck)
+    assert np.array_equal(back["counts"], ck["counts"]) and back["counts"].dtype == np.uint32
+    for k in ("tau", "epochs", "eps", "delta", "seed", "n_calib", "delta_rule", "vertex_diameter"):
+        assert back[k] == ck[k] and type(back[k]) is type(ck[k])
