@@ -112,6 +112,8 @@ typedef struct kadabra_query_info {
     uint64_t cal_done;          /* calibration samples completed (phase 1), else n_calib    */
     uint64_t device_bytes;      /* device memory the query holds (not the graph's)          */
     int64_t launches;           /* sampling launches logged (kadabra_launch_log), ever      */
+    double diameter_ms;         /* host wall time of phase 1 (diameter bound and omega)    */
+    double calibration_ms;      /* host wall time of phase 2 (calibration; batch: budgets)  */
 } kadabra_query_info;
 
 /* Per-sample record written by kadabra_sample_trace (one per sample index). */

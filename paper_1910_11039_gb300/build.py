@@ -100,7 +100,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
             if o.strip():
                 print(o, file=sys.stderr)
     tmp = LIB + f".tmp{os.getpid()}"
-    _run([nvcc, *ARCH, "-shared", "-Xcompiler", "-fPIC", "-o", tmp, *objs], verbose)
+    _run([nvcc, *ARCH, "-shared", "-Xcompiler", "-fPIC", "-o", tmp, *objs, "-ldl"], verbose)
     os.replace(tmp, LIB)
     with open(stamp, "w") as f:
         f.write(dig)

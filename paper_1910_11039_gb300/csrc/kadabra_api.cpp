@@ -13,6 +13,10 @@
 
 #include <cuda_runtime.h>
 
+#include <chrono>
+
+#include <nvtx3/nvToolsExt.h>
+
 #include "kadabra.h"
 #include "kadabra_internal.h"
 
@@ -107,6 +111,8 @@ struct kadabra_query {
     kadabra::BatchState *d_bs = nullptr;
     bool pipe_begun = false;
     int phase = 0;                           // 0 created, 1 calibrating in a batch, 2 calibrated
+    double diameter_ms = 0.0;                // host wall time of phase 1 (diameter bound, omega)
+    double calibration_ms = 0.0;             // host wall time of phase 2 (samples and budgets)
     int64_t pipe_E = 0;
     int pipe_F = 0;
     unsigned int pipe_cap = 0;
@@ -572,6 +578,19 @@ static int clamp_grid(const kadabra_query *q, int64_t count)
     return (int)g;
 }
 
+// An NVTX range (visible to Nsight tools, free otherwise) that also measures
+// its host wall time.
+struct PhaseScope {
+    std::chrono::steady_clock::time_point t0;
+    double *out;
+    PhaseScope(const char *name, double *ms) : t0(std::chrono::steady_clock::now()), out(ms) { nvtxRangePushA(name); }
+    ~PhaseScope()
+    {
+        nvtxRangePop();
+        if (out) *out = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    }
+};
+
 // Phase 1 and the query's device state; no sampling yet.
 static kadabra_status create_query(kadabra_graph *g, const kadabra_params *pin, cudaStream_t st, kadabra_query **out)
 {
@@ -595,6 +614,7 @@ static kadabra_status create_query(kadabra_graph *g, const kadabra_params *pin, 
     q->threads = p.threads;
     q->K = kadabra_sigma_bits(g->n, g->max_degree);
     // phase 1: diameter -> omega
+    PhaseScope scope("kadabra: diameter phase", &q->diameter_ms);
     if (p.vertex_diameter > 0) {
         q->vd = p.vertex_diameter;
     } else {
@@ -735,6 +755,7 @@ extern "C" kadabra_status kadabra_calibrate(kadabra_graph *g, const kadabra_para
         delete q;
         return s;
     }
+    PhaseScope scope("kadabra: calibration phase", &q->calibration_ms);
     // phase 2: calibration samples (stream tag 0) on the device
     kadabra::SampleLaunch a = base_launch(q);
     a.counts = q->d_cal;
@@ -809,6 +830,7 @@ extern "C" kadabra_status kadabra_calibration_finish(kadabra_query *q, void *cud
     KCUDA(cudaMemcpyAsync(&ps, q->d_pipe, sizeof(ps), cudaMemcpyDeviceToHost, st), "read calibration progress");
     KCUDA(cudaStreamSynchronize(st), "synchronise");
     if (ps.done[0] < (unsigned int)q->n_calib) return fail(KADABRA_ERR_STATE, "calibration samples not complete");
+    PhaseScope scope("kadabra: calibration budgets", &q->calibration_ms);
     return finish_calibration(q, st);
 }
 
@@ -944,6 +966,7 @@ static kadabra::QueryDesc make_desc(const kadabra_query *q, kadabra::Counters *l
 extern "C" kadabra_status kadabra_run_pipelined(kadabra_query *q, int64_t epoch_len, int frames, void *cuda_stream)
 {
     KREADY(q);
+    PhaseScope scope("kadabra: pipelined adaptive phase (enqueue)", nullptr);
     kadabra_status s = kadabra_pipeline_begin(q, epoch_len, frames, cuda_stream);
     if (s != KADABRA_OK) return s;
     cudaStream_t st = as_stream(cuda_stream);
@@ -1047,6 +1070,7 @@ extern "C" kadabra_status kadabra_batch_step(kadabra_batch *b, kadabra_query *co
     if (!b || (!qs && count > 0)) return fail(KADABRA_ERR_INVALID_ARG, "batch or queries is null");
     if (count < 0 || count > (int64_t(1) << 20)) return fail(KADABRA_ERR_INVALID_ARG, "count out of range");
     if (count == 0) return KADABRA_OK;
+    PhaseScope scope("kadabra: batch step (enqueue)", nullptr);
     cudaStream_t st = as_stream(cuda_stream);
     std::vector<kadabra::QueryDesc> descs((size_t)count);
     for (int64_t i = 0; i < count; ++i) {
@@ -1400,6 +1424,8 @@ extern "C" kadabra_status kadabra_query_get_info(kadabra_query *q, kadabra_query
     I.stop_ns = j.stopped ? j.stop_ns : 0ULL;
     I.phase = q->phase;
     I.launches = q->launches;
+    I.diameter_ms = q->diameter_ms;
+    I.calibration_ms = q->calibration_ms;
     I.cal_done = q->phase == 2 ? (uint64_t)q->n_calib : 0ULL;
     if (q->phase == 1) {
         kadabra::PipeState ps{};

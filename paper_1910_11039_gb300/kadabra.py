@@ -55,7 +55,7 @@ class QueryInfo(C.Structure):
                 ("slots", C.c_int32), ("threads", C.c_int32), ("offsets_64", C.c_int32),
                 ("budget_classes", C.c_int32), ("stop_ns", C.c_uint64), ("phase", C.c_int32),
                 ("pad0", C.c_int32), ("cal_done", C.c_uint64), ("device_bytes", C.c_uint64),
-                ("launches", C.c_int64)]
+                ("launches", C.c_int64), ("diameter_ms", C.c_double), ("calibration_ms", C.c_double)]
 
 
 class TraceRec(C.Structure):

@@ -394,6 +394,7 @@ def test_vertex_diameter_bound_matches_oracle(K, orc, name):
     G = K.Graph.from_inputs(g)
     q = K.Query(G, eps=0.05, delta=0.1, seed=1, n_calib=10)
     assert q.info().vertex_diameter == orc.vertex_diameter_bound(g)
+    assert q.info().diameter_ms > 0 and q.info().calibration_ms > 0
     if name == "edgeless":
         q.sample_epoch(50)
         assert q.result(btilde=False)["counts"].sum() == 0 and q.info().connected == 0
