@@ -85,16 +85,20 @@ static int bitlen64(uint64_t x) { int b = 0; while (x) { b++; x >>= 1; } return 
 
 static int64_t deg(const int64_t *off, int64_t v) { return off[v + 1] - off[v]; }
 
-/* Largest shift-free sigma width: a layer's sigma values are kept below
- * 2^K + 1, K = min(47 - bitlen(max degree), 63 - bitlen(n)), so that every
- * per-side count (a sum of at most max-degree of them) stays below 2^47 and
- * every meeting-set weight sum fits 128 bits.  This is a reading for the case
- * the paper leaves open (path counts grow exponentially with the distance on
- * grid-like graphs); below 2^K counts are exact, above it a layer is scaled
- * down deterministically (see orc_sample_pair). */
+/* Largest shift-free sigma width K.  Section III-A asks for a shortest s-t
+ * path drawn uniformly, which needs the exact path counts; it does not say
+ * what happens when they outgrow a machine word.  Reading: every per-side
+ * count is an exact uint64.  A layer's counts are kept at most 2^K,
+ * K = min(63 - bitlen(max degree), 63 - bitlen(n)), so that
+ *   - a count of the next layer, a sum of at most max-degree counts of at
+ *     most 2^K each, stays below 2^63 (no 64-bit add can wrap), and
+ *   - a meeting-set weight sum, at most n products of a count below 2^63
+ *     and one of at most 2^K, stays below 2^126 (fits 128 bits).
+ * Below 2^K counts are exact; a layer above it is scaled down
+ * deterministically (see orc_sample_pair). */
 int orc_sigma_bits(int64_t n, int64_t max_degree)
 {
-    int a = 47 - bitlen64((uint64_t)max_degree);
+    int a = 63 - bitlen64((uint64_t)max_degree);
     int b = 63 - bitlen64((uint64_t)n);
     return a < b ? a : b;
 }

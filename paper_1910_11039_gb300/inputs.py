@@ -28,7 +28,7 @@ import numpy as np
 __all__ = [
     "Graph", "csr_from_edges", "largest_component", "er_graph", "rmat_graph",
     "grid_graph", "rgg_graph", "rhg_graph", "path_graph", "star_graph", "cycle_graph",
-    "complete_graph", "full_grid_graph", "config_graph", "CONFIGS",
+    "complete_graph", "full_grid_graph", "layered_graph", "config_graph", "CONFIGS",
     "graph_from_spec", "batched_specs", "SERVING_POOL", "serving_requests",
 ]
 
@@ -286,6 +286,26 @@ def full_grid_graph(rows: int, cols: int) -> Graph:
             if r + 1 < rows:
                 pairs.append((v, v + cols))
     return _from_pairs(rows * cols, pairs, f"fullgrid{rows}x{cols}")
+
+
+def layered_graph(m: int, k: int, hub_leaves: int = 0) -> Graph:
+    """Source 0, then k layers of m vertices with every vertex of a layer
+    joined to every vertex of the next, then the sink 1 + k*m joined to the
+    whole last layer; there are m**k shortest source-sink paths of length
+    k + 1.  With hub_leaves > 0 a separate star (centre 2 + k*m) is added: it
+    raises the maximum degree without touching any source-sink path."""
+    t = 1 + k * m
+    pairs = [(0, 1 + j) for j in range(m)]
+    for layer in range(k - 1):
+        a = 1 + layer * m
+        pairs += [(a + i, a + m + j) for i in range(m) for j in range(m)]
+    pairs += [(1 + (k - 1) * m + j, t) for j in range(m)]
+    n = t + 1
+    if hub_leaves > 0:
+        c = n
+        pairs += [(c, c + 1 + i) for i in range(hub_leaves)]
+        n = c + 1 + hub_leaves
+    return _from_pairs(n, pairs, f"layered{m}x{k}")
 
 
 # Named workloads.  Sizes follow the configurations the library is measured

@@ -175,6 +175,83 @@ def test_grid_sigma_exact_beyond_64_bits(orc):
     assert info.sigma == math.comb(78, 39) and info.sigma > 2**64
 
 
+def test_layered_sigma_matches_enumeration(orc):
+    # m**k shortest paths through k complete layers; networkx enumerates them
+    g = I.layered_graph(3, 5)
+    ws = orc.Workspace(g)
+    t = 1 + 5 * 3
+    interior, info = ws.sample_pair(0, t, 1, 1, 0)
+    assert info.scaled == 0 and info.d == 6
+    assert info.sigma == 3**5 == len(enumerate_paths(to_nx(g), 0, t))
+    check_path(g, 0, t, 6, list(interior), to_nx(g))
+
+
+def test_layered_sigma_exact_above_32_bits(orc):
+    # 18 complete layers of 8 vertices between s and t: 8**18 = 2**54 paths.
+    # Middle layers tie on frontier degree (128), so the s side expands every
+    # layer after its second and its deepest scaled layer (16) holds vertices
+    # with 8**15 = 2**45 paths each.  A separate star of 16384 leaves sets the
+    # maximum degree: K = min(63 - 15, 63 - bitlen(n = 16531)) = 48, so every
+    # per-side count stays an exact 64-bit integer and nothing is scaled.
+    k = 18
+    g = I.layered_graph(8, k, hub_leaves=16384)
+    ws = orc.Workspace(g)
+    assert ws.K == 48
+    t = 1 + k * 8
+    for idx in range(3):
+        interior, info = ws.sample_pair(0, t, 1, 1, idx)
+        assert info.scaled == 0 and info.overflow == 0 and info.d == k + 1
+        assert info.sigma == 8**k
+        # one interior vertex per layer, in any order
+        assert sorted((int(v) - 1) // 8 for v in interior) == list(range(k))
+    # counts kept to 48 bits per side (K = 47 - bitlen(max degree) = 32)
+    # would have scaled these layers and lost the exact count
+    _, narrow = ws.sample_pair(0, t, 1, 1, 0, K=32)
+    assert narrow.scaled == 1 and narrow.sigma != 8**k
+
+
+def test_scaled_sigma_keeps_path_choice_uniform(orc):
+    # Corner to corner of a full 64 x 64 grid every side's middle layers hold
+    # up to C(63, 31) ~ 2**59.7 paths, above 2**K (K = 50), so layers are
+    # scaled.  Rounding a layer's counts up after a shift of sh bits changes
+    # each by a relative 2**(1-K) at most, far below what N samples resolve,
+    # so the crossing point of every anti-diagonal must still follow the
+    # exact law P[path crosses (r, L - r)] = C(L, r) C(D - L, 63 - r) / C(D, 63).
+    k = 64
+    g = I.full_grid_graph(k, k)
+    ws = orc.Workspace(g)
+    assert ws.K == 50
+    D = 2 * (k - 1)
+    t = k * k - 1
+    N = 12000
+    layers = (9, 40, 63, 100)
+    hits = {L: np.zeros(L + 1, dtype=np.int64) for L in layers}
+    scaled = 0
+    for i in range(N):
+        interior, info = ws.sample_pair(0, t, 77, 1, i)
+        scaled += info.scaled
+        rows, cols = np.divmod(interior.astype(np.int64), k)
+        lv = rows + cols
+        for L in layers:
+            sel = np.nonzero(lv == L)[0]
+            assert sel.size == 1
+            hits[L][rows[sel[0]]] += 1
+    assert scaled == N
+    for L in layers:
+        r = np.arange(L + 1)
+        p = np.array([math.comb(L, int(x)) * math.comb(D - L, k - 1 - int(x)) if 0 <= k - 1 - x <= D - L else 0
+                      for x in r], dtype=float) / math.comb(D, k - 1)
+        assert abs(p.sum() - 1) < 1e-12
+        exp = N * p
+        big = exp >= 5
+        obs = np.append(hits[L][big], hits[L][~big].sum())
+        ex = np.append(exp[big], exp[~big].sum())
+        keep = ex > 0
+        chi2 = float((((obs - ex) ** 2)[keep] / ex[keep]).sum())
+        dof = int(keep.sum()) - 1
+        assert chi2 < dof + 6 * math.sqrt(2 * dof) + 10, (L, chi2, dof)
+
+
 def test_grid_sigma_beyond_K_scales_or_flags(orc):
     g = I.full_grid_graph(64, 64)
     ws = orc.Workspace(g)
@@ -311,6 +388,115 @@ def test_stop_functions_limits(orc):
         if prev:
             assert g < prev[1] and f <= prev[0]
         prev = (f, g)
+
+
+def _largest_root(h, lo, hi, iters=400):
+    """Bisection for the largest root of h on [lo, hi] (h(lo) <= 0 < h(hi))."""
+    for _ in range(iters):
+        mid = (lo + hi) / 2
+        if h(mid) <= 0:
+            lo = mid
+        else:
+            hi = mid
+    return lo
+
+
+def test_stop_functions_solve_the_deviation_bound(orc):
+    # f and g are the deviations at which the one-sided tail bound of the
+    # adaptive martingale argument, exp(-lam^2 / (2 (omega b + lam / 3))) with
+    # lam = tau * deviation, equals delta_L resp. delta_U = exp(-L), taking the
+    # unknown b at the far end of the interval: b = b~ - f for the lower
+    # deviation, b = b~ + g for the upper one.  So tau f is the largest root
+    # of lam^2 = 2 L (omega (b~ - lam / tau) + lam / 3), and tau g that of
+    # lam^2 = 2 L (omega (b~ + lam / tau) + lam / 3).  Solved here by 50-digit
+    # bisection on that equation, not by the closed form.
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 50
+    rng = np.random.default_rng(5)
+    for _ in range(300):
+        tau = int(rng.integers(10, 10**7))
+        omega = float(tau * rng.uniform(0.2, 20.0))
+        c = int(rng.integers(0, tau + 1)) if rng.random() < 0.8 else int(rng.integers(0, 4))
+        LL = float(rng.uniform(2.0, 40.0))
+        LU = float(rng.uniform(2.0, 40.0))
+        f, g = orc.stop_functions(c, tau, omega, LL, LU)
+        T, W, bt = mp.mpf(tau), mp.mpf(omega), mp.mpf(c) / mp.mpf(tau)
+        for val, L, sign in ((f, mp.mpf(LL), -1), (g, mp.mpf(LU), +1)):
+            h = lambda lam, L=L, sign=sign: lam**2 - 2 * L * (W * (bt + sign * lam / T) + lam / 3)
+            hi = mp.mpf(1)
+            while h(hi) <= 0:
+                hi *= 2
+            lam = _largest_root(h, mp.mpf(0), hi)
+            exact = lam / T
+            # the closed form's evaluation order loses digits to cancellation
+            # only relative to the size of its terms
+            scale = (L / T) * (abs(mp.mpf(1) / 3 + sign * W / T) + mp.sqrt((mp.mpf(1) / 3 + sign * W / T) ** 2
+                                                                             + 2 * bt * W / L))
+            assert abs(mp.mpf(val) - exact) <= 1e-14 * scale + mp.mpf(10) ** -300, (c, tau, omega, L, sign)
+            # the bound itself: at the computed deviation the tail equals exp(-L)
+            if exact > 0:
+                tail = lam**2 / (2 * (W * (bt + sign * lam / T) + lam / 3))
+                assert abs(tail - L) <= mp.mpf(10) ** -30 * L
+
+
+@pytest.mark.parametrize("eps,delta,vd,hand", [
+    # (0.5 / eps^2) * (floor(log2(VD - 2)) + 1 + ln(2 / delta)), terms by hand:
+    # VD - 2 = 8: floor(log2 8) = 3; ln 20 = 2.995732273553991; 50 * 6.995732273553991
+    (0.1, 0.1, 10, 349.78661367769955),
+    # VD - 2 = 10: floor(log2 10) = 3; 5000 * 6.995732273553991
+    (0.01, 0.1, 12, 34978.66136776995),
+    # VD - 2 = 1: floor(log2 1) = 0; 200 * 3.995732273553991
+    (0.05, 0.1, 3, 799.1464547107982),
+    # VD - 2 = 0 is clamped to 1 (a graph with one edge)
+    (0.05, 0.1, 2, 799.1464547107982),
+    # VD - 2 = 793 (roadNet-PA, D = 794): floor(log2 793) = 9; 500000 * 12.995732273553991
+    (0.001, 0.1, 795, 6497866.136776996),
+    # VD - 2 = 128: floor(log2 128) = 7; ln 200 = 5.298317366548036; 1250 * 13.298317366548036
+    (0.02, 0.01, 130, 16622.896708185045),
+])
+def test_omega_hand_values(orc, eps, delta, vd, hand):
+    # omega with the constant c = 1 instead of 1/2, or ln(1/delta) instead of
+    # ln(2/delta), or log2 without the floor, misses these by far more than
+    # rounding
+    assert orc.omega(eps, delta, vd) == pytest.approx(hand, rel=1e-14)
+
+
+def test_balanced_rule_single_class_closed_form(orc):
+    # one vertex with calibration count 4 of n_cal = 100, nine with none:
+    # the budget (1 - beta) delta / 4 is spent on that vertex alone, so the
+    # constant solves exp(-C eps^2 n_cal / 4) = (1 - beta) delta / 4, i.e.
+    # C* = 4 / (eps^2 n_cal) * ln(4 / ((1 - beta) delta)); bisection returns
+    # the upper end of an interval shorter than eps / 10 that holds C*.
+    eps, delta, beta, ncal = 0.05, 0.1, 1e-3, 100
+    cal = np.zeros(10, dtype=np.uint32)
+    cal[0] = 4
+    LL, LU, C = orc.calibrate_L(cal, ncal, eps, delta, rule=1, beta=beta)
+    Cstar = 4 / (eps**2 * ncal) * math.log(4 / ((1 - beta) * delta))
+    assert Cstar <= C <= Cstar + eps / 10
+    floor = beta * delta / (4 * 10)
+    np.testing.assert_allclose(LL[1:], -math.log(floor), rtol=1e-15)
+    assert LL[0] == pytest.approx(-math.log(math.exp(-C * eps**2 / 0.04) + floor), rel=1e-15)
+    np.testing.assert_array_equal(LU, LL)
+
+
+def test_balanced_rule_two_classes_root(orc):
+    # two classes: h1 vertices with count c1 and h2 with count c2 of n_cal;
+    # C* is the root of h1 exp(-C eps^2 n_cal / c1) + h2 exp(-C eps^2 n_cal / c2)
+    # = (1 - beta) delta / 4, found here by 50-digit bisection
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 50
+    eps, delta, beta, ncal = 0.02, 0.1, 1e-3, 2000
+    cal = np.zeros(5000, dtype=np.uint32)
+    cal[:3] = 150
+    cal[3:40] = 7
+    LL, LU, C = orc.calibrate_L(cal, ncal, eps, delta, rule=1, beta=beta)
+    B = (1 - mp.mpf(beta)) * mp.mpf(delta) / 4
+    e2n = mp.mpf(eps) ** 2 * ncal
+    h = lambda x: B - (3 * mp.exp(-x * e2n / 150) + 37 * mp.exp(-x * e2n / 7))
+    Cstar = _largest_root(h, mp.mpf(0), mp.mpf(10) ** 6)
+    assert Cstar <= C <= Cstar + eps / 10
+    total = float(np.exp(-LL).sum() + np.exp(-LU).sum())
+    assert total <= delta / 2
 
 
 def test_check_stop_at_omega(orc):
