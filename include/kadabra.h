@@ -44,7 +44,7 @@ typedef enum kadabra_status {
     KADABRA_ERR_TIMEOUT = 6,          /* a bounded device wait gave up            */
     KADABRA_ERR_STATE = 7,            /* call out of order (e.g. result before run)*/
     KADABRA_ERR_NO_DEVICE = 8,        /* no CUDA device / library built without it */
-    KADABRA_ERR_DEPTH = 9             /* a BFS side needed more than 65533 layers  */
+    KADABRA_ERR_DEPTH = 9             /* reserved (BFS levels are 32-bit; unused)  */
 } kadabra_status;
 
 typedef struct kadabra_graph kadabra_graph;
@@ -160,12 +160,15 @@ kadabra_status kadabra_validate_csr(int64_t n, int64_t nnz, const void *offsets,
  * Writes NaN and returns KADABRA_ERR_INVALID_ARG for eps or delta outside (0,1). */
 kadabra_status kadabra_omega(double eps, double delta, int64_t vertex_diameter, double *omega);
 
-/* K = min(47 - bitlen(max_degree), 63 - bitlen(n)): per-side path counts up
- * to 2^K are exact; a BFS layer whose largest count exceeds 2^K has all its
- * counts shifted right by the excess (rounding up, so they stay >= 1), which
- * keeps every per-side count below 2^47 and every meeting-set weight sum
- * within 128 bits.  The paper does not say how counts beyond a machine word
- * are handled; this is the library's reading. */
+/* K = min(63 - bitlen(max_degree), 63 - bitlen(n)).  Section III-A samples
+ * a shortest s-t path uniformly, which needs exact path counts; the paper does
+ * not say how counts beyond a machine word are handled.  This library's
+ * reading: every per-side path count is an exact uint64.  Counts up to 2^K
+ * are exact; a BFS layer whose largest count exceeds 2^K has all its counts
+ * shifted right by the excess (rounding up, so they stay >= 1).  Then a count
+ * of the next layer (a sum of at most max_degree counts) stays below 2^63, so
+ * no 64-bit addition can wrap (each is checked all the same), and every
+ * meeting-set weight sum fits 128 bits. */
 int kadabra_sigma_bits(int64_t n, int64_t max_degree);
 
 /* Device global timer (ns; the clock of kadabra_query_info.stop_ns), read by a
@@ -413,10 +416,16 @@ kadabra_status kadabra_launch_log(kadabra_query *q, int64_t max_entries, kadabra
  * allocated.  Graphs need n * 36 bytes per in-flight sample, so n must satisfy
  * n * 36 <= KADABRA_STATIC_SCRATCH_BYTES - 256 (else KADABRA_ERR_INVALID_ARG),
  * and fewer samples run in parallel as n grows.
- * The first call on a device looks up the array's device address (make that
- * first call before any stream capture).  All calls share the array: calls
- * that overlap on the GPU race and must be serialised by the caller.
- * Synchronises `cuda_stream` and reports device errors. */
+ * Set-up: CUDA loads device code lazily, and the array is reserved on a
+ * device only when its code is first loaded there.  kadabra_graph_load does
+ * that set-up on the graph's device (it looks up the array's address, which
+ * loads the code and reserves the 64 MiB), so a call here with a loaded graph
+ * neither loads code nor reserves memory.  Each call looks the address up
+ * again (cheap once loaded).  All calls share the array and each call clears
+ * the part it uses before it samples: calls that overlap on the GPU race and
+ * must be serialised by the caller.
+ * count must be in [0, 2^32).  Synchronises `cuda_stream` and reports device
+ * errors. */
 kadabra_status kadabra_sample_static(const kadabra_graph *g, uint64_t seed, int tag, uint64_t first, int64_t count,
                                      uint32_t *counts, void *cuda_stream);
 

@@ -121,13 +121,14 @@ __global__ void clock_kernel(unsigned long long *out)
     *out = now;
 }
 
-__global__ void reset_job_kernel(Job *job)
+__global__ void reset_job_kernel(Job *job, unsigned long long tau)
 {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         Job z;
         unsigned char *p = reinterpret_cast<unsigned char *>(&z);
         for (size_t i = 0; i < sizeof(Job); ++i) p[i] = 0;
         z.stop_epoch = -1;
+        z.tau = tau;
         *job = z;
     }
 }
@@ -283,9 +284,9 @@ cudaError_t launch_batch_poll(const QueryDesc *d, int nq, int *out, cudaStream_t
     return cudaGetLastError();
 }
 
-cudaError_t launch_reset_job(Job *job, cudaStream_t st)
+cudaError_t launch_reset_job(Job *job, cudaStream_t st, unsigned long long tau)
 {
-    reset_job_kernel<<<1, 32, 0, st>>>(job);
+    reset_job_kernel<<<1, 32, 0, st>>>(job, tau);
     return cudaGetLastError();
 }
 

@@ -278,7 +278,7 @@ extern "C" kadabra_status kadabra_omega(double eps, double delta, int64_t vertex
 
 extern "C" int kadabra_sigma_bits(int64_t n, int64_t max_degree)
 {
-    const int a = 47 - bitlen64((uint64_t)max_degree);
+    const int a = 63 - bitlen64((uint64_t)max_degree);
     const int b = 63 - bitlen64((uint64_t)n);
     return a < b ? a : b;
 }
@@ -430,6 +430,9 @@ extern "C" kadabra_status kadabra_graph_load(int64_t n, int64_t nnz, const void 
     if (dev) g->max_degree = (int64_t)md;
     cudaFree(d_md);
     cudaFree(d_cols_tmp);
+    // reserve kadabra_sample_static's array on this device now, so that
+    // sampling from this graph there later loads and reserves nothing
+    if (e == cudaSuccess) e = kadabra::static_scratch_reserve();
     if (e != cudaSuccess) {
         free_graph_device(g);
         delete g;
@@ -459,7 +462,7 @@ extern "C" kadabra_status kadabra_graph_info(const kadabra_graph *g, int64_t *n,
     return KADABRA_OK;
 }
 
-// Sampling scratch: slots * n * (16 B record + 4 B queue entry).
+// Sampling scratch: slots * (n * (32 B record + 4 B queue entry) + 2 reached-bit maps of n bits).
 static kadabra_status ensure_workspace(kadabra_graph *g, int want_slots, int threads, double fraction)
 {
     int dev = 0, sms = 0, per_sm = 0;
@@ -545,8 +548,6 @@ static kadabra_status device_error_status(const Job &j)
         return fail(KADABRA_ERR_INVALID_ARG, "a sampled path had more interior vertices than VD - 2 (vertex diameter bound too small)");
     if (j.error & kadabra::kErrTimeout)
         return fail(KADABRA_ERR_TIMEOUT, "a pipelined launch gave up waiting for a free counter frame");
-    if (j.error & kadabra::kErrDepth)
-        return fail(KADABRA_ERR_DEPTH, "a BFS side needed more than 65533 layers (16-bit levels)");
     if (j.error & (kadabra::kErrAddOverflow | kadabra::kErrSelect))
         return fail(KADABRA_ERR_CUDA, "internal sampling invariant violated (error bits " + std::to_string(j.error) + ")");
     return KADABRA_OK;
@@ -1510,7 +1511,7 @@ extern "C" kadabra_status kadabra_sample_trace(kadabra_query *q, int tag, uint64
     cudaFree(d_tr);
     cudaFree(d_path);
     if (e != cudaSuccess) return cuda_fail(e, "trace run");
-    return (j.error & ~(kadabra::kErrSigmaOverflow | kadabra::kErrDepth)) ? device_error_status(j) : KADABRA_OK;
+    return (j.error & ~kadabra::kErrSigmaOverflow) ? device_error_status(j) : KADABRA_OK;
 }
 
 extern "C" kadabra_status kadabra_launch_log(kadabra_query *q, int64_t max_entries, kadabra_launch_stats *out,

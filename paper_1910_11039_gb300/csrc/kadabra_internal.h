@@ -8,21 +8,24 @@ struct kadabra_graph;
 
 namespace kadabra {
 
-// Per-vertex sampling state of one in-flight sample (one "slot"): one 64-bit
-// word per BFS side, word = sigma << 16 | level, where
-//   level = BFS distance + 1 from that side's source (0 = not reached; at most
-//           0xffff, so a side explores at most 65533 layers),
-//   sigma = number of shortest paths from that side's source (< 2^47 by the
-//           choice of K, so additions of sigma << 16 never carry out).
-// A first discovery claims the vertex and sets its count with one CAS.
+// Per-vertex sampling state of one in-flight sample (one "slot"), per BFS side:
+//   lvl[side] = BFS distance + 1 from that side's source (0 = not reached);
+//   sig[side] = number of shortest paths from that side's source, an exact
+//               uint64: a layer's counts are kept at most 2^K with
+//               K <= 63 - bitlen(max degree), so a count of the next layer (a
+//               sum of at most max-degree of them) stays below 2^63.
+// A first discovery claims the vertex with a CAS on its level; every
+// contribution to the path count, the first included, is an atomic add.
 // Invariant between samples: every record of a slot is all-zero (the sample
 // that touched a record clears it before the slot takes its next sample).
-// A record fills one 32-byte sector (16 bytes of padding): records of
-// different vertices never share a sector, and the clearing store writes the
-// whole sector, so the cache does not read the sector back from DRAM first.
+// A record fills one 32-byte sector: records of different vertices never
+// share a sector, the two levels come in one 8-byte load and the two counts
+// in one 16-byte load, and the clearing store writes the whole sector, so the
+// cache does not read the sector back from DRAM first.
 struct alignas(32) SlotRec {
-    unsigned long long w[2];
-    unsigned long long pad[2];
+    unsigned int lvl[2];
+    unsigned int pad[2];
+    unsigned long long sig[2];
 };
 static_assert(sizeof(SlotRec) == 32, "SlotRec fills a 32-byte sector");
 
@@ -42,10 +45,10 @@ struct Counters {
 // Device-resident state of one sample stream (adaptive, calibration, trace).
 struct Job {
     unsigned long long tau;        // samples already taken by this stream
-    unsigned int work;             // next sample offset inside the running launch
+    unsigned long long work;       // next sample offset inside the running launch (64-bit: every
+                                   // CTA takes one offset past the end, so it reaches count + grid)
     unsigned int done_ctas;        // CTAs that finished the running launch
     int stopped;                   // stop flag (adaptive stream)
-    int pad0;
     long long epoch;               // checks run so far
     long long stop_epoch;          // check that stopped, -1 if none
     unsigned long long maxf_bits;  // running maxima of the check in flight
@@ -64,7 +67,7 @@ enum : unsigned int {
     kErrAddOverflow = 2u,      // a 64-bit path-count add wrapped (never expected)
     kErrCounterOverflow = 4u,  // a 32-bit c~ counter wrapped
     kErrSelect = 8u,           // weighted choice found no element (never expected)
-    kErrDepth = 16u,           // a BFS side would exceed 65533 layers (16-bit levels)
+    kErrDepth = 16u,           // reserved: levels are 32-bit, so no side can run out of them
     kErrTimeout = 32u,         // a bounded wait for a free counter frame gave up
     kErrLogOverflow = 64u,     // an epoch log overflowed (a path longer than VD - 2)
 };
@@ -210,10 +213,11 @@ int set_last_error(int status, const char *msg);
 
 // Allocation-free sampling (sample_static.cu).
 cudaError_t static_scratch_address(void **out);
-cudaError_t launch_static_job_init(Job *job, unsigned long long first, cudaStream_t st);
+cudaError_t static_scratch_reserve();
 cudaError_t launch_result(int64_t n, const uint32_t *counts, const Job *job, double *btilde,
                           cudaStream_t st);
-cudaError_t launch_reset_job(Job *job, cudaStream_t st);
+// Job record reset to its start state (tau = `tau`, no stop, no error).
+cudaError_t launch_reset_job(Job *job, cudaStream_t st, unsigned long long tau = 0);
 cudaError_t read_device_clock(unsigned long long *ns, cudaStream_t st);
 cudaError_t launch_batch_poll(const QueryDesc *d, int nq, int *out, cudaStream_t st);
 cudaError_t launch_cal_max(int64_t n, const uint32_t *cal, unsigned int *mx, cudaStream_t st);

@@ -19,8 +19,8 @@
 //   the last CTA of the launch advances tau (A5: stream order makes the
 //   counter vector at the next kernel a consistent snapshot).
 //
-// Layout in HBM (per slot): SlotRec[n] (32 B per vertex, one sector: for each
-// side one word holding the path count and the BFS level, then padding), a
+// Layout in HBM (per slot): SlotRec[n] (32 B per vertex, one sector: the two
+// sides' 32-bit BFS levels, padding, the two sides' exact 64-bit path counts), a
 // uint32 queue of n entries shared by both sides (s-side grows from the front,
 // t-side from the back; the balls are disjoint until they meet, so n entries
 // always suffice) and, for each side, one reached bit per vertex.  Records
@@ -31,8 +31,8 @@
 // entries to threads by a block-wide prefix sum over the frontier's degrees
 // (every thread gets the same share whatever the degree skew) and keeps
 // kUnroll entries per thread in flight: their column ids, then their
-// (level_s, level_t) pairs (one 16-byte load), then the claims, then the
-// path-count additions (waited on once per batch).
+// (level_s, level_t) pairs (one 8-byte load), then the claims and the
+// path-count additions, issued together and waited on once per batch.
 //
 // The last layer: as soon as a target of the layer is found on the other
 // side, the layer is the last one and only meeting vertices need records;
@@ -72,19 +72,19 @@ __device__ __forceinline__ unsigned long long ldcg(const unsigned long long *p) 
 
 __device__ __forceinline__ int bitlen64(unsigned long long x) { return 64 - __clzll(x); }
 
-// record words: sigma << 16 | level
-__device__ __forceinline__ unsigned int lvl_of(unsigned long long w) { return (unsigned int)(w & 0xffffULL); }
-__device__ __forceinline__ unsigned long long sig_of(unsigned long long w) { return w >> 16; }
-__device__ __forceinline__ unsigned long long pack(unsigned int lvl, unsigned long long sig)
+// both sides' levels of a record, one 8-byte load from L2
+__device__ __forceinline__ void load_lvls(const SlotRec *r, unsigned int &l0, unsigned int &l1)
 {
-    return (sig << 16) | (unsigned long long)lvl;
+    const uint2 v = __ldcg(reinterpret_cast<const uint2 *>(r->lvl));
+    l0 = v.x;
+    l1 = v.y;
 }
-// both sides' words of a record, one 16-byte load from L2
-__device__ __forceinline__ void load_rec(const SlotRec *r, unsigned long long &w0, unsigned long long &w1)
+// both sides' path counts of a record, one 16-byte load from L2
+__device__ __forceinline__ void load_sigs(const SlotRec *r, unsigned long long &p, unsigned long long &q)
 {
-    const uint4 v = __ldcg(reinterpret_cast<const uint4 *>(r));
-    w0 = (unsigned long long)v.x | ((unsigned long long)v.y << 32);
-    w1 = (unsigned long long)v.z | ((unsigned long long)v.w << 32);
+    const ulonglong2 v = __ldcg(reinterpret_cast<const ulonglong2 *>(r->sig));
+    p = v.x;
+    q = v.y;
 }
 
 __device__ __forceinline__ unsigned long long global_ns()
@@ -118,7 +118,7 @@ struct Smem {
     unsigned int lbeg[2][kMaxLayers];// queue range of layer k of each side (k < kMaxLayers)
     unsigned int lend[2][kMaxLayers];
     int X;                           // side expanded this layer
-    int status;                      // 0 running, 1 met, 2 disconnected, 3 strict overflow, 4 too deep,
+    int status;                      // 0 running, 1 met, 2 disconnected, 3 strict overflow,
                                      // 5 discarded (its query stopped)
     int scaled;
     unsigned int err;
@@ -139,7 +139,7 @@ struct Smem {
     long long chosen;
     long long next_v;
     int found;
-    unsigned int cur;                // work item taken by this CTA
+    unsigned long long cur;          // work item taken by this CTA
     // back-walk: vertices found so far (flushed to the sink by warp 0) and
     // the state handed between warp 0's steps and the whole CTA's steps
     unsigned int path[kPathCap];
@@ -477,8 +477,10 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
         if (t >= s) ++t;
         sh.s = (long long)s;
         sh.t = (long long)t;
-        __stcg(&rec[s].w[0], pack(1u, 1ULL));
-        __stcg(&rec[t].w[1], pack(1u, 1ULL));
+        __stcg(&rec[s].lvl[0], 1u);
+        __stcg(&rec[s].sig[0], 1ULL);
+        __stcg(&rec[t].lvl[1], 1u);
+        __stcg(&rec[t].sig[1], 1ULL);
         if (bits) {
             atomicOr(&bits[s >> 5], 1u << (s & 31));
             atomicOr(&bits[bw + (t >> 5)], 1u << (t & 31));
@@ -528,7 +530,7 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
                 const unsigned int u = qget(queue, n, X, i);
                 b = G.begin(u);
                 d = (unsigned long long)(G.end(u) - b);
-                sg = sig_of(ldcg(&rec[u].w[X]));
+                sg = ldcg(&rec[u].sig[X]);
             }
             unsigned long long total;
             const unsigned long long excl = block_excl_scan<NT>(d, &total, sh);
@@ -566,7 +568,7 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
                         dw[j] = c.y;
                     }
                 }
-                // phase 2: (level_s, level_t) of every target, one 16-byte load
+                // phase 2: (level_s, level_t) of every target, one 8-byte load
                 // each; once the layer is known to be the last, only the other
                 // side's reached bit (a dense map that stays in L2): targets
                 // without it are skipped, targets with it are claimed or counted
@@ -589,10 +591,10 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
                     for (int j = 0; j < kUnroll; ++j) {
                         lx[j] = 1u;
                         if (w[j] != kNone) {
-                            unsigned long long w0, w1;
-                            load_rec(rec + w[j], w0, w1);
-                            lx[j] = lvl_of(X ? w1 : w0);
-                            ymask |= (lvl_of(X ? w0 : w1) != 0 ? 1u : 0u) << j;
+                            unsigned int l0, l1;
+                            load_lvls(rec + w[j], l0, l1);
+                            lx[j] = X ? l1 : l0;
+                            ymask |= ((X ? l0 : l1) != 0 ? 1u : 0u) << j;
                         }
                     }
                 }
@@ -604,32 +606,42 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
                 for (int j = 0; j < kUnroll; ++j)
                     if (w[j] != kNone && lx[j] == 0 && ((ymask >> j) & 1u)) *(volatile int *)&sh.meets = 1;
                 const bool last = *(volatile int *)&sh.meets != 0;
-                // phase 3: claim unseen targets for the new layer; the claim
-                // stores the level and the first path-count contribution at once
+                // phase 3: claim unseen targets for the new layer (a CAS on the
+                // level) and add the source's path count to every target of
+                // the new layer.  A target read as unseen can only have been
+                // claimed for this layer since (by this CTA), so its count gets
+                // the addition whoever wins the claim: claim and addition are
+                // issued back to back.  The additions return their old value,
+                // so a thread has waited for all of them before the layer's
+                // closing barrier and every count is complete when any thread
+                // reads it next.
                 unsigned int cmask = 0;
+                unsigned int old_l[kUnroll];
+                unsigned long long old_s[kUnroll];
 #pragma unroll
                 for (int j = 0; j < kUnroll; ++j) {
+                    old_l[j] = kNone;
                     if (w[j] != kNone && lx[j] == 0 && (!last || ((ymask >> j) & 1u))) {
-                        const unsigned long long su = sh.u.ex.csig[own[j]];
-                        const unsigned long long old = atomicCAS(&rec[w[j]].w[X], 0ULL, pack(nl, su));
-                        if (old == 0) {
-                            cmask |= 1u << j;
-                            my_max = su > my_max ? su : my_max;
-                        }
-                        lx[j] = old == 0 ? nl : lvl_of(old);
+                        old_l[j] = atomicCAS(&rec[w[j]].lvl[X], 0u, nl);
+                        old_s[j] = atomicAdd(&rec[w[j]].sig[X], sh.u.ex.csig[own[j]]);
+                    } else if (w[j] != kNone && lx[j] == nl) {
+                        old_l[j] = nl;
+                        old_s[j] = atomicAdd(&rec[w[j]].sig[X], sh.u.ex.csig[own[j]]);
                     }
                 }
-                // phase 4: path counts of targets in the new layer; the additions
-                // return their old value, so a thread has waited for all of them
-                // before the layer's closing barrier and every count is complete
-                // when any thread reads it next
 #pragma unroll
                 for (int j = 0; j < kUnroll; ++j) {
-                    if (w[j] != kNone && lx[j] == nl && !((cmask >> j) & 1u)) {
-                        const unsigned long long su = sh.u.ex.csig[own[j]];
-                        const unsigned long long nv = sig_of(atomicAdd(&rec[w[j]].w[X], su << 16)) + su;
-                        my_max = nv > my_max ? nv : my_max;
+                    if (old_l[j] == kNone) continue;
+                    if (old_l[j] == 0u) {
+                        cmask |= 1u << j;
+                    } else if (old_l[j] != nl) {
+                        atomicOr(&sh.err, kErrSelect);     // broken invariant: never expected
+                        continue;
                     }
+                    const unsigned long long su = sh.u.ex.csig[own[j]];
+                    const unsigned long long nv = old_s[j] + su;
+                    if (nv < su) atomicOr(&sh.err, kErrAddOverflow);     // excluded by the choice of K
+                    my_max = nv > my_max ? nv : my_max;
                 }
                 // phase 5: claimed targets join the new frontier (warp-aggregated
                 // queue slots) or, if the other side already holds them, the
@@ -703,7 +715,6 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
                 }
                 // the next layer: side with the smaller frontier degree sum (ties: s)
                 const int Xn = (sh.fdeg[0] <= sh.fdeg[1]) ? 0 : 1;
-                if (sh.status == 0 && sh.layer[Xn] + 2u > 0xffffu) sh.status = 4;   // levels are 16-bit
                 if (sh.status == 0) {
                     sh.X = Xn;
                     sh.new_count = 0;
@@ -721,8 +732,8 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
             {
                 for (unsigned int i = sh.fbeg[X] + tid; i < sh.fend[X]; i += NT) {
                     const unsigned int v = qget(queue, n, X, i);
-                    const unsigned long long wv = ldcg(&rec[v].w[X]);
-                    __stcg(&rec[v].w[X], pack(lvl_of(wv), ((sig_of(wv) - 1ULL) >> shv) + 1ULL));
+                    const unsigned long long sv = ldcg(&rec[v].sig[X]);
+                    __stcg(&rec[v].sig[X], ((sv - 1ULL) >> shv) + 1ULL);
                 }
                 __syncthreads();
             }
@@ -751,9 +762,8 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
                 const unsigned int id = have ? sh.cand[lane] : 0xffffffffu;
                 unsigned long long lo = 0, hi = 0;
                 if (have) {
-                    unsigned long long w0, w1;
-                    load_rec(rec + id, w0, w1);
-                    const unsigned long long p = sig_of(w0), q = sig_of(w1);
+                    unsigned long long p, q;
+                    load_sigs(rec + id, p, q);
                     lo = p * q;
                     hi = __umul64hi(p, q);
                 }
@@ -790,8 +800,8 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
                 if (lane == 0) {
                     sh.sig_lo = alo;
                     sh.sig_hi = ahi;
-                    const bool ok = chosen >= 0 && chosen < n && lvl_of(ldcg(&rec[chosen].w[X])) == nl &&
-                                    lvl_of(ldcg(&rec[chosen].w[Y])) != 0;
+                    const bool ok = chosen >= 0 && chosen < n && ldcg(&rec[chosen].lvl[X]) == nl &&
+                                    ldcg(&rec[chosen].lvl[Y]) != 0;
                     sh.chosen = ok ? chosen : -1;
                     if (!ok) sh.err |= kErrSelect;
                 }
@@ -801,9 +811,8 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
             if (in_smem) {
                 for (unsigned int i = tid; i < mcnt; i += NT) {
                     const unsigned int w = sh.cand[i];
-                    unsigned long long w0, w1;
-                    load_rec(rec + w, w0, w1);
-                    const unsigned long long p = sig_of(w0), q = sig_of(w1);
+                    unsigned long long p, q;
+                    load_sigs(rec + w, p, q);
                     const unsigned long long lo = p * q, hi = __umul64hi(p, q);
                     sh.wlo[i] = lo;
                     sh.whi[i] = hi;
@@ -812,10 +821,9 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
             } else {
                 for (unsigned int i = sh.fbeg[Y] + tid; i < sh.fend[Y]; i += NT) {
                     const unsigned int w = qget(queue, n, Y, i);
-                    unsigned long long w0, w1;
-                    load_rec(rec + w, w0, w1);
-                    if (lvl_of(X ? w1 : w0) != nl) continue;
-                    const unsigned long long p = sig_of(w0), q = sig_of(w1);
+                    if (ldcg(&rec[w].lvl[X]) != nl) continue;
+                    unsigned long long p, q;
+                    load_sigs(rec + w, p, q);
                     add128(tlo, thi, p * q, __umul64hi(p, q));
                 }
             }
@@ -847,16 +855,15 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
                     c = radix_choose<NT>(sh, npass, [&](auto &&add) {
                         for (unsigned int i = yb + tid; i < ye; i += NT) {
                             const unsigned int w = qget(queue, n, Y, i);
-                            unsigned long long w0, w1;
-                            load_rec(rec + w, w0, w1);
-                            if (lvl_of(X ? w1 : w0) != nl) continue;
-                            const unsigned long long p = sig_of(w0), q = sig_of(w1);
+                            if (ldcg(&rec[w].lvl[X]) != nl) continue;
+                            unsigned long long p, q;
+                            load_sigs(rec + w, p, q);
                             add(w, p * q, __umul64hi(p, q));
                         }
                     });
                 }
                 if (tid == 0) {
-                    const bool ok = c >= 0 && c < n && lvl_of(ldcg(&rec[c].w[X])) == nl && lvl_of(ldcg(&rec[c].w[Y])) != 0;
+                    const bool ok = c >= 0 && c < n && ldcg(&rec[c].lvl[X]) == nl && ldcg(&rec[c].lvl[Y]) != 0;
                     sh.chosen = ok ? c : -1;
                     if (!ok) sh.err |= kErrSelect;
                 }
@@ -877,12 +884,12 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
         // walk towards s (side 0), then towards t (side 1); draws 2, 3, ...
         unsigned long long k = 2;
         bool walk_ok = w >= 0;
-        unsigned long long ww0 = 0, ww1 = 0;
-        if (walk_ok) load_rec(rec + w, ww0, ww1);
+        unsigned int ww0 = 0, ww1 = 0;
+        if (walk_ok) load_lvls(rec + w, ww0, ww1);
         for (int Z = 0; Z < 2 && walk_ok; ++Z) {
             long long v = w;
             const long long src = Z == 0 ? sh.s : sh.t;
-            unsigned int lz = lvl_of(Z == 0 ? ww0 : ww1);   // level code of v on side Z
+            unsigned int lz = Z == 0 ? ww0 : ww1;   // level code of v on side Z
             for (;;) {
                 // Warp 0 alone takes every step from a vertex of degree <= 32
                 // (lanes hold its neighbours) and every step whose predecessor
@@ -923,10 +930,11 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
                         unsigned long long wt = 0;
                         if (tid < dd) {
                             u = G.col(bb + tid);
-                            const unsigned long long wu = ldcg(&rec[u].w[Z]);
+                            const unsigned int lu = ldcg(&rec[u].lvl[Z]);
+                            const unsigned long long su = ldcg(&rec[u].sig[Z]);
                             ub = G.begin(u);
                             ue = G.end(u);
-                            if (lvl_of(wu) == tg) wt = sig_of(wu);
+                            if (lu == tg) wt = su;
                         }
                         unsigned long long incl = wt;
 #pragma unroll
@@ -1007,7 +1015,7 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
                             if (isadj) {
                                 const unsigned int p = atomicAdd(&sh.pcnt, 1u);
                                 sh.cand[p] = u;
-                                sh.wlo[p] = sig_of(ldcg(&rec[u].w[Z]));
+                                sh.wlo[p] = ldcg(&rec[u].sig[Z]);
                                 sh.whi[p] = 0;
                             }
                         }
@@ -1040,8 +1048,9 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
                         unsigned long long wt = 0;
                         if (tid < d) {
                             u = G.col(b + tid);
-                            const unsigned long long wu = ldcg(&rec[u].w[Z]);
-                            if (lvl_of(wu) == target) wt = sig_of(wu);
+                            const unsigned int lu = ldcg(&rec[u].lvl[Z]);
+                            const unsigned long long su = ldcg(&rec[u].sig[Z]);
+                            if (lu == target) wt = su;
                         }
                         unsigned long long total;
                         const unsigned long long ex = block_excl_scan<NT>(wt, &total, sh);
@@ -1058,13 +1067,14 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
                         unsigned long long part = 0;
                         for (long long j = tid; j < d; j += NT) {
                             const long long u = G.col(b + j);
-                            const unsigned long long wu = ldcg(&rec[u].w[Z]);
-                            if (lvl_of(wu) == target) {
-                                part += sig_of(wu);
+                            const unsigned int lu = ldcg(&rec[u].lvl[Z]);
+                            const unsigned long long su = ldcg(&rec[u].sig[Z]);
+                            if (lu == target) {
+                                part += su;
                                 const unsigned int p = atomicAdd(&sh.pcnt, 1u);
                                 if (p < (unsigned int)kMeetCap) {
                                     sh.cand[p] = (unsigned int)u;
-                                    sh.wlo[p] = sig_of(wu);
+                                    sh.wlo[p] = su;
                                 }
                             }
                         }
@@ -1098,8 +1108,9 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
                             unsigned long long wt = 0;
                             if (j < d) {
                                 u = G.col(b + j);
-                                const unsigned long long wu = ldcg(&rec[u].w[Z]);
-                                if (lvl_of(wu) == target) wt = sig_of(wu);
+                                const unsigned int lu = ldcg(&rec[u].lvl[Z]);
+                                const unsigned long long su = ldcg(&rec[u].sig[Z]);
+                                if (lu == target) wt = su;
                             }
                             unsigned long long ctot;
                             const unsigned long long ex = carry + block_excl_scan<NT>(wt, &ctot, sh);
@@ -1114,7 +1125,7 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
                         }
                     }
                     v = sh.next_v;
-                    if (v < 0 || v >= n || lvl_of(ldcg(&rec[v].w[Z])) != target) {
+                    if (v < 0 || v >= n || ldcg(&rec[v].lvl[Z]) != target) {
                         // no predecessor found: an invariant is broken; record it, stop the walk
                         if (tid == 0) sh.err |= kErrSelect;
                         walk_ok = false;
@@ -1174,7 +1185,6 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
         ls.walk_scan += walk_scan;
         ls.scaled += sh.scaled ? 1 : 0;
         if (sh.status == 3) sh.err |= kErrSigmaOverflow;
-        if (sh.status == 4) sh.err |= kErrDepth;
         if (sh.err) atomicOr(&a.job->error, sh.err);
         if (a.trace) {
             TraceRec tr;
@@ -1188,7 +1198,7 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
             tr.e_scan = (long long)sh.e_scan;
             tr.n_interior = (long long)path_len;
             tr.scaled = sh.scaled;
-            tr.overflow = sh.status == 3 ? 1 : (sh.status == 4 ? 2 : 0);
+            tr.overflow = sh.status == 3 ? 1 : 0;
             tr.ns = (long long)(t_walk - t_start);
             tr.phase_ns[0] = (long long)(t_bfs - t_start);
             tr.phase_ns[1] = (long long)(t_sel - t_bfs);
@@ -1255,7 +1265,7 @@ __global__ void __launch_bounds__(NT, (2048 / NT / 2) > 0 ? (2048 / NT / 2) : 1)
 
     LocalStats ls = {0, 0, 0, 0, 0, 0, 0, 0};
     for (;;) {
-        if (tid == 0) sh.cur = atomicAdd(&job->work, 1u);
+        if (tid == 0) sh.cur = atomicAdd(&job->work, 1ULL);
         __syncthreads();
         const unsigned long long i = sh.cur;
         if (i >= count) break;
@@ -1281,7 +1291,7 @@ __global__ void __launch_bounds__(NT, (2048 / NT / 2) > 0 ? (2048 / NT / 2) : 1)
         if (prev == gridDim.x - 1) {
             __threadfence();
             *reinterpret_cast<volatile unsigned long long *>(&job->tau) = base + count;
-            *reinterpret_cast<volatile unsigned int *>(&job->work) = 0u;
+            *reinterpret_cast<volatile unsigned long long *>(&job->work) = 0ULL;
             *reinterpret_cast<volatile unsigned int *>(&job->done_ctas) = 0u;
             __threadfence();
         }

@@ -12,9 +12,14 @@
 // loads this library, for as long as the process runs.  Every call reuses it,
 // so calls that overlap on the GPU (different streams, or different host
 // threads without ordering) race on it; serialise them.
+//
+// With lazy module loading (the CUDA default) the array is only reserved
+// when this file's device code is first touched on a device.  The library
+// touches it in kadabra_graph_load (static_scratch_reserve), so by the time
+// a caller holds a graph on a device, sampling from it here loads no code
+// and reserves no memory.
 
 #include <cstdint>
-#include <mutex>
 
 #include <cuda_runtime.h>
 
@@ -29,49 +34,25 @@ static_assert(sizeof(Job) <= kStaticJobBytes, "job state must fit its reserved b
 
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
-namespace {
-
-constexpr int kMaxDevices = 64;
-std::mutex g_static_mutex;
-void *g_static_ptr[kMaxDevices] = {};
-
-__global__ void static_job_init(Job *job, unsigned long long first)
-{
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        Job z;
-        unsigned char *p = reinterpret_cast<unsigned char *>(&z);
-        for (size_t i = 0; i < sizeof(Job); ++i) p[i] = 0;
-        z.stop_epoch = -1;
-        z.tau = first;
-        *job = z;
-    }
-}
-
-}  // namespace
-
-// Device address of the static scratch on the current device; looked up once
-// per device (the first call on a device does it).
+// Device address of the static scratch on the current device.  Looked up on
+// every call (cheap once the module is loaded), so a cached address can never
+// outlive a device reset.  The host-side symbol g_static_scratch is only a
+// stand-in for the device array and is never handed to a kernel.
 cudaError_t static_scratch_address(void **out)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_static_mutex);
-    if (!g_static_ptr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_static_scratch);
-        if (e != cudaSuccess) return e;
-        g_static_ptr[dev] = p;
-    }
-    *out = g_static_ptr[dev];
+    *out = p;
     return cudaSuccess;
 }
 
-cudaError_t launch_static_job_init(Job *job, unsigned long long first, cudaStream_t st)
+// Set-up on the current device: loads this file's module, which reserves the
+// array.  kadabra_graph_load calls it with the graph's device current.
+cudaError_t static_scratch_reserve()
 {
-    static_job_init<<<1, 32, 0, st>>>(job, first);
-    return cudaGetLastError();
+    void *p = nullptr;
+    return static_scratch_address(&p);
 }
 
 }  // namespace kadabra
@@ -129,7 +110,7 @@ extern "C" kadabra_status kadabra_sample_static(const kadabra_graph *g, uint64_t
 
     // the sampler requires all-zero records and a fresh job record
     e = cudaMemsetAsync(recs, 0, slots * (size_t)G.n * sizeof(SlotRec), st);
-    if (e == cudaSuccess) e = launch_static_job_init(job, first, st);
+    if (e == cudaSuccess) e = launch_reset_job(job, st, first);
     SampleLaunch a{};
     a.n = G.n;
     a.off = G.off;
@@ -152,7 +133,6 @@ extern "C" kadabra_status kadabra_sample_static(const kadabra_graph *g, uint64_t
     if (e != cudaSuccess) return static_cuda_fail(e);
     if (err & kErrSigmaOverflow) return static_fail(KADABRA_ERR_SIGMA_OVERFLOW, "a per-side path count exceeded 2^K");
     if (err & kErrCounterOverflow) return static_fail(KADABRA_ERR_COUNTER_OVERFLOW, "a 32-bit counter wrapped");
-    if (err & kErrDepth) return static_fail(KADABRA_ERR_DEPTH, "a BFS side needed more than 65533 layers");
     if (err) return static_fail(KADABRA_ERR_CUDA, "internal sampling invariant violated");
     return KADABRA_OK;
 }

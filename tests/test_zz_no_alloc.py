@@ -9,8 +9,10 @@ output array.
 
 These tests call it through the C ABI and require its counters to equal those
 of kadabra_sample_epoch on the same sample indices, for two calls in a row
-(the second call reuses the array the first one left behind).  The file is
-named so that pytest collects it after every other test.
+(the second call reuses the array the first one left behind), with the free
+device memory unchanged across both calls, the first included: loading a
+graph already reserved the array on the device.  The file is named so that
+pytest collects it after every other test.
 """
 import numpy as np
 import pytest
@@ -46,15 +48,18 @@ def test_static_sampling_matches_sample_epoch(K, name, E):
     two_epochs = q.result(btilde=False)["counts"].copy()
 
     counts = torch.zeros(g.n, dtype=torch.int32, device="cuda")
-    # call 1: samples [0, E) of the adaptive stream
+    torch.cuda.synchronize()
+    free = [torch.cuda.mem_get_info()[0]]
+    # call 1 (in a fresh process, the first call of the entry point): samples
+    # [0, E) of the adaptive stream
     K.sample_static(G, 5, 1, 0, E, counts.data_ptr())
+    free.append(torch.cuda.mem_get_info()[0])
     assert np.array_equal(counts.cpu().numpy().view(np.uint32), first_epoch)
     # call 2: samples [E, 2E) added to the same caller-owned array
-    free_before = torch.cuda.mem_get_info()[0]
     K.sample_static(G, 5, 1, E, E, counts.data_ptr())
-    free_after = torch.cuda.mem_get_info()[0]
+    free.append(torch.cuda.mem_get_info()[0])
     assert np.array_equal(counts.cpu().numpy().view(np.uint32), two_epochs)
-    assert free_after == free_before
+    assert free[0] == free[1] == free[2], free
 
 
 def test_static_sampling_calibration_stream(K, orc):
