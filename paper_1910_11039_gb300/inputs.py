@@ -20,8 +20,11 @@ The synthetic families stand in for the paper's workloads (Section V-A):
 """
 from __future__ import annotations
 
+import ctypes
 import dataclasses
 import functools
+import os
+import subprocess
 
 import numpy as np
 
@@ -121,38 +124,56 @@ def er_graph(n: int, avg_degree: float, seed: int, lcc: bool = True) -> Graph:
     return largest_component(g) if lcc else g
 
 
+_GEN_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "gen")
+_GEN_SRC = os.path.join(_GEN_DIR, "graphgen.c")
+_GEN_LIB = os.path.join(_GEN_DIR, "libgraphgen.so")
+_gen = None
+
+
+def build_generator(force: bool = False) -> str:
+    """Compile the native R-MAT builder with gcc (in place, next to its source)."""
+    if force or not os.path.exists(_GEN_LIB) or os.path.getmtime(_GEN_LIB) < os.path.getmtime(_GEN_SRC):
+        tmp = _GEN_LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O3", "-std=c11", "-fPIC", "-shared", "-pthread", "-o", tmp, _GEN_SRC])
+        os.replace(tmp, _GEN_LIB)
+    return _GEN_LIB
+
+
+def _generator():
+    global _gen
+    if _gen is None:
+        L = ctypes.CDLL(build_generator())
+        L.gg_rmat_csr.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double, ctypes.c_double,
+                                  ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+        L.gg_rmat_csr.restype = ctypes.c_int64
+        _gen = L
+    return _gen
+
+
+def _threads() -> int:
+    try:
+        return max(1, len(os.sched_getaffinity(0)))
+    except AttributeError:
+        return max(1, os.cpu_count() or 1)
+
+
 def rmat_graph(scale: int, edge_factor: int, seed: int,
                abcd=(0.57, 0.19, 0.19, 0.05), relabel: bool = True,
                lcc: bool = False) -> Graph:
     """R-MAT (Chakrabarti et al.) with ``edge_factor * 2**scale`` edge draws,
-    no noise, random vertex relabelling, symmetrised and deduplicated."""
-    a, b, c, d = abcd
+    no noise, random vertex relabelling, symmetrised and deduplicated, built by
+    the native counter-based builder (``gen/graphgen.c``): the graph depends
+    only on the arguments, not on the thread count."""
+    a, b, c, _ = abcd
     n = 1 << scale
     m = edge_factor * n
-    rng = np.random.default_rng(seed)
-    t_ab, t_abc = a + b, a + b + c
-    chunk = 1 << 22
-    srcs, dsts = [], []
-    for lo in range(0, m, chunk):
-        k = min(chunk, m - lo)
-        i = np.zeros(k, dtype=np.int64)
-        j = np.zeros(k, dtype=np.int64)
-        for lvl in range(scale):
-            u = rng.random(k)
-            ib = u >= t_ab
-            jb = ((u >= a) & (u < t_ab)) | (u >= t_abc)
-            bit = np.int64(1) << (scale - 1 - lvl)
-            i |= ib * bit
-            j |= jb * bit
-        srcs.append(i)
-        dsts.append(j)
-    src = np.concatenate(srcs)
-    dst = np.concatenate(dsts)
-    del srcs, dsts
-    if relabel:
-        perm = rng.permutation(n).astype(np.int64)
-        src, dst = perm[src], perm[dst]
-    g = csr_from_edges(n, src, dst, name=f"rmat{scale}_ef{edge_factor}")
+    off = np.empty(n + 1, dtype=np.int64)
+    cols = np.empty(2 * m, dtype=np.int32)
+    nnz = _generator().gg_rmat_csr(scale, edge_factor, seed, a, b, c, int(relabel), _threads(),
+                                   off.ctypes.data, cols.ctypes.data)
+    if nnz < 0:
+        raise MemoryError("R-MAT builder failed")
+    g = Graph(n, off, cols[:nnz], name=f"rmat{scale}_ef{edge_factor}")
     return largest_component(g) if lcc else g
 
 

@@ -44,6 +44,45 @@ def test_generators_are_deterministic():
     assert not (a.nnz == c.nnz and np.array_equal(a.cols, c.cols))
 
 
+def _rmat_native(scale, ef, seed, threads, relabel=True):
+    L = I._generator()
+    n = 1 << scale
+    off = np.empty(n + 1, dtype=np.int64)
+    cols = np.empty(2 * ef * n, dtype=np.int32)
+    nnz = L.gg_rmat_csr(scale, ef, seed, 0.57, 0.19, 0.19, int(relabel), threads, off.ctypes.data, cols.ctypes.data)
+    assert nnz >= 0
+    return I.Graph(n, off, cols[:nnz])
+
+
+def test_rmat_builder_is_independent_of_the_thread_count():
+    a = _rmat_native(14, 16, 3, 1)
+    b = _rmat_native(14, 16, 3, 5)
+    assert np.array_equal(a.offsets, b.offsets) and np.array_equal(a.cols, b.cols)
+    assert_valid_csr(a)
+
+
+def test_rmat_quadrant_frequencies():
+    # Without relabelling, an edge lands in the top-left / off-diagonal /
+    # bottom-right quadrant of the adjacency matrix with probability a,
+    # b + c, d (0.57, 0.38, 0.05).  At one edge draw per vertex duplicates
+    # are rare, so the symmetric CSR's entries follow the same split.
+    g = _rmat_native(20, 1, 11, 4, relabel=False)
+    half = g.n // 2
+    rows = np.repeat(np.arange(g.n), g.degrees)
+    top_r, top_c = rows >= half, g.cols >= half
+    frac = lambda m: float(m.sum()) / g.nnz
+    assert abs(frac(~top_r & ~top_c) - 0.57) < 0.01
+    assert abs(frac(top_r & top_c) - 0.05) < 0.005
+    assert abs(frac(top_r ^ top_c) - 0.38) < 0.01
+
+
+def test_rmat_relabelling_is_a_permutation_of_the_unrelabelled_graph():
+    a = _rmat_native(12, 8, 9, 2, relabel=False)
+    b = _rmat_native(12, 8, 9, 2, relabel=True)
+    assert a.nnz == b.nnz
+    assert np.array_equal(np.sort(a.degrees), np.sort(b.degrees))
+
+
 def test_small_families():
     for g in [I.path_graph(5), I.star_graph(6), I.cycle_graph(7), I.complete_graph(5),
               I.full_grid_graph(3, 4)]:
