@@ -45,6 +45,10 @@ WORKLOADS = {
     "rmat20": dict(graph="rmat20", eps=0.01, delta=0.1, seed=1, threads=512,
                    desc="R-MAT scale 20, edge factor 16, (a,b,c,d)=(0.57,0.19,0.19,0.05), symmetrised, "
                         "no self-loops/duplicates, int32 CSR; eps=0.01 delta=0.1 seed=1"),
+    "rmat26": dict(graph="rmat26", eps=0.01, delta=0.1, seed=1, threads=512, steps=5, e2e_steps=1,
+                   cpu_samples=1600, ref_samples=800,
+                   desc="R-MAT scale 26, edge factor 16, (a,b,c,d)=(0.57,0.19,0.19,0.05), symmetrised, "
+                        "no self-loops/duplicates, int64 offsets / int32 columns; eps=0.01 delta=0.1 seed=1"),
     "rhg20": dict(graph="rhg20", eps=0.01, delta=0.1, seed=1, steps=5, cpu_samples=4800, ref_samples=1600, threads=512,
                   desc="random hyperbolic graph, n=2^20, power-law exponent 3, average degree 60 (|E| = 30|V|), "
                        "seed 20, int32 CSR; eps=0.01 delta=0.1 seed=1"),
@@ -266,7 +270,8 @@ def run_gpu(args, wl, g, rank, world, local_rank, cpu_baseline):
     eps, delta = wl["eps"], wl["delta"]
 
     # ---- device-resident arm ----
-    G = K.Graph.from_inputs(g, skip_validate=True)
+    off64 = g.nnz >= 2**31
+    G = K.Graph.from_inputs(g, offsets_64=off64, skip_validate=True)
     q = K.Query(G, eps=eps, delta=delta, seed=seed, slots=args.slots, threads=args.threads)
     info0 = q.info()
     E = args.epoch
@@ -332,7 +337,7 @@ def run_gpu(args, wl, g, rank, world, local_rank, cpu_baseline):
     # roofline of the sampling kernel over the timed steps' launches
     timed = min(256, q.info().launches - launches0)
     launches = [ls for ls in q.launch_log(timed) if ls.samples > 0]
-    ob = 4  # int32 offsets
+    ob = 8 if off64 else 4
     peak, peak_kind = measured_peak_hbm()
     tot_b = sum(algorithmic_bytes(ls, ob) for ls in launches)
     tot_ms = sum(ls.ms for ls in launches)
@@ -354,7 +359,8 @@ def run_gpu(args, wl, g, rank, world, local_rank, cpu_baseline):
     # ---- end to end through the C ABI with pinned host buffers ----
     e2e = None
     if args.e2e_steps > 0:
-        off_h = torch.from_numpy(g.offsets32()).pin_memory()
+        off_np = g.offsets if off64 else g.offsets32()
+        off_h = torch.from_numpy(off_np).pin_memory()
         col_h = torch.from_numpy(g.cols).pin_memory()
         b_h = torch.empty(g.n, dtype=torch.float64).pin_memory()
         c_h = torch.empty(g.n, dtype=torch.int32).pin_memory()
@@ -364,7 +370,7 @@ def run_gpu(args, wl, g, rank, world, local_rank, cpu_baseline):
         for k in range(args.e2e_steps + 1):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            G2 = K.Graph(g.n, off_h.numpy(), col_h.numpy(), offsets_64=False, skip_validate=True, stream=stream)
+            G2 = K.Graph(g.n, off_h.numpy(), col_h.numpy(), offsets_64=off64, skip_validate=True, stream=stream)
             q2 = K.Query(G2, eps=eps, delta=delta, seed=seed, stream=stream, slots=args.slots, threads=args.threads)
             if args.mode == "pipelined":
                 q2.run_pipelined(E, frames=args.frames)
@@ -380,7 +386,7 @@ def run_gpu(args, wl, g, rank, world, local_rank, cpu_baseline):
                 e_times.append(t1 - t0)
                 e_taus.append(tau)
         n = g.n
-        h2d = g.offsets32().nbytes + g.cols.nbytes + 16 * n
+        h2d = off_np.nbytes + g.cols.nbytes + 16 * n
         d2h = 4 * n + 8 * n + 4 * n
         e2e = {"value": sum(e_taus) / sum(e_times), "unit": "samples/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "steps": len(e_times),

@@ -10,13 +10,20 @@ Parity status of each function (details in the C file's header):
   vertex_diameter_*            pinned (numpy Philox, networkx, closed forms,
                                path enumeration)
   omega, calibrate_L, stop_functions, check_stop, kadabra
-                               parity unpinned: the paper does not print these
-                               formulas; weak pins only (Table II sample counts
-                               <= omega, epsilon guarantee against Brandes)
+                               the paper does not print these formulas (read
+                               from KADABRA's publication); pinned by hand
+                               values (omega), closed-form and 50-digit roots
+                               (balanced rule, f and g), Table II sample
+                               counts <= omega and the epsilon guarantee
+                               against Brandes
+  kadabra_threads              the same phases as kadabra, each phase's
+                               sample indices split over host threads and
+                               the per-thread counters summed
 """
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 import subprocess
 import threading
@@ -259,3 +266,62 @@ def brandes(g) -> np.ndarray:
     b = np.zeros(g.n, dtype=np.float64)
     lib().orc_brandes(g.n, _ptr(off), _ptr(col), _ptr(b))
     return b
+
+
+def _split_run(g, seed, tag, begin, end, threads, K=None, strict=False):
+    """Samples [begin, end) of stream `tag` split into `threads` contiguous
+    index ranges, each run by run_samples on its own host thread (ctypes
+    releases the GIL); returns the summed counters and the summed stats."""
+    import concurrent.futures as cf
+    threads = max(1, min(threads, end - begin)) if end > begin else 1
+    cuts = [begin + (end - begin) * k // threads for k in range(threads + 1)]
+    with cf.ThreadPoolExecutor(threads) as ex:
+        parts = list(ex.map(lambda k: run_samples(g, seed, tag, cuts[k], cuts[k + 1], K=K, strict=strict),
+                            range(threads)))
+    counts = np.zeros(g.n, dtype=np.uint32)
+    tot = RunStats()
+    for c, st in parts:
+        counts += c
+        for f, _ in RunStats._fields_:
+            setattr(tot, f, getattr(tot, f) + getattr(st, f))
+    return counts, tot
+
+
+def kadabra_threads(g, eps, delta, seed=1, vertex_diameter=0, n_calib=0, epoch_len=1000, delta_rule=1,
+                    strict=False, beta=1e-3, max_epochs=1 << 40, threads=None, on_epoch=None):
+    """The whole method with every phase's samples spread over host threads:
+    phase 1 diameter bound -> omega, phase 2 calibration samples (tag 0) ->
+    L_L, L_U, phase 3 epochs of `epoch_len` adaptive samples (tag 1), each
+    followed by the stop check on the snapshot of samples [0, tau)
+    (Section III-A, III-B).  The same C functions, in the same order and with
+    the same clipping at ceil(omega) as kadabra(); only the sample loop of
+    each epoch is split into index ranges, and counters are integer sums, so
+    the result equals kadabra()'s.  Returns (counts, cal, L_L, L_U, info)."""
+    threads = threads or max(1, len(os.sched_getaffinity(0)))
+    K = graph_sigma_bits(g)
+    vd = vertex_diameter if vertex_diameter > 0 else vertex_diameter_bound(g)
+    om = omega(eps, delta, vd)
+    om_ceil = math.ceil(om)
+    nc = n_calib if n_calib > 0 else max(1000, math.ceil(om / 100.0))
+    cal, _ = _split_run(g, seed, 0, 0, nc, threads, K=K, strict=strict)
+    LL, LU, Cc = calibrate_L(cal, nc, eps, delta, rule=delta_rule, beta=beta)
+    counts = np.zeros(g.n, dtype=np.uint32)
+    tau, stop_epoch, e_scan, epochs = 0, -1, 0, 0
+    mf = mg = math.inf
+    for e in range(max_epochs):
+        m = min(epoch_len, om_ceil - tau) if tau < om_ceil else 0
+        if m > 0:
+            c, st = _split_run(g, seed, 1, tau, tau + m, threads, K=K, strict=strict)
+            counts += c
+            e_scan += st.e_scan
+        tau += m
+        epochs = e + 1
+        stop, mf, mg = check_stop(counts, tau, om, eps, LL, LU)
+        if on_epoch:
+            on_epoch(e, tau, mf, mg)
+        if stop:
+            stop_epoch = e
+            break
+    info = dict(omega=om, vd=vd, n_calib=nc, K=K, stopped=stop_epoch >= 0, tau=tau, epochs=epochs,
+                stop_epoch=stop_epoch, max_f=mf, max_g=mg, C=Cc, e_scan=e_scan)
+    return counts, cal, LL, LU, info

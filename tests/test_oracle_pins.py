@@ -571,3 +571,17 @@ def test_class_maxima_equal_vertex_maxima(orc):
             f, g = orc.stop_functions(int(counts[members].max()), tau, omega, classes[k, 0], classes[k, 1])
             bf, bg = max(bf, f), max(bg, g)
         assert mf == bf and mg == bg
+
+
+@pytest.mark.parametrize("name,eps,E,rule", [("er2000", 0.05, 100, 1), ("grid64", 0.05, 64, 0),
+                                             ("rmat12", 0.03, 256, 1)])
+def test_threaded_driver_equals_the_serial_method(orc, name, eps, E, rule):
+    # kadabra_threads splits each phase's sample indices over host threads;
+    # the counters are integer sums, so every output equals kadabra()'s
+    g = I.config_graph(name)
+    counts, cal, LL, LU, R = orc.kadabra(g, eps, 0.1, seed=3, epoch_len=E, delta_rule=rule)
+    c2, cal2, LL2, LU2, info = orc.kadabra_threads(g, eps, 0.1, seed=3, epoch_len=E, delta_rule=rule, threads=5)
+    assert np.array_equal(counts, c2) and np.array_equal(cal, cal2)
+    assert np.array_equal(LL, LL2) and np.array_equal(LU, LU2)
+    assert (info["tau"], info["stop_epoch"], info["vd"], info["K"]) == (R.tau, R.stop_epoch, R.vd, R.K)
+    assert (info["max_f"], info["max_g"], info["C"]) == (R.max_f, R.max_g, R.C)
