@@ -77,16 +77,18 @@ def log(*a):
 # CPU oracle (baseline and reference arm)
 # ---------------------------------------------------------------------------
 
-def oracle_rate(g, seed, per_thread, threads):
+def oracle_rate(g, seed, per_thread, threads, pool=None):
     """Run the oracle's sampler on `threads` host threads, each taking
-    `per_thread` consecutive adaptive-phase sample indices; returns
+    `per_thread` consecutive adaptive-phase sample indices on its own
+    workspace (built before the timed region); returns
     (samples/s, samples, e_scan, seconds)."""
     import oracle
     oracle.build()
+    pool = pool or [oracle.Workspace(g) for _ in range(threads)]
     results = [None] * threads
 
     def work(i):
-        results[i] = oracle.run_samples(g, seed, 1, i * per_thread, (i + 1) * per_thread)
+        results[i] = pool[i].run_samples(seed, 1, i * per_thread, (i + 1) * per_thread)
 
     ts = [threading.Thread(target=work, args=(i,)) for i in range(threads)]
     t0 = time.perf_counter()
@@ -98,6 +100,39 @@ def oracle_rate(g, seed, per_thread, threads):
     samples = sum(r[1].samples for r in results)
     e_scan = sum(r[1].e_scan for r in results)
     return samples / dt, samples, e_scan, dt
+
+
+def cpu_baseline_for(g, wl, args):
+    """The oracle as it stands on the host cores: all-core and single-thread
+    samples/s over bounded index ranges of the workload, and its time to the
+    (eps, delta) stop with the benchmarked epoch length (the whole method,
+    threads over each epoch's index range, then the oracle's check), measured
+    when a bounded estimate says it ends within ~2 minutes, else extrapolated
+    from the all-core rate and the stop tau."""
+    import oracle
+    cores = host_cores()
+    pool = [oracle.Workspace(g) for _ in range(cores)]
+    per = max(1, args.cpu_samples // cores)
+    rate, s, e, dt = oracle_rate(g, wl["seed"], per, cores, pool)
+    per1 = max(1, min(per, int(rate / cores * 4) or 1))
+    rate1, s1, _, dt1 = oracle_rate(g, wl["seed"], per1, 1, pool[:1])
+    del pool
+    out = {"value": rate, "unit": "samples/s", "cores": cores, "kind": "oracle",
+           "sample": f"adaptive-phase sample indices [0, {s}) of the same workload, {per} per thread on {cores} "
+                     f"threads ({dt:.1f} s wall); single thread: [0, {s1}) ({dt1:.1f} s)",
+           "gteps": e / dt / 1e9, "single_thread": {"value": rate1, "unit": "samples/s", "threads": 1}}
+    # the oracle's whole run: estimate the adaptive phase from omega's order first
+    est = oracle.omega(wl["eps"], wl["delta"], oracle.vertex_diameter_bound(g)) / 2 / rate
+    if est <= 120 and not args.no_oracle_stop:
+        _, _, _, _, inf = oracle.kadabra_threads(g, wl["eps"], wl["delta"], seed=wl["seed"], epoch_len=args.epoch,
+                                                 threads=cores)
+        out["time_to_stop"] = {"value": inf["seconds"]["adaptive"], "unit": "s", "measured": True,
+                               "tau": inf["tau"], "stop_epoch": inf["stop_epoch"],
+                               "phases_1_2_s": inf["seconds"]["phases_1_2"], "threads": cores}
+    else:
+        out["time_to_stop"] = {"value": None, "unit": "s", "measured": False,
+                               "estimate_from_rate": "stop tau / all-core samples/s (see the GPU line's samples_per_step)"}
+    return out
 
 
 def host_cores():
@@ -230,14 +265,16 @@ def measured_peak_hbm():
 def run_reference(args, wl, g, rank, world):
     if rank != 0:
         return
+    import oracle
     threads = host_cores()
     per_thread = max(1, args.ref_samples // threads)
     seed = wl["seed"]
+    pool = [oracle.Workspace(g) for _ in range(threads)]
     for _ in range(args.warmup):
-        oracle_rate(g, seed, max(1, per_thread // 4), threads)
+        oracle_rate(g, seed, max(1, per_thread // 4), threads, pool)
     rates, total_s, total_dt = [], 0, 0.0
     for k in range(args.steps):
-        rate, s, e, dt = oracle_rate(g, seed, per_thread, threads)
+        rate, s, e, dt = oracle_rate(g, seed, per_thread, threads, pool)
         rates.append(rate)
         total_s += s
         total_dt += dt
@@ -395,6 +432,8 @@ def run_gpu(args, wl, g, rank, world, local_rank, cpu_baseline):
 
     if rank != 0:
         return
+    if cpu_baseline and not cpu_baseline["time_to_stop"].get("measured"):
+        cpu_baseline["time_to_stop"]["value"] = (all_samples / args.steps / world) / cpu_baseline["value"]
     line = {
         "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
@@ -675,6 +714,7 @@ def main():
                     help="oracle samples for the CPU baseline (split over host cores)")
     ap.add_argument("--ref-samples", type=int, default=None, help="oracle samples per reference step")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-oracle-stop", action="store_true", help="skip the oracle's own run to the stop")
     args = ap.parse_args()
     assert args.warmup >= 3 or args.impl == "reference" or os.environ.get("KADABRA_BENCH_ALLOW_SHORT"), \
         "at least 3 warm-up steps"
@@ -714,13 +754,7 @@ def main():
     # CPU baseline first: the oracle runs on host threads before any CUDA call
     cpu_baseline = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cores = host_cores()
-        per = max(1, args.cpu_samples // cores)
-        rate, s, e, dt = oracle_rate(g, wl["seed"], per, cores)
-        cpu_baseline = {"value": rate, "unit": "samples/s", "cores": cores, "kind": "oracle",
-                        "sample": f"adaptive-phase sample indices [0, {s}) of the same workload, "
-                                  f"{per} per thread on {cores} threads ({dt:.1f} s wall)",
-                        "gteps": e / dt / 1e9}
+        cpu_baseline = cpu_baseline_for(g, wl, args)
     if world > 1:
         import torch
         torch.cuda.set_device(local_rank)

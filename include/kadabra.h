@@ -77,6 +77,11 @@ typedef struct kadabra_params {
     int32_t slots;            /* samples in flight (one CTA each); 0 = fill the GPU        */
     int32_t threads;          /* threads per sampling CTA: 128, 256, 512, 1024; 0 = 1024   */
     double scratch_fraction;  /* max share of free device memory for scratch; 0 = 0.6      */
+    int64_t queue_cap;        /* queue positions per slot (the two BFS balls of a sample
+                                 together); 0 = n when the slots fit the scratch budget,
+                                 else what fits.  A sample that outgrows it runs again on
+                                 one of two full-capacity spill slots, so results never
+                                 depend on it                                              */
 } kadabra_params;
 
 /* Snapshot of a query (kadabra_query_get_info). */
@@ -114,6 +119,9 @@ typedef struct kadabra_query_info {
     int64_t launches;           /* sampling launches logged (kadabra_launch_log), ever      */
     double diameter_ms;         /* host wall time of phase 1 (diameter bound and omega)    */
     double calibration_ms;      /* host wall time of phase 2 (calibration; batch: budgets)  */
+    int64_t queue_cap;          /* queue positions per sampling slot (both BFS sides)       */
+    int32_t spill_slots;        /* full-capacity slots for samples that outgrow queue_cap   */
+    int32_t pad1;
 } kadabra_query_info;
 
 /* Per-sample record written by kadabra_sample_trace (one per sample index). */
@@ -413,8 +421,9 @@ kadabra_status kadabra_launch_log(kadabra_query *q, int64_t max_entries, kadabra
  * do, and adds each sampled path's interior vertices to counts[n] (device
  * pointer, caller-owned, accumulated, not cleared).  The scratch lives in a
  * fixed array of KADABRA_STATIC_SCRATCH_BYTES inside the library; nothing is
- * allocated.  Graphs need n * 36 bytes per in-flight sample, so n must satisfy
- * n * 36 <= KADABRA_STATIC_SCRATCH_BYTES - 256 (else KADABRA_ERR_INVALID_ARG),
+ * allocated.  Graphs need about n * 28 bytes per in-flight sample, so n must
+ * satisfy n * 28 <= KADABRA_STATIC_SCRATCH_BYTES - 256 - 1280 (else
+ * KADABRA_ERR_INVALID_ARG),
  * and fewer samples run in parallel as n grows.
  * Set-up: CUDA loads device code lazily, and the array is reserved on a
  * device only when its code is first loaded there.  kadabra_graph_load does

@@ -107,6 +107,9 @@ def lib():
             L.orc_run_samples.argtypes = [_I64, _P, _P, _U64, _U64, _U64, _U64, C.c_int, C.c_int,
                                           _P, C.POINTER(RunStats)]
             L.orc_run_samples.restype = _I64
+            L.orc_run_samples_ws.argtypes = [_I64, _P, _P, _P, _P, _U64, _U64, _U64, _U64, C.c_int, C.c_int,
+                                             _P, C.POINTER(RunStats)]
+            L.orc_run_samples_ws.restype = _I64
             L.orc_vertex_diameter_bound.argtypes = [_I64, _P, _P]
             L.orc_vertex_diameter_bound.restype = _I64
             L.orc_vertex_diameter_exact.argtypes = [_I64, _P, _P]
@@ -176,6 +179,16 @@ class Workspace:
                                     seed, tag, idx, self.K if K is None else K, int(strict),
                                     _ptr(self.path), C.byref(info))
         return self.path[:np_].copy(), info
+
+    def run_samples(self, seed, tag, begin, end, counts=None, strict=False, K=None):
+        """counts[x] += #samples in [begin, end) with x interior, reusing this
+        workspace; returns (counts, RunStats)."""
+        if counts is None:
+            counts = np.zeros(self.g.n, dtype=np.uint32)
+        st = RunStats()
+        lib().orc_run_samples_ws(self.g.n, _ptr(self.off), _ptr(self.col), self.ws, _ptr(self.path), seed, tag,
+                                 begin, end, self.K if K is None else K, int(strict), _ptr(counts), C.byref(st))
+        return counts, st
 
     def sample(self, seed, tag, idx, strict=False, K=None):
         info = SampleInfo()
@@ -268,16 +281,23 @@ def brandes(g) -> np.ndarray:
     return b
 
 
-def _split_run(g, seed, tag, begin, end, threads, K=None, strict=False):
+def _split_run(g, seed, tag, begin, end, threads, K=None, strict=False, pool=None):
     """Samples [begin, end) of stream `tag` split into `threads` contiguous
-    index ranges, each run by run_samples on its own host thread (ctypes
-    releases the GIL); returns the summed counters and the summed stats."""
+    index ranges, each run on its own host thread (ctypes releases the GIL),
+    on the workspaces of `pool` when given; returns the summed counters and
+    the summed stats."""
     import concurrent.futures as cf
-    threads = max(1, min(threads, end - begin)) if end > begin else 1
+    if pool is not None:
+        threads = len(pool)
     cuts = [begin + (end - begin) * k // threads for k in range(threads + 1)]
+
+    def part(k):
+        if pool is not None:
+            return pool[k].run_samples(seed, tag, cuts[k], cuts[k + 1], K=K, strict=strict)
+        return run_samples(g, seed, tag, cuts[k], cuts[k + 1], K=K, strict=strict)
+
     with cf.ThreadPoolExecutor(threads) as ex:
-        parts = list(ex.map(lambda k: run_samples(g, seed, tag, cuts[k], cuts[k + 1], K=K, strict=strict),
-                            range(threads)))
+        parts = list(ex.map(part, range(threads)))
     counts = np.zeros(g.n, dtype=np.uint32)
     tot = RunStats()
     for c, st in parts:
@@ -297,21 +317,25 @@ def kadabra_threads(g, eps, delta, seed=1, vertex_diameter=0, n_calib=0, epoch_l
     the same clipping at ceil(omega) as kadabra(); only the sample loop of
     each epoch is split into index ranges, and counters are integer sums, so
     the result equals kadabra()'s.  Returns (counts, cal, L_L, L_U, info)."""
+    import time
     threads = threads or max(1, len(os.sched_getaffinity(0)))
+    pool = [Workspace(g) for _ in range(threads)]
+    t0 = time.perf_counter()
     K = graph_sigma_bits(g)
     vd = vertex_diameter if vertex_diameter > 0 else vertex_diameter_bound(g)
     om = omega(eps, delta, vd)
     om_ceil = math.ceil(om)
     nc = n_calib if n_calib > 0 else max(1000, math.ceil(om / 100.0))
-    cal, _ = _split_run(g, seed, 0, 0, nc, threads, K=K, strict=strict)
+    cal, _ = _split_run(g, seed, 0, 0, nc, threads, K=K, strict=strict, pool=pool)
     LL, LU, Cc = calibrate_L(cal, nc, eps, delta, rule=delta_rule, beta=beta)
+    t1 = time.perf_counter()
     counts = np.zeros(g.n, dtype=np.uint32)
     tau, stop_epoch, e_scan, epochs = 0, -1, 0, 0
     mf = mg = math.inf
     for e in range(max_epochs):
         m = min(epoch_len, om_ceil - tau) if tau < om_ceil else 0
         if m > 0:
-            c, st = _split_run(g, seed, 1, tau, tau + m, threads, K=K, strict=strict)
+            c, st = _split_run(g, seed, 1, tau, tau + m, threads, K=K, strict=strict, pool=pool)
             counts += c
             e_scan += st.e_scan
         tau += m
@@ -323,5 +347,6 @@ def kadabra_threads(g, eps, delta, seed=1, vertex_diameter=0, n_calib=0, epoch_l
             stop_epoch = e
             break
     info = dict(omega=om, vd=vd, n_calib=nc, K=K, stopped=stop_epoch >= 0, tau=tau, epochs=epochs,
-                stop_epoch=stop_epoch, max_f=mf, max_g=mg, C=Cc, e_scan=e_scan)
+                stop_epoch=stop_epoch, max_f=mf, max_g=mg, C=Cc, e_scan=e_scan,
+                seconds=dict(phases_1_2=t1 - t0, adaptive=time.perf_counter() - t1), threads=threads)
     return counts, cal, LL, LU, info

@@ -350,12 +350,12 @@ typedef struct {
     int64_t samples, e_scan, connected, interior, scaled, overflow;
 } orc_run_stats;
 
-int64_t orc_run_samples(int64_t n, const int64_t *off, const int32_t *col,
-                        uint64_t seed, uint64_t tag, uint64_t idx_begin, uint64_t idx_end,
-                        int K, int strict, uint32_t *counts, orc_run_stats *st)
+/* Same as orc_run_samples, with a caller-owned workspace (reused across
+ * calls; every sample leaves it as it found it) and path buffer (n entries). */
+int64_t orc_run_samples_ws(int64_t n, const int64_t *off, const int32_t *col, orc_ws *w, int32_t *path,
+                           uint64_t seed, uint64_t tag, uint64_t idx_begin, uint64_t idx_end,
+                           int K, int strict, uint32_t *counts, orc_run_stats *st)
 {
-    orc_ws *w = orc_ws_create(n);
-    int32_t *path = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
     orc_run_stats S;
     memset(&S, 0, sizeof(S));
     for (uint64_t i = idx_begin; i < idx_end; i++) {
@@ -369,10 +369,20 @@ int64_t orc_run_samples(int64_t n, const int64_t *off, const int32_t *col,
         S.scaled += I.scaled;
         S.overflow += I.overflow;
     }
-    free(path);
-    orc_ws_free(w);
     if (st) *st = S;
     return S.overflow;
+}
+
+int64_t orc_run_samples(int64_t n, const int64_t *off, const int32_t *col,
+                        uint64_t seed, uint64_t tag, uint64_t idx_begin, uint64_t idx_end,
+                        int K, int strict, uint32_t *counts, orc_run_stats *st)
+{
+    orc_ws *w = orc_ws_create(n);
+    int32_t *path = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    int64_t r = orc_run_samples_ws(n, off, col, w, path, seed, tag, idx_begin, idx_end, K, strict, counts, st);
+    free(path);
+    orc_ws_free(w);
+    return r;
 }
 
 /* ------------------------------------------------------------------------ */

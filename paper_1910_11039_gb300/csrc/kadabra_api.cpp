@@ -66,12 +66,11 @@ struct kadabra_graph {
     void *d_off = nullptr;
     uint2 *d_adj = nullptr;       // (neighbour, neighbour degree) per adjacency entry
     // sampling scratch shared by the graph's queries
-    kadabra::SlotRec *d_recs = nullptr;
-    uint32_t *d_queues = nullptr;
-    uint32_t *d_bits = nullptr;   // reached-bit maps: 2 * ceil(n / 32) words per slot
-    int ws_slots = 0;
+    kadabra::SlotSet ws;          // one slot per CTA
+    kadabra::SlotSet spill;       // full-capacity slots for samples that outgrow ws.cap
     int ws_threads = 0;
     int ws_req = 0;               // slots requested when the scratch was sized
+    int64_t ws_cap_req = 0;       // queue capacity requested when the scratch was sized
 };
 
 struct kadabra_query {
@@ -126,9 +125,8 @@ struct kadabra_query {
 struct kadabra_batch {
     int64_t max_n = 0;
     int slots = 0, threads = 0, off64 = 0;
-    kadabra::SlotRec *d_recs = nullptr;
-    uint32_t *d_queues = nullptr;
-    uint32_t *d_bits = nullptr;
+    kadabra::SlotSet ws;
+    kadabra::SlotSet spill;
     kadabra::QueryDesc *d_descs = nullptr;
     int64_t descs_cap = 0;
     kadabra::BatchState *d_bs = nullptr;
@@ -141,6 +139,94 @@ struct kadabra_batch {
 };
 
 namespace kadabra {
+
+namespace {
+constexpr long long kMaxCap = (1LL << 31) - 2;   // queue positions must fit the code word
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+}  // namespace
+
+size_t slot_set_bytes(int count, long long stride, long long cap, bool bits, bool lock)
+{
+    const size_t c = (size_t)(count > 0 ? count : 0);
+    size_t b = align256(c * (size_t)stride * 4);                          // code
+    b += align256(c * (size_t)cap * 4) * 2;                               // qv, ql
+    b += align256(c * (size_t)cap * 8) * 2;                               // qs, qm
+    if (bits) b += align256(c * 2 * (size_t)bit_words(stride) * 4);       // reached bits
+    if (lock) b += align256(c * sizeof(int));
+    return b;
+}
+
+void free_slot_set(SlotSet *S)
+{
+    cudaFree(S->code);
+    cudaFree(S->qv);
+    cudaFree(S->ql);
+    cudaFree(S->qs);
+    cudaFree(S->qm);
+    cudaFree(S->bits);
+    cudaFree(S->lock);
+    *S = SlotSet{};
+}
+
+cudaError_t alloc_slot_set(SlotSet *S, int count, long long stride, long long cap, bool bits, bool lock)
+{
+    *S = SlotSet{};
+    if (count <= 0) return cudaSuccess;
+    const size_t c = (size_t)count;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&S->code), c * (size_t)stride * 4);
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&S->qv), c * (size_t)cap * 4);
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&S->ql), c * (size_t)cap * 4);
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&S->qs), c * (size_t)cap * 8);
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&S->qm), c * (size_t)cap * 8);
+    if (e == cudaSuccess && bits) e = cudaMalloc(reinterpret_cast<void **>(&S->bits), c * 2 * (size_t)bit_words(stride) * 4);
+    if (e == cudaSuccess && lock) e = cudaMalloc(reinterpret_cast<void **>(&S->lock), c * sizeof(int));
+    // the sampler relies on all-zero code words, counts, bits and locks at rest
+    if (e == cudaSuccess) e = cudaMemset(S->code, 0, c * (size_t)stride * 4);
+    if (e == cudaSuccess) e = cudaMemset(S->qs, 0, c * (size_t)cap * 8);
+    if (e == cudaSuccess) e = cudaMemset(S->qm, 0, c * (size_t)cap * 8);
+    if (e == cudaSuccess && bits) e = cudaMemset(S->bits, 0, c * 2 * (size_t)bit_words(stride) * 4);
+    if (e == cudaSuccess && lock) e = cudaMemset(S->lock, 0, c * sizeof(int));
+    if (e != cudaSuccess) {
+        free_slot_set(S);
+        return e;
+    }
+    S->stride = stride;
+    S->cap = cap;
+    S->count = count;
+    return cudaSuccess;
+}
+
+// How many slots of what queue capacity fit `budget` bytes for graphs of up
+// to `stride` vertices.  Full capacity (cap = stride) when `want` such slots
+// fit; otherwise two full-capacity spill slots and `want` slots whose queue
+// capacity uses the rest (at least 2^16 positions; fewer slots if even that
+// does not fit).  cap_req > 0 forces that capacity (spill slots whenever it
+// is below stride).
+void plan_slots(long long stride, int want, size_t budget, long long cap_req, int *slots, long long *cap, int *nspill)
+{
+    const long long full = stride < kMaxCap ? stride : kMaxCap;
+    long long c = full;
+    if (cap_req > 0) {
+        c = cap_req < full ? cap_req : full;
+        if (c < 2) c = 2;
+    } else if ((size_t)want * slot_set_bytes(1, stride, full, true, false) > budget) {
+        const size_t spill_b = 2 * slot_set_bytes(1, stride, full, true, true);
+        const size_t rest = budget > spill_b ? budget - spill_b : 0;
+        const size_t fixed = slot_set_bytes(1, stride, 0, true, false);
+        const size_t per = rest / (size_t)(want > 0 ? want : 1);
+        long long fit = per > fixed ? (long long)((per - fixed) / 24) : 0;
+        const long long floor_cap = full < (1LL << 16) ? full : (1LL << 16);
+        c = fit < floor_cap ? floor_cap : (fit < full ? fit : full);
+    }
+    const int ns = c < full ? 2 : 0;
+    const size_t spill_b = ns ? (size_t)ns * slot_set_bytes(1, stride, full, true, true) : 0;
+    const size_t avail = budget > spill_b ? budget - spill_b : 0;
+    const size_t per = slot_set_bytes(1, stride, c, true, false);
+    const size_t fit = per ? avail / per : (size_t)want;
+    *slots = (int)((size_t)want < fit ? (size_t)want : fit);
+    *cap = c;
+    *nspill = ns;
+}
 
 bool graph_view(const kadabra_graph *g, GraphView *out)
 {
@@ -345,14 +431,10 @@ static void free_graph_device(kadabra_graph *g)
 {
     cudaFree(g->d_off);
     cudaFree(g->d_adj);
-    cudaFree(g->d_recs);
-    cudaFree(g->d_queues);
-    cudaFree(g->d_bits);
+    kadabra::free_slot_set(&g->ws);
+    kadabra::free_slot_set(&g->spill);
     g->d_off = nullptr;
     g->d_adj = nullptr;
-    g->d_recs = nullptr;
-    g->d_queues = nullptr;
-    g->d_bits = nullptr;
 }
 
 extern "C" kadabra_status kadabra_graph_load(int64_t n, int64_t nnz, const void *offsets, int offsets_is_64,
@@ -462,51 +544,40 @@ extern "C" kadabra_status kadabra_graph_info(const kadabra_graph *g, int64_t *n,
     return KADABRA_OK;
 }
 
-// Sampling scratch: slots * (n * (32 B record + 4 B queue entry) + 2 reached-bit maps of n bits).
-static kadabra_status ensure_workspace(kadabra_graph *g, int want_slots, int threads, double fraction)
+// Sampling scratch of the graph: per slot one code word per vertex, two
+// reached-bit maps and a queue of `cap` positions (24 B each); see SlotSet.
+static kadabra_status ensure_workspace(kadabra_graph *g, int want_slots, int threads, double fraction, int64_t cap_req)
 {
     int dev = 0, sms = 0, per_sm = 0;
     KCUDA(cudaGetDevice(&dev), "cudaGetDevice");
     KCUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
     KCUDA(kadabra::sample_occupancy(threads, g->off64, &per_sm), "occupancy");
     if (per_sm < 1) per_sm = 1;
-    int slots = want_slots > 0 ? want_slots : sms * per_sm;
-    const size_t bits_per_slot = 2 * (size_t)kadabra::bit_words(g->n) * sizeof(uint32_t);
-    const size_t per_slot = (size_t)g->n * (sizeof(kadabra::SlotRec) + sizeof(uint32_t)) + bits_per_slot;
-    if (g->d_recs && g->ws_threads == threads && (g->ws_slots >= slots || g->ws_req == slots)) return KADABRA_OK;
-    const int requested = slots;
+    const int requested = want_slots > 0 ? want_slots : sms * per_sm;
+    if (g->ws.count && g->ws_threads == threads && g->ws_cap_req == cap_req &&
+        (g->ws.count >= requested || g->ws_req == requested))
+        return KADABRA_OK;
     cudaDeviceSynchronize();
-    cudaFree(g->d_recs);
-    cudaFree(g->d_queues);
-    cudaFree(g->d_bits);
-    g->d_recs = nullptr;
-    g->d_queues = nullptr;
-    g->d_bits = nullptr;
-    g->ws_slots = 0;
+    kadabra::free_slot_set(&g->ws);
+    kadabra::free_slot_set(&g->spill);
     size_t free_b = 0, total_b = 0;
     KCUDA(cudaMemGetInfo(&free_b, &total_b), "cudaMemGetInfo");
     if (fraction <= 0.0 || fraction > 0.95) fraction = 0.6;
     const size_t budget = (size_t)((double)free_b * fraction);
-    size_t fit = per_slot ? budget / per_slot : (size_t)slots;
-    if ((size_t)slots > fit) slots = (int)fit;
+    int slots = 0, nspill = 0;
+    long long cap = 0;
+    kadabra::plan_slots(g->n, requested, budget, cap_req, &slots, &cap, &nspill);
     if (slots < 1) return fail(KADABRA_ERR_OOM, "not enough device memory for one sampling slot");
-    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&g->d_recs), (size_t)slots * (size_t)g->n * sizeof(kadabra::SlotRec));
-    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&g->d_queues), (size_t)slots * (size_t)g->n * sizeof(uint32_t));
-    if (e == cudaSuccess) e = cudaMemset(g->d_recs, 0, (size_t)slots * (size_t)g->n * sizeof(kadabra::SlotRec));
-    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&g->d_bits), (size_t)slots * bits_per_slot);
-    if (e == cudaSuccess) e = cudaMemset(g->d_bits, 0, (size_t)slots * bits_per_slot);
+    cudaError_t e = kadabra::alloc_slot_set(&g->ws, slots, g->n, cap, true, false);
+    if (e == cudaSuccess) e = kadabra::alloc_slot_set(&g->spill, nspill, g->n, g->n, true, true);
     if (e != cudaSuccess) {
-        cudaFree(g->d_recs);
-        cudaFree(g->d_queues);
-        cudaFree(g->d_bits);
-        g->d_recs = nullptr;
-        g->d_queues = nullptr;
-        g->d_bits = nullptr;
+        kadabra::free_slot_set(&g->ws);
+        kadabra::free_slot_set(&g->spill);
         return cuda_fail(e, "allocate sampling scratch");
     }
-    g->ws_slots = slots;
     g->ws_threads = threads;
     g->ws_req = requested;
+    g->ws_cap_req = cap_req;
     return KADABRA_OK;
 }
 
@@ -548,6 +619,8 @@ static kadabra_status device_error_status(const Job &j)
         return fail(KADABRA_ERR_INVALID_ARG, "a sampled path had more interior vertices than VD - 2 (vertex diameter bound too small)");
     if (j.error & kadabra::kErrTimeout)
         return fail(KADABRA_ERR_TIMEOUT, "a pipelined launch gave up waiting for a free counter frame");
+    if (j.error & kadabra::kErrScratch)
+        return fail(KADABRA_ERR_OOM, "a sample outgrew its slot's queue and no spill slot was available");
     if (j.error & (kadabra::kErrAddOverflow | kadabra::kErrSelect))
         return fail(KADABRA_ERR_CUDA, "internal sampling invariant violated (error bits " + std::to_string(j.error) + ")");
     return KADABRA_OK;
@@ -560,9 +633,10 @@ static kadabra::SampleLaunch base_launch(const kadabra_query *q)
     a.off = q->g->d_off;
     a.off64 = q->g->off64;
     a.adj = q->g->d_adj;
-    a.recs = q->g->d_recs;
-    a.queues = q->g->d_queues;
-    a.bits = q->vd <= kadabra::kBitsMaxVD ? q->g->d_bits : nullptr;
+    a.slots = q->g->ws;
+    a.spill = q->g->spill;
+    a.use_bits = q->vd <= kadabra::kBitsMaxVD ? 1 : 0;
+    a.spin_limit = 1ULL << 24;
     a.seed = q->p.seed;
     a.K = q->K;
     a.strict = (q->p.flags & KADABRA_STRICT_SIGMA) ? 1 : 0;
@@ -574,7 +648,7 @@ static kadabra::SampleLaunch base_launch(const kadabra_query *q)
 // may have re-sized it), nor more than there are samples.
 static int clamp_grid(const kadabra_query *q, int64_t count)
 {
-    int64_t g = q->slots < q->g->ws_slots ? q->slots : q->g->ws_slots;
+    int64_t g = q->slots < q->g->ws.count ? q->slots : q->g->ws.count;
     if (count < g) g = count;
     return (int)g;
 }
@@ -684,9 +758,9 @@ static kadabra_status slot_events(kadabra_query *q, int slot)
 // Sampling scratch of the graph for launches that serve this query alone.
 static kadabra_status ready_workspace(kadabra_query *q)
 {
-    kadabra_status s = ensure_workspace(q->g, q->p.slots, q->p.threads, q->p.scratch_fraction);
+    kadabra_status s = ensure_workspace(q->g, q->p.slots, q->p.threads, q->p.scratch_fraction, q->p.queue_cap);
     if (s != KADABRA_OK) return s;
-    q->slots = q->p.slots > 0 && q->p.slots < q->g->ws_slots ? q->p.slots : q->g->ws_slots;
+    q->slots = q->p.slots > 0 && q->p.slots < q->g->ws.count ? q->p.slots : q->g->ws.count;
     return KADABRA_OK;
 }
 
@@ -982,10 +1056,8 @@ extern "C" kadabra_status kadabra_run_pipelined(kadabra_query *q, int64_t epoch_
     kadabra::BatchLaunch B{};
     B.queries = q->d_desc;
     B.nq = 1;
-    B.recs = q->g->d_recs;
-    B.queues = q->g->d_queues;
-    B.bits = q->g->d_bits;
-    B.stride = q->g->n;
+    B.slots = q->g->ws;
+    B.spill = q->g->spill;
     B.bs = q->d_bs;
     B.budget = 0;
     B.spin_limit = 1ULL << 24;
@@ -1027,20 +1099,24 @@ extern "C" kadabra_status kadabra_batch_create(int64_t max_n, int32_t slots, int
     b->slots = slots;
     b->threads = threads;
     b->off64 = offsets_is_64 ? 1 : 0;
-    const size_t nrec = (size_t)slots * (size_t)max_n;
-    const size_t nbits = (size_t)slots * 2 * (size_t)kadabra::bit_words(max_n);
-    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&b->d_recs), nrec * sizeof(kadabra::SlotRec));
-    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&b->d_queues), nrec * sizeof(uint32_t));
-    if (e == cudaSuccess) e = cudaMemset(b->d_recs, 0, nrec * sizeof(kadabra::SlotRec));
-    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&b->d_bits), nbits * sizeof(uint32_t));
-    if (e == cudaSuccess) e = cudaMemset(b->d_bits, 0, nbits * sizeof(uint32_t));
+    size_t free_b = 0, total_b = 0;
+    KCUDA(cudaMemGetInfo(&free_b, &total_b), "cudaMemGetInfo");
+    int fit = 0, nspill = 0;
+    long long cap = 0;
+    kadabra::plan_slots(max_n, slots, (size_t)((double)free_b * 0.6), 0, &fit, &cap, &nspill);
+    if (fit < 1) {
+        delete b;
+        return fail(KADABRA_ERR_OOM, "not enough device memory for one sampling slot");
+    }
+    b->slots = fit;
+    cudaError_t e = kadabra::alloc_slot_set(&b->ws, fit, max_n, cap, true, false);
+    if (e == cudaSuccess) e = kadabra::alloc_slot_set(&b->spill, nspill, max_n, max_n, true, true);
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&b->d_bs), sizeof(kadabra::BatchState));
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev1);
     if (e != cudaSuccess) {
-        cudaFree(b->d_recs);
-        cudaFree(b->d_queues);
-        cudaFree(b->d_bits);
+        kadabra::free_slot_set(&b->ws);
+        kadabra::free_slot_set(&b->spill);
         cudaFree(b->d_bs);
         delete b;
         return cuda_fail(e, "allocate batch scratch");
@@ -1053,9 +1129,8 @@ extern "C" kadabra_status kadabra_batch_free(kadabra_batch *b)
 {
     if (!b) return KADABRA_OK;
     cudaDeviceSynchronize();
-    cudaFree(b->d_recs);
-    cudaFree(b->d_queues);
-    cudaFree(b->d_bits);
+    kadabra::free_slot_set(&b->ws);
+    kadabra::free_slot_set(&b->spill);
     cudaFree(b->d_descs);
     cudaFree(b->d_states);
     cudaFree(b->d_bs);
@@ -1101,10 +1176,8 @@ extern "C" kadabra_status kadabra_batch_step(kadabra_batch *b, kadabra_query *co
     kadabra::BatchLaunch B{};
     B.queries = b->d_descs;
     B.nq = (int)count;
-    B.recs = b->d_recs;
-    B.queues = b->d_queues;
-    B.bits = b->d_bits;
-    B.stride = b->max_n;
+    B.slots = b->ws;
+    B.spill = b->spill;
     B.bs = b->d_bs;
     B.budget = sample_budget;
     B.spin_limit = b->spin_limit;
@@ -1427,6 +1500,8 @@ extern "C" kadabra_status kadabra_query_get_info(kadabra_query *q, kadabra_query
     I.launches = q->launches;
     I.diameter_ms = q->diameter_ms;
     I.calibration_ms = q->calibration_ms;
+    I.queue_cap = q->g->ws.cap;
+    I.spill_slots = q->g->spill.count;
     I.cal_done = q->phase == 2 ? (uint64_t)q->n_calib : 0ULL;
     if (q->phase == 1) {
         kadabra::PipeState ps{};

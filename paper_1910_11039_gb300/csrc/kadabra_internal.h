@@ -8,26 +8,37 @@ struct kadabra_graph;
 
 namespace kadabra {
 
-// Per-vertex sampling state of one in-flight sample (one "slot"), per BFS side:
-//   lvl[side] = BFS distance + 1 from that side's source (0 = not reached);
-//   sig[side] = number of shortest paths from that side's source, an exact
-//               uint64: a layer's counts are kept at most 2^K with
-//               K <= 63 - bitlen(max degree), so a count of the next layer (a
-//               sum of at most max-degree of them) stays below 2^63.
-// A first discovery claims the vertex with a CAS on its level; every
-// contribution to the path count, the first included, is an atomic add.
-// Invariant between samples: every record of a slot is all-zero (the sample
-// that touched a record clears it before the slot takes its next sample).
-// A record fills one 32-byte sector: records of different vertices never
-// share a sector, the two levels come in one 8-byte load and the two counts
-// in one 16-byte load, and the clearing store writes the whole sector, so the
-// cache does not read the sector back from DRAM first.
-struct alignas(32) SlotRec {
-    unsigned int lvl[2];
-    unsigned int pad[2];
-    unsigned long long sig[2];
+// Sampling scratch of a set of slots, one in-flight sample each.  Per slot:
+//   code[stride]  one word per vertex: 0 = not reached; else bit 31 = the side
+//                 that reached it (0: s, 1: t) and bits 0..30 = its queue
+//                 position + 1, or all ones while the claim that reached it is
+//                 being published.  Zero at rest.
+//   cap queue positions shared by the two sides (s from the front, t from
+//   the back; the balls are disjoint until they meet), in four arrays:
+//     qv  vertex id,   ql  BFS level (distance from the side's source),
+//     qs  exact path count from the side's source, an exact uint64: a
+//         layer's counts are kept at most 2^K with K <= 63 - bitlen(max
+//         degree), so a count of the next layer stays below 2^63;
+//     qm  for vertices of the other side's last layer: their path count from
+//         the expanding side (the meeting vertices' second factor).
+//     qs and qm are zero at rest.
+//   bits (optional): two reached-bit maps of ceil(stride / 32) words each.
+// A sample clears what it set before the slot takes its next sample, so no
+// O(n) reset is needed.  A slot with cap < stride serves samples whose two
+// balls hold at most cap vertices; a sample that outgrows it is cleared and
+// re-run on a spill slot (cap = stride), so results never depend on cap.
+struct SlotSet {
+    uint32_t *code = nullptr;
+    uint32_t *qv = nullptr;
+    uint32_t *ql = nullptr;
+    unsigned long long *qs = nullptr;
+    unsigned long long *qm = nullptr;
+    uint32_t *bits = nullptr;
+    long long stride = 0;      // largest n the slots serve
+    long long cap = 0;         // queue positions per slot (2 <= cap <= stride)
+    int count = 0;             // slots
+    int *lock = nullptr;       // spill sets: one word per slot, 0 = free
 };
-static_assert(sizeof(SlotRec) == 32, "SlotRec fills a 32-byte sector");
 
 // words of one side's reached-bit map for n vertices
 inline __host__ __device__ long long bit_words(long long n) { return (n + 31) / 32; }
@@ -70,6 +81,7 @@ enum : unsigned int {
     kErrDepth = 16u,           // reserved: levels are 32-bit, so no side can run out of them
     kErrTimeout = 32u,         // a bounded wait for a free counter frame gave up
     kErrLogOverflow = 64u,     // an epoch log overflowed (a path longer than VD - 2)
+    kErrScratch = 128u,        // a sample outgrew its slot and no spill slot was configured
 };
 
 // Per-sample trace record (mirrors kadabra_trace_rec).
@@ -87,8 +99,8 @@ struct SampleLaunch {
     const void *off;           // int32 or int64 offsets (n + 1)
     int off64;
     const uint2 *adj;          // (neighbour id, neighbour degree) per adjacency entry
-    SlotRec *recs;             // slots * n
-    uint32_t *queues;          // slots * n
+    SlotSet slots;             // one per CTA (stride >= n)
+    SlotSet spill;             // taken by samples that outgrow their slot (may be empty)
     uint32_t *counts;          // c~[n]; nullptr: do not count (trace runs)
     Job *job;
     Counters *launch_ctr;      // this launch's own counters (zeroed before the launch), may be null
@@ -105,11 +117,15 @@ struct SampleLaunch {
     int grid;
     int threads;
     const int *abandon;        // optional: a sample stops at its next layer once *abandon != 0
-    uint32_t *bits;            // optional: per slot, one bit per vertex and side (reached by
-                               // that side), 2 * ceil(n / 32) words per slot, zero at rest
+    int use_bits;              // use the slots' reached-bit maps (graphs of small diameter)
+    unsigned long long spin_limit;   // bounded waits (spill slot, claims being published)
 };
 
 cudaError_t launch_sample(const SampleLaunch &a, cudaStream_t st);
+// Device bytes of `count` slots; allocation (zeroed) and release of a slot set.
+size_t slot_set_bytes(int count, long long stride, long long cap, bool bits, bool lock);
+cudaError_t alloc_slot_set(SlotSet *S, int count, long long stride, long long cap, bool bits, bool lock);
+void free_slot_set(SlotSet *S);
 cudaError_t launch_build_adj(int64_t nnz, const void *off, int off64, const int32_t *col, uint2 *adj,
                              cudaStream_t st);
 // diameter phase (graph_kernels.cu)
@@ -135,6 +151,9 @@ struct PipeState {
     unsigned long long base;            // tau when the pipeline began
     unsigned long long R;               // samples the pipeline may take (ceil(omega) - base)
     long long nE;                       // epochs in R
+    Counters fc[kMaxFrames];            // counters of the epoch each frame holds: added to the
+                                        // query's totals when that epoch is checked, so samples
+                                        // of epochs after the stop are never counted
 };
 
 // One query of a pipelined launch (device memory, written by the host).
@@ -172,10 +191,8 @@ struct BatchState {
 struct BatchLaunch {
     QueryDesc *queries;        // device array
     int nq;
-    SlotRec *recs;             // slots * stride
-    uint32_t *queues;          // slots * stride
-    uint32_t *bits;            // slots * 2 * ceil(stride / 32) words (may be null)
-    long long stride;          // largest n the scratch serves
+    SlotSet slots;             // one per CTA; stride = largest n of the batch
+    SlotSet spill;             // taken by samples that outgrow their slot (may be empty)
     BatchState *bs;
     unsigned long long budget; // samples this launch may hand out (0 = no limit)
     unsigned long long spin_limit;

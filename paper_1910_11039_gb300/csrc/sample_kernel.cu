@@ -19,26 +19,33 @@
 //   the last CTA of the launch advances tau (A5: stream order makes the
 //   counter vector at the next kernel a consistent snapshot).
 //
-// Layout in HBM (per slot): SlotRec[n] (32 B per vertex, one sector: the two
-// sides' 32-bit BFS levels, padding, the two sides' exact 64-bit path counts), a
-// uint32 queue of n entries shared by both sides (s-side grows from the front,
-// t-side from the back; the balls are disjoint until they meet, so n entries
-// always suffice) and, for each side, one reached bit per vertex.  Records
-// and bits are cleared by the sample that set them, so no per-sample O(n)
-// reset is needed; the clearing store writes a record's whole sector.
+// Layout in HBM (per slot, see SlotSet): one 32-bit code word per vertex
+// (0 = not reached; else the side that reached it and its queue position), a
+// queue of `cap` positions shared by both sides (s-side grows from the front,
+// t-side from the back; the balls are disjoint until they meet) holding each
+// reached vertex's id, BFS level and exact 64-bit path count, a meeting-count
+// array beside it, and, for each side, one reached bit per vertex.  The code
+// word is the only per-vertex state (4 B per vertex and slot), so many slots
+// fit even when n is large; a sample whose balls outgrow `cap` runs again on
+// a spill slot with cap = n.  Everything is cleared by the sample that set it,
+// so no per-sample O(n) reset is needed.
 //
 // Latency hiding inside one CTA: the layer expansion assigns adjacency
 // entries to threads by a block-wide prefix sum over the frontier's degrees
 // (every thread gets the same share whatever the degree skew) and keeps
-// kUnroll entries per thread in flight: their column ids, then their
-// (level_s, level_t) pairs (one 8-byte load), then the claims and the
-// path-count additions, issued together and waited on once per batch.
+// kUnroll entries per thread in flight: their column ids, then their code
+// words (one 4-byte load), then the claims and the path-count additions,
+// issued together and waited on once per batch.  A claim CASes the code word
+// to "pending", takes a queue position (warp-aggregated) and publishes it;
+// an addition that meets a pending claim waits (bounded) for the position.
+// A meeting vertex (a target in the other side's last layer) is never
+// claimed: its second path count is added at its existing queue position.
 //
 // The last layer: as soon as a target of the layer is found on the other
-// side, the layer is the last one and only meeting vertices need records;
+// side, the layer is the last one and only meeting vertices need counts;
 // other targets are not claimed, and on graphs of small diameter an edge then
 // reads only the other side's reached bit (a dense map that stays in L2)
-// instead of the target's record.
+// before the target's code word.
 //
 // The meeting-vertex choice and walk steps with at most 32 candidates run in
 // warp 0 with shuffles, without block barriers; larger ones use the CTA (and,
@@ -67,25 +74,9 @@ constexpr int kPathCap = 1024;     // path vertices buffered in shared memory be
 constexpr int kUnroll = KADABRA_UNROLL;   // adjacency entries in flight per thread
 constexpr unsigned int kNone = 0xffffffffu;
 
-__device__ __forceinline__ unsigned int ldcg(const unsigned int *p) { return __ldcg(p); }
 __device__ __forceinline__ unsigned long long ldcg(const unsigned long long *p) { return __ldcg(p); }
 
 __device__ __forceinline__ int bitlen64(unsigned long long x) { return 64 - __clzll(x); }
-
-// both sides' levels of a record, one 8-byte load from L2
-__device__ __forceinline__ void load_lvls(const SlotRec *r, unsigned int &l0, unsigned int &l1)
-{
-    const uint2 v = __ldcg(reinterpret_cast<const uint2 *>(r->lvl));
-    l0 = v.x;
-    l1 = v.y;
-}
-// both sides' path counts of a record, one 16-byte load from L2
-__device__ __forceinline__ void load_sigs(const SlotRec *r, unsigned long long &p, unsigned long long &q)
-{
-    const ulonglong2 v = __ldcg(reinterpret_cast<const ulonglong2 *>(r->sig));
-    p = v.x;
-    q = v.y;
-}
 
 __device__ __forceinline__ unsigned long long global_ns()
 {
@@ -119,7 +110,7 @@ struct Smem {
     unsigned int lend[2][kMaxLayers];
     int X;                           // side expanded this layer
     int status;                      // 0 running, 1 met, 2 disconnected, 3 strict overflow,
-                                     // 5 discarded (its query stopped)
+                                     // 5 discarded (its query stopped), 6 out of queue positions
     int scaled;
     unsigned int err;
     // per-layer accumulators
@@ -137,6 +128,9 @@ struct Smem {
     unsigned int prefix;
     unsigned int pcnt;
     long long chosen;
+    unsigned int pw;                 // queue position of the chosen meeting vertex on the other side
+    int ovf;                         // a claim found no free queue position
+    int spill_k;                     // spill slot taken by this CTA (-1: none)
     long long next_v;
     int found;
     unsigned long long cur;          // work item taken by this CTA
@@ -152,6 +146,7 @@ struct Smem {
     unsigned long long tmp[NT / 32];
     unsigned long long tmp2[NT / 32];
     unsigned int cand[kMeetCap];     // candidate ids (meeting set or predecessors)
+    unsigned int cpos[kMeetCap];     // meeting set: queue positions on the other side
     unsigned long long wlo[kMeetCap];
     unsigned long long whi[kMeetCap];
     union {
@@ -381,19 +376,41 @@ __device__ __forceinline__ void warp_pick64(Smem<NT> &sh, unsigned int cnt, unsi
     if (lane == 0) sh.next_v = m ? (long long)pick : -1;
 }
 
-// ---- queue of one side ---------------------------------------------------
+// ---- one slot's scratch ----------------------------------------------------
 
-__device__ __forceinline__ unsigned int qget(const uint32_t *q, long long n, int side, unsigned int i)
-{
-    return side == 0 ? __ldcg(q + i) : __ldcg(q + (n - 1 - i));
-}
+constexpr unsigned int kSideBit = 0x80000000u;
+constexpr unsigned int kPosMask = 0x7fffffffu;
+constexpr unsigned int kPending = kPosMask;   // position field while a claim is being published
 
-__device__ __forceinline__ void qset(uint32_t *q, long long n, int side, unsigned int i, unsigned int v)
+__device__ __forceinline__ unsigned int code_of(int side, unsigned int p) { return (side ? kSideBit : 0u) | (p + 1u); }
+__device__ __forceinline__ int side_of(unsigned int c) { return (int)(c >> 31); }
+__device__ __forceinline__ bool is_pending(unsigned int c) { return (c & kPosMask) == kPending; }
+__device__ __forceinline__ unsigned int pos_of(unsigned int c) { return (c & kPosMask) - 1u; }
+
+// One slot's view of a SlotSet.
+struct Slot {
+    uint32_t *code;
+    uint32_t *qv, *ql;
+    unsigned long long *qs, *qm;
+    uint32_t *bits;            // null: the sample does not use reached-bit maps
+    long long bw;              // words of one side's map
+    unsigned int cap;
+    // array index of a side's queue position p
+    __device__ __forceinline__ unsigned int at(int side, unsigned int p) const { return side ? cap - 1u - p : p; }
+};
+
+__device__ __forceinline__ Slot slot_of(const SlotSet &S, int k, bool use_bits)
 {
-    if (side == 0)
-        __stcg(q + i, v);
-    else
-        __stcg(q + (n - 1 - i), v);
+    Slot s;
+    s.code = S.code + (size_t)k * (size_t)S.stride;
+    s.qv = S.qv + (size_t)k * (size_t)S.cap;
+    s.ql = S.ql + (size_t)k * (size_t)S.cap;
+    s.qs = S.qs + (size_t)k * (size_t)S.cap;
+    s.qm = S.qm + (size_t)k * (size_t)S.cap;
+    s.bw = bit_words(S.stride);
+    s.bits = (use_bits && S.bits) ? S.bits + (size_t)k * (size_t)(2 * s.bw) : nullptr;
+    s.cap = (unsigned int)S.cap;
+    return s;
 }
 
 // Is `key` in the ascending neighbour list adj[b, b + d)?
@@ -408,6 +425,15 @@ __device__ __forceinline__ bool contains(const uint2 *adj, long long b, long lon
     return lo < b + d && (long long)__ldg(&adj[lo].x) == key;
 }
 
+// Path count of u if it was reached by `side` at BFS level `level`, else 0.
+__device__ __forceinline__ unsigned long long pred_weight(const Slot &S, int side, long long u, unsigned int level)
+{
+    const unsigned int c = __ldcg(S.code + u);
+    if (c == 0u || side_of(c) != side || is_pending(c)) return 0ULL;
+    const unsigned int ph = S.at(side, pos_of(c));
+    return __ldcg(S.ql + ph) == level ? __ldcg(S.qs + ph) : 0ULL;
+}
+
 // ---- one sample ------------------------------------------------------------
 
 // Where a sample's interior vertices go: straight into c~ (epoch launches,
@@ -417,19 +443,6 @@ struct CountSink {
     uint32_t *log;
     unsigned int *len;
     unsigned int cap;
-    __device__ __forceinline__ unsigned int add(long long v) const
-    {
-        if (counts) {
-            const unsigned int old = atomicAdd(&counts[v], 1u);
-            return old == 0xffffffffu ? kErrCounterOverflow : 0u;
-        }
-        if (log) {
-            const unsigned int p = atomicAdd(len, 1u);
-            if (p >= cap) return kErrLogOverflow;
-            __stcg(log + p, (unsigned int)v);
-        }
-        return 0u;
-    }
 };
 
 // Warp 0 hands the buffered path vertices path[0, cnt) to the sink (counter
@@ -459,10 +472,15 @@ struct LocalStats {
     unsigned long long samples, connected, e_scan, expanded, touched, interior, walk_scan, scaled;
 };
 
+// kinds of a scanned adjacency target (phase 2 of a layer)
+enum : int { kTSkip = 0, kTUnseen = 1, kTMeet = 2, kTSame = 3, kTPend = 4 };
+
+// Runs sample `idx` in slot S.  Returns false if the sample's two balls
+// outgrew the slot's queue capacity: the slot is then clear again and
+// nothing was counted, and the caller runs the sample on a larger slot.
 template <int NT, typename OffT>
-__device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotRec *rec, uint32_t *queue,
-                           uint32_t *bits, long long bw, Smem<NT> &sh, unsigned long long idx,
-                           unsigned long long trace_i, LocalStats &ls, const CountSink &sink)
+__device__ bool run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, const Slot &S, Smem<NT> &sh,
+                           unsigned long long idx, unsigned long long trace_i, LocalStats &ls, const CountSink &sink)
 {
     const int tid = threadIdx.x;
     const long long n = G.n;
@@ -477,16 +495,19 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
         if (t >= s) ++t;
         sh.s = (long long)s;
         sh.t = (long long)t;
-        __stcg(&rec[s].lvl[0], 1u);
-        __stcg(&rec[s].sig[0], 1ULL);
-        __stcg(&rec[t].lvl[1], 1u);
-        __stcg(&rec[t].sig[1], 1ULL);
-        if (bits) {
-            atomicOr(&bits[s >> 5], 1u << (s & 31));
-            atomicOr(&bits[bw + (t >> 5)], 1u << (t & 31));
+        const unsigned int ps = S.at(0, 0u), pt = S.at(1, 0u);
+        __stcg(S.code + s, code_of(0, 0u));
+        __stcg(S.code + t, code_of(1, 0u));
+        __stcg(S.qv + ps, (unsigned int)s);
+        __stcg(S.qv + pt, (unsigned int)t);
+        __stcg(S.ql + ps, 0u);
+        __stcg(S.ql + pt, 0u);
+        __stcg(S.qs + ps, 1ULL);
+        __stcg(S.qs + pt, 1ULL);
+        if (S.bits) {
+            atomicOr(&S.bits[s >> 5], 1u << (s & 31));
+            atomicOr(&S.bits[S.bw + (t >> 5)], 1u << (t & 31));
         }
-        qset(queue, n, 0, 0, (unsigned int)s);
-        qset(queue, n, 1, 0, (unsigned int)t);
         sh.qlen[0] = sh.qlen[1] = 1;
         sh.fbeg[0] = sh.fbeg[1] = 0;
         sh.fend[0] = sh.fend[1] = 1;
@@ -498,6 +519,7 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
         sh.status = 0;
         sh.scaled = 0;
         sh.err = 0;
+        sh.ovf = 0;
         sh.e_scan = 0;
         sh.expanded = 0;
         sh.meet_count = 0;
@@ -515,10 +537,13 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
     // the next layer is chosen, and the layer accumulators cleared, by thread
     // 0 at the end of the previous layer, inside that layer's last barrier.
     for (;;) {
-        const int X = sh.X;
-        const unsigned int nl = sh.layer[X] + 2;    // level code of the new layer
+        const int X = sh.X, Y = 1 - X;
+        const unsigned int nl = sh.layer[X] + 1;     // level of the new layer
         const unsigned int fb = sh.fbeg[X], fe = sh.fend[X];
-        const unsigned int qbase = sh.qlen[X];
+        const unsigned int qbase = sh.qlen[X];       // queue position of the new layer's first vertex
+        const unsigned int room = S.cap - sh.qlen[Y];   // positions this side may fill
+        const unsigned int yb = sh.fbeg[Y], ye = sh.fend[Y];
+        const unsigned int pend_code = (X ? kSideBit : 0u) | kPending;
         unsigned long long my_max = 0, my_scan = 0, my_deg = 0;
         const int lane = tid & 31;
 
@@ -527,10 +552,11 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
             long long b = 0;
             unsigned long long d = 0, sg = 0;
             if (i < fe) {
-                const unsigned int u = qget(queue, n, X, i);
+                const unsigned int ph = S.at(X, i);
+                const unsigned int u = __ldcg(S.qv + ph);
                 b = G.begin(u);
                 d = (unsigned long long)(G.end(u) - b);
-                sg = ldcg(&rec[u].sig[X]);
+                sg = ldcg(S.qs + ph);
             }
             unsigned long long total;
             const unsigned long long excl = block_excl_scan<NT>(d, &total, sh);
@@ -568,104 +594,154 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
                         dw[j] = c.y;
                     }
                 }
-                // phase 2: (level_s, level_t) of every target, one 8-byte load
-                // each; once the layer is known to be the last, only the other
-                // side's reached bit (a dense map that stays in L2): targets
-                // without it are skipped, targets with it are claimed or counted
-                // (lx = 0 lets the claim decide; 1 is no level of this layer)
-                unsigned int lx[kUnroll];
-                unsigned int ymask = 0;
-                const bool fast = bits != nullptr && *(volatile int *)&sh.meets != 0;
+                // phase 2: the code word of every target (one 4-byte load each);
+                // once the layer is known to be the last, only the other side's
+                // reached bit first (a dense map that stays in L2), and the code
+                // only of targets that have it
+                unsigned int cd[kUnroll];
+                int kind[kUnroll];
+                const bool fast = S.bits != nullptr && *(volatile int *)&sh.meets != 0;
                 if (fast) {
-                    const uint32_t *ybits = bits + (X ? 0 : bw);
+                    const uint32_t *ybits = S.bits + (X ? 0 : S.bw);
+                    unsigned int ymask = 0;
 #pragma unroll
-                    for (int j = 0; j < kUnroll; ++j) {
-                        lx[j] = 1u;
-                        if (w[j] != kNone && ((__ldcg(ybits + (w[j] >> 5)) >> (w[j] & 31)) & 1u)) {
-                            lx[j] = 0u;
-                            ymask |= 1u << j;
-                        }
-                    }
+                    for (int j = 0; j < kUnroll; ++j)
+                        if (w[j] != kNone && ((__ldcg(ybits + (w[j] >> 5)) >> (w[j] & 31)) & 1u)) ymask |= 1u << j;
+#pragma unroll
+                    for (int j = 0; j < kUnroll; ++j) cd[j] = ((ymask >> j) & 1u) ? __ldcg(S.code + w[j]) : 0u;
+#pragma unroll
+                    for (int j = 0; j < kUnroll; ++j) kind[j] = ((ymask >> j) & 1u) ? kTMeet : kTSkip;
                 } else {
 #pragma unroll
+                    for (int j = 0; j < kUnroll; ++j) cd[j] = w[j] != kNone ? __ldcg(S.code + w[j]) : 0u;
+#pragma unroll
                     for (int j = 0; j < kUnroll; ++j) {
-                        lx[j] = 1u;
-                        if (w[j] != kNone) {
-                            unsigned int l0, l1;
-                            load_lvls(rec + w[j], l0, l1);
-                            lx[j] = X ? l1 : l0;
-                            ymask |= ((X ? l0 : l1) != 0 ? 1u : 0u) << j;
+                        const unsigned int c = cd[j];
+                        kind[j] = w[j] == kNone ? kTSkip
+                                  : c == 0u ? kTUnseen
+                                  : side_of(c) != X ? kTMeet
+                                  : is_pending(c) ? kTPend
+                                  : pos_of(c) >= qbase ? kTSame : kTSkip;
+                    }
+                }
+                // a target held by the other side makes this layer the last one:
+                // from then on only meeting vertices need counts, so other unseen
+                // targets of the last layer are not claimed
+#pragma unroll
+                for (int j = 0; j < kUnroll; ++j)
+                    if (kind[j] == kTMeet) *(volatile int *)&sh.meets = 1;
+                const bool last = *(volatile int *)&sh.meets != 0;
+                // phase 3: claims (CAS on the code word to "pending"), path-count
+                // additions to targets already in the new layer, and meeting
+                // counts (the other side's last layer, indexed by its queue
+                // position).  The additions return their old value, so a thread
+                // has waited for all of them before the layer's closing barrier
+                // and every count is complete when any thread reads it next.
+                unsigned int cmask = 0, mfirst = 0, retry = 0;
+#pragma unroll
+                for (int j = 0; j < kUnroll; ++j) {
+                    if (kind[j] == kTUnseen) {
+                        if (last) {
+                            kind[j] = kTSkip;
+                        } else {
+                            const unsigned int old = atomicCAS(S.code + w[j], 0u, pend_code);
+                            if (old == 0u) {
+                                cmask |= 1u << j;
+                            } else {
+                                // claimed in this layer by another thread meanwhile
+                                cd[j] = old;
+                                kind[j] = is_pending(old) ? kTPend : kTSame;
+                            }
                         }
                     }
                 }
-                // an unseen target that the other side holds makes this layer
-                // the last one: from then on only meeting vertices need a record
-                // (their path counts); other targets of the last layer are never
-                // read again, so their claims are skipped
-#pragma unroll
-                for (int j = 0; j < kUnroll; ++j)
-                    if (w[j] != kNone && lx[j] == 0 && ((ymask >> j) & 1u)) *(volatile int *)&sh.meets = 1;
-                const bool last = *(volatile int *)&sh.meets != 0;
-                // phase 3: claim unseen targets for the new layer (a CAS on the
-                // level) and add the source's path count to every target of
-                // the new layer.  A target read as unseen can only have been
-                // claimed for this layer since (by this CTA), so its count gets
-                // the addition whoever wins the claim: claim and addition are
-                // issued back to back.  The additions return their old value,
-                // so a thread has waited for all of them before the layer's
-                // closing barrier and every count is complete when any thread
-                // reads it next.
-                unsigned int cmask = 0;
-                unsigned int old_l[kUnroll];
-                unsigned long long old_s[kUnroll];
 #pragma unroll
                 for (int j = 0; j < kUnroll; ++j) {
-                    old_l[j] = kNone;
-                    if (w[j] != kNone && lx[j] == 0 && (!last || ((ymask >> j) & 1u))) {
-                        old_l[j] = atomicCAS(&rec[w[j]].lvl[X], 0u, nl);
-                        old_s[j] = atomicAdd(&rec[w[j]].sig[X], sh.u.ex.csig[own[j]]);
-                    } else if (w[j] != kNone && lx[j] == nl) {
-                        old_l[j] = nl;
-                        old_s[j] = atomicAdd(&rec[w[j]].sig[X], sh.u.ex.csig[own[j]]);
-                    }
-                }
-#pragma unroll
-                for (int j = 0; j < kUnroll; ++j) {
-                    if (old_l[j] == kNone) continue;
-                    if (old_l[j] == 0u) {
-                        cmask |= 1u << j;
-                    } else if (old_l[j] != nl) {
-                        atomicOr(&sh.err, kErrSelect);     // broken invariant: never expected
-                        continue;
-                    }
                     const unsigned long long su = sh.u.ex.csig[own[j]];
-                    const unsigned long long nv = old_s[j] + su;
-                    if (nv < su) atomicOr(&sh.err, kErrAddOverflow);     // excluded by the choice of K
-                    my_max = nv > my_max ? nv : my_max;
+                    if (kind[j] == kTMeet) {
+                        const unsigned int p = pos_of(cd[j]);
+                        if (side_of(cd[j]) != Y || is_pending(cd[j]) || p < yb || p >= ye) {
+                            atomicOr(&sh.err, kErrSelect);     // broken invariant: never expected
+                            continue;
+                        }
+                        const unsigned long long old = atomicAdd(S.qm + S.at(Y, p), su);
+                        if (old == 0ULL) mfirst |= 1u << j;
+                        if (old + su < su) atomicOr(&sh.err, kErrAddOverflow);
+                    } else if (kind[j] == kTSame) {
+                        const unsigned int p = pos_of(cd[j]);
+                        if (side_of(cd[j]) != X || p < qbase) {
+                            atomicOr(&sh.err, kErrSelect);
+                            continue;
+                        }
+                        const unsigned long long nv = atomicAdd(S.qs + S.at(X, p), su) + su;
+                        if (nv < su) atomicOr(&sh.err, kErrAddOverflow);      // excluded by the choice of K
+                        my_max = nv > my_max ? nv : my_max;
+                    } else if (kind[j] == kTPend) {
+                        retry |= 1u << j;
+                    }
                 }
-                // phase 5: claimed targets join the new frontier (warp-aggregated
-                // queue slots) or, if the other side already holds them, the
-                // meeting set
+                // phase 4: claimed targets join the new frontier (warp-aggregated
+                // queue positions), get their first path count and publish their
+                // position; first-touched meeting vertices join the meeting set
 #pragma unroll
                 for (int j = 0; j < kUnroll; ++j) {
                     const bool claimed = (cmask >> j) & 1u;
-                    const bool meets = claimed && ((ymask >> j) & 1u);
-                    const bool joins = claimed && !meets;
-                    const unsigned int m = __ballot_sync(0xffffffffu, joins);
+                    const unsigned int m = __ballot_sync(0xffffffffu, claimed);
                     if (m) {
                         const int leader = __ffs(m) - 1;
                         unsigned int slot0 = 0;
                         if (lane == leader) slot0 = atomicAdd(&sh.new_count, (unsigned int)__popc(m));
                         slot0 = __shfl_sync(0xffffffffu, slot0, leader);
-                        if (joins) {
-                            qset(queue, n, X, qbase + slot0 + __popc(m & ((1u << lane) - 1u)), w[j]);
-                            my_deg += dw[j];
-                            if (bits) atomicOr(&bits[(X ? bw : 0) + (w[j] >> 5)], 1u << (w[j] & 31));
+                        if (claimed) {
+                            const unsigned int p = qbase + slot0 + __popc(m & ((1u << lane) - 1u));
+                            if (p < room) {
+                                const unsigned int ph = S.at(X, p);
+                                const unsigned long long su = sh.u.ex.csig[own[j]];
+                                __stcg(S.qv + ph, w[j]);
+                                __stcg(S.ql + ph, nl);
+                                const unsigned long long nv = atomicAdd(S.qs + ph, su) + su;
+                                if (nv < su) atomicOr(&sh.err, kErrAddOverflow);
+                                my_max = nv > my_max ? nv : my_max;
+                                __stcg(S.code + w[j], code_of(X, p));
+                                my_deg += dw[j];
+                                if (S.bits) atomicOr(&S.bits[(X ? S.bw : 0) + (w[j] >> 5)], 1u << (w[j] & 31));
+                            } else {
+                                // out of queue positions: the sample restarts on a larger slot
+                                *(volatile int *)&sh.ovf = 1;
+                                __stcg(S.code + w[j], 0u);
+                            }
                         }
                     }
-                    if (meets) {
+                    if ((mfirst >> j) & 1u) {
                         const unsigned int p = atomicAdd(&sh.meet_count, 1u);
-                        if (p < kMeetCap) sh.cand[p] = w[j];
+                        if (p < kMeetCap) {
+                            sh.cand[p] = w[j];
+                            sh.cpos[p] = pos_of(cd[j]);
+                        }
+                    }
+                }
+                // phase 5: additions to targets whose claim (by another warp) was
+                // still being published; this warp published its own claims above
+                __syncwarp();
+                if (retry) {
+#pragma unroll
+                    for (int j = 0; j < kUnroll; ++j) {
+                        if (!((retry >> j) & 1u)) continue;
+                        unsigned int c = *reinterpret_cast<volatile unsigned int *>(S.code + w[j]);
+                        unsigned long long spins = 0;
+                        while (is_pending(c) && ++spins < a.spin_limit) {
+                            __nanosleep(32);
+                            c = *reinterpret_cast<volatile unsigned int *>(S.code + w[j]);
+                        }
+                        if (is_pending(c)) {
+                            atomicOr(&sh.err, kErrTimeout);
+                            continue;
+                        }
+                        if (c == 0u) continue;      // the claim ran out of positions: the sample restarts
+                        const unsigned long long su = sh.u.ex.csig[own[j]];
+                        const unsigned long long nv = atomicAdd(S.qs + S.at(X, pos_of(c)), su) + su;
+                        if (nv < su) atomicOr(&sh.err, kErrAddOverflow);
+                        my_max = nv > my_max ? nv : my_max;
                     }
                 }
             }
@@ -689,22 +765,28 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
         if (tid == 0) {
             sh.e_scan += my_scan;
             sh.expanded += fe - fb;
-            const unsigned int L = sh.layer[X] + 1;
-            sh.layer[X] = L;
-            sh.qlen[X] += sh.new_count;
-            if (L < (unsigned int)kMaxLayers) {
-                sh.lbeg[X][L] = qbase;
-                sh.lend[X][L] = qbase + sh.new_count;
+            sh.layer[X] = nl;
+            unsigned int nc = sh.new_count;
+            if (nc > room - qbase) {
+                nc = room - qbase;
+                sh.ovf = 1;
             }
-            if (sh.meet_count > 0) {
+            sh.qlen[X] = qbase + nc;
+            if (nl < (unsigned int)kMaxLayers) {
+                sh.lbeg[X][nl] = qbase;
+                sh.lend[X][nl] = qbase + nc;
+            }
+            if (sh.ovf) {
+                sh.status = 6;      // out of queue positions: clear and restart elsewhere
+            } else if (sh.meet_count > 0) {
                 sh.status = 1;
-            } else if (sh.new_count == 0) {
+            } else if (nc == 0) {
                 sh.status = 2;
             } else if (a.abandon && *reinterpret_cast<const volatile int *>(a.abandon)) {
-                sh.status = 5;      // discarded sample: clear its records and leave
+                sh.status = 5;      // discarded sample: clear its state and leave
             } else {
                 sh.fbeg[X] = qbase;
-                sh.fend[X] = qbase + sh.new_count;
+                sh.fend[X] = qbase + nc;
                 sh.fdeg[X] = sh.ldeg;
                 // keep the new layer's counts <= 2^K, rounding up so that they stay >= 1
                 const int shv = bitlen64(sh.lmax) - a.K;
@@ -729,14 +811,11 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
         if (sh.status != 0) break;
         if (sh.shv > 0) {
             const int shv = sh.shv;
-            {
-                for (unsigned int i = sh.fbeg[X] + tid; i < sh.fend[X]; i += NT) {
-                    const unsigned int v = qget(queue, n, X, i);
-                    const unsigned long long sv = ldcg(&rec[v].sig[X]);
-                    __stcg(&rec[v].sig[X], ((sv - 1ULL) >> shv) + 1ULL);
-                }
-                __syncthreads();
+            for (unsigned int i = sh.fbeg[X] + tid; i < sh.fend[X]; i += NT) {
+                unsigned long long *q = S.qs + S.at(X, i);
+                __stcg(q, ((ldcg(q) - 1ULL) >> shv) + 1ULL);
             }
+            __syncthreads();
         }
     }
 
@@ -747,11 +826,11 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
     const int nbits = bitlen64((unsigned long long)(n - 1)) > 0 ? bitlen64((unsigned long long)(n - 1)) : 1;
     const int npass = (nbits + 7) / 8;
     if (met) {
+        // The meeting set is the part of Y's last layer that X's last layer
+        // reached: weight of w = sigma_Y(w) (qs) * sigma_X(w) (qm).
         const int X = sh.X, Y = 1 - X;
-        const unsigned int nl = sh.layer[X] + 1;    // level code of X's last layer
         const unsigned int mcnt = sh.meet_count;
         const bool in_smem = mcnt <= (unsigned int)kMeetCap;
-        // weights sigma_s(w) * sigma_t(w) and their 128-bit total
         unsigned long long tlo = 0, thi = 0;
         if (mcnt <= 32u) {
             // small meeting set: warp 0 alone weighs the candidates, orders
@@ -760,10 +839,11 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
                 const int lane = tid;
                 const bool have = (unsigned int)lane < mcnt;
                 const unsigned int id = have ? sh.cand[lane] : 0xffffffffu;
+                const unsigned int myp = have ? sh.cpos[lane] : 0u;
                 unsigned long long lo = 0, hi = 0;
                 if (have) {
-                    unsigned long long p, q;
-                    load_sigs(rec + id, p, q);
+                    const unsigned int ph = S.at(Y, myp);
+                    const unsigned long long p = ldcg(S.qs + ph), q = ldcg(S.qm + ph);
                     lo = p * q;
                     hi = __umul64hi(p, q);
                 }
@@ -776,11 +856,11 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
                     add128(alo, ahi, ljo, hjo);
                     if (idj < id) add128(plo, phi, ljo, hjo);
                 }
-                long long chosen = -1;
-                unsigned long long rlo = 0, rhi = 0;
+                int pick = -1;
                 if (mcnt == 1) {
-                    chosen = sh.cand[0];
+                    pick = 0;
                 } else {
+                    unsigned long long rlo = 0, rhi = 0;
                     if (lane == 0) {
                         const U64x4 x = sample_draw(a.seed, a.tag, idx, 1);
                         const unsigned __int128 R = ((unsigned __int128)x.v[1] << 64) | x.v[0];
@@ -795,24 +875,21 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
                     add128(elo, ehi, lo, hi);
                     const bool mine = have && !less128(rlo, rhi, plo, phi) && less128(rlo, rhi, elo, ehi);
                     const unsigned int m = __ballot_sync(0xffffffffu, mine);
-                    chosen = m ? (long long)__shfl_sync(0xffffffffu, id, __ffs(m) - 1) : -1;
+                    pick = m ? __ffs(m) - 1 : -1;
                 }
                 if (lane == 0) {
                     sh.sig_lo = alo;
                     sh.sig_hi = ahi;
-                    const bool ok = chosen >= 0 && chosen < n && ldcg(&rec[chosen].lvl[X]) == nl &&
-                                    ldcg(&rec[chosen].lvl[Y]) != 0;
-                    sh.chosen = ok ? chosen : -1;
-                    if (!ok) sh.err |= kErrSelect;
+                    sh.chosen = pick >= 0 ? (long long)sh.cand[pick] : -1;
+                    sh.pw = pick >= 0 ? sh.cpos[pick] : 0u;
                 }
             }
             __syncthreads();
         } else {
             if (in_smem) {
                 for (unsigned int i = tid; i < mcnt; i += NT) {
-                    const unsigned int w = sh.cand[i];
-                    unsigned long long p, q;
-                    load_sigs(rec + w, p, q);
+                    const unsigned int ph = S.at(Y, sh.cpos[i]);
+                    const unsigned long long p = ldcg(S.qs + ph), q = ldcg(S.qm + ph);
                     const unsigned long long lo = p * q, hi = __umul64hi(p, q);
                     sh.wlo[i] = lo;
                     sh.whi[i] = hi;
@@ -820,10 +897,10 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
                 }
             } else {
                 for (unsigned int i = sh.fbeg[Y] + tid; i < sh.fend[Y]; i += NT) {
-                    const unsigned int w = qget(queue, n, Y, i);
-                    if (ldcg(&rec[w].lvl[X]) != nl) continue;
-                    unsigned long long p, q;
-                    load_sigs(rec + w, p, q);
+                    const unsigned int ph = S.at(Y, i);
+                    const unsigned long long q = ldcg(S.qm + ph);
+                    if (q == 0ULL) continue;
+                    const unsigned long long p = ldcg(S.qs + ph);
                     add128(tlo, thi, p * q, __umul64hi(p, q));
                 }
             }
@@ -831,45 +908,54 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
             if (tid == 0) {
                 sh.sig_lo = tlo;
                 sh.sig_hi = thi;
-                if (in_smem && mcnt == 1) {
-                    sh.chosen = sh.cand[0];
-                } else {
-                    const U64x4 x = sample_draw(a.seed, a.tag, idx, 1);
-                    const unsigned __int128 R = ((unsigned __int128)x.v[1] << 64) | x.v[0];
-                    const unsigned __int128 T = ((unsigned __int128)thi << 64) | tlo;
-                    const unsigned __int128 r = R % T;
-                    sh.r_lo = (unsigned long long)r;
-                    sh.r_hi = (unsigned long long)(r >> 64);
-                    sh.chosen = -1;
-                }
+                const U64x4 x = sample_draw(a.seed, a.tag, idx, 1);
+                const unsigned __int128 R = ((unsigned __int128)x.v[1] << 64) | x.v[0];
+                const unsigned __int128 T = ((unsigned __int128)thi << 64) | tlo;
+                const unsigned __int128 r = R % T;
+                sh.r_lo = (unsigned long long)r;
+                sh.r_hi = (unsigned long long)(r >> 64);
+                sh.chosen = -1;
             }
             __syncthreads();
-            if (sh.chosen < 0) {
-                long long c;
-                if (in_smem) {
-                    c = radix_choose<NT>(sh, npass, [&](auto &&add) {
-                        for (unsigned int i = tid; i < mcnt; i += NT) add(sh.cand[i], sh.wlo[i], sh.whi[i]);
-                    });
-                } else {
-                    const unsigned int yb = sh.fbeg[Y], ye = sh.fend[Y];
-                    c = radix_choose<NT>(sh, npass, [&](auto &&add) {
-                        for (unsigned int i = yb + tid; i < ye; i += NT) {
-                            const unsigned int w = qget(queue, n, Y, i);
-                            if (ldcg(&rec[w].lvl[X]) != nl) continue;
-                            unsigned long long p, q;
-                            load_sigs(rec + w, p, q);
-                            add(w, p * q, __umul64hi(p, q));
-                        }
-                    });
-                }
-                if (tid == 0) {
-                    const bool ok = c >= 0 && c < n && ldcg(&rec[c].lvl[X]) == nl && ldcg(&rec[c].lvl[Y]) != 0;
-                    sh.chosen = ok ? c : -1;
-                    if (!ok) sh.err |= kErrSelect;
-                }
-                __syncthreads();
+            long long c;
+            if (in_smem) {
+                c = radix_choose<NT>(sh, npass, [&](auto &&add) {
+                    for (unsigned int i = tid; i < mcnt; i += NT) add(sh.cand[i], sh.wlo[i], sh.whi[i]);
+                });
+            } else {
+                const unsigned int yb = sh.fbeg[Y], ye = sh.fend[Y];
+                c = radix_choose<NT>(sh, npass, [&](auto &&add) {
+                    for (unsigned int i = yb + tid; i < ye; i += NT) {
+                        const unsigned int ph = S.at(Y, i);
+                        const unsigned long long q = ldcg(S.qm + ph);
+                        if (q == 0ULL) continue;
+                        const unsigned long long p = ldcg(S.qs + ph);
+                        add(__ldcg(S.qv + ph), p * q, __umul64hi(p, q));
+                    }
+                });
+            }
+            if (tid == 0) {
+                sh.chosen = c;
+                const unsigned int cc = (c >= 0 && c < n) ? __ldcg(S.code + c) : 0u;
+                sh.pw = pos_of(cc);
+            }
+            __syncthreads();
+        }
+        if (tid == 0) {
+            // the chosen vertex must be in Y's last layer and reached by X
+            const long long c = sh.chosen;
+            bool ok = c >= 0 && c < n;
+            if (ok) {
+                const unsigned int cc = __ldcg(S.code + c);
+                ok = cc == code_of(Y, sh.pw) && sh.pw >= sh.fbeg[Y] && sh.pw < sh.fend[Y] &&
+                     ldcg(S.qm + S.at(Y, sh.pw)) != 0ULL;
+            }
+            if (!ok) {
+                sh.chosen = -1;
+                sh.err |= kErrSelect;
             }
         }
+        __syncthreads();
 
         const long long w = sh.chosen;
         if (tid == 0 && a.trace) t_sel = global_ns();
@@ -882,14 +968,16 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
             }
         }
         // walk towards s (side 0), then towards t (side 1); draws 2, 3, ...
+        // w's level: one past X's last expanded layer on side X, its queue
+        // level on side Y
         unsigned long long k = 2;
         bool walk_ok = w >= 0;
-        unsigned int ww0 = 0, ww1 = 0;
-        if (walk_ok) load_lvls(rec + w, ww0, ww1);
+        const unsigned int lw[2] = {X == 0 ? sh.layer[0] : (walk_ok ? __ldcg(S.ql + S.at(0, sh.pw)) : 0u),
+                                    X == 1 ? sh.layer[1] : (walk_ok ? __ldcg(S.ql + S.at(1, sh.pw)) : 0u)};
         for (int Z = 0; Z < 2 && walk_ok; ++Z) {
             long long v = w;
             const long long src = Z == 0 ? sh.s : sh.t;
-            unsigned int lz = Z == 0 ? ww0 : ww1;   // level code of v on side Z
+            unsigned int lz = lw[Z];     // level of v on side Z
             for (;;) {
                 // Warp 0 alone takes every step from a vertex of degree <= 32
                 // (lanes hold its neighbours) and every step whose predecessor
@@ -903,16 +991,16 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
                     int state = 0;        // 0: a large step at vv, 1: source reached, 2: broken invariant
                     unsigned long long scan = 0;
                     // row of vv, when already known (each lane reads its
-                    // candidate's row with its record, so the chosen
+                    // candidate's row with its state, so the chosen
                     // predecessor's row comes with the choice)
                     long long bb = -1, be = -1;
                     for (;;) {
-                        if (ll <= 1) {
+                        if (ll == 0) {
                             state = 1;
                             break;
                         }
                         const unsigned int tg = ll - 1;
-                        if (ll == 2) {
+                        if (ll == 1) {
                             vv = src;
                             ll = tg;
                             ++kk;
@@ -930,11 +1018,9 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
                         unsigned long long wt = 0;
                         if (tid < dd) {
                             u = G.col(bb + tid);
-                            const unsigned int lu = ldcg(&rec[u].lvl[Z]);
-                            const unsigned long long su = ldcg(&rec[u].sig[Z]);
                             ub = G.begin(u);
                             ue = G.end(u);
-                            if (lu == tg) wt = su;
+                            wt = pred_weight(S, Z, u, tg);
                         }
                         unsigned long long incl = wt;
 #pragma unroll
@@ -994,8 +1080,8 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
                     walk_ok = false;
                     break;
                 }
-                const unsigned int target = lz - 1;      // level code of the predecessors
-                const unsigned int P = lz - 2;           // their layer index (>= 1 here)
+                const unsigned int target = lz - 1;      // level of the predecessors (>= 1 here)
+                const unsigned int P = target;           // their layer index
                 const unsigned long long draw = k++;
                 {
                     const long long b = G.begin(v);
@@ -1009,13 +1095,14 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
                         __syncthreads();
                         const unsigned int lb = sh.lbeg[Z][P];
                         for (unsigned int i = tid; i < lsz; i += NT) {
-                            const unsigned int u = qget(queue, n, Z, lb + i);
+                            const unsigned int ph = S.at(Z, lb + i);
+                            const unsigned int u = __ldcg(S.qv + ph);
                             const long long bu = G.begin(u), du = G.end(u) - bu;
                             const bool isadj = du <= d ? contains(G.adj, bu, du, v) : contains(G.adj, b, d, u);
                             if (isadj) {
                                 const unsigned int p = atomicAdd(&sh.pcnt, 1u);
                                 sh.cand[p] = u;
-                                sh.wlo[p] = ldcg(&rec[u].sig[Z]);
+                                sh.wlo[p] = ldcg(S.qs + ph);
                                 sh.whi[p] = 0;
                             }
                         }
@@ -1048,9 +1135,7 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
                         unsigned long long wt = 0;
                         if (tid < d) {
                             u = G.col(b + tid);
-                            const unsigned int lu = ldcg(&rec[u].lvl[Z]);
-                            const unsigned long long su = ldcg(&rec[u].sig[Z]);
-                            if (lu == target) wt = su;
+                            wt = pred_weight(S, Z, u, target);
                         }
                         unsigned long long total;
                         const unsigned long long ex = block_excl_scan<NT>(wt, &total, sh);
@@ -1067,9 +1152,8 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
                         unsigned long long part = 0;
                         for (long long j = tid; j < d; j += NT) {
                             const long long u = G.col(b + j);
-                            const unsigned int lu = ldcg(&rec[u].lvl[Z]);
-                            const unsigned long long su = ldcg(&rec[u].sig[Z]);
-                            if (lu == target) {
+                            const unsigned long long su = pred_weight(S, Z, u, target);
+                            if (su) {
                                 part += su;
                                 const unsigned int p = atomicAdd(&sh.pcnt, 1u);
                                 if (p < (unsigned int)kMeetCap) {
@@ -1108,9 +1192,7 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
                             unsigned long long wt = 0;
                             if (j < d) {
                                 u = G.col(b + j);
-                                const unsigned int lu = ldcg(&rec[u].lvl[Z]);
-                                const unsigned long long su = ldcg(&rec[u].sig[Z]);
-                                if (lu == target) wt = su;
+                                wt = pred_weight(S, Z, u, target);
                             }
                             unsigned long long ctot;
                             const unsigned long long ex = carry + block_excl_scan<NT>(wt, &ctot, sh);
@@ -1125,7 +1207,7 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
                         }
                     }
                     v = sh.next_v;
-                    if (v < 0 || v >= n || ldcg(&rec[v].lvl[Z]) != target) {
+                    if (v < 0 || v >= n || pred_weight(S, Z, v, target) == 0ULL) {
                         // no predecessor found: an invariant is broken; record it, stop the walk
                         if (tid == 0) sh.err |= kErrSelect;
                         walk_ok = false;
@@ -1135,7 +1217,7 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
                     lz = target;
                 }
                 if (tid == 0) {
-                    sh.path[sh.plen++] = (unsigned int)v;    // P >= 1: v is interior
+                    sh.path[sh.plen++] = (unsigned int)v;    // level >= 1: v is interior
                     ++path_len;
                 }
                 __syncthreads();   // sh.next_v is rewritten by the next step
@@ -1170,8 +1252,10 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
         __syncthreads();
     }
 
-    // per-sample bookkeeping (thread 0)
-    if (tid == 0) {
+    const bool done = sh.status != 6;
+    // per-sample bookkeeping (thread 0); a sample that ran out of queue
+    // positions is not counted here (it runs again on a larger slot)
+    if (tid == 0 && done) {
         if (a.trace) {
             t_walk = global_ns();
             if (!met) t_sel = t_bfs;
@@ -1185,7 +1269,6 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
         ls.walk_scan += walk_scan;
         ls.scaled += sh.scaled ? 1 : 0;
         if (sh.status == 3) sh.err |= kErrSigmaOverflow;
-        if (sh.err) atomicOr(&a.job->error, sh.err);
         if (a.trace) {
             TraceRec tr;
             tr.s = sh.s;
@@ -1207,32 +1290,88 @@ __device__ void run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, SlotR
             a.trace[trace_i] = tr;
         }
     }
+    if (tid == 0 && sh.err) atomicOr(&a.job->error, sh.err);
 
-    // clear every record this sample touched (meeting vertices sit in the
-    // other side's queue), restoring the all-zero invariant
+    // clear every code word, path count and meeting count this sample set,
+    // restoring the all-zero invariant
     __syncthreads();
+    if (sh.meet_count > 0) {
+        const int Y = 1 - sh.X;
+        for (unsigned int i = sh.fbeg[Y] + tid; i < sh.fend[Y]; i += NT) __stcg(S.qm + S.at(Y, i), 0ULL);
+    }
     for (int side = 0; side < 2; ++side) {
         const unsigned int len = sh.qlen[side];
         for (unsigned int i0 = tid; i0 < len; i0 += 4 * NT) {
             unsigned int v[4];
+            unsigned int ph[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const unsigned int i = i0 + (unsigned int)j * NT;
-                v[j] = i < len ? qget(queue, n, side, i) : kNone;
+                ph[j] = S.at(side, i);
+                v[j] = i < len ? __ldcg(S.qv + ph[j]) : kNone;
             }
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 if (v[j] == kNone) continue;
-                // one 32-byte store clears the record's whole sector
-                asm volatile("st.global.cg.v4.u64 [%0], {%1, %1, %1, %1};" ::"l"(rec + v[j]), "l"(0ULL) : "memory");
+                __stcg(S.code + v[j], 0u);
+                __stcg(S.qs + ph[j], 0ULL);
                 // every set bit of this side's map belongs to a queued vertex of
                 // this sample, so the whole word can go
-                if (bits) __stcg(bits + (side ? bw : 0) + (v[j] >> 5), 0u);
+                if (S.bits) __stcg(S.bits + (side ? S.bw : 0) + (v[j] >> 5), 0u);
             }
         }
     }
     __syncthreads();
-    if (tid == 0 && a.trace) a.trace[trace_i].phase_ns[3] = (long long)(global_ns() - t_walk);
+    if (tid == 0 && a.trace && done) a.trace[trace_i].phase_ns[3] = (long long)(global_ns() - t_walk);
+    return done;
+}
+
+// Runs sample `idx` in this CTA's slot; a sample that outgrows the slot runs
+// again on a spill slot (queue capacity = n), taken and released under a
+// lock word with a bounded wait.  One call site of run_sample, so that it is
+// inlined once.
+template <int NT, typename OffT>
+__device__ void run_sample_any(const SampleLaunch &a, const GraphRef<OffT> &G, const Slot &mine, const SlotSet &spill,
+                               bool use_bits, Smem<NT> &sh, unsigned long long idx, unsigned long long trace_i,
+                               LocalStats &ls, const CountSink &sink)
+{
+    Slot S = mine;
+    for (int attempt = 0;; ++attempt) {
+        if (run_sample<NT, OffT>(a, G, S, sh, idx, trace_i, ls, sink)) break;
+        if (threadIdx.x == 0) {
+            if (attempt > 0) {
+                atomicOr(&a.job->error, kErrScratch);      // a spill slot holds any sample: never expected
+                sh.spill_k = -1;
+            } else if (spill.count > 0 && spill.lock) {
+                int got = -1;
+                unsigned long long w = 0;
+                for (;;) {
+                    for (int k = 0; k < spill.count && got < 0; ++k)
+                        if (atomicCAS(spill.lock + k, 0, 1) == 0) got = k;
+                    if (got >= 0 || ++w > a.spin_limit) break;
+                    __nanosleep(1024);
+                }
+                if (got < 0) atomicOr(&a.job->error, kErrTimeout);
+                sh.spill_k = got;
+                __threadfence();
+            } else {
+                atomicOr(&a.job->error, kErrScratch);
+                sh.spill_k = -1;
+            }
+        }
+        __syncthreads();
+        if (attempt > 0 || sh.spill_k < 0) break;
+        S = slot_of(spill, sh.spill_k, use_bits);
+    }
+    if (S.code != mine.code) {
+        // release the spill slot once this CTA is done with it
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicExch(spill.lock + sh.spill_k, 0);
+        }
+    }
+    __syncthreads();
 }
 
 template <int NT, typename OffT>
@@ -1243,10 +1382,7 @@ __global__ void __launch_bounds__(NT, (2048 / NT / 2) > 0 ? (2048 / NT / 2) : 1)
     __shared__ unsigned long long s_count;
     const int tid = threadIdx.x;
     GraphRef<OffT> G{reinterpret_cast<const OffT *>(a.off), a.adj, (long long)a.n};
-    SlotRec *rec = a.recs + (size_t)blockIdx.x * (size_t)a.n;
-    uint32_t *queue = a.queues + (size_t)blockIdx.x * (size_t)a.n;
-    const long long bw = bit_words(a.n);
-    uint32_t *bits = a.bits ? a.bits + (size_t)blockIdx.x * (size_t)(2 * bw) : nullptr;
+    const Slot slot = slot_of(a.slots, blockIdx.x, a.use_bits != 0);
     Job *job = a.job;
 
     if (tid == 0) {
@@ -1269,7 +1405,8 @@ __global__ void __launch_bounds__(NT, (2048 / NT / 2) > 0 ? (2048 / NT / 2) : 1)
         __syncthreads();
         const unsigned long long i = sh.cur;
         if (i >= count) break;
-        run_sample<NT, OffT>(a, G, rec, queue, bits, bw, sh, base + i, i, ls, CountSink{a.counts, nullptr, nullptr, 0u});
+        run_sample_any<NT, OffT>(a, G, slot, a.spill, a.use_bits != 0, sh, base + i, i, ls,
+                                 CountSink{a.counts, nullptr, nullptr, 0u});
     }
 
     if (tid == 0) {
@@ -1419,10 +1556,6 @@ __global__ void __launch_bounds__(NT, (2048 / NT / 2) > 0 ? (2048 / NT / 2) : 1)
     __shared__ SampleLaunch sa;
     __shared__ int s_qi;
     const int tid = threadIdx.x;
-    SlotRec *rec = B.recs + (size_t)blockIdx.x * (size_t)B.stride;
-    uint32_t *queue = B.queues + (size_t)blockIdx.x * (size_t)B.stride;
-    const long long bw = bit_words(B.stride);
-    uint32_t *bits = B.bits ? B.bits + (size_t)blockIdx.x * (size_t)(2 * bw) : nullptr;
     volatile BatchState *vbs = B.bs;
     if (B.nq == 1) {
         // one query: its descriptor stays in shared memory for the whole launch
@@ -1545,6 +1678,8 @@ __global__ void __launch_bounds__(NT, (2048 / NT / 2) > 0 ? (2048 / NT / 2) : 1)
                 // a sample still running when its query stops belongs to an
                 // epoch after the stopping one and is discarded: end it early
                 t.abandon = qd.tag != 0 ? &qd.job->stopped : nullptr;
+                t.use_bits = qd.use_bits;
+                t.spin_limit = B.spin_limit;
                 sa = t;
             }
         }
@@ -1558,12 +1693,13 @@ __global__ void __launch_bounds__(NT, (2048 / NT / 2) > 0 ? (2048 / NT / 2) : 1)
         Job *job = qd.job;
         GraphRef<OffT> G{reinterpret_cast<const OffT *>(qd.off), qd.adj, qd.n};
         LocalStats ls = {0, 0, 0, 0, 0, 0, 0, 0};
-        run_sample<NT, OffT>(sa, G, rec, queue, qd.use_bits ? bits : nullptr, bw, sh, st->base + pm.idx, pm.idx, ls,
-                             qd.tag == 0 ? CountSink{qd.counts, nullptr, nullptr, 0u}
-                                         : CountSink{nullptr, qd.logs + (size_t)f * qd.log_cap, &st->log_len[f],
-                                                     qd.log_cap});
+        run_sample_any<NT, OffT>(sa, G, slot_of(B.slots, blockIdx.x, qd.use_bits != 0), B.spill, qd.use_bits != 0, sh,
+                                 st->base + pm.idx, pm.idx, ls,
+                                 qd.tag == 0 ? CountSink{qd.counts, nullptr, nullptr, 0u}
+                                             : CountSink{nullptr, qd.logs + (size_t)f * qd.log_cap, &st->log_len[f],
+                                                         qd.log_cap});
         if (tid == 0) {
-            Counters *cs[2] = {&job->total, qd.launch_ctr};
+            Counters *cs[2] = {qd.tag != 0 ? &st->fc[f] : &job->total, qd.launch_ctr};
             for (int c = 0; c < 2; ++c) {
                 if (!cs[c]) continue;
                 atomicAdd(&cs[c]->samples, ls.samples);
@@ -1626,6 +1762,18 @@ __global__ void __launch_bounds__(NT, (2048 / NT / 2) > 0 ? (2048 / NT / 2) : 1)
                         job->stopped = 1;
                     }
                     job->epoch += 1;
+                    // the checked epoch's counters join the query's totals
+                    volatile Counters *fc = &st->fc[cf];
+                    job->total.samples += fc->samples;
+                    job->total.connected += fc->connected;
+                    job->total.e_scan += fc->e_scan;
+                    job->total.expanded += fc->expanded;
+                    job->total.touched += fc->touched;
+                    job->total.interior += fc->interior;
+                    job->total.walk_scan += fc->walk_scan;
+                    job->total.scaled += fc->scaled;
+                    fc->samples = fc->connected = fc->e_scan = fc->expanded = 0;
+                    fc->touched = fc->interior = fc->walk_scan = fc->scaled = 0;
                     st->done[cf] = 0u;
                     st->log_len[cf] = 0u;
                     __threadfence();

@@ -71,7 +71,18 @@ kadabra_status static_cuda_fail(cudaError_t e)
 
 }  // namespace
 
-// Layout of the array for one call: [Job | slots * n records | slots * n queue entries].
+// Layout of the array for one call, each part starting on a 256-byte
+// boundary: [Job | code words: slots * n | qv, ql: slots * n each | qs, qm:
+// slots * n each] -- full queue capacity (cap = n), so no sample needs a
+// spill slot.
+namespace {
+size_t up256(size_t b) { return (b + 255) & ~size_t(255); }
+size_t static_bytes(size_t slots, size_t n)
+{
+    return up256(slots * n * 4) + 2 * up256(slots * n * 4) + 2 * up256(slots * n * 8);
+}
+}  // namespace
+
 extern "C" kadabra_status kadabra_sample_static(const kadabra_graph *g, uint64_t seed, int tag, uint64_t first,
                                                 int64_t count, uint32_t *counts, void *cuda_stream)
 {
@@ -82,12 +93,13 @@ extern "C" kadabra_status kadabra_sample_static(const kadabra_graph *g, uint64_t
     if (tag != 0 && tag != 1) return static_fail(KADABRA_ERR_INVALID_ARG, "tag must be 0 or 1");
     if (count < 0 || count >= (int64_t(1) << 32)) return static_fail(KADABRA_ERR_INVALID_ARG, "count must be in [0, 2^32)");
     if (G.n < 2) return static_fail(KADABRA_ERR_INVALID_ARG, "sampling pairs needs n >= 2");
-    const size_t per_slot = (size_t)G.n * (sizeof(SlotRec) + sizeof(uint32_t));
-    const size_t max_slots = (kStaticScratchBytes - kStaticJobBytes) / per_slot;
-    if (max_slots < 1)
+    const size_t n = (size_t)G.n;
+    if (static_bytes(1, n) > kStaticScratchBytes - kStaticJobBytes)
         return static_fail(KADABRA_ERR_INVALID_ARG,
-                           "graph too large for the static scratch: n * 36 bytes must fit in "
+                           "graph too large for the static scratch: n * 28 bytes (rounded up) must fit in "
                            "KADABRA_STATIC_SCRATCH_BYTES - 256");
+    size_t max_slots = 1;
+    while (static_bytes(max_slots + 1, n) <= kStaticScratchBytes - kStaticJobBytes) ++max_slots;
     if (count == 0) return KADABRA_OK;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
     const int threads = 1024;
@@ -105,19 +117,32 @@ extern "C" kadabra_status kadabra_sample_static(const kadabra_graph *g, uint64_t
     if (e != cudaSuccess) return static_cuda_fail(e);
     unsigned char *bytes = static_cast<unsigned char *>(base);
     Job *job = reinterpret_cast<Job *>(bytes);
-    SlotRec *recs = reinterpret_cast<SlotRec *>(bytes + kStaticJobBytes);
-    uint32_t *queues = reinterpret_cast<uint32_t *>(bytes + kStaticJobBytes + slots * (size_t)G.n * sizeof(SlotRec));
+    SlotSet S;
+    size_t off = kStaticJobBytes;
+    S.code = reinterpret_cast<uint32_t *>(bytes + off);
+    off += up256(slots * n * 4);
+    S.qv = reinterpret_cast<uint32_t *>(bytes + off);
+    off += up256(slots * n * 4);
+    S.ql = reinterpret_cast<uint32_t *>(bytes + off);
+    off += up256(slots * n * 4);
+    S.qs = reinterpret_cast<unsigned long long *>(bytes + off);
+    off += up256(slots * n * 8);
+    S.qm = reinterpret_cast<unsigned long long *>(bytes + off);
+    S.stride = G.n;
+    S.cap = G.n;
+    S.count = (int)slots;
 
-    // the sampler requires all-zero records and a fresh job record
-    e = cudaMemsetAsync(recs, 0, slots * (size_t)G.n * sizeof(SlotRec), st);
+    // the sampler requires all-zero code words and counts and a fresh job record
+    e = cudaMemsetAsync(S.code, 0, slots * n * 4, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(S.qs, 0, slots * n * 8, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(S.qm, 0, slots * n * 8, st);
     if (e == cudaSuccess) e = launch_reset_job(job, st, first);
     SampleLaunch a{};
     a.n = G.n;
     a.off = G.off;
     a.off64 = G.off64;
     a.adj = G.adj;
-    a.recs = recs;
-    a.queues = queues;
+    a.slots = S;
     a.counts = counts;
     a.job = job;
     a.seed = seed;
@@ -126,6 +151,7 @@ extern "C" kadabra_status kadabra_sample_static(const kadabra_graph *g, uint64_t
     a.epoch_len = count;
     a.grid = (int)slots;
     a.threads = threads;
+    a.spin_limit = 1ULL << 24;
     if (e == cudaSuccess) e = launch_sample(a, st);
     unsigned int err = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&err, &job->error, sizeof(err), cudaMemcpyDeviceToHost, st);

@@ -187,6 +187,8 @@ def test_pipelined_run_matches_oracle(K, orc, name, eps, E, frames):
     assert R.stopped and info.stopped == 1
     assert res["tau"] == R.tau and res["stop_epoch"] == R.stop_epoch == info.epochs - 1
     assert np.array_equal(res["counts"], counts)
+    # only samples of checked epochs count: those after the stop are discarded
+    assert info.samples == R.tau and info.e_scan == R.e_scan
     assert math.isclose(info.max_f, R.max_f, rel_tol=REL, abs_tol=0)
     assert math.isclose(info.max_g, R.max_g, rel_tol=REL, abs_tol=0)
     # a second pipelined launch on a stopped query takes no samples
@@ -317,6 +319,35 @@ def test_launch_variants_agree(K, orc, variant):
     assert np.array_equal(res["counts"], want)
 
 
+@pytest.mark.parametrize("name,cap", [("er2000", 64), ("rmat14", 96), ("grid64", 200), ("layered", 900),
+                                      ("fullgrid64", 1000), ("star", 40)])
+def test_small_queue_capacity_spills_and_matches_oracle(K, orc, name, cap):
+    # A queue capacity far below what most samples touch: those samples run
+    # out of positions, clear their slot and run again on a full-capacity
+    # spill slot.  Per-sample records, epoch counters and the pipelined run
+    # must still equal the oracle's.
+    g = GRAPHS[name]()
+    G = K.Graph.from_inputs(g)
+    q = K.Query(G, eps=0.03, delta=0.1, seed=5, n_calib=100, queue_cap=cap)
+    info = q.info()
+    assert info.queue_cap == cap and info.spill_slots == 2
+    recs, paths = q.sample_trace(1, 0, 200, path_cap=512)
+    compare_trace(recs, paths, oracle_trace(orc, g, 5, 1, 0, 200), 512)
+    assert max(r.e_scan for r in recs) > 0
+    q.sample_epoch(700)
+    want, st = orc.run_samples(g, 5, 1, 0, 700)
+    res = q.result(btilde=False)
+    assert np.array_equal(res["counts"], want)
+    info = q.info()
+    assert info.samples == 700 and info.e_scan == st.e_scan and info.device_error == 0
+    q.reset()
+    q.run_pipelined(128, frames=4)
+    counts, cal, LL, LU, R = orc.kadabra(g, 0.03, 0.1, seed=5, n_calib=100, epoch_len=128)
+    res = q.result(btilde=False)
+    assert res["tau"] == R.tau and res["stop_epoch"] == R.stop_epoch
+    assert np.array_equal(res["counts"], counts)
+
+
 def test_omega_clip_and_single_samples(K, orc):
     g = GRAPHS["er2000"]()
     G = K.Graph.from_inputs(g)
@@ -445,9 +476,6 @@ def test_grid4096_full_size_sampled(K, orc):
 
 
 @pytest.mark.slow
-@pytest.mark.skipif(not os.environ.get("KADABRA_FULL_SIZE"),
-                    reason="R-MAT scale 26 takes minutes and ~70 GB of host memory to generate; "
-                           "set KADABRA_FULL_SIZE=1")
 def test_rmat26_full_size_sampled(K, orc):
     """R-MAT scale 26, edge factor 16 (int64 offsets) at full size: the
     vertex-diameter bound, one epoch of counters bit-exact, and per-sample
@@ -455,7 +483,7 @@ def test_rmat26_full_size_sampled(K, orc):
     g = I.config_graph("rmat26")
     assert g.n == 1 << 26 and g.nnz > 2_000_000_000
     G = K.Graph.from_inputs(g, offsets_64=True, skip_validate=True)
-    q = K.Query(G, eps=0.01, delta=0.1, seed=1, n_calib=256)
+    q = K.Query(G, eps=0.01, delta=0.1, seed=1, n_calib=256, threads=512)
     info = q.info()
     assert info.offsets_64 == 1
     assert info.vertex_diameter == orc.vertex_diameter_bound(g)
@@ -467,6 +495,61 @@ def test_rmat26_full_size_sampled(K, orc):
     assert q.info().e_scan == st.e_scan
     recs, paths = q.sample_trace(1, 5_000_000, 32, path_cap=64)
     compare_trace(recs, paths, oracle_trace(orc, g, 1, 1, 5_000_000, 32), 64)
+
+
+def _sha(a):
+    import hashlib
+    return hashlib.sha256(np.ascontiguousarray(a).view(np.uint8)).hexdigest()
+
+
+def _graph_sha(g):
+    import hashlib
+    h = hashlib.sha256()
+    h.update(np.int64(g.n).tobytes())
+    h.update(np.ascontiguousarray(g.offsets, dtype=np.int64).view(np.uint8))
+    h.update(np.ascontiguousarray(g.cols, dtype=np.int32).view(np.uint8))
+    return h.hexdigest()
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name,threads", [("rmat26", 512), ("grid4096", 1024)])
+def test_whole_run_at_full_size_matches_oracle_golden(K, name, threads):
+    """The two largest single-query workloads, R-MAT scale 26 and the
+    4096 x 4096 grid, through the whole method in the benchmarked form
+    (diameter bound, calibration, pipelined adaptive phase with E = 1024 and
+    8 frames): omega, the diameter bound, the calibration counts, the
+    balancing constant, tau, the stop epoch and the counters equal what the
+    oracle alone wrote to tests/golden/<name>_run.json (make_config3_runs.py),
+    and the f/g maxima agree to 1e-12 relative."""
+    import json
+    path = os.path.join(os.path.dirname(__file__), "golden", f"{name}_run.json")
+    if not os.path.exists(path):
+        pytest.skip(f"{path} not written yet")
+    gold = json.load(open(path))
+    P = gold["params"]
+    g = I.config_graph(name)
+    assert g.n == gold["n"] and g.nnz == gold["nnz"]
+    assert _graph_sha(g) == gold["graph_sha256"], "the input generator changed since the golden run was written"
+    G = K.Graph.from_inputs(g, offsets_64=g.nnz >= 2**31, skip_validate=True)
+    q = K.Query(G, eps=P["eps"], delta=P["delta"], seed=P["seed"], delta_rule=P["delta_rule"], beta=P["beta"],
+                threads=threads)
+    info = q.info()
+    assert info.omega == float.fromhex(gold["omega"])
+    assert info.vertex_diameter == gold["vertex_diameter"] and info.n_calib == gold["n_calib"]
+    assert info.sigma_bits == gold["sigma_bits"]
+    assert info.balance_C == float.fromhex(gold["C"])
+    LL, LU, cal = q.budgets()
+    assert _sha(cal) == gold["cal_sha256"]
+    q.run_pipelined(P["epoch_len"], frames=8)
+    res = q.result(btilde=False)
+    info = q.info()
+    assert info.stopped == 1 and info.device_error == 0
+    assert res["tau"] == gold["tau"] and res["stop_epoch"] == gold["stop_epoch"]
+    assert int(res["counts"].sum(dtype=np.uint64)) == gold["counts_sum"]
+    assert _sha(res["counts"]) == gold["counts_sha256"]
+    assert info.samples == gold["tau"] and info.e_scan == gold["e_scan"]
+    assert math.isclose(info.max_f, float.fromhex(gold["max_f"]), rel_tol=REL, abs_tol=0)
+    assert math.isclose(info.max_g, float.fromhex(gold["max_g"]), rel_tol=REL, abs_tol=0)
 
 
 @pytest.mark.slow
