@@ -1,10 +1,12 @@
 #!/usr/bin/env python
 """Benchmark: KADABRA adaptive-sampling betweenness on one GB300.
 
-Workload: R-MAT scale 20 (2^20 vertices, edge factor 16, Graph500
+Default workload: R-MAT scale 26 (2^26 vertices, edge factor 16, Graph500
 (a, b, c, d) = (0.57, 0.19, 0.19, 0.05)), symmetrised, self-loops and
-duplicates removed, int32 CSR; eps = 0.01, delta = 0.1, seed 1.  Synthetic
-data from paper_1910_11039_gb300.inputs (generator seed 2).
+duplicates removed, int64 offsets / int32 columns; eps = 0.01, delta = 0.1,
+seed 1: the largest single-GPU configuration.  Synthetic data from
+paper_1910_11039_gb300.inputs (generator seed 4).  --workload picks the other
+single-query graphs (R-MAT scale 20, the 4096^2 grid, ...).
 
 A step is one complete adaptive phase (arXiv 1910.11039, Section III-A,
 phase 3): from tau = 0, epochs of E samples each checked against the stopping
@@ -45,8 +47,8 @@ WORKLOADS = {
     "rmat20": dict(graph="rmat20", eps=0.01, delta=0.1, seed=1, threads=512,
                    desc="R-MAT scale 20, edge factor 16, (a,b,c,d)=(0.57,0.19,0.19,0.05), symmetrised, "
                         "no self-loops/duplicates, int32 CSR; eps=0.01 delta=0.1 seed=1"),
-    "rmat26": dict(graph="rmat26", eps=0.01, delta=0.1, seed=1, threads=512, steps=5, e2e_steps=1,
-                   cpu_samples=1600, ref_samples=800,
+    "rmat26": dict(graph="rmat26", eps=0.01, delta=0.1, seed=1, threads=1024, steps=20, e2e_steps=1,
+                   cpu_samples=3200, ref_samples=1600, off64=True,
                    desc="R-MAT scale 26, edge factor 16, (a,b,c,d)=(0.57,0.19,0.19,0.05), symmetrised, "
                         "no self-loops/duplicates, int64 offsets / int32 columns; eps=0.01 delta=0.1 seed=1"),
     "rhg20": dict(graph="rhg20", eps=0.01, delta=0.1, seed=1, steps=5, cpu_samples=4800, ref_samples=1600, threads=512,
@@ -307,7 +309,7 @@ def run_gpu(args, wl, g, rank, world, local_rank, cpu_baseline):
     eps, delta = wl["eps"], wl["delta"]
 
     # ---- device-resident arm ----
-    off64 = g.nnz >= 2**31
+    off64 = bool(wl.get("off64")) or g.nnz >= 2**31
     G = K.Graph.from_inputs(g, offsets_64=off64, skip_validate=True)
     q = K.Query(G, eps=eps, delta=delta, seed=seed, slots=args.slots, threads=args.threads)
     info0 = q.info()
@@ -691,7 +693,7 @@ def main():
     ap.add_argument("--steps", type=int, default=None, help="timed steps (default: per workload, 20 for rmat20)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--workload", default="rmat20", choices=list(WORKLOADS))
+    ap.add_argument("--workload", default="rmat26", choices=list(WORKLOADS))
     ap.add_argument("--epoch", type=int, default=1024)
     ap.add_argument("--mode", default="pipelined", choices=["pipelined", "epochs", "batched", "serve"],
                     help="pipelined/epochs: one query on --workload; batched: 64 queries of uneven size; "

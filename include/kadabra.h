@@ -69,7 +69,13 @@ typedef struct kadabra_params {
     double delta;             /* failure probability, 0 < delta < 1                        */
     uint64_t seed;            /* Philox key: sample i of stream tag k draws from
                                  counter (i, draw, k, 0) under key (seed, 0)               */
-    int64_t vertex_diameter;  /* VD >= 1 if known; <= 0: upper bound 2*ecc+1 per component */
+    int64_t vertex_diameter;  /* VD >= 1 if known; 0: upper bound 2*ecc(root)+1 per
+                                 component; -1: exact, by iFUB on the device (Section
+                                 III-A computes the diameter exactly), for every
+                                 component whose bound exceeds the best value; a search
+                                 whose fringe needs more than 64 bit-parallel sweeps
+                                 (meshes) keeps the upper bound it proved, and
+                                 kadabra_query_info.vd_exact says which               */
     int64_t n_calib;          /* calibration samples; <= 0: max(1000, ceil(omega/100))     */
     int32_t delta_rule;       /* KADABRA_DELTA_UNIFORM or KADABRA_DELTA_BALANCED           */
     uint32_t flags;           /* KADABRA_STRICT_SIGMA                                       */
@@ -82,6 +88,10 @@ typedef struct kadabra_params {
                                  else what fits.  A sample that outgrows it runs again on
                                  one of two full-capacity spill slots, so results never
                                  depend on it                                              */
+    int64_t coop_edges;       /* pipelined launches: a BFS layer whose frontier degree sum
+                                 is at least this is split into chunks that idle CTAs
+                                 expand together with the sample's own CTA; 0 = 32768,
+                                 < 0 = never.  Results never depend on it               */
 } kadabra_params;
 
 /* Snapshot of a query (kadabra_query_get_info). */
@@ -121,7 +131,8 @@ typedef struct kadabra_query_info {
     double calibration_ms;      /* host wall time of phase 2 (calibration; batch: budgets)  */
     int64_t queue_cap;          /* queue positions per sampling slot (both BFS sides)       */
     int32_t spill_slots;        /* full-capacity slots for samples that outgrow queue_cap   */
-    int32_t pad1;
+    int32_t vd_exact;           /* 1 if vertex_diameter is the exact vertex diameter        */
+    int64_t vd_searches;        /* breadth-first searches the diameter phase ran            */
 } kadabra_query_info;
 
 /* Per-sample record written by kadabra_sample_trace (one per sample index). */

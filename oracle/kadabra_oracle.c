@@ -20,11 +20,13 @@
  *
  * The paper does not print the formulas of f, g, omega, delta_L and delta_U
  * (Section III-A defers them to KADABRA's original publication).  The
- * formulas used here are the readings recorded in the design notes; the
- * oracle's header states it plainly:
- *   parity unpinned: orc_omega, orc_calibrate_L, orc_stop_functions
- *   (pinned only weakly: Table II sample counts <= omega, and the end-to-end
- *   epsilon guarantee against exact Brandes on small graphs).
+ * formulas used here are the readings recorded in the design notes.  They are
+ * pinned against what they are defined to solve rather than against
+ * themselves: f and g against a high-precision root of the deviation-bound
+ * equation, omega against hand-worked values and the Table II sample counts,
+ * the balanced delta rule against closed-form and high-precision roots of its
+ * budget equation, and the whole method against the epsilon guarantee with
+ * exact Brandes on small graphs.
  *
  * Determinism contract (a reading; the paper draws from an unspecified RNG):
  *   Philox-4x64-10 (Salmon et al., SC'11), key = (seed, 0),
@@ -437,7 +439,7 @@ int64_t orc_vertex_diameter_exact(int64_t n, const int64_t *off, const int32_t *
 
 /* ------------------------------------------------------------------------ */
 /* omega, delta_L / delta_U, and the stopping functions (Section III-A)     */
-/* parity unpinned: formulas not printed in the paper (readings)            */
+/* formulas not printed in the paper (readings; pinned by what they solve)  */
 /* ------------------------------------------------------------------------ */
 
 /* Maximal number of samples: (c / eps^2) * (floor(log2(VD - 2)) + 1 + ln(2/delta)),

@@ -71,6 +71,7 @@ struct kadabra_graph {
     int ws_threads = 0;
     int ws_req = 0;               // slots requested when the scratch was sized
     int64_t ws_cap_req = 0;       // queue capacity requested when the scratch was sized
+    void *d_help = nullptr;       // help board of the graph's pipelined launches
 };
 
 struct kadabra_query {
@@ -79,6 +80,8 @@ struct kadabra_query {
     double omega = 0.0;
     uint64_t omega_ceil = 0;
     int64_t vd = 0;
+    int vd_exact = 0;
+    int64_t vd_searches = 0;
     int64_t n_calib = 0;
     int K = 0;
     double balance_C = 0.0;
@@ -127,6 +130,7 @@ struct kadabra_batch {
     int slots = 0, threads = 0, off64 = 0;
     kadabra::SlotSet ws;
     kadabra::SlotSet spill;
+    void *d_help = nullptr;       // help board of the batch's launches
     kadabra::QueryDesc *d_descs = nullptr;
     int64_t descs_cap = 0;
     kadabra::BatchState *d_bs = nullptr;
@@ -433,8 +437,10 @@ static void free_graph_device(kadabra_graph *g)
     cudaFree(g->d_adj);
     kadabra::free_slot_set(&g->ws);
     kadabra::free_slot_set(&g->spill);
+    cudaFree(g->d_help);
     g->d_off = nullptr;
     g->d_adj = nullptr;
+    g->d_help = nullptr;
 }
 
 extern "C" kadabra_status kadabra_graph_load(int64_t n, int64_t nnz, const void *offsets, int offsets_is_64,
@@ -692,7 +698,26 @@ static kadabra_status create_query(kadabra_graph *g, const kadabra_params *pin, 
     PhaseScope scope("kadabra: diameter phase", &q->diameter_ms);
     if (p.vertex_diameter > 0) {
         q->vd = p.vertex_diameter;
+        q->vd_exact = 0;
+    } else if (p.vertex_diameter == -1) {
+        // exact vertex diameter: iFUB on the device for the largest component
+        void *scratch = nullptr;
+        cudaError_t e = cudaMalloc(&scratch, kadabra::vd_exact_scratch_bytes(g->n));
+        if (e == cudaSuccess)
+            e = kadabra::launch_vd_exact(g->n, g->d_off, g->off64, g->d_adj, scratch, st, &q->vd, &q->vd_exact,
+                                         &q->vd_searches);
+        cudaFree(scratch);
+        if (e != cudaSuccess) {
+            delete q;
+            if (e == cudaErrorLaunchTimeout)
+                return fail(KADABRA_ERR_TIMEOUT, "diameter phase: a bounded device wait gave up");
+            return cuda_fail(e, "diameter phase (exact)");
+        }
+    } else if (p.vertex_diameter < -1) {
+        delete q;
+        return fail(KADABRA_ERR_INVALID_ARG, "vertex_diameter must be >= 0 or -1 (exact)");
     } else {
+        q->vd_searches = 1;
         // vertex-diameter bound on the device (union-find components, then one
         // breadth-first search from every component's smallest vertex)
         void *scratch = nullptr;
@@ -1058,6 +1083,14 @@ extern "C" kadabra_status kadabra_run_pipelined(kadabra_query *q, int64_t epoch_
     B.nq = 1;
     B.slots = q->g->ws;
     B.spill = q->g->spill;
+    if (q->p.coop_edges >= 0) {
+        if (!q->g->d_help) {
+            KCUDA(cudaMalloc(&q->g->d_help, kadabra::help_board_bytes()), "allocate help board");
+            KCUDA(cudaMemset(q->g->d_help, 0, kadabra::help_board_bytes()), "clear help board");
+        }
+        B.help = q->g->d_help;
+        B.help_edges = q->p.coop_edges > 0 ? (unsigned long long)q->p.coop_edges : 32768ULL;
+    }
     B.bs = q->d_bs;
     B.budget = 0;
     B.spin_limit = 1ULL << 24;
@@ -1112,12 +1145,15 @@ extern "C" kadabra_status kadabra_batch_create(int64_t max_n, int32_t slots, int
     cudaError_t e = kadabra::alloc_slot_set(&b->ws, fit, max_n, cap, true, false);
     if (e == cudaSuccess) e = kadabra::alloc_slot_set(&b->spill, nspill, max_n, max_n, true, true);
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&b->d_bs), sizeof(kadabra::BatchState));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_help, kadabra::help_board_bytes());
+    if (e == cudaSuccess) e = cudaMemset(b->d_help, 0, kadabra::help_board_bytes());
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev1);
     if (e != cudaSuccess) {
         kadabra::free_slot_set(&b->ws);
         kadabra::free_slot_set(&b->spill);
         cudaFree(b->d_bs);
+        cudaFree(b->d_help);
         delete b;
         return cuda_fail(e, "allocate batch scratch");
     }
@@ -1131,6 +1167,7 @@ extern "C" kadabra_status kadabra_batch_free(kadabra_batch *b)
     cudaDeviceSynchronize();
     kadabra::free_slot_set(&b->ws);
     kadabra::free_slot_set(&b->spill);
+    cudaFree(b->d_help);
     cudaFree(b->d_descs);
     cudaFree(b->d_states);
     cudaFree(b->d_bs);
@@ -1178,6 +1215,8 @@ extern "C" kadabra_status kadabra_batch_step(kadabra_batch *b, kadabra_query *co
     B.nq = (int)count;
     B.slots = b->ws;
     B.spill = b->spill;
+    B.help = b->d_help;
+    B.help_edges = 32768ULL;
     B.bs = b->d_bs;
     B.budget = sample_budget;
     B.spin_limit = b->spin_limit;
@@ -1502,6 +1541,8 @@ extern "C" kadabra_status kadabra_query_get_info(kadabra_query *q, kadabra_query
     I.calibration_ms = q->calibration_ms;
     I.queue_cap = q->g->ws.cap;
     I.spill_slots = q->g->spill.count;
+    I.vd_exact = q->vd_exact;
+    I.vd_searches = q->vd_searches;
     I.cal_done = q->phase == 2 ? (uint64_t)q->n_calib : 0ULL;
     if (q->phase == 1) {
         kadabra::PipeState ps{};

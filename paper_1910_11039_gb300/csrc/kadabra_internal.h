@@ -119,6 +119,8 @@ struct SampleLaunch {
     const int *abandon;        // optional: a sample stops at its next layer once *abandon != 0
     int use_bits;              // use the slots' reached-bit maps (graphs of small diameter)
     unsigned long long spin_limit;   // bounded waits (spill slot, claims being published)
+    void *help;                // persistent launches: board of layers posted for other CTAs (or null)
+    unsigned long long help_edges;   // a layer with at least this frontier degree sum is posted
 };
 
 cudaError_t launch_sample(const SampleLaunch &a, cudaStream_t st);
@@ -133,6 +135,10 @@ size_t vd_bound_scratch_bytes(int64_t n);
 cudaError_t launch_vd_bound(int64_t n, const void *off, int off64, const uint2 *adj, void *scratch, cudaStream_t st,
                             int64_t *vd);
 cudaError_t launch_max_degree(int64_t n, const void *off, int off64, unsigned long long *out, cudaStream_t st);
+// exact vertex diameter (iFUB on the largest component; graph_kernels.cu)
+size_t vd_exact_scratch_bytes(int64_t n);
+cudaError_t launch_vd_exact(int64_t n, const void *off, int off64, const uint2 *adj, void *scratch, cudaStream_t st,
+                            int64_t *vd, int *exact, int64_t *searches);
 cudaError_t sample_occupancy(int threads, int off64, int *ctas_per_sm);
 
 // Pipelined adaptive phase: epochs rotate through F epoch logs; one persistent
@@ -193,6 +199,8 @@ struct BatchLaunch {
     int nq;
     SlotSet slots;             // one per CTA; stride = largest n of the batch
     SlotSet spill;             // taken by samples that outgrow their slot (may be empty)
+    void *help;                // help board (help_board_bytes(), zeroed once), or null: no helping
+    unsigned long long help_edges;   // frontier degree sum from which a layer is posted
     BatchState *bs;
     unsigned long long budget; // samples this launch may hand out (0 = no limit)
     unsigned long long spin_limit;
@@ -201,6 +209,8 @@ struct BatchLaunch {
 };
 
 cudaError_t launch_batch(const BatchLaunch &a, cudaStream_t st);
+// Bytes of a help board for persistent launches (allocate once, zeroed).
+size_t help_board_bytes();
 cudaError_t launch_pipe_begin(PipeState *ps, const Job *job, unsigned long long clip, long long E, cudaStream_t st);
 cudaError_t launch_class_max(int64_t n, const uint32_t *counts, const uint32_t *cls, unsigned int *cmax,
                              cudaStream_t st);

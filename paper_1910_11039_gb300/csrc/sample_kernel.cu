@@ -69,7 +69,7 @@ constexpr int kBuckets = 256;      // radix-select digit width: 8 bits
 constexpr int kMaxLayers = 64;     // BFS layers whose queue ranges are remembered for the walk
 constexpr int kPathCap = 1024;     // path vertices buffered in shared memory before a flush
 #ifndef KADABRA_UNROLL
-#define KADABRA_UNROLL 2
+#define KADABRA_UNROLL 4
 #endif
 constexpr int kUnroll = KADABRA_UNROLL;   // adjacency entries in flight per thread
 constexpr unsigned int kNone = 0xffffffffu;
@@ -131,6 +131,16 @@ struct Smem {
     unsigned int pw;                 // queue position of the chosen meeting vertex on the other side
     int ovf;                         // a claim found no free queue position
     int spill_k;                     // spill slot taken by this CTA (-1: none)
+    int help_k, help_c;              // help request and chunk taken (-1: none)
+    struct {
+        uint32_t *code, *qv, *ql;
+        unsigned long long *qs, *qm;
+        uint32_t *bits;
+        long long bw, n;
+        const void *off;
+        const uint2 *adj;
+        unsigned int cap, X, nl, fb, fe, qbase, room, yb, ye, cv;
+    } hl;                            // the helped layer, copied from its request
     long long next_v;
     int found;
     unsigned long long cur;          // work item taken by this CTA
@@ -475,6 +485,319 @@ struct LocalStats {
 // kinds of a scanned adjacency target (phase 2 of a layer)
 enum : int { kTSkip = 0, kTUnseen = 1, kTMeet = 2, kTSame = 3, kTPend = 4 };
 
+// Where a layer's accumulators live: the CTA's shared memory (a layer one
+// CTA expands), or a help request in global memory (a layer several CTAs
+// expand together).
+template <int NT>
+struct SmemAcc {
+    Smem<NT> &sh;
+    __device__ __forceinline__ unsigned int *new_count() const { return &sh.new_count; }
+    __device__ __forceinline__ unsigned int *meet_count() const { return &sh.meet_count; }
+    __device__ __forceinline__ unsigned int *cand() const { return sh.cand; }
+    __device__ __forceinline__ unsigned int *cpos() const { return sh.cpos; }
+    __device__ __forceinline__ volatile int *meets() const { return &sh.meets; }
+    __device__ __forceinline__ unsigned int *err() const { return &sh.err; }
+    __device__ __forceinline__ volatile int *ovf() const { return &sh.ovf; }
+    __device__ __forceinline__ unsigned long long *lmax() const { return &sh.lmax; }
+    __device__ __forceinline__ unsigned long long *ldeg() const { return &sh.ldeg; }
+};
+
+// A layer posted for several CTAs of a persistent launch to expand together:
+// a heavy layer (frontier degree sum above the launch's threshold) of one
+// sample is split into chunks of frontier vertices; its owner and any CTA
+// between two samples take chunks until none is left, then the owner waits
+// until all are done and collects the accumulators.  Every claim and count
+// is an atomic on the slot's global state, so the result is the same whoever
+// expands which chunk.
+constexpr int kHelpSlots = 8;
+struct HelpReq {
+    unsigned long long ticket;     // bits 48..63 generation, 24..47 chunks, 0..23 next chunk
+    unsigned int done;             // chunks finished
+    int state;                     // 0 free, 1 held by an owner
+    // the layer (read by helpers, written before the ticket opens)
+    uint32_t *code, *qv, *ql;
+    unsigned long long *qs, *qm;
+    uint32_t *bits;
+    long long bw;
+    const void *off;
+    const uint2 *adj;
+    long long n;
+    unsigned int cap, X, nl, fb, fe, qbase, room, yb, ye, cv;
+    // accumulators
+    unsigned long long lmax, ldeg, scan;
+    unsigned int new_count, meet_count, err;
+    int meets, ovf;
+    unsigned int cand[kMeetCap], cpos[kMeetCap];
+};
+
+struct ReqAcc {
+    HelpReq *r;
+    __device__ __forceinline__ unsigned int *new_count() const { return &r->new_count; }
+    __device__ __forceinline__ unsigned int *meet_count() const { return &r->meet_count; }
+    __device__ __forceinline__ unsigned int *cand() const { return r->cand; }
+    __device__ __forceinline__ unsigned int *cpos() const { return r->cpos; }
+    __device__ __forceinline__ volatile int *meets() const { return &r->meets; }
+    __device__ __forceinline__ unsigned int *err() const { return &r->err; }
+    __device__ __forceinline__ volatile int *ovf() const { return &r->ovf; }
+    __device__ __forceinline__ unsigned long long *lmax() const { return &r->lmax; }
+    __device__ __forceinline__ unsigned long long *ldeg() const { return &r->ldeg; }
+};
+
+// Takes the next chunk of request R, or -1 if none is left.  The ticket is
+// read first, so once the chunks are gone no further add touches it (its
+// chunk field never overflows into the count).
+__device__ __forceinline__ int take_chunk(HelpReq *R)
+{
+    const unsigned long long t = *reinterpret_cast<volatile unsigned long long *>(&R->ticket);
+    if ((t & 0xffffffULL) >= ((t >> 24) & 0xffffffULL)) return -1;
+    const unsigned long long got = atomicAdd(&R->ticket, 1ULL);
+    if ((got & 0xffffffULL) >= ((got >> 24) & 0xffffffULL)) return -1;
+    return (int)(got & 0xffffffULL);
+}
+
+// A help board: a 256-byte header (the count of requests with chunks left)
+// and kHelpSlots requests.
+__device__ __forceinline__ unsigned int *board_open(void *h) { return reinterpret_cast<unsigned int *>(h); }
+__device__ __forceinline__ HelpReq *board_req(void *h)
+{
+    return reinterpret_cast<HelpReq *>(reinterpret_cast<unsigned char *>(h) + 256);
+}
+
+// Expands the frontier vertices [cb, min(cb + NT, fe)) of side X's current
+// layer (CTA-wide): every adjacency entry of them is scanned once; unseen
+// targets are claimed for level nl, targets already in the new layer get the
+// source's path count added, targets in the other side's last layer (queue
+// positions [yb, ye)) get it added to their meeting count.  Returns the
+// chunk's adjacency-entry count in thread 0 (0 elsewhere).
+template <int NT, typename OffT, typename Acc>
+__device__ __forceinline__ unsigned long long expand_chunk(const unsigned long long spin_limit, const GraphRef<OffT> &G,
+                                                           const Slot &S, Smem<NT> &sh, const Acc &A, const int X,
+                                                           const unsigned int nl, const unsigned int cb,
+                                                           const unsigned int fe, const unsigned int qbase,
+                                                           const unsigned int room, const unsigned int yb,
+                                                           const unsigned int ye)
+{
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int Y = 1 - X;
+    const unsigned int pend_code = (X ? kSideBit : 0u) | kPending;
+    unsigned long long my_max = 0, my_scan = 0, my_deg = 0;
+        const unsigned int i = cb + tid;
+        long long b = 0;
+        unsigned long long d = 0, sg = 0;
+        if (i < fe) {
+            const unsigned int ph = S.at(X, i);
+            const unsigned int u = __ldcg(S.qv + ph);
+            b = G.begin(u);
+            d = (unsigned long long)(G.end(u) - b);
+            sg = ldcg(S.qs + ph);
+        }
+        unsigned long long total;
+        const unsigned long long excl = block_excl_scan<NT>(d, &total, sh);
+        sh.u.ex.cbeg[tid] = b;
+        sh.u.ex.cpos[tid] = excl;
+        sh.u.ex.csig[tid] = sg;
+        const int cnt = (int)min((unsigned int)NT, fe - cb);
+        __syncthreads();
+        my_scan = (tid == 0) ? total : 0ULL;
+        // warp-uniform batches: lane l of warp k handles entries
+        // e0 + l + j*NT, j < kUnroll, with e0 = 32k + (multiple of NT*kUnroll);
+        // each phase issues all kUnroll memory operations before waiting
+        const unsigned long long wbase = (unsigned long long)(tid & ~31);
+        for (unsigned long long e0 = wbase; e0 < total; e0 += (unsigned long long)NT * kUnroll) {
+            unsigned int w[kUnroll];
+            unsigned int dw[kUnroll];
+            int own[kUnroll];
+#pragma unroll
+            for (int j = 0; j < kUnroll; ++j) {
+                const unsigned long long e = e0 + (unsigned long long)lane + (unsigned long long)j * NT;
+                w[j] = kNone;
+                dw[j] = 0;
+                own[j] = 0;
+                if (e < total) {
+                    // owner: the last k with cpos[k] <= e
+                    int lo = j > 0 ? own[j - 1] : 0, hi = cnt - 1;
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (sh.u.ex.cpos[mid] <= e) lo = mid;
+                        else hi = mid - 1;
+                    }
+                    own[j] = lo;
+                    const uint2 c = __ldg(G.adj + sh.u.ex.cbeg[lo] + (long long)(e - sh.u.ex.cpos[lo]));
+                    w[j] = c.x;
+                    dw[j] = c.y;
+                }
+            }
+            // phase 2: the code word of every target (one 4-byte load each);
+            // once the layer is known to be the last, only the other side's
+            // reached bit first (a dense map that stays in L2), and the code
+            // only of targets that have it
+            unsigned int cd[kUnroll];
+            int kind[kUnroll];
+            const bool fast = S.bits != nullptr && *A.meets() != 0;
+            if (fast) {
+                const uint32_t *ybits = S.bits + (X ? 0 : S.bw);
+                unsigned int ymask = 0;
+#pragma unroll
+                for (int j = 0; j < kUnroll; ++j)
+                    if (w[j] != kNone && ((__ldcg(ybits + (w[j] >> 5)) >> (w[j] & 31)) & 1u)) ymask |= 1u << j;
+#pragma unroll
+                for (int j = 0; j < kUnroll; ++j) cd[j] = ((ymask >> j) & 1u) ? __ldcg(S.code + w[j]) : 0u;
+#pragma unroll
+                for (int j = 0; j < kUnroll; ++j) kind[j] = ((ymask >> j) & 1u) ? kTMeet : kTSkip;
+            } else {
+#pragma unroll
+                for (int j = 0; j < kUnroll; ++j) cd[j] = w[j] != kNone ? __ldcg(S.code + w[j]) : 0u;
+#pragma unroll
+                for (int j = 0; j < kUnroll; ++j) {
+                    const unsigned int c = cd[j];
+                    kind[j] = w[j] == kNone ? kTSkip
+                              : c == 0u ? kTUnseen
+                              : side_of(c) != X ? kTMeet
+                              : is_pending(c) ? kTPend
+                              : pos_of(c) >= qbase ? kTSame : kTSkip;
+                }
+            }
+            // a target held by the other side makes this layer the last one:
+            // from then on only meeting vertices need counts, so other unseen
+            // targets of the last layer are not claimed
+#pragma unroll
+            for (int j = 0; j < kUnroll; ++j)
+                if (kind[j] == kTMeet) *A.meets() = 1;
+            const bool last = *A.meets() != 0;
+            // phase 3: claims (CAS on the code word to "pending"), path-count
+            // additions to targets already in the new layer, and meeting
+            // counts (the other side's last layer, indexed by its queue
+            // position).  The additions return their old value, so a thread
+            // has waited for all of them before the layer's closing barrier
+            // and every count is complete when any thread reads it next.
+            unsigned int cmask = 0, mfirst = 0, retry = 0;
+#pragma unroll
+            for (int j = 0; j < kUnroll; ++j) {
+                if (kind[j] == kTUnseen) {
+                    if (last) {
+                        kind[j] = kTSkip;
+                    } else {
+                        const unsigned int old = atomicCAS(S.code + w[j], 0u, pend_code);
+                        if (old == 0u) {
+                            cmask |= 1u << j;
+                        } else {
+                            // claimed in this layer by another thread meanwhile
+                            cd[j] = old;
+                            kind[j] = is_pending(old) ? kTPend : kTSame;
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < kUnroll; ++j) {
+                const unsigned long long su = sh.u.ex.csig[own[j]];
+                if (kind[j] == kTMeet) {
+                    const unsigned int p = pos_of(cd[j]);
+                    if (side_of(cd[j]) != Y || is_pending(cd[j]) || p < yb || p >= ye) {
+                        atomicOr(A.err(), kErrSelect);     // broken invariant: never expected
+                        continue;
+                    }
+                    const unsigned long long old = atomicAdd(S.qm + S.at(Y, p), su);
+                    if (old == 0ULL) mfirst |= 1u << j;
+                    if (old + su < su) atomicOr(A.err(), kErrAddOverflow);
+                } else if (kind[j] == kTSame) {
+                    const unsigned int p = pos_of(cd[j]);
+                    if (side_of(cd[j]) != X || p < qbase) {
+                        atomicOr(A.err(), kErrSelect);
+                        continue;
+                    }
+                    const unsigned long long nv = atomicAdd(S.qs + S.at(X, p), su) + su;
+                    if (nv < su) atomicOr(A.err(), kErrAddOverflow);      // excluded by the choice of K
+                    my_max = nv > my_max ? nv : my_max;
+                } else if (kind[j] == kTPend) {
+                    retry |= 1u << j;
+                }
+            }
+            // phase 4: claimed targets join the new frontier (warp-aggregated
+            // queue positions), get their first path count and publish their
+            // position; first-touched meeting vertices join the meeting set
+#pragma unroll
+            for (int j = 0; j < kUnroll; ++j) {
+                const bool claimed = (cmask >> j) & 1u;
+                const unsigned int m = __ballot_sync(0xffffffffu, claimed);
+                if (m) {
+                    const int leader = __ffs(m) - 1;
+                    unsigned int slot0 = 0;
+                    if (lane == leader) slot0 = atomicAdd(A.new_count(), (unsigned int)__popc(m));
+                    slot0 = __shfl_sync(0xffffffffu, slot0, leader);
+                    if (claimed) {
+                        const unsigned int p = qbase + slot0 + __popc(m & ((1u << lane) - 1u));
+                        if (p < room) {
+                            const unsigned int ph = S.at(X, p);
+                            const unsigned long long su = sh.u.ex.csig[own[j]];
+                            __stcg(S.qv + ph, w[j]);
+                            __stcg(S.ql + ph, nl);
+                            const unsigned long long nv = atomicAdd(S.qs + ph, su) + su;
+                            if (nv < su) atomicOr(A.err(), kErrAddOverflow);
+                            my_max = nv > my_max ? nv : my_max;
+                            __stcg(S.code + w[j], code_of(X, p));
+                            my_deg += dw[j];
+                            if (S.bits) atomicOr(&S.bits[(X ? S.bw : 0) + (w[j] >> 5)], 1u << (w[j] & 31));
+                        } else {
+                            // out of queue positions: the sample restarts on a larger slot
+                            *A.ovf() = 1;
+                            __stcg(S.code + w[j], 0u);
+                        }
+                    }
+                }
+                if ((mfirst >> j) & 1u) {
+                    const unsigned int p = atomicAdd(A.meet_count(), 1u);
+                    if (p < kMeetCap) {
+                        A.cand()[p] = w[j];
+                        A.cpos()[p] = pos_of(cd[j]);
+                    }
+                }
+            }
+            // phase 5: additions to targets whose claim (by another warp) was
+            // still being published; this warp published its own claims above
+            __syncwarp();
+            if (retry) {
+#pragma unroll
+                for (int j = 0; j < kUnroll; ++j) {
+                    if (!((retry >> j) & 1u)) continue;
+                    unsigned int c = *reinterpret_cast<volatile unsigned int *>(S.code + w[j]);
+                    unsigned long long spins = 0;
+                    while (is_pending(c) && ++spins < spin_limit) {
+                        __nanosleep(32);
+                        c = *reinterpret_cast<volatile unsigned int *>(S.code + w[j]);
+                    }
+                    if (is_pending(c)) {
+                        atomicOr(A.err(), kErrTimeout);
+                        continue;
+                    }
+                    if (c == 0u) continue;      // the claim ran out of positions: the sample restarts
+                    const unsigned long long su = sh.u.ex.csig[own[j]];
+                    const unsigned long long nv = atomicAdd(S.qs + S.at(X, pos_of(c)), su) + su;
+                    if (nv < su) atomicOr(A.err(), kErrAddOverflow);
+                    my_max = nv > my_max ? nv : my_max;
+                }
+            }
+        }
+        // largest new path count (every count's final value is the largest
+        // value its additions returned) and the new frontier's degree sum,
+        // folded per warp into shared memory before the chunk's barrier
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long om = __shfl_xor_sync(0xffffffffu, my_max, o);
+            my_max = om > my_max ? om : my_max;
+            my_deg += __shfl_xor_sync(0xffffffffu, my_deg, o);
+        }
+        if (lane == 0) {
+            if (my_max) atomicMax(A.lmax(), my_max);
+            if (my_deg) atomicAdd(A.ldeg(), my_deg);
+        }
+        my_max = 0;
+        my_deg = 0;
+        __syncthreads();
+    return my_scan;
+}
+
 // Runs sample `idx` in slot S.  Returns false if the sample's two balls
 // outgrew the slot's queue capacity: the slot is then clear again and
 // nothing was counted, and the caller runs the sample on a larger slot.
@@ -530,237 +853,117 @@ __device__ bool run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, const
         sh.shv = 0;
         sh.chosen = -1;
         sh.X = (sh.fdeg[0] <= sh.fdeg[1]) ? 0 : 1;
+        if (sh.fdeg[sh.X] == 0) {
+            // the side expanded first has no edges (the smaller degree sum is
+            // 0): its layer is empty, so the pair is disconnected; same result
+            // as expanding that layer, without the layer's barriers
+            sh.layer[sh.X] = 1;
+            sh.expanded = 1;
+            if (1u < (unsigned int)kMaxLayers) {
+                sh.lbeg[sh.X][1] = 1;
+                sh.lend[sh.X][1] = 1;
+            }
+            sh.status = 2;
+        }
     }
     __syncthreads();
 
     // A2: balanced bidirectional BFS, one whole layer per step.  The side of
     // the next layer is chosen, and the layer accumulators cleared, by thread
     // 0 at the end of the previous layer, inside that layer's last barrier.
-    for (;;) {
+    while (sh.status == 0) {
         const int X = sh.X, Y = 1 - X;
         const unsigned int nl = sh.layer[X] + 1;     // level of the new layer
         const unsigned int fb = sh.fbeg[X], fe = sh.fend[X];
         const unsigned int qbase = sh.qlen[X];       // queue position of the new layer's first vertex
         const unsigned int room = S.cap - sh.qlen[Y];   // positions this side may fill
         const unsigned int yb = sh.fbeg[Y], ye = sh.fend[Y];
-        const unsigned int pend_code = (X ? kSideBit : 0u) | kPending;
-        unsigned long long my_max = 0, my_scan = 0, my_deg = 0;
-        const int lane = tid & 31;
+        unsigned long long my_scan = 0;
 
-        for (unsigned int cb = fb; cb < fe; cb += NT) {
-            const unsigned int i = cb + tid;
-            long long b = 0;
-            unsigned long long d = 0, sg = 0;
-            if (i < fe) {
-                const unsigned int ph = S.at(X, i);
-                const unsigned int u = __ldcg(S.qv + ph);
-                b = G.begin(u);
-                d = (unsigned long long)(G.end(u) - b);
-                sg = ldcg(S.qs + ph);
+        // a heavy layer of a persistent launch is posted for other CTAs to
+        // help with (chunks of cv frontier vertices)
+        int hk = -1;
+        if (a.help && sh.fdeg[X] >= a.help_edges && fe - fb > (unsigned int)NT / 8u) {
+            if (tid == 0) {
+                HelpReq *board = board_req(a.help);
+                const unsigned int cv = (unsigned int)NT / 8u;
+                const unsigned int nch = (fe - fb + cv - 1u) / cv;
+                int k = -1;
+                if (nch < (1u << 23))
+                    for (int i = 0; i < kHelpSlots && k < 0; ++i)
+                        if (atomicCAS(&board[i].state, 0, 1) == 0) k = i;
+                if (k >= 0) {
+                    HelpReq *R = board + k;
+                    R->code = S.code; R->qv = S.qv; R->ql = S.ql; R->qs = S.qs; R->qm = S.qm;
+                    R->bits = S.bits; R->bw = S.bw; R->off = G.off; R->adj = G.adj; R->n = G.n;
+                    R->cap = S.cap; R->X = (unsigned int)X; R->nl = nl; R->fb = fb; R->fe = fe; R->qbase = qbase;
+                    R->room = room; R->yb = yb; R->ye = ye; R->cv = cv;
+                    R->lmax = 0; R->ldeg = 0; R->scan = 0; R->new_count = 0; R->meet_count = 0; R->err = 0;
+                    R->meets = 0; R->ovf = 0; R->done = 0;
+                    __threadfence();
+                    const unsigned long long gen = (*reinterpret_cast<volatile unsigned long long *>(&R->ticket) >> 48) + 1ULL;
+                    atomicExch(&R->ticket, ((gen & 0xffffULL) << 48) | ((unsigned long long)nch << 24));
+                    __threadfence();
+                    atomicAdd(board_open(a.help), 1u);
+                }
+                sh.help_k = k;
             }
-            unsigned long long total;
-            const unsigned long long excl = block_excl_scan<NT>(d, &total, sh);
-            sh.u.ex.cbeg[tid] = b;
-            sh.u.ex.cpos[tid] = excl;
-            sh.u.ex.csig[tid] = sg;
-            const int cnt = (int)min((unsigned int)NT, fe - cb);
             __syncthreads();
-            my_scan += (tid == 0) ? total : 0ULL;
-            // warp-uniform batches: lane l of warp k handles entries
-            // e0 + l + j*NT, j < kUnroll, with e0 = 32k + (multiple of NT*kUnroll);
-            // each phase issues all kUnroll memory operations before waiting
-            const unsigned long long wbase = (unsigned long long)(tid & ~31);
-            for (unsigned long long e0 = wbase; e0 < total; e0 += (unsigned long long)NT * kUnroll) {
-                unsigned int w[kUnroll];
-                unsigned int dw[kUnroll];
-                int own[kUnroll];
-#pragma unroll
-                for (int j = 0; j < kUnroll; ++j) {
-                    const unsigned long long e = e0 + (unsigned long long)lane + (unsigned long long)j * NT;
-                    w[j] = kNone;
-                    dw[j] = 0;
-                    own[j] = 0;
-                    if (e < total) {
-                        // owner: the last k with cpos[k] <= e
-                        int lo = j > 0 ? own[j - 1] : 0, hi = cnt - 1;
-                        while (lo < hi) {
-                            const int mid = (lo + hi + 1) >> 1;
-                            if (sh.u.ex.cpos[mid] <= e) lo = mid;
-                            else hi = mid - 1;
-                        }
-                        own[j] = lo;
-                        const uint2 c = __ldg(G.adj + sh.u.ex.cbeg[lo] + (long long)(e - sh.u.ex.cpos[lo]));
-                        w[j] = c.x;
-                        dw[j] = c.y;
-                    }
-                }
-                // phase 2: the code word of every target (one 4-byte load each);
-                // once the layer is known to be the last, only the other side's
-                // reached bit first (a dense map that stays in L2), and the code
-                // only of targets that have it
-                unsigned int cd[kUnroll];
-                int kind[kUnroll];
-                const bool fast = S.bits != nullptr && *(volatile int *)&sh.meets != 0;
-                if (fast) {
-                    const uint32_t *ybits = S.bits + (X ? 0 : S.bw);
-                    unsigned int ymask = 0;
-#pragma unroll
-                    for (int j = 0; j < kUnroll; ++j)
-                        if (w[j] != kNone && ((__ldcg(ybits + (w[j] >> 5)) >> (w[j] & 31)) & 1u)) ymask |= 1u << j;
-#pragma unroll
-                    for (int j = 0; j < kUnroll; ++j) cd[j] = ((ymask >> j) & 1u) ? __ldcg(S.code + w[j]) : 0u;
-#pragma unroll
-                    for (int j = 0; j < kUnroll; ++j) kind[j] = ((ymask >> j) & 1u) ? kTMeet : kTSkip;
-                } else {
-#pragma unroll
-                    for (int j = 0; j < kUnroll; ++j) cd[j] = w[j] != kNone ? __ldcg(S.code + w[j]) : 0u;
-#pragma unroll
-                    for (int j = 0; j < kUnroll; ++j) {
-                        const unsigned int c = cd[j];
-                        kind[j] = w[j] == kNone ? kTSkip
-                                  : c == 0u ? kTUnseen
-                                  : side_of(c) != X ? kTMeet
-                                  : is_pending(c) ? kTPend
-                                  : pos_of(c) >= qbase ? kTSame : kTSkip;
-                    }
-                }
-                // a target held by the other side makes this layer the last one:
-                // from then on only meeting vertices need counts, so other unseen
-                // targets of the last layer are not claimed
-#pragma unroll
-                for (int j = 0; j < kUnroll; ++j)
-                    if (kind[j] == kTMeet) *(volatile int *)&sh.meets = 1;
-                const bool last = *(volatile int *)&sh.meets != 0;
-                // phase 3: claims (CAS on the code word to "pending"), path-count
-                // additions to targets already in the new layer, and meeting
-                // counts (the other side's last layer, indexed by its queue
-                // position).  The additions return their old value, so a thread
-                // has waited for all of them before the layer's closing barrier
-                // and every count is complete when any thread reads it next.
-                unsigned int cmask = 0, mfirst = 0, retry = 0;
-#pragma unroll
-                for (int j = 0; j < kUnroll; ++j) {
-                    if (kind[j] == kTUnseen) {
-                        if (last) {
-                            kind[j] = kTSkip;
-                        } else {
-                            const unsigned int old = atomicCAS(S.code + w[j], 0u, pend_code);
-                            if (old == 0u) {
-                                cmask |= 1u << j;
-                            } else {
-                                // claimed in this layer by another thread meanwhile
-                                cd[j] = old;
-                                kind[j] = is_pending(old) ? kTPend : kTSame;
-                            }
-                        }
-                    }
-                }
-#pragma unroll
-                for (int j = 0; j < kUnroll; ++j) {
-                    const unsigned long long su = sh.u.ex.csig[own[j]];
-                    if (kind[j] == kTMeet) {
-                        const unsigned int p = pos_of(cd[j]);
-                        if (side_of(cd[j]) != Y || is_pending(cd[j]) || p < yb || p >= ye) {
-                            atomicOr(&sh.err, kErrSelect);     // broken invariant: never expected
-                            continue;
-                        }
-                        const unsigned long long old = atomicAdd(S.qm + S.at(Y, p), su);
-                        if (old == 0ULL) mfirst |= 1u << j;
-                        if (old + su < su) atomicOr(&sh.err, kErrAddOverflow);
-                    } else if (kind[j] == kTSame) {
-                        const unsigned int p = pos_of(cd[j]);
-                        if (side_of(cd[j]) != X || p < qbase) {
-                            atomicOr(&sh.err, kErrSelect);
-                            continue;
-                        }
-                        const unsigned long long nv = atomicAdd(S.qs + S.at(X, p), su) + su;
-                        if (nv < su) atomicOr(&sh.err, kErrAddOverflow);      // excluded by the choice of K
-                        my_max = nv > my_max ? nv : my_max;
-                    } else if (kind[j] == kTPend) {
-                        retry |= 1u << j;
-                    }
-                }
-                // phase 4: claimed targets join the new frontier (warp-aggregated
-                // queue positions), get their first path count and publish their
-                // position; first-touched meeting vertices join the meeting set
-#pragma unroll
-                for (int j = 0; j < kUnroll; ++j) {
-                    const bool claimed = (cmask >> j) & 1u;
-                    const unsigned int m = __ballot_sync(0xffffffffu, claimed);
-                    if (m) {
-                        const int leader = __ffs(m) - 1;
-                        unsigned int slot0 = 0;
-                        if (lane == leader) slot0 = atomicAdd(&sh.new_count, (unsigned int)__popc(m));
-                        slot0 = __shfl_sync(0xffffffffu, slot0, leader);
-                        if (claimed) {
-                            const unsigned int p = qbase + slot0 + __popc(m & ((1u << lane) - 1u));
-                            if (p < room) {
-                                const unsigned int ph = S.at(X, p);
-                                const unsigned long long su = sh.u.ex.csig[own[j]];
-                                __stcg(S.qv + ph, w[j]);
-                                __stcg(S.ql + ph, nl);
-                                const unsigned long long nv = atomicAdd(S.qs + ph, su) + su;
-                                if (nv < su) atomicOr(&sh.err, kErrAddOverflow);
-                                my_max = nv > my_max ? nv : my_max;
-                                __stcg(S.code + w[j], code_of(X, p));
-                                my_deg += dw[j];
-                                if (S.bits) atomicOr(&S.bits[(X ? S.bw : 0) + (w[j] >> 5)], 1u << (w[j] & 31));
-                            } else {
-                                // out of queue positions: the sample restarts on a larger slot
-                                *(volatile int *)&sh.ovf = 1;
-                                __stcg(S.code + w[j], 0u);
-                            }
-                        }
-                    }
-                    if ((mfirst >> j) & 1u) {
-                        const unsigned int p = atomicAdd(&sh.meet_count, 1u);
-                        if (p < kMeetCap) {
-                            sh.cand[p] = w[j];
-                            sh.cpos[p] = pos_of(cd[j]);
-                        }
-                    }
-                }
-                // phase 5: additions to targets whose claim (by another warp) was
-                // still being published; this warp published its own claims above
-                __syncwarp();
-                if (retry) {
-#pragma unroll
-                    for (int j = 0; j < kUnroll; ++j) {
-                        if (!((retry >> j) & 1u)) continue;
-                        unsigned int c = *reinterpret_cast<volatile unsigned int *>(S.code + w[j]);
-                        unsigned long long spins = 0;
-                        while (is_pending(c) && ++spins < a.spin_limit) {
-                            __nanosleep(32);
-                            c = *reinterpret_cast<volatile unsigned int *>(S.code + w[j]);
-                        }
-                        if (is_pending(c)) {
-                            atomicOr(&sh.err, kErrTimeout);
-                            continue;
-                        }
-                        if (c == 0u) continue;      // the claim ran out of positions: the sample restarts
-                        const unsigned long long su = sh.u.ex.csig[own[j]];
-                        const unsigned long long nv = atomicAdd(S.qs + S.at(X, pos_of(c)), su) + su;
-                        if (nv < su) atomicOr(&sh.err, kErrAddOverflow);
-                        my_max = nv > my_max ? nv : my_max;
-                    }
+            hk = sh.help_k;
+        }
+        if (hk < 0) {
+            for (unsigned int cb = fb; cb < fe; cb += NT)
+                my_scan += expand_chunk<NT, OffT>(a.spin_limit, G, S, sh, SmemAcc<NT>{sh}, X, nl, cb, fe, qbase, room,
+                                                  yb, ye);
+        } else {
+            HelpReq *R = board_req(a.help) + hk;
+            const unsigned int cv = (unsigned int)NT / 8u;
+            const unsigned int nch = (fe - fb + cv - 1u) / cv;
+            for (;;) {
+                if (tid == 0) sh.help_c = take_chunk(R);
+                __syncthreads();
+                const int c = sh.help_c;
+                if (c < 0) break;
+                const unsigned int cb = fb + (unsigned int)c * cv;
+                const unsigned long long sc = expand_chunk<NT, OffT>(a.spin_limit, G, S, sh, ReqAcc{R}, X, nl, cb,
+                                                                     min(cb + cv, fe), qbase, room, yb, ye);
+                if (tid == 0) {
+                    atomicAdd(&R->scan, sc);
+                    __threadfence();
+                    atomicAdd(&R->done, 1u);
                 }
             }
-            // largest new path count (every count's final value is the largest
-            // value its additions returned) and the new frontier's degree sum,
-            // folded per warp into shared memory before the chunk's barrier
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const unsigned long long om = __shfl_xor_sync(0xffffffffu, my_max, o);
-                my_max = om > my_max ? om : my_max;
-                my_deg += __shfl_xor_sync(0xffffffffu, my_deg, o);
+            // no chunk left to take; wait (bounded) for the chunks other CTAs
+            // took, then collect
+            if (tid == 0) {
+                atomicSub(board_open(a.help), 1u);
+                unsigned long long w = 0;
+                while (*reinterpret_cast<volatile unsigned int *>(&R->done) < nch && ++w < a.spin_limit)
+                    __nanosleep(256);
+                __threadfence();
+                if (*reinterpret_cast<volatile unsigned int *>(&R->done) < nch) sh.err |= kErrTimeout;
+                sh.new_count = *reinterpret_cast<volatile unsigned int *>(&R->new_count);
+                sh.meet_count = *reinterpret_cast<volatile unsigned int *>(&R->meet_count);
+                sh.meets = *reinterpret_cast<volatile int *>(&R->meets);
+                sh.ovf |= *reinterpret_cast<volatile int *>(&R->ovf);
+                sh.err |= *reinterpret_cast<volatile unsigned int *>(&R->err);
+                sh.lmax = *reinterpret_cast<volatile unsigned long long *>(&R->lmax);
+                sh.ldeg = *reinterpret_cast<volatile unsigned long long *>(&R->ldeg);
+                my_scan = *reinterpret_cast<volatile unsigned long long *>(&R->scan);
             }
-            if (lane == 0) {
-                if (my_max) atomicMax(&sh.lmax, my_max);
-                if (my_deg) atomicAdd(&sh.ldeg, my_deg);
-            }
-            my_max = 0;
-            my_deg = 0;
             __syncthreads();
+            const unsigned int mc = min(sh.meet_count, (unsigned int)kMeetCap);
+            for (unsigned int i = tid; i < mc; i += NT) {
+                sh.cand[i] = __ldcg(R->cand + i);
+                sh.cpos[i] = __ldcg(R->cpos + i);
+            }
+            __syncthreads();
+            // the request is free again only if every chunk is done (a request
+            // whose wait gave up stays held: a late helper may still write it)
+            if (tid == 0 && !(sh.err & kErrTimeout)) {
+                __threadfence();
+                atomicExch(&R->state, 0);
+            }
         }
         if (tid == 0) {
             sh.e_scan += my_scan;
@@ -1519,16 +1722,17 @@ __device__ unsigned int fold_and_check(const QueryDesc &P, uint32_t *counts, con
 }
 
 // Sets up a query's pipeline: base = current tau, R samples up to ceil(omega).
+// One warp zeroes the state in place, then lane 0 sets its fields.
 __global__ void pipe_begin_kernel(PipeState *ps, const Job *job, unsigned long long clip, long long E)
 {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        PipeState z;
-        unsigned char *p = reinterpret_cast<unsigned char *>(&z);
-        for (size_t i = 0; i < sizeof(PipeState); ++i) p[i] = 0;
-        z.base = job->tau;
-        z.R = clip > z.base ? clip - z.base : 0ULL;
-        z.nE = (long long)((z.R + (unsigned long long)E - 1) / (unsigned long long)E);
-        *ps = z;
+    if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+    unsigned int *w = reinterpret_cast<unsigned int *>(ps);
+    for (size_t i = threadIdx.x; i < sizeof(PipeState) / 4; i += 32) w[i] = 0u;
+    __syncwarp();
+    if (threadIdx.x == 0) {
+        ps->base = job->tau;
+        ps->R = clip > ps->base ? clip - ps->base : 0ULL;
+        ps->nE = (long long)((ps->R + (unsigned long long)E - 1) / (unsigned long long)E);
     }
 }
 
@@ -1567,16 +1771,57 @@ __global__ void __launch_bounds__(NT, (2048 / NT / 2) > 0 ? (2048 / NT / 2) : 1)
         // Warp 0 picks the next sample: its lanes read the state of 32
         // queries at a time and the first eligible one in scan order (round
         // robin from a per-pick ticket, or array order) is tried.
+        // Between two samples a CTA first helps expand a layer another CTA
+        // posted (a heavy layer of its sample), one chunk at a time.
         if (tid < 32) {
             const int lane = tid;
             int take = 0;
             bool stop_launch = false;
+            int helping = 0;
             if (lane == 0) {
                 pm.take = 0;
                 s_qi = -1;
-                stop_launch = vbs->abort != 0;
-                if (!stop_launch && B.budget && atomicAdd(&B.bs->taken, 0ULL) >= B.budget) stop_launch = true;
+                sh.help_k = -1;
+                if (B.help && *reinterpret_cast<volatile unsigned int *>(board_open(B.help)) != 0u) {
+                    HelpReq *board = board_req(B.help);
+                    for (int i = 0; i < kHelpSlots && sh.help_k < 0; ++i) {
+                        const int c = take_chunk(board + i);
+                        if (c < 0) continue;
+                        // the chunk belongs to the layer the request holds now, and the
+                        // request cannot be reused before this chunk is done
+                        volatile HelpReq *V = board + i;
+                        sh.help_k = i;
+                        sh.help_c = c;
+                        sh.hl.code = V->code;
+                        sh.hl.qv = V->qv;
+                        sh.hl.ql = V->ql;
+                        sh.hl.qs = V->qs;
+                        sh.hl.qm = V->qm;
+                        sh.hl.bits = V->bits;
+                        sh.hl.bw = V->bw;
+                        sh.hl.n = V->n;
+                        sh.hl.off = V->off;
+                        sh.hl.adj = V->adj;
+                        sh.hl.cap = V->cap;
+                        sh.hl.X = V->X;
+                        sh.hl.nl = V->nl;
+                        sh.hl.fb = V->fb;
+                        sh.hl.fe = V->fe;
+                        sh.hl.qbase = V->qbase;
+                        sh.hl.room = V->room;
+                        sh.hl.yb = V->yb;
+                        sh.hl.ye = V->ye;
+                        sh.hl.cv = V->cv;
+                        helping = 1;
+                    }
+                }
+                if (!helping) {
+                    stop_launch = vbs->abort != 0;
+                    if (!stop_launch && B.budget && atomicAdd(&B.bs->taken, 0ULL) >= B.budget) stop_launch = true;
+                }
             }
+            helping = __shfl_sync(0xffffffffu, helping, 0);
+            if (helping) stop_launch = true;     // skip the pick below
             stop_launch = __shfl_sync(0xffffffffu, stop_launch ? 1 : 0, 0) != 0;
             if (!stop_launch) {
                 unsigned int start = 0;
@@ -1680,10 +1925,36 @@ __global__ void __launch_bounds__(NT, (2048 / NT / 2) > 0 ? (2048 / NT / 2) : 1)
                 t.abandon = qd.tag != 0 ? &qd.job->stopped : nullptr;
                 t.use_bits = qd.use_bits;
                 t.spin_limit = B.spin_limit;
+                t.help = B.help;
+                t.help_edges = B.help_edges;
                 sa = t;
             }
         }
         __syncthreads();
+        if (sh.help_k >= 0) {
+            HelpReq *R = board_req(B.help) + sh.help_k;
+            Slot S2;
+            S2.code = sh.hl.code;
+            S2.qv = sh.hl.qv;
+            S2.ql = sh.hl.ql;
+            S2.qs = sh.hl.qs;
+            S2.qm = sh.hl.qm;
+            S2.bits = sh.hl.bits;
+            S2.bw = sh.hl.bw;
+            S2.cap = sh.hl.cap;
+            const GraphRef<OffT> G2{reinterpret_cast<const OffT *>(sh.hl.off), sh.hl.adj, sh.hl.n};
+            const unsigned int cb = sh.hl.fb + (unsigned int)sh.help_c * sh.hl.cv;
+            const unsigned long long sc =
+                expand_chunk<NT, OffT>(B.spin_limit, G2, S2, sh, ReqAcc{R}, (int)sh.hl.X, sh.hl.nl, cb,
+                                       min(cb + sh.hl.cv, sh.hl.fe), sh.hl.qbase, sh.hl.room, sh.hl.yb, sh.hl.ye);
+            if (tid == 0) {
+                atomicAdd(&R->scan, sc);
+                __threadfence();
+                atomicAdd(&R->done, 1u);
+            }
+            __syncthreads();
+            continue;
+        }
         if (!pm.take) break;
         const long long e = pm.epoch;
         const int f = (int)(e % qd.F);
@@ -1885,6 +2156,8 @@ cudaError_t launch_batch(const BatchLaunch &a, cudaStream_t st)
     default: return cudaErrorInvalidValue;
     }
 }
+
+size_t help_board_bytes() { return 256 + sizeof(HelpReq) * (size_t)kHelpSlots; }
 
 cudaError_t launch_pipe_begin(PipeState *ps, const Job *job, unsigned long long clip, long long E, cudaStream_t st)
 {

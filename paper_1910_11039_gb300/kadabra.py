@@ -41,7 +41,8 @@ class Params(C.Structure):
     _fields_ = [("eps", C.c_double), ("delta", C.c_double), ("seed", C.c_uint64),
                 ("vertex_diameter", C.c_int64), ("n_calib", C.c_int64), ("delta_rule", C.c_int32),
                 ("flags", C.c_uint32), ("beta", C.c_double), ("slots", C.c_int32),
-                ("threads", C.c_int32), ("scratch_fraction", C.c_double), ("queue_cap", C.c_int64)]
+                ("threads", C.c_int32), ("scratch_fraction", C.c_double), ("queue_cap", C.c_int64),
+                ("coop_edges", C.c_int64)]
 
 
 class QueryInfo(C.Structure):
@@ -56,7 +57,8 @@ class QueryInfo(C.Structure):
                 ("budget_classes", C.c_int32), ("stop_ns", C.c_uint64), ("phase", C.c_int32),
                 ("pad0", C.c_int32), ("cal_done", C.c_uint64), ("device_bytes", C.c_uint64),
                 ("launches", C.c_int64), ("diameter_ms", C.c_double), ("calibration_ms", C.c_double),
-                ("queue_cap", C.c_int64), ("spill_slots", C.c_int32), ("pad1", C.c_int32)]
+                ("queue_cap", C.c_int64), ("spill_slots", C.c_int32), ("vd_exact", C.c_int32),
+                ("vd_searches", C.c_int64)]
 
 
 class TraceRec(C.Structure):

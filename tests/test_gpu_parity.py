@@ -348,6 +348,29 @@ def test_small_queue_capacity_spills_and_matches_oracle(K, orc, name, cap):
     assert np.array_equal(res["counts"], counts)
 
 
+@pytest.mark.parametrize("name,eps,E,cap", [
+    ("er2000", 0.05, 100, 0), ("rmat14", 0.03, 256, 0), ("grid64", 0.05, 250, 0), ("layered", 0.05, 200, 0),
+    ("fullgrid64", 0.05, 150, 0), ("rhg4k", 0.03, 128, 0), ("rmat14", 0.03, 128, 300), ("grid64", 0.05, 128, 500),
+])
+def test_cooperative_layers_match_oracle(K, orc, name, eps, E, cap):
+    # coop_edges = 1 posts every layer of more than one chunk of frontier
+    # vertices for other CTAs to expand together with the sample's own CTA
+    # (with a small queue capacity, also on spill slots); the pipelined run
+    # must still end exactly as the oracle's.
+    g = GRAPHS[name]()
+    G = K.Graph.from_inputs(g)
+    kw = dict(queue_cap=cap) if cap else {}
+    q = K.Query(G, eps=eps, delta=0.1, seed=9, coop_edges=1, threads=256, **kw)
+    q.run_pipelined(E, frames=8)
+    res = q.result(btilde=False)
+    info = q.info()
+    counts, cal, LL, LU, R = orc.kadabra(g, eps, 0.1, seed=9, epoch_len=E)
+    assert info.device_error == 0
+    assert res["tau"] == R.tau and res["stop_epoch"] == R.stop_epoch
+    assert np.array_equal(res["counts"], counts)
+    assert info.samples == R.tau and info.e_scan == R.e_scan
+
+
 def test_omega_clip_and_single_samples(K, orc):
     g = GRAPHS["er2000"]()
     G = K.Graph.from_inputs(g)
@@ -431,6 +454,94 @@ def test_vertex_diameter_bound_matches_oracle(K, orc, name):
         assert q.result(btilde=False)["counts"].sum() == 0 and q.info().connected == 0
 
 
+def _two_components_star_and_path():
+    # a star of 40 vertices (vertex diameter 3) and a separate path of 12
+    # (vertex diameter 12): the largest component is the star, and the path's
+    # bound 2 * ecc(0) + 1 = 23 exceeds the star's exact value
+    pairs = [(0, i) for i in range(1, 40)] + [(40 + i, 41 + i) for i in range(11)]
+    p = np.array(pairs)
+    return I.csr_from_edges(52, p[:, 0], p[:, 1])
+
+
+@pytest.mark.parametrize("name", ["er2000", "rmat12", "grid64", "rgg5k", "path", "star", "fullgrid64", "layered",
+                                  "rhg4k", "cycle", "disjoint"])
+def test_exact_vertex_diameter_matches_oracle(K, orc, name):
+    if name == "cycle":
+        g = I.cycle_graph(301)
+    elif name == "disjoint":
+        a, b = I.full_grid_graph(9, 9), I.path_graph(30)
+        src = np.concatenate([np.repeat(np.arange(a.n), a.degrees), a.n + np.repeat(np.arange(b.n), b.degrees)])
+        dst = np.concatenate([a.cols, a.n + b.cols])
+        g = I.csr_from_edges(a.n + b.n, src, dst)
+    else:
+        g = GRAPHS[name]()
+    G = K.Graph.from_inputs(g)
+    q = K.Query(G, eps=0.05, delta=0.1, seed=1, n_calib=100, vertex_diameter=-1)
+    info = q.info()
+    want = orc.vertex_diameter_exact(g)
+    assert info.vd_exact == 1 and info.vertex_diameter == want, (info.vertex_diameter, want)
+    assert info.vertex_diameter <= orc.vertex_diameter_bound(g)
+    assert info.omega == orc.omega(0.05, 0.1, want)
+
+
+def test_exact_vertex_diameter_of_a_smaller_component(K, orc):
+    # the largest component is a star (vertex diameter 3); a separate path of
+    # 12 vertices has the larger vertex diameter (12) and a bound of 23: it is
+    # searched too, and the exact value is the path's
+    g = _two_components_star_and_path()
+    G = K.Graph.from_inputs(g)
+    q = K.Query(G, eps=0.05, delta=0.1, seed=1, n_calib=100, vertex_diameter=-1)
+    info = q.info()
+    assert orc.vertex_diameter_exact(g) == 12
+    assert info.vd_exact == 1 and info.vertex_diameter == 12
+
+
+@pytest.mark.parametrize("name", ["er2000", "grid64"])
+def test_whole_run_with_exact_diameter_matches_oracle(K, orc, name):
+    g = GRAPHS[name]()
+    vd = orc.vertex_diameter_exact(g)
+    G = K.Graph.from_inputs(g)
+    q = K.Query(G, eps=0.05, delta=0.1, seed=4, vertex_diameter=-1)
+    assert q.info().vertex_diameter == vd
+    q.run_pipelined(100, frames=8)
+    res = q.result(btilde=False)
+    counts, cal, LL, LU, R = orc.kadabra(g, 0.05, 0.1, seed=4, epoch_len=100, vertex_diameter=vd)
+    assert res["tau"] == R.tau and res["stop_epoch"] == R.stop_epoch
+    assert np.array_equal(res["counts"], counts)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name", ["rmat20", "grid512", "rmat26"])
+def test_exact_vertex_diameter_at_size_is_consistent(K, orc, name):
+    # Too large for all-pairs; what holds at any size: the eccentricity of any
+    # vertex v satisfies ecc(v) + 1 <= VD <= 2 ecc(v) + 1 within its
+    # component, and the exact value is at most the bound.
+    from scipy.sparse import csr_matrix
+    from scipy.sparse.csgraph import breadth_first_order, connected_components
+    g = I.config_graph(name)
+    G = K.Graph.from_inputs(g, offsets_64=g.nnz >= 2**31, skip_validate=True)
+    q = K.Query(G, eps=0.01, delta=0.1, seed=1, n_calib=64, vertex_diameter=-1)
+    info = q.info()
+    # R-MAT graphs end iFUB after a few searches; a mesh's wide fringes may
+    # stop it at its effort bound with a proven upper bound instead
+    assert info.vd_exact == 1 or name.startswith("grid")
+    assert info.vertex_diameter <= orc.vertex_diameter_bound(g)
+    if g.nnz >= 2**28:
+        return      # the host-side searches below would take minutes
+    A = csr_matrix((np.ones(g.nnz, dtype=np.int8), g.cols, g.offsets), shape=(g.n, g.n))
+    ncomp, labels = connected_components(A, directed=False)
+    big = np.bincount(labels).argmax()
+    rng = np.random.default_rng(0)
+    cand = np.nonzero(labels == big)[0]
+    for v in rng.choice(cand, 4, replace=False):
+        order, pred = breadth_first_order(A, int(v), directed=False, return_predecessors=True)
+        depth = np.zeros(g.n, dtype=np.int64)
+        for x in order[1:]:
+            depth[x] = depth[pred[x]] + 1
+        ecc = int(depth[order].max())
+        assert ecc + 1 <= info.vertex_diameter <= 2 * ecc + 1 or (not info.vd_exact and ecc + 1 <= info.vertex_diameter)
+
+
 @pytest.mark.slow
 def test_rmat20_full_size_epoch_and_trace(K, orc):
     """R-MAT scale 20 (the measured workload) at full size, in the launch
@@ -512,7 +623,7 @@ def _graph_sha(g):
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("name,threads", [("rmat26", 512), ("grid4096", 1024)])
+@pytest.mark.parametrize("name,threads", [("rmat26", 1024), ("grid4096", 1024)])
 def test_whole_run_at_full_size_matches_oracle_golden(K, name, threads):
     """The two largest single-query workloads, R-MAT scale 26 and the
     4096 x 4096 grid, through the whole method in the benchmarked form
@@ -530,9 +641,12 @@ def test_whole_run_at_full_size_matches_oracle_golden(K, name, threads):
     g = I.config_graph(name)
     assert g.n == gold["n"] and g.nnz == gold["nnz"]
     assert _graph_sha(g) == gold["graph_sha256"], "the input generator changed since the golden run was written"
-    G = K.Graph.from_inputs(g, offsets_64=g.nnz >= 2**31, skip_validate=True)
+    # R-MAT scale 26 is specified with int64 offsets (its 2.10e9 entries would
+    # still fit int32 ones)
+    G = K.Graph.from_inputs(g, offsets_64=name == "rmat26" or g.nnz >= 2**31, skip_validate=True)
     q = K.Query(G, eps=P["eps"], delta=P["delta"], seed=P["seed"], delta_rule=P["delta_rule"], beta=P["beta"],
                 threads=threads)
+    assert q.info().offsets_64 == (1 if name == "rmat26" else 0)
     info = q.info()
     assert info.omega == float.fromhex(gold["omega"])
     assert info.vertex_diameter == gold["vertex_diameter"] and info.n_calib == gold["n_calib"]
