@@ -462,6 +462,84 @@ def run_gpu(args, wl, g, rank, world, local_rank, cpu_baseline):
 
 
 # ---------------------------------------------------------------------------
+# one query sharded over the ranks: epoch logs exchanged, two frames
+# ---------------------------------------------------------------------------
+
+def run_sharded(args, wl, g, rank, world, local_rank):
+    """Every rank takes its share of each epoch's sample indices (a contiguous
+    range), samples it into an epoch log on a side stream while the previous
+    epoch's logs are all-gathered, folded and checked on every rank (the
+    paper's epoch aggregation, Section IV, with logs instead of counter
+    vectors).  value = the query's samples (tau at the stop) per second of the
+    slowest rank; the work per step is fixed, so the scaling is strong."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_1910_11039_gb300 import build as B
+    from paper_1910_11039_gb300 import kadabra as K
+    from paper_1910_11039_gb300.distributed import LibraryShard, ShardedRun
+
+    B.build()
+    K.load()
+    dev = torch.device("cuda", local_rank)
+    off64 = bool(wl.get("off64")) or g.nnz >= 2**31
+    G = K.Graph.from_inputs(g, offsets_64=off64, skip_validate=True)
+    q = K.Query(G, eps=wl["eps"], delta=wl["delta"], seed=wl["seed"], slots=args.slots, threads=args.threads)
+    info0 = q.info()
+    E = args.epoch
+    share = -(-E // world)
+    shard = LibraryShard(q, device=dev, log_cap=share * max(1, info0.vertex_diameter))
+    runner = ShardedRun(shard, shard, info0.omega_ceil, dist)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        flush.fill_(1)
+        q.reset()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        stopped, tau, epochs = runner.run_logs(E)
+        e1.record(stream)
+        e1.synchronize()
+        assert stopped
+        return e0.elapsed_time(e1), tau, epochs
+
+    for _ in range(args.warmup):
+        step()
+    dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    times, taus = [], []
+    for _ in range(args.steps):
+        ms, tau, epochs = step()
+        times.append(ms)
+        taus.append(tau)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    t = torch.tensor([sum(times)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    dist.barrier()
+    if rank != 0:
+        return
+    samples = float(sum(taus))
+    line = {
+        "metric": METRIC, "value": samples / (total_ms / 1e3), "unit": "samples/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "strong", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": wl["desc"], "name": args.workload, "n": g.n, "nnz": g.nnz, "epoch_len": E,
+                   "mode": "sharded", "threads": info0.threads, "slots": info0.slots,
+                   "l2": "flushed before every step (256 MiB write)",
+                   "parallelism": f"one query sharded over {world} rank(s): epoch logs all-gathered, two frames"},
+        "time_to_stop_ms": total_ms / args.steps, "samples_per_step": samples / args.steps,
+        "stop_epoch": epochs - 1, "gpu_launches": None, "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
 # many queries of uneven size: one persistent launch vs one launch per query
 # ---------------------------------------------------------------------------
 
@@ -695,9 +773,9 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default="rmat26", choices=list(WORKLOADS))
     ap.add_argument("--epoch", type=int, default=1024)
-    ap.add_argument("--mode", default="pipelined", choices=["pipelined", "epochs", "batched", "serve"],
-                    help="pipelined/epochs: one query on --workload; batched: 64 queries of uneven size; "
-                         "serve: a Poisson stream of queries")
+    ap.add_argument("--mode", default="pipelined", choices=["pipelined", "epochs", "batched", "serve", "sharded"],
+                    help="pipelined/epochs: one query on --workload; sharded: one query split over the ranks; "
+                         "batched: 64 queries of uneven size; serve: a Poisson stream of queries")
     ap.add_argument("--serve-queries", type=int, default=2000)
     ap.add_argument("--serve-rate", type=float, default=20.0)
     ap.add_argument("--serve-pool", default="rmat", choices=["rmat", "full", "mixed"],
@@ -755,8 +833,19 @@ def main():
 
     # CPU baseline first: the oracle runs on host threads before any CUDA call
     cpu_baseline = None
-    if rank == 0 and world == 1 and not args.no_cpu:
+    if rank == 0 and world == 1 and not args.no_cpu and args.mode != "sharded":
         cpu_baseline = cpu_baseline_for(g, wl, args)
+    if args.mode == "sharded":
+        import torch
+        torch.cuda.set_device(local_rank)
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        os.environ.setdefault("MASTER_PORT", "29511")
+        torch.distributed.init_process_group("nccl", rank=rank, world_size=world)
+        try:
+            run_sharded(args, wl, g, rank, world, local_rank)
+        finally:
+            torch.distributed.destroy_process_group()
+        return
     if world > 1:
         import torch
         torch.cuda.set_device(local_rank)

@@ -349,6 +349,21 @@ kadabra_status kadabra_sample_range(kadabra_query *q, int tag, uint64_t first, i
                                     void *cuda_stream);
 kadabra_status kadabra_absorb(kadabra_query *q, const uint32_t *delta, uint64_t samples, void *cuda_stream);
 
+/* The same exchange with epoch logs instead of counter vectors (an epoch's
+ * logs hold at most E * (VD - 2) vertex ids, against n counters).
+ * kadabra_sample_range_log takes sample indices [first, first + count) of
+ * stream `tag` and appends the interior vertices of each sampled path to
+ * log[log_cap] (device pointer, caller-owned; order unspecified); *log_len
+ * (device word) is set to the number appended -- a value above log_cap means
+ * the log overflowed and the entries beyond it were dropped (async).
+ * kadabra_absorb_log adds 1 to c~[x] for every entry x of log[len] (device
+ * pointer: the concatenated logs of every rank for one epoch, in any order)
+ * and advances tau by `samples` (async). */
+kadabra_status kadabra_sample_range_log(kadabra_query *q, int tag, uint64_t first, int64_t count, uint32_t *log,
+                                        uint32_t log_cap, uint32_t *log_len, void *cuda_stream);
+kadabra_status kadabra_absorb_log(kadabra_query *q, const uint32_t *log, uint64_t len, uint64_t samples,
+                                  void *cuda_stream);
+
 /* The stream-ordered epochs of kadabra_run as a CUDA graph: the first call
  * for a given (epoch_len, epochs_per_graph) captures epochs_per_graph epochs
  * (sampling launch + stop-check launch each) on a private stream and

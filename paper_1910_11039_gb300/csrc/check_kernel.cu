@@ -114,6 +114,23 @@ __global__ void absorb_kernel(long long n, uint32_t *counts, const uint32_t *del
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&job->tau, samples);
 }
 
+// c~[log[i]] += 1 for i < len, tau += samples: the epoch logs of all shards
+// folded into the counters (integer sums, any order)
+__global__ void absorb_log_kernel(const uint32_t *log, unsigned long long len, long long n, uint32_t *counts, Job *job,
+                                  unsigned long long samples)
+{
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += stride) {
+        const unsigned int x = __ldg(log + i);
+        if ((long long)x >= n) {
+            atomicOr(&job->error, kErrSelect);
+            continue;
+        }
+        if (atomicAdd(counts + x, 1u) == 0xffffffffu) atomicOr(&job->error, kErrCounterOverflow);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&job->tau, samples);
+}
+
 __global__ void clock_kernel(unsigned long long *out)
 {
     unsigned long long now;
@@ -165,6 +182,15 @@ cudaError_t launch_absorb(int64_t n, uint32_t *counts, const uint32_t *delta, Jo
                           cudaStream_t st)
 {
     absorb_kernel<<<grid_for(n, 256), 256, 0, st>>>((long long)n, counts, delta, job, (unsigned long long)samples);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_absorb_log(const uint32_t *log, uint64_t len, int64_t n, uint32_t *counts, Job *job, uint64_t samples,
+                              cudaStream_t st)
+{
+    const int grid = len ? grid_for((long long)len, 256) : 1;
+    absorb_log_kernel<<<grid, 256, 0, st>>>(log, (unsigned long long)len, (long long)n, counts, job,
+                                            (unsigned long long)samples);
     return cudaGetLastError();
 }
 

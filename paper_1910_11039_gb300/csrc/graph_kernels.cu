@@ -764,12 +764,18 @@ cudaError_t vd_exact_t(int64_t n, const OffT *off, const uint2 *adj, unsigned in
         lb = ecc_a > lb ? ecc_a : lb;
         lb = ecc_b > lb ? ecc_b : lb;
         lb = ecc_m > lb ? ecc_m : lb;
-        // fringe levels of m, deepest first, until lb > 2 (i - 1)
-        for (unsigned int i = ecc_m; i >= 1 && 2ULL * i > (unsigned long long)lb; --i) {
-            unsigned int cnt = 0;
+        // fringe levels of m, deepest first, until lb > 2 (i - 1); consecutive
+        // levels are gathered into one batch of sources until it holds 64
+        unsigned int i = ecc_m;
+        while (i >= 1 && 2ULL * i > (unsigned long long)lb) {
+            unsigned int lo = i, cnt = 0;
             if ((ee = cudaMemsetAsync(w32 + 1, 0, 4, st)) != cudaSuccess) return ee;
-            fringe_kernel<<<grid, 256, 0, st>>>((long long)n, dm, i, fringe, w32 + 1);
-            if ((ee = read_back(w32 + 1, &cnt, st)) != cudaSuccess) return ee;
+            for (;;) {
+                fringe_kernel<<<grid, 256, 0, st>>>((long long)n, dm, lo, fringe, w32 + 1);
+                if ((ee = read_back(w32 + 1, &cnt, st)) != cudaSuccess) return ee;
+                if (cnt >= 64u || lo == 1 || 2ULL * (lo - 1) < (unsigned long long)lb) break;
+                --lo;
+            }
             if (sweeps + (int)((cnt + 63u) / 64u) > kMaxSweeps) {
                 // levels above i are done: D <= max(lb, 2 i)
                 *diam = 2 * i > lb ? 2 * i : lb;
@@ -800,7 +806,9 @@ cudaError_t vd_exact_t(int64_t n, const OffT *off, const uint2 *adj, unsigned in
                 ++nsearch;
             }
             lb = bi > lb ? bi : lb;
-            if (i == 1 || (unsigned long long)lb > 2ULL * (i - 1)) break;
+            // levels lo..i are done: every pair closer to m than lo is within 2 (lo - 1)
+            if (lo == 1 || (unsigned long long)lb > 2ULL * (lo - 1)) break;
+            i = lo - 1;
         }
         *diam = lb;
         return cudaSuccess;

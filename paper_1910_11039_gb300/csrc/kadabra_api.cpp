@@ -1370,6 +1370,48 @@ extern "C" kadabra_status kadabra_sample_range(kadabra_query *q, int tag, uint64
     return KADABRA_OK;
 }
 
+extern "C" kadabra_status kadabra_sample_range_log(kadabra_query *q, int tag, uint64_t first, int64_t count,
+                                                   uint32_t *log, uint32_t log_cap, uint32_t *log_len,
+                                                   void *cuda_stream)
+{
+    KREADY(q);
+    if (!q || !log || !log_len) return fail(KADABRA_ERR_INVALID_ARG, "query, log or log_len is null");
+    if (tag != 0 && tag != 1) return fail(KADABRA_ERR_INVALID_ARG, "tag must be 0 or 1");
+    if (count < 0 || count >= (int64_t(1) << 32)) return fail(KADABRA_ERR_INVALID_ARG, "count must be in [0, 2^32)");
+    cudaStream_t st = as_stream(cuda_stream);
+    KCUDA(cudaMemsetAsync(log_len, 0, sizeof(uint32_t), st), "clear log length");
+    if (count == 0) return KADABRA_OK;
+    kadabra::SampleLaunch a = base_launch(q);
+    a.counts = nullptr;
+    a.log = log;
+    a.log_len = log_len;
+    a.log_cap = log_cap;
+    a.job = q->d_trace_job;
+    a.tag = (uint32_t)tag;
+    a.use_stop = 0;
+    a.epoch_len = count;
+    a.clip = 0;
+    a.grid = clamp_grid(q, count);
+    const unsigned long long tau0 = first;
+    KCUDA(kadabra::launch_reset_job(q->d_trace_job, st), "reset range state");
+    KCUDA(cudaMemcpyAsync(&q->d_trace_job->tau, &tau0, 8, cudaMemcpyHostToDevice, st), "set range start");
+    KCUDA(kadabra::launch_sample(a, st), "sampling kernel launch");
+    return KADABRA_OK;
+}
+
+extern "C" kadabra_status kadabra_absorb_log(kadabra_query *q, const uint32_t *log, uint64_t len, uint64_t samples,
+                                            void *cuda_stream)
+{
+    {
+        kadabra_status s = need_calibrated(q);
+        if (s != KADABRA_OK) return s;
+    }
+    if (!q || (!log && len > 0)) return fail(KADABRA_ERR_INVALID_ARG, "query or log is null");
+    KCUDA(kadabra::launch_absorb_log(log, len, q->g->n, q->d_counts, q->d_job, samples, as_stream(cuda_stream)),
+          "absorb kernel launch");
+    return KADABRA_OK;
+}
+
 extern "C" kadabra_status kadabra_absorb(kadabra_query *q, const uint32_t *delta, uint64_t samples, void *cuda_stream)
 {
     {

@@ -121,6 +121,9 @@ struct SampleLaunch {
     unsigned long long spin_limit;   // bounded waits (spill slot, claims being published)
     void *help;                // persistent launches: board of layers posted for other CTAs (or null)
     unsigned long long help_edges;   // a layer with at least this frontier degree sum is posted
+    uint32_t *log;             // optional (counts == nullptr): interior vertices appended here
+    unsigned int *log_len;     //   entries appended (may exceed log_cap: then the log overflowed)
+    unsigned int log_cap;
 };
 
 cudaError_t launch_sample(const SampleLaunch &a, cudaStream_t st);
@@ -254,5 +257,7 @@ cudaError_t launch_fill_budgets(int64_t n, const uint32_t *cal, const int *class
                                 uint32_t *cls, double2 *L, cudaStream_t st);
 cudaError_t launch_absorb(int64_t n, uint32_t *counts, const uint32_t *delta, Job *job, uint64_t samples,
                           cudaStream_t st);
+cudaError_t launch_absorb_log(const uint32_t *log, uint64_t len, int64_t n, uint32_t *counts, Job *job, uint64_t samples,
+                              cudaStream_t st);
 
 }  // namespace kadabra

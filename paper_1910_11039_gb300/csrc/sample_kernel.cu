@@ -1609,7 +1609,7 @@ __global__ void __launch_bounds__(NT, (2048 / NT / 2) > 0 ? (2048 / NT / 2) : 1)
         const unsigned long long i = sh.cur;
         if (i >= count) break;
         run_sample_any<NT, OffT>(a, G, slot, a.spill, a.use_bits != 0, sh, base + i, i, ls,
-                                 CountSink{a.counts, nullptr, nullptr, 0u});
+                                 CountSink{a.counts, a.log, a.log_len, a.log_cap});
     }
 
     if (tid == 0) {

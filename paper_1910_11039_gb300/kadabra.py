@@ -113,6 +113,8 @@ SIGNATURES = {
     "kadabra_sample_static": (_ST, [_P, _U64, C.c_int, _U64, _I64, _P, _P]),
     "kadabra_sample_range": (_ST, [_P, C.c_int, _U64, _I64, _P, _P]),
     "kadabra_absorb": (_ST, [_P, _P, _U64, _P]),
+    "kadabra_sample_range_log": (_ST, [_P, C.c_int, _U64, _I64, _P, C.c_uint32, _P, _P]),
+    "kadabra_absorb_log": (_ST, [_P, _P, _U64, _U64, _P]),
     "kadabra_pipeline_begin": (_ST, [_P, _I64, C.c_int, _P]),
     "kadabra_run_graph": (_ST, [_P, _I64, C.c_int, _I64, _P, C.POINTER(C.c_int)]),
     "kadabra_batch_set_policy": (_ST, [_P, C.c_int]),
@@ -341,6 +343,18 @@ class Query:
     def absorb(self, delta_device_ptr, samples, stream=None):
         """c~ += delta, tau += samples (the epoch aggregate of a sharded run)."""
         _check(load().kadabra_absorb(self.handle, C.c_void_p(int(delta_device_ptr)), samples, _stream(stream)))
+
+    def sample_range_log(self, tag, first, count, log_device_ptr, log_cap, len_device_ptr, stream=None):
+        """Append the interior vertices of samples [first, first+count) to a
+        caller-owned device log; the device word at len_device_ptr receives
+        the number appended (above log_cap: the log overflowed)."""
+        _check(load().kadabra_sample_range_log(self.handle, tag, first, count, C.c_void_p(int(log_device_ptr)),
+                                               log_cap, C.c_void_p(int(len_device_ptr)), _stream(stream)))
+
+    def absorb_log(self, log_device_ptr, length, samples, stream=None):
+        """c~[x] += 1 for every entry x of a device log, tau += samples."""
+        _check(load().kadabra_absorb_log(self.handle, C.c_void_p(int(log_device_ptr)), length, samples,
+                                         _stream(stream)))
 
     def run_graph(self, epoch_len, epochs_per_graph=4, max_epochs=1 << 30, stream=None) -> bool:
         """Stream-ordered epochs replayed from a captured CUDA graph."""

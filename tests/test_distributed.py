@@ -47,6 +47,21 @@ class OracleShard:
         self.counts += delta.numpy().astype(np.int64)
         self.tau += samples
 
+    def sample_log(self, first, count, frame):
+        # the interior vertices of each sampled path, concatenated
+        if not hasattr(self, "ws"):
+            self.ws = self.orc.Workspace(self.g)
+        parts = [self.ws.sample(self.seed, 1, i)[0] for i in range(first, first + count)]
+        log = np.concatenate(parts) if parts else np.zeros(0, dtype=np.int32)
+        return self.torch.from_numpy(log.astype(np.int32))
+
+    def local_log(self, handle):
+        return handle
+
+    def absorb_log(self, log, samples):
+        self.counts += np.bincount(log.numpy(), minlength=self.g.n).astype(np.int64)
+        self.tau += samples
+
     def check(self):
         stop, _, _ = self.orc.check_stop(self.counts.astype(np.uint32), self.tau, self.omega, self.eps, self.LL, self.LU)
         return stop
@@ -55,7 +70,7 @@ class OracleShard:
         return self.torch.tensor([1 if value else 0], dtype=self.torch.int32)
 
 
-def _rank_main(rank, world, port, out_dir, E):
+def _rank_main(rank, world, port, out_dir, E, form="reduce"):
     import torch.distributed as dist
     import oracle
     from paper_1910_11039_gb300 import inputs as I
@@ -67,7 +82,7 @@ def _rank_main(rank, world, port, out_dir, E):
         g = I.config_graph("er2000")
         shard = OracleShard(g, 0.05, 0.1, 1, 1000)
         run = ShardedRun(shard, shard, int(np.ceil(shard.omega)), dist)
-        stopped, tau, epochs = run.run(E)
+        stopped, tau, epochs = run.run(E) if form == "reduce" else run.run_logs(E)
         np.savez(os.path.join(out_dir, f"rank{rank}.npz"), counts=shard.counts, tau=tau, epochs=epochs,
                  stopped=int(stopped))
     finally:
@@ -80,12 +95,16 @@ def _free_port():
         return s.getsockname()[1]
 
 
+@pytest.mark.parametrize("form", ["reduce", "logs"])
 @pytest.mark.parametrize("world,E", [(2, 100), (3, 77)])
-def test_sharded_run_equals_single_process(orc, world, E):
+def test_sharded_run_equals_single_process(orc, world, E, form):
+    # reduce: counter deltas summed, rank 0 checks and broadcasts;
+    # logs: epoch logs all-gathered, every rank folds them and checks, with the
+    # next epoch sampled before the current one is exchanged (two frames)
     import torch.multiprocessing as mp
     from paper_1910_11039_gb300 import inputs as I
     with tempfile.TemporaryDirectory() as d:
-        mp.spawn(_rank_main, args=(world, _free_port(), d, E), nprocs=world, join=True)
+        mp.spawn(_rank_main, args=(world, _free_port(), d, E, form), nprocs=world, join=True)
         res = [np.load(os.path.join(d, f"rank{r}.npz")) for r in range(world)]
     g = I.config_graph("er2000")
     counts, cal, LL, LU, R = orc.kadabra(g, 0.05, 0.1, seed=1, epoch_len=E, n_calib=1000)

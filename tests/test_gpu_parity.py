@@ -266,6 +266,64 @@ def test_sharded_run_driver_single_rank(K, orc):
         dist.destroy_process_group()
 
 
+@pytest.mark.parametrize("name,eps,E", [("rmat14", 0.03, 500), ("grid64", 0.05, 250)])
+def test_sharded_log_epochs_on_one_gpu(K, orc, name, eps, E):
+    """Three ranks' shares of every epoch sampled into separate epoch logs,
+    concatenated and absorbed (the log exchange), equal a single run."""
+    import torch
+    from paper_1910_11039_gb300.distributed import epoch_share
+    g = GRAPHS[name]()
+    G = K.Graph.from_inputs(g)
+    q = K.Query(G, eps=eps, delta=0.1, seed=1)
+    info = q.info()
+    cap = E * max(1, info.vertex_diameter)
+    logs = [torch.empty(cap, dtype=torch.int32, device="cuda") for _ in range(3)]
+    lens = torch.zeros(3, dtype=torch.int32, device="cuda")
+    tau, epochs = 0, 0
+    while True:
+        m = min(E, info.omega_ceil - tau)
+        for r in range(3):
+            first, count = epoch_share(tau, m, 3, r)
+            q.sample_range_log(1, first, count, logs[r].data_ptr(), cap, lens.data_ptr() + 4 * r)
+        ln = lens.tolist()
+        assert max(ln) <= cap
+        allv = torch.cat([logs[r][:ln[r]] for r in range(3)])
+        q.absorb_log(allv.data_ptr(), allv.numel(), m)
+        tau += m
+        epochs += 1
+        stopped, mf, mg = q.check_stop()
+        if stopped:
+            break
+    counts, cal, LL, LU, R = orc.kadabra(g, eps, 0.1, seed=1, epoch_len=E)
+    res = q.result()
+    assert res["tau"] == R.tau == tau and res["stop_epoch"] == R.stop_epoch == epochs - 1
+    assert np.array_equal(res["counts"], counts)
+
+
+def test_sharded_log_driver_single_rank(K, orc):
+    # the overlapped driver (epoch e + 1 sampled on a side stream while epoch
+    # e's logs are exchanged over NCCL, folded and checked) on a one-rank group
+    import torch.distributed as dist
+    from paper_1910_11039_gb300.distributed import LibraryShard, ShardedRun
+    import socket
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    os.environ["MASTER_ADDR"], os.environ["MASTER_PORT"] = "127.0.0.1", str(port)
+    dist.init_process_group("nccl", rank=0, world_size=1)
+    try:
+        g = GRAPHS["rmat14"]()
+        G = K.Graph.from_inputs(g)
+        q = K.Query(G, eps=0.03, delta=0.1, seed=1)
+        shard = LibraryShard(q, log_cap=256 * max(1, q.info().vertex_diameter))
+        stopped, tau, epochs = ShardedRun(shard, shard, q.info().omega_ceil, dist).run_logs(256)
+        counts, cal, LL, LU, R = orc.kadabra(g, 0.03, 0.1, seed=1, epoch_len=256)
+        assert stopped and tau == R.tau and epochs == R.stop_epoch + 1
+        assert np.array_equal(q.result()["counts"], counts)
+    finally:
+        dist.destroy_process_group()
+
+
 @pytest.mark.parametrize("name,eps,E,k", [("er2000", 0.05, 100, 4), ("rmat14", 0.03, 500, 1), ("grid64", 0.05, 250, 7)])
 def test_graph_epochs_match_oracle(K, orc, name, eps, E, k):
     g = GRAPHS[name]()
