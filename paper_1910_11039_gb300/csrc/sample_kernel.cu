@@ -119,7 +119,6 @@ struct Smem {
     int meets;                       // a target of this layer is on the other side: it is the last
     unsigned long long lmax;         // largest path count of the new layer
     unsigned long long ldeg;         // degree sum of the new frontier
-    int shv;                         // shift that scales the new layer (> 0: scale)
     unsigned long long e_scan;       // this sample
     unsigned long long expanded;
     // selection and walk
@@ -246,6 +245,31 @@ __device__ __forceinline__ unsigned long long block_excl_scan(unsigned long long
         tot += sh.tmp[i];
     }
     __syncthreads();
+    *total = tot;
+    return before + incl - v;
+}
+
+// The same scan with one barrier: sh.tmp must not be written again before
+// the caller's next block barrier (the caller's next barrier protects it).
+template <int NT>
+__device__ __forceinline__ unsigned long long block_excl_scan_open(unsigned long long v, unsigned long long *total,
+                                                                   Smem<NT> &sh)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned long long incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) sh.tmp[wid] = incl;
+    __syncthreads();
+    unsigned long long before = 0, tot = 0;
+#pragma unroll
+    for (int i = 0; i < NT / 32; ++i) {
+        if (i < wid) before += sh.tmp[i];
+        tot += sh.tmp[i];
+    }
     *total = tot;
     return before + incl - v;
 }
@@ -593,7 +617,8 @@ __device__ __forceinline__ unsigned long long expand_chunk(const unsigned long l
             sg = ldcg(S.qs + ph);
         }
         unsigned long long total;
-        const unsigned long long excl = block_excl_scan<NT>(d, &total, sh);
+        // one barrier: sh.tmp is next written after this chunk's closing barrier
+        const unsigned long long excl = block_excl_scan_open<NT>(d, &total, sh);
         sh.u.ex.cbeg[tid] = b;
         sh.u.ex.cpos[tid] = excl;
         sh.u.ex.csig[tid] = sg;
@@ -850,7 +875,6 @@ __device__ bool run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, const
         sh.meets = 0;
         sh.lmax = 0;
         sh.ldeg = 0;
-        sh.shv = 0;
         sh.chosen = -1;
         sh.X = (sh.fdeg[0] <= sh.fdeg[1]) ? 0 : 1;
         if (sh.fdeg[sh.X] == 0) {
@@ -869,9 +893,18 @@ __device__ bool run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, const
     __syncthreads();
 
     // A2: balanced bidirectional BFS, one whole layer per step.  The side of
-    // the next layer is chosen, and the layer accumulators cleared, by thread
-    // 0 at the end of the previous layer, inside that layer's last barrier.
+    // the next layer is chosen by thread 0 at the end of the previous layer;
+    // the layer accumulators are cleared by thread 0 here, before the first
+    // barrier of the layer (every thread read the previous layer's values
+    // before that layer's closing barrier).
     while (sh.status == 0) {
+        if (tid == 0) {
+            sh.new_count = 0;
+            sh.meet_count = 0;
+            sh.meets = 0;
+            sh.lmax = 0;
+            sh.ldeg = 0;
+        }
         const int X = sh.X, Y = 1 - X;
         const unsigned int nl = sh.layer[X] + 1;     // level of the new layer
         const unsigned int fb = sh.fbeg[X], fe = sh.fend[X];
@@ -965,6 +998,24 @@ __device__ bool run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, const
                 atomicExch(&R->state, 0);
             }
         }
+        // The layer's outcome (final after the last chunk's barrier), read
+        // alike by every thread: if the search goes on, every thread scales
+        // its share of the new layer's counts now (keeping them <= 2^K,
+        // rounding up so that they stay >= 1) while thread 0 books the layer,
+        // and one barrier closes both.
+        {
+            const unsigned int ncount = *reinterpret_cast<volatile unsigned int *>(&sh.new_count);
+            const unsigned int mcl = *reinterpret_cast<volatile unsigned int *>(&sh.meet_count);
+            const unsigned long long lmaxl = *reinterpret_cast<volatile unsigned long long *>(&sh.lmax);
+            const int ovfl = *reinterpret_cast<volatile int *>(&sh.ovf);
+            const int shv = bitlen64(lmaxl) - a.K;
+            if (!ovfl && ncount <= room - qbase && mcl == 0 && ncount > 0 && shv > 0 && !a.strict) {
+                for (unsigned int i = qbase + tid; i < qbase + ncount; i += NT) {
+                    unsigned long long *q = S.qs + S.at(X, i);
+                    __stcg(q, ((ldcg(q) - 1ULL) >> shv) + 1ULL);
+                }
+            }
+        }
         if (tid == 0) {
             sh.e_scan += my_scan;
             sh.expanded += fe - fb;
@@ -991,35 +1042,16 @@ __device__ bool run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, const
                 sh.fbeg[X] = qbase;
                 sh.fend[X] = qbase + nc;
                 sh.fdeg[X] = sh.ldeg;
-                // keep the new layer's counts <= 2^K, rounding up so that they stay >= 1
                 const int shv = bitlen64(sh.lmax) - a.K;
-                sh.shv = shv > 0 ? shv : 0;
                 if (shv > 0) {
                     sh.scaled = 1;
                     if (a.strict) sh.status = 3;
                 }
                 // the next layer: side with the smaller frontier degree sum (ties: s)
-                const int Xn = (sh.fdeg[0] <= sh.fdeg[1]) ? 0 : 1;
-                if (sh.status == 0) {
-                    sh.X = Xn;
-                    sh.new_count = 0;
-                    sh.meet_count = 0;
-                    sh.meets = 0;
-                    sh.lmax = 0;
-                    sh.ldeg = 0;
-                }
+                if (sh.status == 0) sh.X = (sh.fdeg[0] <= sh.fdeg[1]) ? 0 : 1;
             }
         }
         __syncthreads();
-        if (sh.status != 0) break;
-        if (sh.shv > 0) {
-            const int shv = sh.shv;
-            for (unsigned int i = sh.fbeg[X] + tid; i < sh.fend[X]; i += NT) {
-                unsigned long long *q = S.qs + S.at(X, i);
-                __stcg(q, ((ldcg(q) - 1ULL) >> shv) + 1ULL);
-            }
-            __syncthreads();
-        }
     }
 
     // A3 + A4: choose the meeting vertex, walk back, count interior vertices
