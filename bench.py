@@ -405,18 +405,24 @@ def run_gpu(args, wl, g, rank, world, local_rank, cpu_baseline):
         c_h = torch.empty(g.n, dtype=torch.int32).pin_memory()
         del q, G
         torch.cuda.synchronize()
-        e_times, e_taus = [], []
+        e_times, e_taus, e_phases = [], [], []
         for k in range(args.e2e_steps + 1):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             G2 = K.Graph(g.n, off_h.numpy(), col_h.numpy(), offsets_64=off64, skip_validate=True, stream=stream)
+            stream.synchronize()
+            ta = time.perf_counter()
             q2 = K.Query(G2, eps=eps, delta=delta, seed=seed, stream=stream, slots=args.slots, threads=args.threads)
+            stream.synchronize()
+            tb = time.perf_counter()
             if args.mode == "pipelined":
                 q2.run_pipelined(E, frames=args.frames)
             else:
                 for _ in range(math.ceil(q2.info().omega_ceil / E) + 1):
                     q2.sample_epoch(E)
                     q2.check_stop_async()
+            stream.synchronize()
+            tc = time.perf_counter()
             tau, se = q2.result_into(b_h.data_ptr(), c_h.data_ptr())
             t1 = time.perf_counter()
             q2.free()
@@ -424,13 +430,16 @@ def run_gpu(args, wl, g, rank, world, local_rank, cpu_baseline):
             if k > 0:      # the first query warms allocator and caches
                 e_times.append(t1 - t0)
                 e_taus.append(tau)
+                e_phases.append((ta - t0, tb - ta, tc - tb, t1 - tc))
         n = g.n
         h2d = off_np.nbytes + g.cols.nbytes + 16 * n
         d2h = 4 * n + 8 * n + 4 * n
         e2e = {"value": sum(e_taus) / sum(e_times), "unit": "samples/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "steps": len(e_times),
                "time_to_stop_ms": 1e3 * statistics.mean(e_times),
-               "step": "graph upload + diameter bound + calibration + adaptive phase + result download"}
+               "step": "graph upload + diameter bound + calibration + adaptive phase + result download",
+               "phases_ms": {name: 1e3 * statistics.mean(p[i] for p in e_phases) for i, name in
+                             enumerate(("graph_load", "query_create_calibrate", "adaptive", "result_download"))}}
 
     if rank != 0:
         return

@@ -92,6 +92,12 @@ typedef struct kadabra_params {
                                  is at least this is split into chunks that idle CTAs
                                  expand together with the sample's own CTA; 0 = 32768,
                                  < 0 = never.  Results never depend on it               */
+    int64_t probe_edges;      /* queries whose vertex-diameter bound is at most 64: a BFS
+                                 layer whose frontier degree sum is at least this first
+                                 tests its targets against a shared-memory bitmap of the
+                                 other side's frontier and, if it meets that frontier,
+                                 ends the search without claiming anything; 0 = the
+                                 default (256), < 0 = never.  Results never depend on it   */
 } kadabra_params;
 
 /* Snapshot of a query (kadabra_query_get_info). */

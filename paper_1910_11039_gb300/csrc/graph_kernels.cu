@@ -175,8 +175,8 @@ __global__ void roots_kernel(long long n, const OffT *off, unsigned int *parent,
         unsigned long long d = 0;
         if (v < n && find_root(parent, (unsigned int)v) == (unsigned int)v) {
             dist[v] = 0;
-            take = true;
             d = (unsigned long long)((long long)off[v + 1] - (long long)off[v]);
+            take = d > 0;     // an isolated vertex is its own whole search (eccentricity 0)
         }
         warp_append(take, (unsigned int)v, d, queue, qlen, fdeg);
     }
@@ -224,8 +224,8 @@ __device__ bool grid_barrier(BfsState *s)
 }
 
 // Multi-source breadth-first search, direction-optimising (Beamer, Asanovic
-// and Patterson, SC 2012): a level expands its frontier top-down (one warp per
-// frontier vertex) while the frontier's edges are few against the edges not
+// and Patterson, SC 2012): a level expands its frontier top-down (32 frontier
+// vertices per warp) while the frontier's edges are few against the edges not
 // yet explored, and bottom-up (every unreached vertex looks for a neighbour in
 // the frontier) while the frontier is large.  Both give every vertex its exact
 // distance from its component's root.
@@ -253,17 +253,45 @@ __global__ void msbfs_kernel(long long n, const OffT *off, const uint2 *adj, uns
         unsigned int *nlen = &s->len[cur ^ 1];
         unsigned long long *nfdeg = &s->fdeg[cur ^ 1];
         if (!bottom_up) {
-            // one warp per frontier vertex: lanes stride its adjacency
-            for (long long i = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < len; i += warps) {
-                const unsigned int u = __ldcg(q[cur] + i);
-                const long long b = (long long)__ldg(off + u), e = (long long)__ldg(off + u + 1);
-                for (long long k0 = b; k0 < e; k0 += 32) {
-                    const long long k = k0 + lane;
+            // 32 frontier vertices per warp: their adjacency lists form one
+            // range (a warp-wide prefix sum of the degrees) that the lanes
+            // stride, so no lane idles on a low-degree vertex
+            const long long groups = ((long long)len + 31) / 32;
+            for (long long gi = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); gi < groups;
+                 gi += warps) {
+                const long long i = gi * 32 + lane;
+                long long b = 0;
+                unsigned long long d = 0;
+                if (i < (long long)len) {
+                    const unsigned int u = __ldcg(q[cur] + i);
+                    b = (long long)__ldg(off + u);
+                    d = (unsigned long long)((long long)__ldg(off + u + 1) - b);
+                }
+                unsigned long long incl = d;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const unsigned long long t = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += t;
+                }
+                const unsigned long long excl = incl - d;
+                const unsigned long long total = __shfl_sync(0xffffffffu, incl, 31);
+                for (unsigned long long k0 = 0; k0 < total; k0 += 32) {
+                    const unsigned long long k = k0 + lane;
+                    // owner of entry k: the last lane whose exclusive prefix is <= k
+                    int lo = 0;
+#pragma unroll
+                    for (int step = 16; step > 0; step >>= 1) {
+                        const int cand = lo + step;
+                        const unsigned long long ex = __shfl_sync(0xffffffffu, excl, cand < 32 ? cand : 31);
+                        if (cand < 32 && ex <= k) lo = cand;
+                    }
+                    const long long ob = __shfl_sync(0xffffffffu, b, lo);
+                    const unsigned long long oe = __shfl_sync(0xffffffffu, excl, lo);
                     bool take = false;
                     unsigned int w = 0;
                     unsigned long long dw = 0;
-                    if (k < e) {
-                        const uint2 c = __ldg(&adj[k]);
+                    if (k < total) {
+                        const uint2 c = __ldg(&adj[ob + (long long)(k - oe)]);
                         w = c.x;
                         dw = c.y;
                         take = __ldcg(dist + w) == kUnvisited && atomicCAS(dist + w, kUnvisited, level + 1) == kUnvisited;

@@ -71,6 +71,7 @@ struct kadabra_graph {
     int ws_threads = 0;
     int ws_req = 0;               // slots requested when the scratch was sized
     int64_t ws_cap_req = 0;       // queue capacity requested when the scratch was sized
+    int probe_log2 = 0;           // probe bitmap of launches with ws_threads threads (0: none)
     void *d_help = nullptr;       // help board of the graph's pipelined launches
 };
 
@@ -130,6 +131,7 @@ struct kadabra_batch {
     int slots = 0, threads = 0, off64 = 0;
     kadabra::SlotSet ws;
     kadabra::SlotSet spill;
+    int probe_log2 = 0;           // probe bitmap of the batch's launches (0: none)
     void *d_help = nullptr;       // help board of the batch's launches
     kadabra::QueryDesc *d_descs = nullptr;
     int64_t descs_cap = 0;
@@ -487,37 +489,43 @@ extern "C" kadabra_status kadabra_graph_load(int64_t n, int64_t nnz, const void 
             return s;
         }
     }
-    if (!dev) {
-        int64_t md = 0;
-        for (int64_t v = 0; v < n; ++v) {
-            const int64_t d = offsets_is_64 ? static_cast<const int64_t *>(offsets)[v + 1] - static_cast<const int64_t *>(offsets)[v]
-                                            : (int64_t)static_cast<const int32_t *>(offsets)[v + 1] -
-                                                  (int64_t)static_cast<const int32_t *>(offsets)[v];
-            md = d > md ? d : md;
-        }
-        g->max_degree = md;
-    }
-
     // device copy: offsets, and the adjacency as (neighbour, neighbour degree)
-    // pairs built on the device from a temporary copy of the columns
+    // pairs built on the device from the columns; host columns in page-locked
+    // memory are read in place by that kernel (one pass over the host link),
+    // other host columns go through a temporary device copy.  The maximum
+    // degree is reduced on the device from the copied offsets.
+    const int32_t *cols_in = dev ? cols : nullptr;
+    if (!dev && cb) {
+        cudaPointerAttributes pa{};
+        if (cudaPointerGetAttributes(&pa, cols) == cudaSuccess && pa.type == cudaMemoryTypeHost && pa.devicePointer)
+            cols_in = static_cast<const int32_t *>(pa.devicePointer);
+        else
+            cudaGetLastError();     // pageable memory: clear the query's error, if any
+    }
     int32_t *d_cols_tmp = nullptr;
+    uint32_t *d_deg = nullptr;
     cudaError_t e = cudaMalloc(&g->d_off, ob);
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&g->d_adj), (size_t)(nnz > 0 ? nnz : 1) * sizeof(uint2));
-    if (e == cudaSuccess && !dev && cb) e = cudaMalloc(reinterpret_cast<void **>(&d_cols_tmp), cb);
+    if (e == cudaSuccess && cb) e = cudaMalloc(reinterpret_cast<void **>(&d_deg), (size_t)n * sizeof(uint32_t));
+    if (e == cudaSuccess && !cols_in && cb) e = cudaMalloc(reinterpret_cast<void **>(&d_cols_tmp), cb);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(g->d_off, offsets, ob, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess && !dev && cb) e = cudaMemcpyAsync(d_cols_tmp, cols, cb, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && d_cols_tmp) {
+        e = cudaMemcpyAsync(d_cols_tmp, cols, cb, cudaMemcpyHostToDevice, st);
+        cols_in = d_cols_tmp;
+    }
     if (e == cudaSuccess)
-        e = kadabra::launch_build_adj(nnz, g->d_off, g->off64, dev ? cols : d_cols_tmp, g->d_adj, st);
+        e = kadabra::launch_build_adj(n, nnz, g->d_off, g->off64, cols_in, g->d_adj, d_deg, st);
     unsigned long long *d_md = nullptr;
     unsigned long long md = 0;
-    if (e == cudaSuccess && dev) e = cudaMalloc(reinterpret_cast<void **>(&d_md), sizeof(unsigned long long));
-    if (e == cudaSuccess && dev) e = kadabra::launch_max_degree(n, g->d_off, g->off64, d_md, st);
-    if (e == cudaSuccess && dev) e = cudaMemcpyAsync(&md, d_md, sizeof(md), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&d_md), sizeof(unsigned long long));
+    if (e == cudaSuccess) e = kadabra::launch_max_degree(n, g->d_off, g->off64, d_md, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&md, d_md, sizeof(md), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (dev) g->max_degree = (int64_t)md;
+    g->max_degree = (int64_t)md;
     cudaFree(d_md);
     cudaFree(d_cols_tmp);
+    cudaFree(d_deg);
     // reserve kadabra_sample_static's array on this device now, so that
     // sampling from this graph there later loads and reserves nothing
     if (e == cudaSuccess) e = kadabra::static_scratch_reserve();
@@ -584,6 +592,7 @@ static kadabra_status ensure_workspace(kadabra_graph *g, int want_slots, int thr
     g->ws_threads = threads;
     g->ws_req = requested;
     g->ws_cap_req = cap_req;
+    KCUDA(kadabra::probe_prepare(threads, g->off64, per_sm, &g->probe_log2), "probe bitmap set-up");
     return KADABRA_OK;
 }
 
@@ -632,6 +641,19 @@ static kadabra_status device_error_status(const Job &j)
     return KADABRA_OK;
 }
 
+// frontier degree sum from which a small-diameter sample probes a layer
+static unsigned long long probe_edges_of(const kadabra_params &p)
+{
+    return p.probe_edges > 0 ? (unsigned long long)p.probe_edges : 256ULL;
+}
+
+// probe bitmap of a launch of this query (sized for the threads the graph's
+// scratch was planned with; none if the query asks for no probing)
+static int probe_log2_of(const kadabra_query *q)
+{
+    return (q->p.probe_edges >= 0 && q->threads == q->g->ws_threads) ? q->g->probe_log2 : 0;
+}
+
 static kadabra::SampleLaunch base_launch(const kadabra_query *q)
 {
     kadabra::SampleLaunch a{};
@@ -642,6 +664,8 @@ static kadabra::SampleLaunch base_launch(const kadabra_query *q)
     a.slots = q->g->ws;
     a.spill = q->g->spill;
     a.use_bits = q->vd <= kadabra::kBitsMaxVD ? 1 : 0;
+    a.probe_log2 = a.use_bits ? probe_log2_of(q) : 0;
+    a.probe_edges = probe_edges_of(q->p);
     a.spin_limit = 1ULL << 24;
     a.seed = q->p.seed;
     a.K = q->K;
@@ -1097,6 +1121,8 @@ extern "C" kadabra_status kadabra_run_pipelined(kadabra_query *q, int64_t epoch_
     B.grid = clamp_grid(q, int64_t(1) << 40);
     B.threads = q->threads;
     B.off64 = q->g->off64;
+    B.probe_log2 = probe_log2_of(q);
+    B.probe_edges = probe_edges_of(q->p);
     {
         kadabra_status se = slot_events(q, slot);
         if (se != KADABRA_OK) return se;
@@ -1149,6 +1175,7 @@ extern "C" kadabra_status kadabra_batch_create(int64_t max_n, int32_t slots, int
     if (e == cudaSuccess) e = cudaMemset(b->d_help, 0, kadabra::help_board_bytes());
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev1);
+    if (e == cudaSuccess) e = kadabra::probe_prepare(threads, b->off64, per_sm, &b->probe_log2);
     if (e != cudaSuccess) {
         kadabra::free_slot_set(&b->ws);
         kadabra::free_slot_set(&b->spill);
@@ -1224,6 +1251,8 @@ extern "C" kadabra_status kadabra_batch_step(kadabra_batch *b, kadabra_query *co
     B.threads = b->threads;
     B.off64 = b->off64;
     B.policy = b->policy;
+    B.probe_log2 = b->probe_log2;
+    B.probe_edges = 256ULL;
     KCUDA(cudaEventRecord(b->ev0, st), "event");
     KCUDA(kadabra::launch_batch(B, st), "batch kernel launch");
     KCUDA(cudaEventRecord(b->ev1, st), "event");

@@ -124,6 +124,10 @@ struct SampleLaunch {
     uint32_t *log;             // optional (counts == nullptr): interior vertices appended here
     unsigned int *log_len;     //   entries appended (may exceed log_cap: then the log overflowed)
     unsigned int log_cap;
+    int probe_log2;            // log2 of the bits of the shared-memory frontier bitmap (dynamic
+                               //   shared memory of the launch); 0: no bitmap, no probe pass
+    unsigned long long probe_edges;  // samples with reached-bit maps probe a layer first when its
+                                     //   frontier degree sum is at least this
 };
 
 cudaError_t launch_sample(const SampleLaunch &a, cudaStream_t st);
@@ -131,8 +135,10 @@ cudaError_t launch_sample(const SampleLaunch &a, cudaStream_t st);
 size_t slot_set_bytes(int count, long long stride, long long cap, bool bits, bool lock);
 cudaError_t alloc_slot_set(SlotSet *S, int count, long long stride, long long cap, bool bits, bool lock);
 void free_slot_set(SlotSet *S);
-cudaError_t launch_build_adj(int64_t nnz, const void *off, int off64, const int32_t *col, uint2 *adj,
-                             cudaStream_t st);
+// adj[e] = (col[e], degree of col[e]); off in device memory, col in device
+// memory or device-accessible page-locked host memory; deg_tmp: n words.
+cudaError_t launch_build_adj(int64_t n, int64_t nnz, const void *off, int off64, const int32_t *col, uint2 *adj,
+                             uint32_t *deg_tmp, cudaStream_t st);
 // diameter phase (graph_kernels.cu)
 size_t vd_bound_scratch_bytes(int64_t n);
 cudaError_t launch_vd_bound(int64_t n, const void *off, int off64, const uint2 *adj, void *scratch, cudaStream_t st,
@@ -143,6 +149,11 @@ size_t vd_exact_scratch_bytes(int64_t n);
 cudaError_t launch_vd_exact(int64_t n, const void *off, int off64, const uint2 *adj, void *scratch, cudaStream_t st,
                             int64_t *vd, int *exact, int64_t *searches);
 cudaError_t sample_occupancy(int threads, int off64, int *ctas_per_sm);
+// Size of the probe bitmap that leaves `ctas_per_sm` sampling CTAs of
+// `threads` threads resident on an SM (log2 of its bits; 0 if below 2^15
+// bits), with both sampling kernels allowed that much dynamic shared memory.
+// Host-side set-up: call outside stream capture.
+cudaError_t probe_prepare(int threads, int off64, int ctas_per_sm, int *log2_bits);
 
 // Pipelined adaptive phase: epochs rotate through F epoch logs; one persistent
 // launch serves one or many queries (see batch_kernel in sample_kernel.cu).
@@ -209,6 +220,8 @@ struct BatchLaunch {
     unsigned long long spin_limit;
     int grid, threads, off64;
     int policy;                // 0: round robin over the queries; 1: first in array order
+    int probe_log2;            // as in SampleLaunch (queries with use_bits only)
+    unsigned long long probe_edges;
 };
 
 cudaError_t launch_batch(const BatchLaunch &a, cudaStream_t st);

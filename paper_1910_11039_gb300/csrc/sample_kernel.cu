@@ -73,8 +73,24 @@ constexpr int kPathCap = 1024;     // path vertices buffered in shared memory be
 #endif
 constexpr int kUnroll = KADABRA_UNROLL;   // adjacency entries in flight per thread
 constexpr unsigned int kNone = 0xffffffffu;
+constexpr int kProbeMinLog2 = 15;  // smallest probe bitmap worth a pass (4 KB)
+constexpr int kProbeMaxLog2 = 20;  // largest probe bitmap (128 KB)
 
 __device__ __forceinline__ unsigned long long ldcg(const unsigned long long *p) { return __ldcg(p); }
+
+// The launch's dynamic shared memory: the probe bitmap (2^probe_log2 bits)
+// of the other side's frontier, present when the launch sets probe_log2.
+__device__ __forceinline__ uint32_t *probe_map()
+{
+    extern __shared__ __align__(16) uint32_t kadabra_dyn_smem[];
+    return kadabra_dyn_smem;
+}
+// bit of vertex w in a bitmap of 2^log2b bits (Fibonacci hashing: ids of a
+// structured layer, e.g. a grid diagonal, spread over the whole map)
+__device__ __forceinline__ unsigned int probe_hash(unsigned int w, int log2b)
+{
+    return (w * 0x9E3779B1u) >> (32 - log2b);
+}
 
 __device__ __forceinline__ int bitlen64(unsigned long long x) { return 64 - __clzll(x); }
 
@@ -142,6 +158,10 @@ struct Smem {
     } hl;                            // the helped layer, copied from its request
     long long next_v;
     int found;
+    // the probe bitmap holds side pf_Y's queue positions [pf_yb, pf_ye) of
+    // this sample (pf_ok = 0: nothing valid)
+    int pf_ok, pf_Y;
+    unsigned int pf_yb, pf_ye;
     unsigned long long cur;          // work item taken by this CTA
     // back-walk: vertices found so far (flushed to the sink by warp 0) and
     // the state handed between warp 0's steps and the whole CTA's steps
@@ -823,6 +843,148 @@ __device__ __forceinline__ unsigned long long expand_chunk(const unsigned long l
     return my_scan;
 }
 
+// ---- probe pass --------------------------------------------------------
+// On graphs of small diameter a layer is often the last one: some of its
+// targets are in the other side's frontier.  The probe pass scans the layer's
+// adjacency once, tests every target against a shared-memory bitmap of that
+// frontier, and reads the code word only of targets whose bit is set, so the
+// scan costs the adjacency reads alone.  If it finds meeting vertices their
+// meeting counts are complete (every adjacency entry was scanned) and the
+// layer ends without claiming anything: the next layer is never expanded.  If
+// it finds none, no target is on the other side (the bitmap has no false
+// negatives) and the layer is expanded as usual.
+
+// Fills the bitmap with side Y's queue positions [yb, ye) (CTA-wide; the
+// caller has ensured ye - yb fits the map's load limit).
+template <int NT>
+__device__ __forceinline__ void probe_build(const int log2b, const Slot &S, const int Y, const unsigned int yb,
+                                            const unsigned int ye)
+{
+    uint4 *m4 = reinterpret_cast<uint4 *>(probe_map());
+    const int n4 = 1 << (log2b - 7);
+    for (int i = threadIdx.x; i < n4; i += NT) m4[i] = make_uint4(0u, 0u, 0u, 0u);
+    __syncthreads();
+    uint32_t *m = probe_map();
+    for (unsigned int p = yb + threadIdx.x; p < ye; p += NT) {
+        const unsigned int h = probe_hash(__ldcg(S.qv + S.at(Y, p)), log2b);
+        atomicOr(&m[h >> 5], 1u << (h & 31));
+    }
+    __syncthreads();
+}
+
+// Probes the frontier vertices [cb, min(cb + NT, fe)) of side X's current
+// layer (CTA-wide): a target in side Y's frontier (queue positions [yb, ye))
+// gets the source's path count added to its meeting count and joins the
+// meeting set, exactly as in expand_chunk; nothing else is written.  Returns
+// the chunk's adjacency-entry count in thread 0 (0 elsewhere).
+template <int NT, typename OffT>
+__device__ __forceinline__ unsigned long long probe_chunk(const GraphRef<OffT> &G, const Slot &S, Smem<NT> &sh,
+                                                          const int log2b, const int X, const unsigned int cb,
+                                                          const unsigned int fe, const unsigned int yb,
+                                                          const unsigned int ye)
+{
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int Y = 1 - X;
+    const uint32_t *m = probe_map();
+    const unsigned int i = cb + tid;
+    long long b = 0;
+    unsigned long long d = 0, sg = 0;
+    if (i < fe) {
+        const unsigned int ph = S.at(X, i);
+        const unsigned int u = __ldcg(S.qv + ph);
+        b = G.begin(u);
+        d = (unsigned long long)(G.end(u) - b);
+        sg = ldcg(S.qs + ph);
+    }
+    unsigned long long total;
+    const unsigned long long excl = block_excl_scan_open<NT>(d, &total, sh);
+    sh.u.ex.cbeg[tid] = b;
+    sh.u.ex.cpos[tid] = excl;
+    sh.u.ex.csig[tid] = sg;
+    const int cnt = (int)min((unsigned int)NT, fe - cb);
+    __syncthreads();
+    const unsigned long long wbase = (unsigned long long)(tid & ~31);
+    for (unsigned long long e0 = wbase; e0 < total; e0 += (unsigned long long)NT * kUnroll) {
+        unsigned int w[kUnroll];
+        int own[kUnroll];
+#pragma unroll
+        for (int j = 0; j < kUnroll; ++j) {
+            const unsigned long long e = e0 + (unsigned long long)lane + (unsigned long long)j * NT;
+            w[j] = kNone;
+            own[j] = 0;
+            if (e < total) {
+                int lo = j > 0 ? own[j - 1] : 0, hi = cnt - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (sh.u.ex.cpos[mid] <= e) lo = mid;
+                    else hi = mid - 1;
+                }
+                own[j] = lo;
+                w[j] = __ldg(&G.adj[sh.u.ex.cbeg[lo] + (long long)(e - sh.u.ex.cpos[lo])].x);
+            }
+        }
+        unsigned int cd[kUnroll];
+#pragma unroll
+        for (int j = 0; j < kUnroll; ++j) {
+            cd[j] = 0u;
+            if (w[j] != kNone) {
+                const unsigned int h = probe_hash(w[j], log2b);
+                if ((m[h >> 5] >> (h & 31)) & 1u) cd[j] = __ldcg(S.code + w[j]);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kUnroll; ++j) {
+            const unsigned int c = cd[j];
+            if (c == 0u || side_of(c) != Y) continue;     // unseen, or on this side
+            const unsigned int p = pos_of(c);
+            if (is_pending(c) || p < yb || p >= ye) {
+                atomicOr(&sh.err, kErrSelect);             // broken invariant: never expected
+                continue;
+            }
+            const unsigned long long su = sh.u.ex.csig[own[j]];
+            const unsigned long long old = atomicAdd(S.qm + S.at(Y, p), su);
+            if (old + su < su) atomicOr(&sh.err, kErrAddOverflow);
+            sh.meets = 1;
+            if (old == 0ULL) {
+                const unsigned int q = atomicAdd(&sh.meet_count, 1u);
+                if (q < kMeetCap) {
+                    sh.cand[q] = w[j];
+                    sh.cpos[q] = p;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    return tid == 0 ? total : 0ULL;
+}
+
+// The probe pass over side X's whole current layer [fb, fe) (CTA-wide;
+// builds the bitmap unless it already holds side Y's frontier [yb, ye)).
+// Returns the layer's adjacency-entry count in thread 0 (0 elsewhere); after
+// it, sh.meets says whether the layer met side Y.
+template <int NT, typename OffT>
+__device__ __noinline__ unsigned long long probe_layer(const GraphRef<OffT> &G, const Slot &S, Smem<NT> &sh,
+                                                       const int log2b, const int X, const unsigned int fb,
+                                                       const unsigned int fe, const unsigned int yb,
+                                                       const unsigned int ye)
+{
+    const int Y = 1 - X;
+    if (!(sh.pf_ok && sh.pf_Y == Y && sh.pf_yb == yb && sh.pf_ye == ye)) {
+        probe_build<NT>(log2b, S, Y, yb, ye);
+        // read next after the layer's closing barrier
+        if (threadIdx.x == 0) {
+            sh.pf_ok = 1;
+            sh.pf_Y = Y;
+            sh.pf_yb = yb;
+            sh.pf_ye = ye;
+        }
+    }
+    unsigned long long ps = 0;
+    for (unsigned int cb = fb; cb < fe; cb += NT) ps += probe_chunk<NT, OffT>(G, S, sh, log2b, X, cb, fe, yb, ye);
+    return ps;
+}
+
 // Runs sample `idx` in slot S.  Returns false if the sample's two balls
 // outgrew the slot's queue capacity: the slot is then clear again and
 // nothing was counted, and the caller runs the sample on a larger slot.
@@ -876,6 +1038,7 @@ __device__ bool run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, const
         sh.lmax = 0;
         sh.ldeg = 0;
         sh.chosen = -1;
+        sh.pf_ok = 0;
         sh.X = (sh.fdeg[0] <= sh.fdeg[1]) ? 0 : 1;
         if (sh.fdeg[sh.X] == 0) {
             // the side expanded first has no edges (the smaller degree sum is
@@ -913,10 +1076,21 @@ __device__ bool run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, const
         const unsigned int yb = sh.fbeg[Y], ye = sh.fend[Y];
         unsigned long long my_scan = 0;
 
+        // probe pass (small-diameter samples): if the layer meets side Y's
+        // frontier, its meeting counts are complete and it claims nothing
+        bool probed_last = false;
+        if (a.probe_log2 && S.bits && sh.fdeg[X] >= a.probe_edges && ye - yb <= (1u << (a.probe_log2 - 4))) {
+            const unsigned long long ps = probe_layer<NT, OffT>(G, S, sh, a.probe_log2, X, fb, fe, yb, ye);
+            if (*reinterpret_cast<volatile int *>(&sh.meets)) {
+                probed_last = true;
+                my_scan = ps;
+            }
+        }
+
         // a heavy layer of a persistent launch is posted for other CTAs to
         // help with (chunks of cv frontier vertices)
         int hk = -1;
-        if (a.help && sh.fdeg[X] >= a.help_edges && fe - fb > (unsigned int)NT / 8u) {
+        if (!probed_last && a.help && sh.fdeg[X] >= a.help_edges && fe - fb > (unsigned int)NT / 8u) {
             if (tid == 0) {
                 HelpReq *board = board_req(a.help);
                 const unsigned int cv = (unsigned int)NT / 8u;
@@ -944,7 +1118,9 @@ __device__ bool run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, const
             __syncthreads();
             hk = sh.help_k;
         }
-        if (hk < 0) {
+        if (probed_last) {
+            // the meeting counts are complete; nothing to expand
+        } else if (hk < 0) {
             for (unsigned int cb = fb; cb < fe; cb += NT)
                 my_scan += expand_chunk<NT, OffT>(a.spin_limit, G, S, sh, SmemAcc<NT>{sh}, X, nl, cb, fe, qbase, room,
                                                   yb, ye);
@@ -1959,6 +2135,8 @@ __global__ void __launch_bounds__(NT, (2048 / NT / 2) > 0 ? (2048 / NT / 2) : 1)
                 t.spin_limit = B.spin_limit;
                 t.help = B.help;
                 t.help_edges = B.help_edges;
+                t.probe_log2 = qd.use_bits ? B.probe_log2 : 0;
+                t.probe_edges = B.probe_edges;
                 sa = t;
             }
         }
@@ -2112,22 +2290,48 @@ __global__ void class_max_kernel(long long n, const uint32_t *counts, const uint
 
 // adj[e] = (col[e], degree of col[e]) for every adjacency entry
 template <typename OffT>
-__global__ void build_adj_kernel(long long nnz, const OffT *off, const int32_t *col, uint2 *adj)
+__global__ void degree_kernel(long long n, const OffT *off, uint32_t *deg)
 {
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += stride) {
-        const int32_t w = __ldg(col + e);
-        adj[e] = make_uint2((unsigned int)w, (unsigned int)((long long)__ldg(off + w + 1) - (long long)__ldg(off + w)));
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
+        deg[v] = (uint32_t)((long long)__ldg(off + v + 1) - (long long)__ldg(off + v));
+}
+
+// adj[e] = (col[e], deg[col[e]]).  col may be page-locked host memory read in
+// place over the host link: plain loads (no read-only path), kAdjPer
+// independent entries per thread in flight to cover the link's latency.
+constexpr int kAdjPer = 8;
+__global__ void build_adj_kernel(long long nnz, const uint32_t *deg, const int32_t *col, uint2 *adj)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; e + (long long)(kAdjPer - 1) * stride < nnz; e += (long long)kAdjPer * stride) {
+        int32_t w[kAdjPer];
+#pragma unroll
+        for (int j = 0; j < kAdjPer; ++j) w[j] = col[e + (long long)j * stride];
+        uint32_t d[kAdjPer];
+#pragma unroll
+        for (int j = 0; j < kAdjPer; ++j) d[j] = __ldg(deg + w[j]);
+#pragma unroll
+        for (int j = 0; j < kAdjPer; ++j) adj[e + (long long)j * stride] = make_uint2((unsigned int)w[j], d[j]);
+    }
+    for (; e < nnz; e += stride) {
+        const int32_t w = col[e];
+        adj[e] = make_uint2((unsigned int)w, __ldg(deg + w));
     }
 }
+
+// dynamic shared memory of a launch: the probe bitmap, if any
+inline size_t probe_bytes(int log2b) { return log2b ? (size_t)1 << (log2b - 3) : 0; }
 
 template <int NT>
 cudaError_t launch_nt(const SampleLaunch &a, cudaStream_t st)
 {
+    const size_t dyn = probe_bytes(a.probe_log2);
     if (a.off64)
-        sample_kernel<NT, long long><<<a.grid, NT, 0, st>>>(a);
+        sample_kernel<NT, long long><<<a.grid, NT, dyn, st>>>(a);
     else
-        sample_kernel<NT, int><<<a.grid, NT, 0, st>>>(a);
+        sample_kernel<NT, int><<<a.grid, NT, dyn, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -2152,29 +2356,64 @@ cudaError_t launch_sample(const SampleLaunch &a, cudaStream_t st)
     }
 }
 
-cudaError_t launch_build_adj(int64_t nnz, const void *off, int off64, const int32_t *col, uint2 *adj, cudaStream_t st)
+cudaError_t launch_build_adj(int64_t n, int64_t nnz, const void *off, int off64, const int32_t *col, uint2 *adj,
+                             uint32_t *deg_tmp, cudaStream_t st)
 {
     if (nnz <= 0) return cudaSuccess;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const long long want = (nnz + 255) / 256;
-    const int grid = (int)(want < (long long)sms * 16 ? want : (long long)sms * 16);
+    const long long vgrid = (n + 255) / 256 < (long long)sms * 8 ? (n + 255) / 256 : (long long)sms * 8;
     if (off64)
-        build_adj_kernel<long long><<<grid, 256, 0, st>>>((long long)nnz, static_cast<const long long *>(off), col, adj);
+        degree_kernel<long long><<<(int)vgrid, 256, 0, st>>>((long long)n, static_cast<const long long *>(off), deg_tmp);
     else
-        build_adj_kernel<int><<<grid, 256, 0, st>>>((long long)nnz, static_cast<const int *>(off), col, adj);
+        degree_kernel<int><<<(int)vgrid, 256, 0, st>>>((long long)n, static_cast<const int *>(off), deg_tmp);
+    const long long want = (nnz + 255) / 256;
+    const int grid = (int)(want < (long long)sms * 8 ? want : (long long)sms * 8);
+    build_adj_kernel<<<grid, 256, 0, st>>>((long long)nnz, deg_tmp, col, adj);
     return cudaGetLastError();
 }
 
 template <int NT>
 cudaError_t launch_batch_nt(const BatchLaunch &a, cudaStream_t st)
 {
+    const size_t dyn = probe_bytes(a.probe_log2);
     if (a.off64)
-        batch_kernel<NT, long long><<<a.grid, NT, 0, st>>>(a);
+        batch_kernel<NT, long long><<<a.grid, NT, dyn, st>>>(a);
     else
-        batch_kernel<NT, int><<<a.grid, NT, 0, st>>>(a);
+        batch_kernel<NT, int><<<a.grid, NT, dyn, st>>>(a);
     return cudaGetLastError();
+}
+
+// Largest probe bitmap (log2 of its bits, 0 if none) that keeps `per_sm` CTAs
+// of both kernels resident, and the kernels' dynamic shared memory limit
+// raised to it.
+template <int NT, typename OffT>
+cudaError_t probe_prepare_nt(int per_sm, int *log2b)
+{
+    size_t a1 = 0, a2 = 0;
+    cudaError_t e = cudaOccupancyAvailableDynamicSMemPerBlock(&a1, sample_kernel<NT, OffT>, per_sm, NT);
+    if (e == cudaSuccess) e = cudaOccupancyAvailableDynamicSMemPerBlock(&a2, batch_kernel<NT, OffT>, per_sm, NT);
+    if (e != cudaSuccess) return e;
+    const size_t avail = a1 < a2 ? a1 : a2;
+    int lb = kProbeMaxLog2;
+    while (lb >= kProbeMinLog2 && probe_bytes(lb) > avail) --lb;
+    if (lb < kProbeMinLog2) {
+        *log2b = 0;
+        return cudaSuccess;
+    }
+    const int bytes = (int)probe_bytes(lb);
+    e = cudaFuncSetAttribute(sample_kernel<NT, OffT>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(batch_kernel<NT, OffT>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    *log2b = e == cudaSuccess ? lb : 0;
+    return e;
+}
+
+template <int NT>
+cudaError_t probe_prepare_t(int off64, int per_sm, int *log2b)
+{
+    return off64 ? probe_prepare_nt<NT, long long>(per_sm, log2b) : probe_prepare_nt<NT, int>(per_sm, log2b);
 }
 
 cudaError_t launch_batch(const BatchLaunch &a, cudaStream_t st)
@@ -2207,6 +2446,19 @@ cudaError_t launch_class_max(int64_t n, const uint32_t *counts, const uint32_t *
     const int grid = (int)(want < (long long)sms * 8 ? want : (long long)sms * 8);
     class_max_kernel<<<grid > 0 ? grid : 1, 256, 0, st>>>((long long)n, counts, cls, cmax);
     return cudaGetLastError();
+}
+
+cudaError_t probe_prepare(int threads, int off64, int ctas_per_sm, int *log2_bits)
+{
+    *log2_bits = 0;
+    if (ctas_per_sm < 1) ctas_per_sm = 1;
+    switch (threads) {
+    case 128: return probe_prepare_t<128>(off64, ctas_per_sm, log2_bits);
+    case 256: return probe_prepare_t<256>(off64, ctas_per_sm, log2_bits);
+    case 512: return probe_prepare_t<512>(off64, ctas_per_sm, log2_bits);
+    case 1024: return probe_prepare_t<1024>(off64, ctas_per_sm, log2_bits);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t sample_occupancy(int threads, int off64, int *ctas_per_sm)

@@ -42,7 +42,7 @@ class Params(C.Structure):
                 ("vertex_diameter", C.c_int64), ("n_calib", C.c_int64), ("delta_rule", C.c_int32),
                 ("flags", C.c_uint32), ("beta", C.c_double), ("slots", C.c_int32),
                 ("threads", C.c_int32), ("scratch_fraction", C.c_double), ("queue_cap", C.c_int64),
-                ("coop_edges", C.c_int64)]
+                ("coop_edges", C.c_int64), ("probe_edges", C.c_int64)]
 
 
 class QueryInfo(C.Structure):

@@ -356,13 +356,21 @@ def test_reset_reproduces(K):
     assert np.array_equal(a["counts"], b["counts"])
 
 
-@pytest.mark.parametrize("variant", ["off64", "threads128", "threads512", "one_slot", "device_ptrs"])
+@pytest.mark.parametrize("variant", ["off64", "threads128", "threads512", "one_slot", "device_ptrs", "pinned",
+                                     "pinned_off64"])
 def test_launch_variants_agree(K, orc, variant):
     import torch
     g = GRAPHS["rmat14"]()
     kw = {}
     if variant == "off64":
         G = K.Graph.from_inputs(g, offsets_64=True)
+    elif variant.startswith("pinned"):
+        # page-locked host columns are read in place by the adjacency builder
+        o64 = variant == "pinned_off64"
+        off = torch.from_numpy(g.offsets if o64 else g.offsets32()).pin_memory()
+        col = torch.from_numpy(g.cols).pin_memory()
+        G = K.Graph(g.n, off.numpy(), col.numpy(), offsets_64=o64)
+        assert G.info()["max_degree"] == int(np.diff(g.offsets).max())
     elif variant == "device_ptrs":
         off = torch.from_numpy(g.offsets32()).cuda()
         col = torch.from_numpy(g.cols).cuda()
@@ -427,6 +435,35 @@ def test_cooperative_layers_match_oracle(K, orc, name, eps, E, cap):
     assert res["tau"] == R.tau and res["stop_epoch"] == R.stop_epoch
     assert np.array_equal(res["counts"], counts)
     assert info.samples == R.tau and info.e_scan == R.e_scan
+
+
+@pytest.mark.parametrize("name,eps,E,threads", [
+    ("er2000", 0.05, 100, 1024), ("rmat14", 0.03, 256, 1024), ("rmat14", 0.03, 256, 128), ("layered", 0.05, 200, 256),
+    ("rhg4k", 0.03, 128, 512), ("fullgrid64", 0.05, 150, 1024),
+])
+def test_probe_pass_matches_oracle(K, orc, name, eps, E, threads):
+    # Small-diameter queries probe a layer against a shared-memory bitmap of
+    # the other side's frontier first (probe_edges 1 = every layer, 0 = the
+    # default threshold, -1 = never; 128 threads get the smallest map, 2^15
+    # bits, which skips frontiers above 2048 vertices).  With the probe, without it,
+    # and in the oracle the run ends alike, and the adjacency entries scanned
+    # are the same.
+    g = GRAPHS[name]()
+    G = K.Graph.from_inputs(g)
+    counts, cal, LL, LU, R = orc.kadabra(g, eps, 0.1, seed=11, epoch_len=E)
+    ora = oracle_trace(orc, g, 11, 1, 0, 64)
+    for probe in (1, 0, -1):
+        q = K.Query(G, eps=eps, delta=0.1, seed=11, threads=threads, probe_edges=probe)
+        q.run_pipelined(E, frames=4)
+        res = q.result(btilde=False)
+        info = q.info()
+        assert info.device_error == 0
+        assert res["tau"] == R.tau and res["stop_epoch"] == R.stop_epoch
+        assert np.array_equal(res["counts"], counts)
+        assert info.samples == R.tau and info.e_scan == R.e_scan
+        recs, paths = q.sample_trace(1, 0, 64, path_cap=256)
+        compare_trace(recs, paths, ora, 256)
+        q.free()
 
 
 def test_omega_clip_and_single_samples(K, orc):
