@@ -74,6 +74,12 @@ constexpr int kPathCap = 1024;     // path vertices buffered in shared memory be
 constexpr int kUnroll = KADABRA_UNROLL;   // adjacency entries in flight per thread
 constexpr unsigned int kNone = 0xffffffffu;
 constexpr int kProbeMinLog2 = 15;  // smallest probe bitmap worth a pass (4 KB)
+// adjacency entries in flight per thread in the probe pass: 8 for CTAs of
+// 1024 threads (one per SM: the pass is the SM's only work), 4 below
+template <int NT>
+struct ProbeUnroll {
+    static constexpr int value = NT >= 1024 ? 8 : 4;
+};
 constexpr int kProbeMaxLog2 = 20;  // largest probe bitmap (128 KB)
 
 __device__ __forceinline__ unsigned long long ldcg(const unsigned long long *p) { return __ldcg(p); }
@@ -155,13 +161,16 @@ struct Smem {
         const void *off;
         const uint2 *adj;
         unsigned int cap, X, nl, fb, fe, qbase, room, yb, ye, cv;
+        int mode, log2b;
+        unsigned int id;             // request index << 16 | its generation
     } hl;                            // the helped layer, copied from its request
     long long next_v;
     int found;
     // the probe bitmap holds side pf_Y's queue positions [pf_yb, pf_ye) of
-    // this sample (pf_ok = 0: nothing valid)
+    // this sample (pf_ok = 1), or the frontier of helped request pf_req
+    // (pf_ok = 2); pf_ok = 0: nothing valid
     int pf_ok, pf_Y;
-    unsigned int pf_yb, pf_ye;
+    unsigned int pf_yb, pf_ye, pf_req;
     unsigned long long cur;          // work item taken by this CTA
     // back-walk: vertices found so far (flushed to the sink by warp 0) and
     // the state handed between warp 0's steps and the whole CTA's steps
@@ -567,6 +576,8 @@ struct HelpReq {
     const uint2 *adj;
     long long n;
     unsigned int cap, X, nl, fb, fe, qbase, room, yb, ye, cv;
+    int mode;                      // 0: expand the layer; 1: probe pass
+    int log2b;                     // probe bitmap size of the launch
     // accumulators
     unsigned long long lmax, ldeg, scan;
     unsigned int new_count, meet_count, err;
@@ -877,12 +888,13 @@ __device__ __forceinline__ void probe_build(const int log2b, const Slot &S, cons
 // gets the source's path count added to its meeting count and joins the
 // meeting set, exactly as in expand_chunk; nothing else is written.  Returns
 // the chunk's adjacency-entry count in thread 0 (0 elsewhere).
-template <int NT, typename OffT>
+template <int NT, typename OffT, typename Acc>
 __device__ __forceinline__ unsigned long long probe_chunk(const GraphRef<OffT> &G, const Slot &S, Smem<NT> &sh,
-                                                          const int log2b, const int X, const unsigned int cb,
-                                                          const unsigned int fe, const unsigned int yb,
-                                                          const unsigned int ye)
+                                                          const Acc &A, const int log2b, const int X,
+                                                          const unsigned int cb, const unsigned int fe,
+                                                          const unsigned int yb, const unsigned int ye)
 {
+    constexpr int kProbeUnroll = ProbeUnroll<NT>::value;
     const int tid = threadIdx.x;
     const int lane = tid & 31;
     const int Y = 1 - X;
@@ -905,11 +917,11 @@ __device__ __forceinline__ unsigned long long probe_chunk(const GraphRef<OffT> &
     const int cnt = (int)min((unsigned int)NT, fe - cb);
     __syncthreads();
     const unsigned long long wbase = (unsigned long long)(tid & ~31);
-    for (unsigned long long e0 = wbase; e0 < total; e0 += (unsigned long long)NT * kUnroll) {
-        unsigned int w[kUnroll];
-        int own[kUnroll];
+    for (unsigned long long e0 = wbase; e0 < total; e0 += (unsigned long long)NT * kProbeUnroll) {
+        unsigned int w[kProbeUnroll];
+        int own[kProbeUnroll];
 #pragma unroll
-        for (int j = 0; j < kUnroll; ++j) {
+        for (int j = 0; j < kProbeUnroll; ++j) {
             const unsigned long long e = e0 + (unsigned long long)lane + (unsigned long long)j * NT;
             w[j] = kNone;
             own[j] = 0;
@@ -924,9 +936,9 @@ __device__ __forceinline__ unsigned long long probe_chunk(const GraphRef<OffT> &
                 w[j] = __ldg(&G.adj[sh.u.ex.cbeg[lo] + (long long)(e - sh.u.ex.cpos[lo])].x);
             }
         }
-        unsigned int cd[kUnroll];
+        unsigned int cd[kProbeUnroll];
 #pragma unroll
-        for (int j = 0; j < kUnroll; ++j) {
+        for (int j = 0; j < kProbeUnroll; ++j) {
             cd[j] = 0u;
             if (w[j] != kNone) {
                 const unsigned int h = probe_hash(w[j], log2b);
@@ -934,23 +946,23 @@ __device__ __forceinline__ unsigned long long probe_chunk(const GraphRef<OffT> &
             }
         }
 #pragma unroll
-        for (int j = 0; j < kUnroll; ++j) {
+        for (int j = 0; j < kProbeUnroll; ++j) {
             const unsigned int c = cd[j];
             if (c == 0u || side_of(c) != Y) continue;     // unseen, or on this side
             const unsigned int p = pos_of(c);
             if (is_pending(c) || p < yb || p >= ye) {
-                atomicOr(&sh.err, kErrSelect);             // broken invariant: never expected
+                atomicOr(A.err(), kErrSelect);             // broken invariant: never expected
                 continue;
             }
             const unsigned long long su = sh.u.ex.csig[own[j]];
             const unsigned long long old = atomicAdd(S.qm + S.at(Y, p), su);
-            if (old + su < su) atomicOr(&sh.err, kErrAddOverflow);
-            sh.meets = 1;
+            if (old + su < su) atomicOr(A.err(), kErrAddOverflow);
+            *A.meets() = 1;
             if (old == 0ULL) {
-                const unsigned int q = atomicAdd(&sh.meet_count, 1u);
+                const unsigned int q = atomicAdd(A.meet_count(), 1u);
                 if (q < kMeetCap) {
-                    sh.cand[q] = w[j];
-                    sh.cpos[q] = p;
+                    A.cand()[q] = w[j];
+                    A.cpos()[q] = p;
                 }
             }
         }
@@ -959,18 +971,13 @@ __device__ __forceinline__ unsigned long long probe_chunk(const GraphRef<OffT> &
     return tid == 0 ? total : 0ULL;
 }
 
-// The probe pass over side X's whole current layer [fb, fe) (CTA-wide;
-// builds the bitmap unless it already holds side Y's frontier [yb, ye)).
-// Returns the layer's adjacency-entry count in thread 0 (0 elsewhere); after
-// it, sh.meets says whether the layer met side Y.
-template <int NT, typename OffT>
-__device__ __noinline__ unsigned long long probe_layer(const GraphRef<OffT> &G, const Slot &S, Smem<NT> &sh,
-                                                       const int log2b, const int X, const unsigned int fb,
-                                                       const unsigned int fe, const unsigned int yb,
-                                                       const unsigned int ye)
+// Makes the bitmap hold side Y's frontier [yb, ye) of the CTA's own sample
+// (CTA-wide; nothing to do if it already does).
+template <int NT>
+__device__ __forceinline__ void probe_ready(const int log2b, const Slot &S, Smem<NT> &sh, const int Y,
+                                            const unsigned int yb, const unsigned int ye)
 {
-    const int Y = 1 - X;
-    if (!(sh.pf_ok && sh.pf_Y == Y && sh.pf_yb == yb && sh.pf_ye == ye)) {
+    if (!(sh.pf_ok == 1 && sh.pf_Y == Y && sh.pf_yb == yb && sh.pf_ye == ye)) {
         probe_build<NT>(log2b, S, Y, yb, ye);
         // read next after the layer's closing barrier
         if (threadIdx.x == 0) {
@@ -980,9 +987,112 @@ __device__ __noinline__ unsigned long long probe_layer(const GraphRef<OffT> &G, 
             sh.pf_ye = ye;
         }
     }
+}
+
+// The probe pass over side X's whole current layer [fb, fe) by this CTA
+// alone.  Returns the layer's adjacency-entry count in thread 0 (0
+// elsewhere); after it, sh.meets says whether the layer met side Y.
+template <int NT, typename OffT>
+__device__ __noinline__ unsigned long long probe_layer(const GraphRef<OffT> &G, const Slot &S, Smem<NT> &sh,
+                                                       const int log2b, const int X, const unsigned int fb,
+                                                       const unsigned int fe, const unsigned int yb,
+                                                       const unsigned int ye)
+{
+    probe_ready<NT>(log2b, S, sh, 1 - X, yb, ye);
     unsigned long long ps = 0;
-    for (unsigned int cb = fb; cb < fe; cb += NT) ps += probe_chunk<NT, OffT>(G, S, sh, log2b, X, cb, fe, yb, ye);
+    for (unsigned int cb = fb; cb < fe; cb += NT)
+        ps += probe_chunk<NT, OffT>(G, S, sh, SmemAcc<NT>{sh}, log2b, X, cb, fe, yb, ye);
     return ps;
+}
+
+// A heavy layer of a persistent launch, posted on the help board (mode 0:
+// expand, 1: probe): the CTA takes chunks of cv frontier vertices with every
+// CTA that joins until none is left, waits (bounded) for the chunks others
+// took, and copies the request's accumulators into its own.  Returns false,
+// having done nothing, if no request was free.
+template <int NT, typename OffT>
+__device__ __noinline__ bool help_layer(const SampleLaunch &a, const GraphRef<OffT> &G, const Slot &S, Smem<NT> &sh,
+                                        const int mode, const int X, const unsigned int nl, const unsigned int fb,
+                                        const unsigned int fe, const unsigned int qbase, const unsigned int room,
+                                        const unsigned int yb, const unsigned int ye, unsigned long long &my_scan)
+{
+    const int tid = threadIdx.x;
+    const unsigned int cv = (unsigned int)NT / 8u;
+    const unsigned int nch = (fe - fb + cv - 1u) / cv;
+    if (tid == 0) {
+        HelpReq *board = board_req(a.help);
+        int k = -1;
+        if (nch < (1u << 23))
+            for (int i = 0; i < kHelpSlots && k < 0; ++i)
+                if (atomicCAS(&board[i].state, 0, 1) == 0) k = i;
+        if (k >= 0) {
+            HelpReq *R = board + k;
+            R->code = S.code; R->qv = S.qv; R->ql = S.ql; R->qs = S.qs; R->qm = S.qm;
+            R->bits = S.bits; R->bw = S.bw; R->off = G.off; R->adj = G.adj; R->n = G.n;
+            R->cap = S.cap; R->X = (unsigned int)X; R->nl = nl; R->fb = fb; R->fe = fe; R->qbase = qbase;
+            R->room = room; R->yb = yb; R->ye = ye; R->cv = cv;
+            R->mode = mode; R->log2b = a.probe_log2;
+            R->lmax = 0; R->ldeg = 0; R->scan = 0; R->new_count = 0; R->meet_count = 0; R->err = 0;
+            R->meets = 0; R->ovf = 0; R->done = 0;
+            __threadfence();
+            const unsigned long long gen = (*reinterpret_cast<volatile unsigned long long *>(&R->ticket) >> 48) + 1ULL;
+            atomicExch(&R->ticket, ((gen & 0xffffULL) << 48) | ((unsigned long long)nch << 24));
+            __threadfence();
+            atomicAdd(board_open(a.help), 1u);
+        }
+        sh.help_k = k;
+    }
+    __syncthreads();
+    const int hk = sh.help_k;
+    if (hk < 0) return false;
+    HelpReq *R = board_req(a.help) + hk;
+    for (;;) {
+        if (tid == 0) sh.help_c = take_chunk(R);
+        __syncthreads();
+        const int c = sh.help_c;
+        if (c < 0) break;
+        const unsigned int cb = fb + (unsigned int)c * cv;
+        const unsigned long long sc =
+            mode ? probe_chunk<NT, OffT>(G, S, sh, ReqAcc{R}, a.probe_log2, X, cb, min(cb + cv, fe), yb, ye)
+                 : expand_chunk<NT, OffT>(a.spin_limit, G, S, sh, ReqAcc{R}, X, nl, cb, min(cb + cv, fe), qbase,
+                                          room, yb, ye);
+        if (tid == 0) {
+            atomicAdd(&R->scan, sc);
+            __threadfence();
+            atomicAdd(&R->done, 1u);
+        }
+    }
+    // no chunk left to take; wait (bounded) for the chunks other CTAs took,
+    // then collect
+    if (tid == 0) {
+        atomicSub(board_open(a.help), 1u);
+        unsigned long long w = 0;
+        while (*reinterpret_cast<volatile unsigned int *>(&R->done) < nch && ++w < a.spin_limit) __nanosleep(256);
+        __threadfence();
+        if (*reinterpret_cast<volatile unsigned int *>(&R->done) < nch) sh.err |= kErrTimeout;
+        sh.new_count = *reinterpret_cast<volatile unsigned int *>(&R->new_count);
+        sh.meet_count = *reinterpret_cast<volatile unsigned int *>(&R->meet_count);
+        sh.meets = *reinterpret_cast<volatile int *>(&R->meets);
+        sh.ovf |= *reinterpret_cast<volatile int *>(&R->ovf);
+        sh.err |= *reinterpret_cast<volatile unsigned int *>(&R->err);
+        sh.lmax = *reinterpret_cast<volatile unsigned long long *>(&R->lmax);
+        sh.ldeg = *reinterpret_cast<volatile unsigned long long *>(&R->ldeg);
+        my_scan = *reinterpret_cast<volatile unsigned long long *>(&R->scan);
+    }
+    __syncthreads();
+    const unsigned int mc = min(sh.meet_count, (unsigned int)kMeetCap);
+    for (unsigned int i = tid; i < mc; i += NT) {
+        sh.cand[i] = __ldcg(R->cand + i);
+        sh.cpos[i] = __ldcg(R->cpos + i);
+    }
+    __syncthreads();
+    // the request is free again only if every chunk is done (a request
+    // whose wait gave up stays held: a late helper may still write it)
+    if (tid == 0 && !(sh.err & kErrTimeout)) {
+        __threadfence();
+        atomicExch(&R->state, 0);
+    }
+    return true;
 }
 
 // Runs sample `idx` in slot S.  Returns false if the sample's two balls
@@ -1077,102 +1187,29 @@ __device__ bool run_sample(const SampleLaunch &a, const GraphRef<OffT> &G, const
         unsigned long long my_scan = 0;
 
         // probe pass (small-diameter samples): if the layer meets side Y's
-        // frontier, its meeting counts are complete and it claims nothing
+        // frontier, its meeting counts are complete and it claims nothing.
+        // A heavy layer of a persistent launch is posted for other CTAs to
+        // help with, for the probe pass and for the expansion alike.
+        const bool heavy = a.help && sh.fdeg[X] >= a.help_edges && fe - fb > (unsigned int)NT / 8u;
         bool probed_last = false;
         if (a.probe_log2 && S.bits && sh.fdeg[X] >= a.probe_edges && ye - yb <= (1u << (a.probe_log2 - 4))) {
-            const unsigned long long ps = probe_layer<NT, OffT>(G, S, sh, a.probe_log2, X, fb, fe, yb, ye);
+            unsigned long long ps = 0;
+            bool shared = false;
+            if (heavy) {
+                probe_ready<NT>(a.probe_log2, S, sh, Y, yb, ye);
+                shared = help_layer<NT, OffT>(a, G, S, sh, 1, X, nl, fb, fe, qbase, room, yb, ye, ps);
+            }
+            if (!shared) ps = probe_layer<NT, OffT>(G, S, sh, a.probe_log2, X, fb, fe, yb, ye);
             if (*reinterpret_cast<volatile int *>(&sh.meets)) {
                 probed_last = true;
                 my_scan = ps;
             }
         }
-
-        // a heavy layer of a persistent launch is posted for other CTAs to
-        // help with (chunks of cv frontier vertices)
-        int hk = -1;
-        if (!probed_last && a.help && sh.fdeg[X] >= a.help_edges && fe - fb > (unsigned int)NT / 8u) {
-            if (tid == 0) {
-                HelpReq *board = board_req(a.help);
-                const unsigned int cv = (unsigned int)NT / 8u;
-                const unsigned int nch = (fe - fb + cv - 1u) / cv;
-                int k = -1;
-                if (nch < (1u << 23))
-                    for (int i = 0; i < kHelpSlots && k < 0; ++i)
-                        if (atomicCAS(&board[i].state, 0, 1) == 0) k = i;
-                if (k >= 0) {
-                    HelpReq *R = board + k;
-                    R->code = S.code; R->qv = S.qv; R->ql = S.ql; R->qs = S.qs; R->qm = S.qm;
-                    R->bits = S.bits; R->bw = S.bw; R->off = G.off; R->adj = G.adj; R->n = G.n;
-                    R->cap = S.cap; R->X = (unsigned int)X; R->nl = nl; R->fb = fb; R->fe = fe; R->qbase = qbase;
-                    R->room = room; R->yb = yb; R->ye = ye; R->cv = cv;
-                    R->lmax = 0; R->ldeg = 0; R->scan = 0; R->new_count = 0; R->meet_count = 0; R->err = 0;
-                    R->meets = 0; R->ovf = 0; R->done = 0;
-                    __threadfence();
-                    const unsigned long long gen = (*reinterpret_cast<volatile unsigned long long *>(&R->ticket) >> 48) + 1ULL;
-                    atomicExch(&R->ticket, ((gen & 0xffffULL) << 48) | ((unsigned long long)nch << 24));
-                    __threadfence();
-                    atomicAdd(board_open(a.help), 1u);
-                }
-                sh.help_k = k;
-            }
-            __syncthreads();
-            hk = sh.help_k;
-        }
-        if (probed_last) {
-            // the meeting counts are complete; nothing to expand
-        } else if (hk < 0) {
+        if (!probed_last && !(heavy && help_layer<NT, OffT>(a, G, S, sh, 0, X, nl, fb, fe, qbase, room, yb, ye,
+                                                              my_scan))) {
             for (unsigned int cb = fb; cb < fe; cb += NT)
                 my_scan += expand_chunk<NT, OffT>(a.spin_limit, G, S, sh, SmemAcc<NT>{sh}, X, nl, cb, fe, qbase, room,
                                                   yb, ye);
-        } else {
-            HelpReq *R = board_req(a.help) + hk;
-            const unsigned int cv = (unsigned int)NT / 8u;
-            const unsigned int nch = (fe - fb + cv - 1u) / cv;
-            for (;;) {
-                if (tid == 0) sh.help_c = take_chunk(R);
-                __syncthreads();
-                const int c = sh.help_c;
-                if (c < 0) break;
-                const unsigned int cb = fb + (unsigned int)c * cv;
-                const unsigned long long sc = expand_chunk<NT, OffT>(a.spin_limit, G, S, sh, ReqAcc{R}, X, nl, cb,
-                                                                     min(cb + cv, fe), qbase, room, yb, ye);
-                if (tid == 0) {
-                    atomicAdd(&R->scan, sc);
-                    __threadfence();
-                    atomicAdd(&R->done, 1u);
-                }
-            }
-            // no chunk left to take; wait (bounded) for the chunks other CTAs
-            // took, then collect
-            if (tid == 0) {
-                atomicSub(board_open(a.help), 1u);
-                unsigned long long w = 0;
-                while (*reinterpret_cast<volatile unsigned int *>(&R->done) < nch && ++w < a.spin_limit)
-                    __nanosleep(256);
-                __threadfence();
-                if (*reinterpret_cast<volatile unsigned int *>(&R->done) < nch) sh.err |= kErrTimeout;
-                sh.new_count = *reinterpret_cast<volatile unsigned int *>(&R->new_count);
-                sh.meet_count = *reinterpret_cast<volatile unsigned int *>(&R->meet_count);
-                sh.meets = *reinterpret_cast<volatile int *>(&R->meets);
-                sh.ovf |= *reinterpret_cast<volatile int *>(&R->ovf);
-                sh.err |= *reinterpret_cast<volatile unsigned int *>(&R->err);
-                sh.lmax = *reinterpret_cast<volatile unsigned long long *>(&R->lmax);
-                sh.ldeg = *reinterpret_cast<volatile unsigned long long *>(&R->ldeg);
-                my_scan = *reinterpret_cast<volatile unsigned long long *>(&R->scan);
-            }
-            __syncthreads();
-            const unsigned int mc = min(sh.meet_count, (unsigned int)kMeetCap);
-            for (unsigned int i = tid; i < mc; i += NT) {
-                sh.cand[i] = __ldcg(R->cand + i);
-                sh.cpos[i] = __ldcg(R->cpos + i);
-            }
-            __syncthreads();
-            // the request is free again only if every chunk is done (a request
-            // whose wait gave up stays held: a late helper may still write it)
-            if (tid == 0 && !(sh.err & kErrTimeout)) {
-                __threadfence();
-                atomicExch(&R->state, 0);
-            }
         }
         // The layer's outcome (final after the last chunk's barrier), read
         // alike by every thread: if the search goes on, every thread scales
@@ -1969,11 +2006,12 @@ __global__ void __launch_bounds__(NT, (2048 / NT / 2) > 0 ? (2048 / NT / 2) : 1)
     __shared__ int s_qi;
     const int tid = threadIdx.x;
     volatile BatchState *vbs = B.bs;
-    if (B.nq == 1) {
+    if (tid == 0) {
+        sh.pf_ok = 0;       // the probe bitmap holds nothing yet
         // one query: its descriptor stays in shared memory for the whole launch
-        if (tid == 0) qd = B.queries[0];
-        __syncthreads();
+        if (B.nq == 1) qd = B.queries[0];
     }
+    __syncthreads();
 
     for (;;) {
         // Warp 0 picks the next sample: its lanes read the state of 32
@@ -2020,6 +2058,9 @@ __global__ void __launch_bounds__(NT, (2048 / NT / 2) > 0 ? (2048 / NT / 2) : 1)
                         sh.hl.yb = V->yb;
                         sh.hl.ye = V->ye;
                         sh.hl.cv = V->cv;
+                        sh.hl.mode = V->mode;
+                        sh.hl.log2b = V->log2b;
+                        sh.hl.id = ((unsigned int)i << 16) | (unsigned int)((V->ticket >> 48) & 0xffffULL);
                         helping = 1;
                     }
                 }
@@ -2154,9 +2195,25 @@ __global__ void __launch_bounds__(NT, (2048 / NT / 2) > 0 ? (2048 / NT / 2) : 1)
             S2.cap = sh.hl.cap;
             const GraphRef<OffT> G2{reinterpret_cast<const OffT *>(sh.hl.off), sh.hl.adj, sh.hl.n};
             const unsigned int cb = sh.hl.fb + (unsigned int)sh.help_c * sh.hl.cv;
-            const unsigned long long sc =
-                expand_chunk<NT, OffT>(B.spin_limit, G2, S2, sh, ReqAcc{R}, (int)sh.hl.X, sh.hl.nl, cb,
-                                       min(cb + sh.hl.cv, sh.hl.fe), sh.hl.qbase, sh.hl.room, sh.hl.yb, sh.hl.ye);
+            unsigned long long sc;
+            if (sh.hl.mode) {
+                // probe chunk: this CTA's bitmap gets the request's frontier
+                // (between two samples the bitmap is free; the next sample of
+                // this CTA builds its own)
+                if (!(sh.pf_ok == 2 && sh.pf_req == sh.hl.id)) {
+                    probe_build<NT>(sh.hl.log2b, S2, 1 - (int)sh.hl.X, sh.hl.yb, sh.hl.ye);
+                    if (tid == 0) {
+                        sh.pf_ok = 2;
+                        sh.pf_req = sh.hl.id;
+                    }
+                }
+                sc = probe_chunk<NT, OffT>(G2, S2, sh, ReqAcc{R}, sh.hl.log2b, (int)sh.hl.X, cb,
+                                           min(cb + sh.hl.cv, sh.hl.fe), sh.hl.yb, sh.hl.ye);
+            } else {
+                sc = expand_chunk<NT, OffT>(B.spin_limit, G2, S2, sh, ReqAcc{R}, (int)sh.hl.X, sh.hl.nl, cb,
+                                            min(cb + sh.hl.cv, sh.hl.fe), sh.hl.qbase, sh.hl.room, sh.hl.yb,
+                                            sh.hl.ye);
+            }
             if (tid == 0) {
                 atomicAdd(&R->scan, sc);
                 __threadfence();
