@@ -57,6 +57,13 @@ typedef struct kadabra_query kadabra_query;
 /* kadabra_params.flags */
 #define KADABRA_STRICT_SIGMA 1u  /* a per-side path count above 2^K is an error instead
                                     of being scaled down (see kadabra_sigma_bits)        */
+#define KADABRA_FULL_LOOKAHEAD 2u /* pipelined launches: keep all epoch frames open until
+                                    the stop.  By default, once the last check's maxima
+                                    of f and g predict the stop within the frames (both
+                                    shrink about as 1/sqrt(tau)), samples are handed out
+                                    only up to the predicted stop epoch and one more, and
+                                    CTAs without a sample help heavy layers instead.
+                                    Results never depend on it                           */
 
 /* kadabra_params.delta_rule */
 #define KADABRA_DELTA_UNIFORM  0  /* delta_L = delta_U = delta / (4n)                     */
@@ -78,7 +85,7 @@ typedef struct kadabra_params {
                                  kadabra_query_info.vd_exact says which               */
     int64_t n_calib;          /* calibration samples; <= 0: max(1000, ceil(omega/100))     */
     int32_t delta_rule;       /* KADABRA_DELTA_UNIFORM or KADABRA_DELTA_BALANCED           */
-    uint32_t flags;           /* KADABRA_STRICT_SIGMA                                       */
+    uint32_t flags;           /* KADABRA_STRICT_SIGMA | KADABRA_FULL_LOOKAHEAD              */
     double beta;              /* balanced rule floor weight (default 1e-3)                 */
     int32_t slots;            /* samples in flight (one CTA each); 0 = fill the GPU        */
     int32_t threads;          /* threads per sampling CTA: 128, 256, 512, 1024; 0 = 1024   */

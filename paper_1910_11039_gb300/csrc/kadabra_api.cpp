@@ -1072,6 +1072,7 @@ static kadabra::QueryDesc make_desc(const kadabra_query *q, kadabra::Counters *l
     d.ps = q->d_pipe;
     d.launch_ctr = launch_ctr;
     d.use_bits = q->vd <= kadabra::kBitsMaxVD ? 1 : 0;
+    d.lookahead = (q->p.flags & KADABRA_FULL_LOOKAHEAD) ? 0 : 1;
     d.tag = 1;
     if (q->phase == 1) {
         // calibration samples: one epoch of n_calib samples counted into the

@@ -193,6 +193,8 @@ struct QueryDesc {
     unsigned int *cmax;        // largest c~ in every class
     int nclass;
     int use_bits;              // the query uses the slots' reached-bit maps
+    int lookahead;             // 1: near the predicted stop, open only the epochs up to it
+                               //    (and one more); 0: always all F frames
     int tag;                   // 1: adaptive phase (epochs, logs, checks); 0: calibration samples
                                //    counted straight into `counts` (E = n_calib, F = 1, no check)
     double omega, eps;

@@ -1996,6 +1996,68 @@ __device__ __forceinline__ unsigned long long epoch_size(const PipeState *st, lo
 // epochs in order.  The launch ends when every query has stopped or reached
 // ceil(omega), or once `budget` samples have been handed out; the pipeline
 // state persists, so the next launch continues where this one ended.
+// Epoch frames a pipelined query may fill ahead of its oldest unchecked
+// epoch.  While its stop is far, all F.  f and g shrink about as 1/sqrt(tau),
+// so after the last check (tau samples, maxima m of f and g) the stop is
+// expected near tau * (m / eps)^2 samples: once that is within the frames,
+// samples are handed out only up to the predicted stop epoch and one more,
+// so that fewer samples are discarded and CTAs without one help heavy layers.
+// A late stop only delays later hand-outs: results never depend on it.
+__device__ __forceinline__ long long lookahead(const QueryDesc *Q, volatile PipeState *vst, volatile Job *vjob)
+{
+    if (!Q->lookahead || Q->tag == 0) return Q->F;
+    if (vst->next_check < 2) return Q->F;      // no trend yet
+    const double m = fmax(vjob->last_maxf, vjob->last_maxg);
+    const double r = m / Q->eps;
+    if (!(r >= 1.0) || !(r < 4.0)) return Q->F;
+    const double ahead = (double)vjob->tau * (r * r - 1.0) / (double)Q->E;    // epochs to the predicted stop
+    const long long f = (long long)ceil(ahead) + 1;
+    return f < (long long)Q->F ? f : (long long)Q->F;
+}
+
+// Lane 0 of warp 0: takes a chunk of a request on the help board, if any,
+// and copies the request's layer into sh.hl.  Returns whether it took one.
+template <int NT>
+__device__ __forceinline__ bool board_take(const BatchLaunch &B, Smem<NT> &sh)
+{
+    if (!B.help || *reinterpret_cast<volatile unsigned int *>(board_open(B.help)) == 0u) return false;
+    HelpReq *board = board_req(B.help);
+    for (int i = 0; i < kHelpSlots; ++i) {
+        const int c = take_chunk(board + i);
+        if (c < 0) continue;
+        // the chunk belongs to the layer the request holds now, and the
+        // request cannot be reused before this chunk is done
+        volatile HelpReq *V = board + i;
+        sh.help_k = i;
+        sh.help_c = c;
+        sh.hl.code = V->code;
+        sh.hl.qv = V->qv;
+        sh.hl.ql = V->ql;
+        sh.hl.qs = V->qs;
+        sh.hl.qm = V->qm;
+        sh.hl.bits = V->bits;
+        sh.hl.bw = V->bw;
+        sh.hl.n = V->n;
+        sh.hl.off = V->off;
+        sh.hl.adj = V->adj;
+        sh.hl.cap = V->cap;
+        sh.hl.X = V->X;
+        sh.hl.nl = V->nl;
+        sh.hl.fb = V->fb;
+        sh.hl.fe = V->fe;
+        sh.hl.qbase = V->qbase;
+        sh.hl.room = V->room;
+        sh.hl.yb = V->yb;
+        sh.hl.ye = V->ye;
+        sh.hl.cv = V->cv;
+        sh.hl.mode = V->mode;
+        sh.hl.log2b = V->log2b;
+        sh.hl.id = ((unsigned int)i << 16) | (unsigned int)((V->ticket >> 48) & 0xffffULL);
+        return true;
+    }
+    return false;
+}
+
 template <int NT, typename OffT>
 __global__ void __launch_bounds__(NT, (2048 / NT / 2) > 0 ? (2048 / NT / 2) : 1) batch_kernel(BatchLaunch B)
 {
@@ -2028,42 +2090,7 @@ __global__ void __launch_bounds__(NT, (2048 / NT / 2) > 0 ? (2048 / NT / 2) : 1)
                 pm.take = 0;
                 s_qi = -1;
                 sh.help_k = -1;
-                if (B.help && *reinterpret_cast<volatile unsigned int *>(board_open(B.help)) != 0u) {
-                    HelpReq *board = board_req(B.help);
-                    for (int i = 0; i < kHelpSlots && sh.help_k < 0; ++i) {
-                        const int c = take_chunk(board + i);
-                        if (c < 0) continue;
-                        // the chunk belongs to the layer the request holds now, and the
-                        // request cannot be reused before this chunk is done
-                        volatile HelpReq *V = board + i;
-                        sh.help_k = i;
-                        sh.help_c = c;
-                        sh.hl.code = V->code;
-                        sh.hl.qv = V->qv;
-                        sh.hl.ql = V->ql;
-                        sh.hl.qs = V->qs;
-                        sh.hl.qm = V->qm;
-                        sh.hl.bits = V->bits;
-                        sh.hl.bw = V->bw;
-                        sh.hl.n = V->n;
-                        sh.hl.off = V->off;
-                        sh.hl.adj = V->adj;
-                        sh.hl.cap = V->cap;
-                        sh.hl.X = V->X;
-                        sh.hl.nl = V->nl;
-                        sh.hl.fb = V->fb;
-                        sh.hl.fe = V->fe;
-                        sh.hl.qbase = V->qbase;
-                        sh.hl.room = V->room;
-                        sh.hl.yb = V->yb;
-                        sh.hl.ye = V->ye;
-                        sh.hl.cv = V->cv;
-                        sh.hl.mode = V->mode;
-                        sh.hl.log2b = V->log2b;
-                        sh.hl.id = ((unsigned int)i << 16) | (unsigned int)((V->ticket >> 48) & 0xffffULL);
-                        helping = 1;
-                    }
-                }
+                if (board_take<NT>(B, sh)) helping = 1;
                 if (!helping) {
                     stop_launch = vbs->abort != 0;
                     if (!stop_launch && B.budget && atomicAdd(&B.bs->taken, 0ULL) >= B.budget) stop_launch = true;
@@ -2092,7 +2119,8 @@ __global__ void __launch_bounds__(NT, (2048 / NT / 2) > 0 ? (2048 / NT / 2) : 1)
                                 const unsigned long long nx = vst->next_idx;
                                 if (nx < vst->R) {
                                     running = true;
-                                    eligible = (long long)(nx / (unsigned long long)Q->E) < vst->next_check + Q->F;
+                                    eligible = (long long)(nx / (unsigned long long)Q->E) <
+                                               vst->next_check + lookahead(Q, vst, vjob);
                                 }
                             }
                         }
@@ -2142,7 +2170,11 @@ __global__ void __launch_bounds__(NT, (2048 / NT / 2) > 0 ? (2048 / NT / 2) : 1)
                         }
                     }
                     if (take || !any_running) break;
-                    // every running query waits for an epoch check: back off (bounded)
+                    // every running query waits for an epoch check: help with a
+                    // posted heavy layer meanwhile, else back off (bounded)
+                    int helped = 0;
+                    if (lane == 0) helped = board_take<NT>(B, sh) ? 1 : 0;
+                    if (__shfl_sync(0xffffffffu, helped, 0)) break;
                     if (++polls > B.spin_limit) {
                         if (lane == 0) {
                             atomicOr(&B.bs->abort, 1u);

@@ -27,6 +27,7 @@ STATUS = {0: "KADABRA_OK", 1: "KADABRA_ERR_INVALID_ARG", 2: "KADABRA_ERR_OOM", 3
 GRAPH_DEVICE_PTRS = 1
 GRAPH_SKIP_VALIDATE = 2
 STRICT_SIGMA = 1
+FULL_LOOKAHEAD = 2
 DELTA_UNIFORM = 0
 DELTA_BALANCED = 1
 

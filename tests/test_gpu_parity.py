@@ -466,6 +466,29 @@ def test_probe_pass_matches_oracle(K, orc, name, eps, E, threads):
         q.free()
 
 
+@pytest.mark.parametrize("name,eps,E", [("rmat14", 0.03, 128), ("grid64", 0.05, 100), ("er2000", 0.05, 64)])
+def test_adaptive_lookahead_matches_full_lookahead(K, orc, name, eps, E):
+    # Near the predicted stop a pipelined launch opens fewer epoch frames
+    # (the default) than KADABRA_FULL_LOOKAHEAD keeps open; the scheduling
+    # differs, the run's end does not.
+    g = GRAPHS[name]()
+    G = K.Graph.from_inputs(g)
+    counts, cal, LL, LU, R = orc.kadabra(g, eps, 0.1, seed=13, epoch_len=E)
+    launched = {}
+    for flags in (0, K.FULL_LOOKAHEAD):
+        q = K.Query(G, eps=eps, delta=0.1, seed=13, flags=flags)
+        q.run_pipelined(E, frames=16)
+        res = q.result(btilde=False)
+        info = q.info()
+        assert info.device_error == 0
+        assert res["tau"] == R.tau and res["stop_epoch"] == R.stop_epoch
+        assert np.array_equal(res["counts"], counts)
+        assert info.samples == R.tau and info.e_scan == R.e_scan
+        launched[flags] = q.last_launch().samples
+        q.free()
+    assert launched[0] >= R.tau and launched[K.FULL_LOOKAHEAD] >= R.tau
+
+
 def test_omega_clip_and_single_samples(K, orc):
     g = GRAPHS["er2000"]()
     G = K.Graph.from_inputs(g)
