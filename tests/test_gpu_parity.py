@@ -772,7 +772,7 @@ def test_whole_run_at_full_size_matches_oracle_golden(K, name, threads):
     assert info.balance_C == float.fromhex(gold["C"])
     LL, LU, cal = q.budgets()
     assert _sha(cal) == gold["cal_sha256"]
-    q.run_pipelined(P["epoch_len"], frames=8)
+    q.run_pipelined(P["epoch_len"], frames=12)     # the benchmarked launch
     res = q.result(btilde=False)
     info = q.info()
     assert info.stopped == 1 and info.device_error == 0
@@ -816,13 +816,13 @@ def test_batched_mix_members_match_oracle(K, orc):
 @pytest.mark.slow
 def test_rmat20_benchmarked_configuration_matches_oracle(K, orc):
     """R-MAT scale 20 (the benchmarked workload) in exactly the benchmarked
-    launch configuration (pipelined, 512 threads per sample, E = 1024, 8
+    launch configuration (pipelined, 512 threads per sample, E = 1024, 12
     frames): the whole adaptive phase ends with the oracle's tau, stop epoch
     and counters."""
     g = I.config_graph("rmat20")
     G = K.Graph.from_inputs(g, skip_validate=True)
     q = K.Query(G, eps=0.01, delta=0.1, seed=1, threads=512)
-    q.run_pipelined(1024, frames=8)
+    q.run_pipelined(1024, frames=12)
     res = q.result(btilde=False)
     counts, cal, LL, LU, R = orc.kadabra(g, 0.01, 0.1, seed=1, epoch_len=1024)
     assert R.stopped and q.info().stopped == 1
