@@ -331,6 +331,32 @@ def test_vertex_diameter(orc, seed):
     assert orc.vertex_diameter_bound(g) >= exact
 
 
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_vertex_diameter_bound_by_components(orc, seed):
+    # The bound written out with networkx: every component contributes
+    # 2 * ecc(its smallest vertex) + 1, the maximum is taken (1 without edges).
+    # Sparse graphs: several components, isolated vertices, and components
+    # whose smallest vertex is not an end of their longest path.
+    g = random_small_graph(60, 0.03, seed)
+    G = to_nx(g)
+    want = 1
+    comps = list(nx.connected_components(G))
+    assert len(comps) > 1
+    for comp in comps:
+        ecc = max(nx.single_source_shortest_path_length(G, min(comp)).values())
+        want = max(want, 2 * ecc + 1)
+    assert orc.vertex_diameter_bound(g) == want
+
+
+def test_vertex_diameter_bound_edgeless_and_midpoint_root(orc):
+    assert orc.vertex_diameter_bound(I.csr_from_edges(5, np.array([], dtype=np.int64),
+                                                      np.array([], dtype=np.int64))) == 1
+    # path 3-1-0-2-4: the component's smallest vertex 0 is its midpoint (ecc 2)
+    g = I.csr_from_edges(5, np.array([3, 1, 0, 2]), np.array([1, 0, 2, 4]))
+    assert orc.vertex_diameter_bound(g) == 5
+    assert orc.vertex_diameter_exact(g) == 5
+
+
 def test_vertex_diameter_path(orc):
     g = I.path_graph(9)
     assert orc.vertex_diameter_exact(g) == 9
