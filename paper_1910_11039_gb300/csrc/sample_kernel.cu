@@ -1997,9 +1997,11 @@ __device__ __forceinline__ unsigned long long epoch_size(const PipeState *st, lo
 // ceil(omega), or once `budget` samples have been handed out; the pipeline
 // state persists, so the next launch continues where this one ended.
 // Epoch frames a pipelined query may fill ahead of its oldest unchecked
-// epoch.  While its stop is far, all F.  f and g shrink about as 1/sqrt(tau),
-// so after the last check (tau samples, maxima m of f and g) the stop is
-// expected near tau * (m / eps)^2 samples: once that is within the frames,
+// epoch.  While its stop is far, all F.  Modelling f and g as shrinking like
+// 1/sqrt(tau) (their slowest regime: near the stop they fall faster, so the
+// prediction is late and the narrowing mild), after the last check (tau
+// samples, maxima m of f and g) the stop is expected near tau * (m / eps)^2
+// samples: once that is within the frames,
 // samples are handed out only up to the predicted stop epoch and one more,
 // so that fewer samples are discarded and CTAs without one help heavy layers.
 // A late stop only delays later hand-outs: results never depend on it.
