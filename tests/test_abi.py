@@ -122,3 +122,40 @@ def test_graph_load_rejects_before_touching_the_device(K):
     assert ei.value.status == 1 and "self-loop" in str(ei.value)
     with pytest.raises(K.KadabraError):
         K.Graph(0, np.zeros(1, dtype=np.int64), np.zeros(0, dtype=np.int32))
+
+
+def test_binding_structs_match_the_header_layout(K, tmp_path):
+    # Every ctypes structure of the binding has the field offsets and the size
+    # that a C compiler gives the header's struct, and the flag constants equal
+    # the header's macros: a layout drift would hand the library wrong fields.
+    import ctypes
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    pairs = [("kadabra_params", K.Params), ("kadabra_query_info", K.QueryInfo),
+             ("kadabra_trace_rec", K.TraceRec), ("kadabra_launch_stats", K.LaunchStats)]
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "kadabra.h"', "int main(void) {"]
+    want = []
+    for cname, cls in pairs:
+        lines.append(f'printf("%zu\\n", sizeof({cname}));')
+        want.append(ctypes.sizeof(cls))
+        for fname, _ in cls._fields_:
+            if fname.startswith("pad"):
+                continue
+            lines.append(f'printf("%zu\\n", offsetof({cname}, {fname}));')
+            want.append(getattr(cls, fname).offset)
+    macros = [("KADABRA_GRAPH_DEVICE_PTRS", K.GRAPH_DEVICE_PTRS), ("KADABRA_GRAPH_SKIP_VALIDATE", K.GRAPH_SKIP_VALIDATE),
+              ("KADABRA_STRICT_SIGMA", K.STRICT_SIGMA), ("KADABRA_FULL_LOOKAHEAD", K.FULL_LOOKAHEAD),
+              ("KADABRA_DELTA_UNIFORM", K.DELTA_UNIFORM), ("KADABRA_DELTA_BALANCED", K.DELTA_BALANCED)]
+    for m, v in macros:
+        lines.append(f'printf("%zu\\n", (size_t)({m}));')
+        want.append(v)
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    assert got == want
