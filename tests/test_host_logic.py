@@ -66,3 +66,32 @@ def test_checkpoint_file_roundtrip(tmp_path):
     assert np.array_equal(back["counts"], ck["counts"]) and back["counts"].dtype == np.uint32
     for k in ("tau", "epochs", "eps", "delta", "seed", "n_calib", "delta_rule", "vertex_diameter"):
         assert back[k] == ck[k] and type(back[k]) is type(ck[k])
+
+
+def test_autotune_coordinate_descent_on_a_synthetic_cost():
+    # The search with a stand-in runner: threads first (at the base divisor and
+    # frames), then the divisor at the best threads, then frames; each schedule
+    # is tried once, a trial whose queries do not all stop counts as infinite,
+    # and the cheapest schedule seen wins.
+    from paper_1910_11039_gb300 import autotune as AT
+
+    def cost(s):
+        return abs(s.threads - 256) + 3 * abs(math.log2(s.divisor) - 6) + 5 * abs(s.frames - 8)
+
+    calls = []
+
+    def runner(batch, queries, s, stream):
+        calls.append(s)
+        return {"ms": cost(s), "stopped": [s.frames != 16]}
+
+    class Pool:
+        def get(self, threads):
+            return None
+
+    best, trials, secs = AT.autotune([object()], Pool(), runner=runner)
+    assert (best.threads, best.divisor, best.frames) == (256, 64, 8)
+    assert len(calls) == len(set(calls)) == len(trials)
+    assert [s.threads for s in calls[:4]] == [1024, 128, 256, 512]     # base first, then the others
+    assert all(s.threads == 256 for s in calls[4:])
+    assert dict(trials)[AT.Schedule(threads=256, divisor=64, frames=16)] == float("inf")
+    assert min(ms for _, ms in trials) == cost(best) and secs >= 0.0
