@@ -209,14 +209,18 @@ kadabra_status kadabra_device_clock(uint64_t *ns, void *cuda_stream);
 
 /* ---- graph ------------------------------------------------------------- */
 
-/* Copy a CSR graph into library-owned device memory (async on `cuda_stream`
- * for device pointers, synchronous for host pointers).
+/* Copy a CSR graph into library-owned device memory, on `cuda_stream`;
+ * synchronises before returning (the maximum degree is read back), so the
+ * caller's arrays are no longer referenced afterwards.
  *   n        number of vertices (1 <= n < 2^31)
  *   nnz      number of adjacency entries (= offsets[n])
  *   offsets  n+1 entries, int32 if offsets_is_64 == 0 else int64
  *   cols     nnz int32 neighbour ids, each row ascending
  *   flags    KADABRA_GRAPH_DEVICE_PTRS, KADABRA_GRAPH_SKIP_VALIDATE
- * Host inputs are validated (kadabra_validate_csr) unless skipped. */
+ * Host inputs are validated (kadabra_validate_csr) unless skipped.  Host
+ * columns in page-locked memory (cudaHostAlloc, cudaHostRegister) are read
+ * in place by the kernel that builds the device adjacency (one pass over the
+ * host link); pageable host columns go through a temporary device copy. */
 kadabra_status kadabra_graph_load(int64_t n, int64_t nnz, const void *offsets, int offsets_is_64,
                                   const int32_t *cols, uint32_t flags, void *cuda_stream,
                                   kadabra_graph **out);
